@@ -1,0 +1,624 @@
+/*
+ * qpm_oracle.c -- plain, slow, obviously-correct CPU oracle for the cascaded-THG
+ * quasi-phase-matching design method (HWSDA: DE + grey-wolf hybrid).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  The product path (the CUDA
+ * library) never calls it, shares no code with it, and fails loudly when its own
+ * extension is missing.
+ *
+ * What it computes, and where the paper defines it:
+ *   - d_eff (Sec. 2.1, the double integral that closes the derivation):
+ *       d_eff = int_0^L d(z) e^{-i dk2 z} ( int_0^z d(x) e^{-i dk1 x} dx ) dz
+ *     over N equal-width domains, d(z) = +-1 per domain (Sec. 2.1: +1 up, -1 down).
+ *     Here it is integrated DIRECTLY: the integrand is split at the domain walls
+ *     (the only places it is not smooth) and every piece is integrated with a
+ *     Q-node Gauss-Legendre rule, the inner integral nested inside the outer one.
+ *     Lengths are in units of the domain width w, so kappa = dk*w and the
+ *     physical value is w^2 times the returned one.
+ *   - the relaxed gradient d|d_eff|^2/d(theta_k), d_k = tanh(theta_k), by exact
+ *     differentiation of the same quadrature sum, and by central differences.
+ *   - the HWSDA loop (Sec. 2.2.1 DE, Sec. 2.2.2 GWO, Sec. 3.2 Steps 1-7) with
+ *     FP32 genes and FP32 update arithmetic in a fixed operation order (no FMA:
+ *     build with -ffp-contract=off), random numbers from Philox4x32-10
+ *     (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ *     SC'11), written here from that published definition.
+ *
+ * Readings of the paper taken here (garbled or silent passages):
+ *   - objective: maximise |d_eff|^2 (Sec. 2.1 asks for the largest d_eff);
+ *   - greedy selection keeps the trial when f(trial) >= f(target) (Sec. 2.2.1
+ *     step 4 is printed garbled and for minimisation; mirrored for maximisation);
+ *   - binomial crossover takes the mutant gene when U <= CR or j == jrand;
+ *   - GWO: X2 uses d_beta and X3 uses d_gamma (the paper prints d_alpha in all
+ *     three, a typo); combination is the plain mean (X1+X2+X3)/3 by default, or
+ *     the paper's |X_k|-weighted form read per dimension;
+ *   - only the omega wolves move in the GWO phase; the three leaders are the
+ *     top three by fitness after the DE phase (Sec. 3.2 Step 3), ties broken
+ *     towards the lower index;
+ *   - real gene -> domain sign: d = (x < 0) ? -1 : +1;
+ *   - genes are clamped to [-1, 1] after mutation and after the GWO move;
+ *   - a decays linearly from 2 to 0: a_g = 2(G-g)/G, one rounded FP32 division.
+ * Parity status: every function here is pinned by the CPU test-suite
+ * (closed forms, invariants, an independent analytic closed form, brute force,
+ * curand's host Philox); none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------- */
+/* Gauss-Legendre rule on [-1, 1] (Newton iteration on P_Q, three-term recurrence) */
+/* ------------------------------------------------------------------------- */
+#define QMAX 32
+static int g_Q = 0;
+static double g_t[QMAX], g_w[QMAX];
+
+static void legendre(int Q, double x, double *p, double *dp) {
+  double p0 = 1.0, p1 = x;
+  for (int k = 2; k <= Q; ++k) {
+    double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = pk;
+  }
+  *p = p1;
+  *dp = Q * (x * p1 - p0) / (x * x - 1.0);
+}
+
+ORC_API int orc_gauss_legendre(int Q, double *t, double *w) {
+  if (Q < 2 || Q > QMAX) return -1;
+  for (int k = 0; k < Q; ++k) {
+    double x = cos(M_PI * (k + 0.75) / (Q + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(Q, x, &p, &dp);
+      double dx = p / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    double p, dp;
+    legendre(Q, x, &p, &dp);
+    t[k] = x;
+    w[k] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return 0;
+}
+
+static void ensure_rule(int Q) {
+  if (g_Q != Q) {
+    orc_gauss_legendre(Q, g_t, g_w);
+    g_Q = Q;
+  }
+}
+
+/* e^{-i k x} */
+static inline void cis_neg(double k, double x, double *re, double *im) {
+  double ph = k * x;
+  *re = cos(ph);
+  *im = -sin(ph);
+}
+
+/* Neumaier-compensated complex accumulator */
+typedef struct { double sr, si, cr, ci; } acc_t;
+static inline void acc_add(acc_t *a, double xr, double xi) {
+  double t = a->sr + xr;
+  if (fabs(a->sr) >= fabs(xr)) a->cr += (a->sr - t) + xr; else a->cr += (xr - t) + a->sr;
+  a->sr = t;
+  t = a->si + xi;
+  if (fabs(a->si) >= fabs(xi)) a->ci += (a->si - t) + xi; else a->ci += (xi - t) + a->si;
+  a->si = t;
+}
+static inline double acc_re(const acc_t *a) { return a->sr + a->cr; }
+static inline double acc_im(const acc_t *a) { return a->si + a->ci; }
+
+/* ------------------------------------------------------------------------- */
+/* d_eff by nested quadrature (Sec. 2.1).                                     */
+/*   domain j covers z in [j, j+1]; for z in that domain                      */
+/*   I1(z) = sum_{m<j} d_m int_m^{m+1} e^{-ik1 x}dx + d_j int_j^z e^{-ik1 x}dx */
+/*   d_eff = sum_j d_j int_j^{j+1} e^{-ik2 z} I1(z) dz                         */
+/* ------------------------------------------------------------------------- */
+static void deff_quad_one(int N, double k1, double k2, const double *d, int Q,
+                          double *Dre, double *Dim) {
+  ensure_rule(Q);
+  acc_t D = {0, 0, 0, 0};
+  acc_t C = {0, 0, 0, 0}; /* running inner integral over whole domains m < j */
+  for (int j = 0; j < N; ++j) {
+    double Cre = acc_re(&C), Cim = acc_im(&C);
+    double outr = 0.0, outi = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      double z = j + 0.5 * (1.0 + g_t[q]);
+      double wq = 0.5 * g_w[q];
+      double h = z - j; /* inner partial-domain integral over [j, z] */
+      double inr = 0.0, ini = 0.0;
+      for (int r = 0; r < Q; ++r) {
+        double x = j + 0.5 * h * (1.0 + g_t[r]);
+        double er, ei;
+        cis_neg(k1, x, &er, &ei);
+        inr += 0.5 * h * g_w[r] * er;
+        ini += 0.5 * h * g_w[r] * ei;
+      }
+      double I1r = Cre + d[j] * inr, I1i = Cim + d[j] * ini;
+      double er, ei;
+      cis_neg(k2, z, &er, &ei);
+      outr += wq * (er * I1r - ei * I1i);
+      outi += wq * (er * I1i + ei * I1r);
+    }
+    acc_add(&D, d[j] * outr, d[j] * outi);
+    /* whole-domain inner integral of domain j, added for the domains after it */
+    double fr = 0.0, fi = 0.0;
+    for (int r = 0; r < Q; ++r) {
+      double x = j + 0.5 * (1.0 + g_t[r]);
+      double er, ei;
+      cis_neg(k1, x, &er, &ei);
+      fr += 0.5 * g_w[r] * er;
+      fi += 0.5 * g_w[r] * ei;
+    }
+    acc_add(&C, d[j] * fr, d[j] * fi);
+  }
+  *Dre = acc_re(&D);
+  *Dim = acc_im(&D);
+}
+
+/* D[2*i], D[2*i+1] = d_eff of row i of d (rows of length N, leading dim ld) */
+ORC_API void orc_deff_quad(int NP, int N, int64_t ld, double kappa1, double kappa2,
+                           const double *d, int Q, double *D) {
+  ensure_rule(Q);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < NP; ++i)
+    deff_quad_one(N, kappa1, kappa2, d + (int64_t)i * ld, Q, &D[2 * i], &D[2 * i + 1]);
+}
+
+/* same, from FP32 genes mapped to domain signs d = (x < 0) ? -1 : +1 */
+ORC_API void orc_deff_genes(int NP, int N, int64_t ld, double kappa1, double kappa2,
+                            const float *X, int Q, double *D) {
+  ensure_rule(Q);
+#pragma omp parallel
+  {
+    double *d = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < NP; ++i) {
+      for (int j = 0; j < N; ++j) d[j] = (X[(int64_t)i * ld + j] < 0.0f) ? -1.0 : 1.0;
+      deff_quad_one(N, kappa1, kappa2, d, Q, &D[2 * i], &D[2 * i + 1]);
+    }
+    free(d);
+  }
+}
+
+/* exhaustive search over all 2^N sign patterns (bit m set -> d_m = -1).
+ * Writes f = |d_eff|^2 of every pattern to fit[2^N] (may be NULL) and returns
+ * the best value; best_mask gets the lowest pattern index attaining it. */
+ORC_API double orc_bruteforce(int N, double kappa1, double kappa2, int Q, double *fit,
+                              int64_t *best_mask) {
+  if (N < 1 || N > 24) return -1.0;
+  ensure_rule(Q);
+  int64_t M = (int64_t)1 << N;
+  double best = -1.0;
+  int64_t bm = 0;
+#pragma omp parallel
+  {
+    double d[24];
+    double lb = -1.0;
+    int64_t lm = 0;
+#pragma omp for schedule(static)
+    for (int64_t s = 0; s < M; ++s) {
+      for (int m = 0; m < N; ++m) d[m] = ((s >> m) & 1) ? -1.0 : 1.0;
+      double re, im;
+      deff_quad_one(N, kappa1, kappa2, d, Q, &re, &im);
+      double f = re * re + im * im;
+      if (fit) fit[s] = f;
+      if (f > lb) { lb = f; lm = s; }
+    }
+#pragma omp critical
+    {
+      if (lb > best || (lb == best && lm < bm)) { best = lb; bm = lm; }
+    }
+  }
+  if (best_mask) *best_mask = bm;
+  return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Relaxed gradient: d_k = tanh(theta_k), f = |D|^2.                          */
+/* D is a quadratic form in d; its derivative is taken term by term from the  */
+/* quadrature sum of deff_quad_one:                                           */
+/*   D = sum_j d_j O_j,  O_j = sum_q wq e^{-ik2 z_q} (C_j + d_j in_{j,q}),     */
+/*   C_j = sum_{m<j} d_m F1_m                                                 */
+/*   dD/dd_k = O_k + d_k S_k + F1_k sum_{j>k} d_j F2_j                        */
+/* with S_k = sum_q wq e^{-ik2 z_q} in_{k,q} and F2_j = sum_q wq e^{-ik2 z_q}. */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_grad_relaxed(int N, double kappa1, double kappa2, const double *theta,
+                              int Q, double *grad, double *Dout) {
+  ensure_rule(Q);
+  double *d = (double *)malloc(sizeof(double) * N);
+  double *O = (double *)malloc(sizeof(double) * 2 * N);
+  double *S = (double *)malloc(sizeof(double) * 2 * N);
+  double *F1 = (double *)malloc(sizeof(double) * 2 * N);
+  double *F2 = (double *)malloc(sizeof(double) * 2 * N);
+  for (int j = 0; j < N; ++j) d[j] = tanh(theta[j]);
+  acc_t C = {0, 0, 0, 0}, D = {0, 0, 0, 0};
+  for (int j = 0; j < N; ++j) {
+    double Cre = acc_re(&C), Cim = acc_im(&C);
+    double outr = 0, outi = 0, sr = 0, si = 0, f2r = 0, f2i = 0;
+    for (int q = 0; q < Q; ++q) {
+      double z = j + 0.5 * (1.0 + g_t[q]);
+      double wq = 0.5 * g_w[q];
+      double h = z - j;
+      double inr = 0.0, ini = 0.0;
+      for (int r = 0; r < Q; ++r) {
+        double x = j + 0.5 * h * (1.0 + g_t[r]);
+        double er, ei;
+        cis_neg(kappa1, x, &er, &ei);
+        inr += 0.5 * h * g_w[r] * er;
+        ini += 0.5 * h * g_w[r] * ei;
+      }
+      double er, ei;
+      cis_neg(kappa2, z, &er, &ei);
+      double I1r = Cre + d[j] * inr, I1i = Cim + d[j] * ini;
+      outr += wq * (er * I1r - ei * I1i);
+      outi += wq * (er * I1i + ei * I1r);
+      sr += wq * (er * inr - ei * ini);
+      si += wq * (er * ini + ei * inr);
+      f2r += wq * er;
+      f2i += wq * ei;
+    }
+    O[2 * j] = outr; O[2 * j + 1] = outi;
+    S[2 * j] = sr; S[2 * j + 1] = si;
+    F2[2 * j] = f2r; F2[2 * j + 1] = f2i;
+    acc_add(&D, d[j] * outr, d[j] * outi);
+    double fr = 0.0, fi = 0.0;
+    for (int r = 0; r < Q; ++r) {
+      double x = j + 0.5 * (1.0 + g_t[r]);
+      double er, ei;
+      cis_neg(kappa1, x, &er, &ei);
+      fr += 0.5 * g_w[r] * er;
+      fi += 0.5 * g_w[r] * ei;
+    }
+    F1[2 * j] = fr; F1[2 * j + 1] = fi;
+    acc_add(&C, d[j] * fr, d[j] * fi);
+  }
+  double Dre = acc_re(&D), Dim = acc_im(&D);
+  acc_t R = {0, 0, 0, 0}; /* suffix sum_{j>k} d_j F2_j */
+  for (int k = N - 1; k >= 0; --k) {
+    double Rr = acc_re(&R), Ri = acc_im(&R);
+    double gr = O[2 * k] + d[k] * S[2 * k] + (F1[2 * k] * Rr - F1[2 * k + 1] * Ri);
+    double gi = O[2 * k + 1] + d[k] * S[2 * k + 1] + (F1[2 * k] * Ri + F1[2 * k + 1] * Rr);
+    /* df/dd_k = 2 Re(conj(D) dD/dd_k);  dd_k/dtheta_k = 1 - d_k^2 */
+    grad[k] = 2.0 * (Dre * gr + Dim * gi) * (1.0 - d[k] * d[k]);
+    acc_add(&R, d[k] * F2[2 * k], d[k] * F2[2 * k + 1]);
+  }
+  if (Dout) { Dout[0] = Dre; Dout[1] = Dim; }
+  free(d); free(O); free(S); free(F1); free(F2);
+}
+
+/* f = |D|^2 of the relaxed sequence d = tanh(theta) */
+ORC_API double orc_fit_relaxed(int N, double kappa1, double kappa2, const double *theta,
+                               int Q, double *Dout) {
+  ensure_rule(Q);
+  double *d = (double *)malloc(sizeof(double) * N);
+  for (int j = 0; j < N; ++j) d[j] = tanh(theta[j]);
+  double re, im;
+  deff_quad_one(N, kappa1, kappa2, d, Q, &re, &im);
+  free(d);
+  if (Dout) { Dout[0] = re; Dout[1] = im; }
+  return re * re + im * im;
+}
+
+/* central finite differences of f(theta) at the coordinates idx[0..n) */
+ORC_API void orc_fd_grad(int N, double kappa1, double kappa2, const double *theta,
+                         const int32_t *idx, int n, double h, int Q, double *out) {
+  ensure_rule(Q);
+#pragma omp parallel
+  {
+    double *t = (double *)malloc(sizeof(double) * N);
+    double *d = (double *)malloc(sizeof(double) * N);
+#pragma omp for schedule(dynamic, 1)
+    for (int c = 0; c < n; ++c) {
+      memcpy(t, theta, sizeof(double) * N);
+      int k = idx[c];
+      double fp, fm, re, im;
+      t[k] = theta[k] + h;
+      for (int j = 0; j < N; ++j) d[j] = tanh(t[j]);
+      deff_quad_one(N, kappa1, kappa2, d, Q, &re, &im);
+      fp = re * re + im * im;
+      t[k] = theta[k] - h;
+      for (int j = 0; j < N; ++j) d[j] = tanh(t[j]);
+      deff_quad_one(N, kappa1, kappa2, d, Q, &re, &im);
+      fm = re * re + im * im;
+      out[c] = (fp - fm) / (2.0 * h);
+    }
+    free(t);
+    free(d);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the 4x32 Philox round,  */
+/* multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 /      */
+/* 0xBB67AE85 (the golden ratio and sqrt(3)-1 in 0.32 fixed point).           */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Random-number contract of this implementation (the paper fixes none):     */
+/*   key = (seed low word, seed high word)                                    */
+/*   counter = (j/4, i, g, (instance << 8) | tag); word j%4 serves gene j     */
+/*   tags: 0 init, 1 DE indices (counter word 0 = 0), 2 crossover,            */
+/*         3..8 GWO r1/r2 for alpha, beta, gamma                              */
+/*   uniform U = (w >> 8) * 2^-24 in [0, 1)                                   */
+/*   index in [0, m): (w * m) >> 32  (Lemire multiply-shift)                  */
+/* ------------------------------------------------------------------------- */
+enum { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3 };
+
+static inline uint32_t rng_word(uint64_t seed, uint32_t inst, uint32_t tag, uint32_t g,
+                                uint32_t i, uint32_t j) {
+  uint32_t ctr[4] = {j >> 2, i, g, (inst << 8) | tag};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox(ctr, key, out);
+  return out[j & 3];
+}
+static inline float u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+static inline uint32_t lemire(uint32_t w, uint32_t m) {
+  return (uint32_t)(((uint64_t)w * m) >> 32);
+}
+
+ORC_API float orc_uniform(uint64_t seed, uint32_t inst, uint32_t tag, uint32_t g, uint32_t i,
+                          uint32_t j) {
+  return u24(rng_word(seed, inst, tag, g, i, j));
+}
+
+/* DE rand/1 donor indices r1, r2, r3 (distinct, != i; NP >= 4, Sec. 2.2.1 step 2) and
+ * the forced crossover dimension jrand (rnbr(i) in Sec. 2.2.1 step 3). */
+ORC_API void orc_de_indices(uint64_t seed, uint32_t inst, uint32_t g, int32_t i, int32_t NP,
+                            int32_t N, int32_t out[4]) {
+  uint32_t ctr[4] = {0, (uint32_t)i, g, (inst << 8) | TAG_DEIDX};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  orc_philox(ctr, key, w);
+  int32_t ex[4];
+  int ne = 0;
+  ex[ne++] = i;
+  int32_t r[3];
+  for (int k = 0; k < 3; ++k) {
+    int32_t t = (int32_t)lemire(w[k], (uint32_t)(NP - 1 - k));
+    /* skip the excluded values in ascending order: a bijection onto the rest */
+    int32_t s[3];
+    for (int a = 0; a < ne; ++a) s[a] = ex[a];
+    for (int a = 1; a < ne; ++a)
+      for (int b = a; b > 0 && s[b - 1] > s[b]; --b) { int32_t tmp = s[b]; s[b] = s[b - 1]; s[b - 1] = tmp; }
+    for (int a = 0; a < ne; ++a)
+      if (t >= s[a]) ++t;
+    r[k] = t;
+    ex[ne++] = t;
+  }
+  out[0] = r[0]; out[1] = r[1]; out[2] = r[2];
+  out[3] = (int32_t)lemire(w[3], (uint32_t)N);
+}
+
+typedef struct {
+  int32_t NP, N;
+  int64_t ld;
+  int32_t G;
+  float F, CR;
+  uint64_t seed;
+  uint32_t inst;
+  int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension */
+} orc_cfg;
+
+static inline float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
+
+/* Step 1 / Sec. 2.2.1 step 1: x_ij = U(-1, 1), computed as 2U - 1 (exact in FP32) */
+ORC_API void orc_init_population(const orc_cfg *c, float *X) {
+  for (int32_t i = 0; i < c->NP; ++i)
+    for (int32_t j = 0; j < c->N; ++j) {
+      float U = u24(rng_word(c->seed, c->inst, TAG_INIT, 0, (uint32_t)i, (uint32_t)j));
+      X[(int64_t)i * c->ld + j] = 2.0f * U - 1.0f;
+    }
+}
+
+/* Sec. 2.2.1 steps 2-3 for target i: mutant v = x_r1 + F (x_r2 - x_r3), clamped,
+ * then binomial crossover with the target -> trial u */
+static void de_trial_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X, float *u) {
+  int32_t r[4];
+  orc_de_indices(c->seed, c->inst, g, i, c->NP, c->N, r);
+  const float *x = X + (int64_t)i * c->ld;
+  const float *x1 = X + (int64_t)r[0] * c->ld;
+  const float *x2 = X + (int64_t)r[1] * c->ld;
+  const float *x3 = X + (int64_t)r[2] * c->ld;
+  for (int32_t j = 0; j < c->N; ++j) {
+    float diff = x2[j] - x3[j];
+    float step = c->F * diff;
+    float v = clamp1(x1[j] + step);
+    float randb = u24(rng_word(c->seed, c->inst, TAG_CR, g, (uint32_t)i, (uint32_t)j));
+    u[j] = (randb <= c->CR || j == r[3]) ? v : x[j];
+  }
+}
+
+ORC_API void orc_de_trials(const orc_cfg *c, uint32_t g, const float *X, float *U) {
+#pragma omp parallel for schedule(static)
+  for (int32_t i = 0; i < c->NP; ++i) de_trial_one(c, g, i, X, U + (int64_t)i * c->ld);
+}
+
+/* Sec. 3.2 Step 3: the three best wolves (descending f, ties to the lower index) */
+ORC_API void orc_top3(int32_t NP, const float *f, int32_t lead[3]) {
+  for (int k = 0; k < 3; ++k) lead[k] = -1;
+  for (int32_t i = 0; i < NP; ++i) {
+    for (int k = 0; k < 3; ++k) {
+      if (lead[k] < 0 || f[i] > f[lead[k]]) {
+        for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+        lead[k] = i;
+        break;
+      }
+    }
+  }
+}
+
+/* a_g = 2 (G - g) / G  (linear decay from 2 towards 0, Sec. 2.2.2) */
+ORC_API float orc_a_of(int32_t g, int32_t G) {
+  return (float)(2 * (G - g)) / (float)G;
+}
+
+/* Sec. 2.2.2: encircling of the prey by the three leaders, then the combination */
+static void gwo_cand_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X,
+                         const int32_t lead[3], float *y) {
+  float a = orc_a_of((int32_t)g, c->G);
+  float two_a = 2.0f * a;
+  const float *x = X + (int64_t)i * c->ld;
+  for (int32_t j = 0; j < c->N; ++j) {
+    float Xk[3];
+    for (int k = 0; k < 3; ++k) {
+      const float *Xp = X + (int64_t)lead[k] * c->ld; /* alpha, beta, gamma */
+      float r1 = u24(rng_word(c->seed, c->inst, TAG_GWO + 2 * k, g, (uint32_t)i, (uint32_t)j));
+      float r2 = u24(rng_word(c->seed, c->inst, TAG_GWO + 2 * k + 1, g, (uint32_t)i, (uint32_t)j));
+      float A = two_a * r1 - a;           /* A = 2 a r1 - a */
+      float C = 2.0f * r2;                /* C = 2 r2 */
+      float dist = fabsf(C * Xp[j] - x[j]); /* d = |C Xp - X| */
+      Xk[k] = Xp[j] - A * dist;           /* X_k = Xp - A d */
+    }
+    float yj;
+    if (c->combine == 0) {
+      yj = ((Xk[0] + Xk[1]) + Xk[2]) / 3.0f;
+    } else {
+      float m0 = fabsf(Xk[0]), m1 = fabsf(Xk[1]), m2 = fabsf(Xk[2]);
+      float s = (m0 + m1) + m2;
+      float num = ((m0 * Xk[0]) + (m1 * Xk[1])) + (m2 * Xk[2]);
+      yj = (s == 0.0f) ? 0.0f : num / (3.0f * s);
+    }
+    y[j] = clamp1(yj);
+  }
+}
+
+/* candidate positions for every omega wolf (rows of leaders are left untouched in Y) */
+ORC_API void orc_gwo_candidates(const orc_cfg *c, uint32_t g, const float *X,
+                                const int32_t lead[3], float *Y) {
+#pragma omp parallel for schedule(static)
+  for (int32_t i = 0; i < c->NP; ++i) {
+    if (i == lead[0] || i == lead[1] || i == lead[2]) continue;
+    gwo_cand_one(c, g, i, X, lead, Y + (int64_t)i * c->ld);
+  }
+}
+
+static void eval_rows(const orc_cfg *c, double kappa1, double kappa2, int Q, const float *X,
+                      const uint8_t *mask, double *f64) {
+#pragma omp parallel
+  {
+    double *d = (double *)malloc(sizeof(double) * (size_t)c->N);
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = 0; i < c->NP; ++i) {
+      if (mask && !mask[i]) { f64[i] = NAN; continue; }
+      for (int32_t j = 0; j < c->N; ++j) d[j] = (X[(int64_t)i * c->ld + j] < 0.0f) ? -1.0 : 1.0;
+      double re, im;
+      deff_quad_one(c->N, kappa1, kappa2, d, Q, &re, &im);
+      f64[i] = re * re + im * im;
+    }
+    free(d);
+  }
+}
+
+/* The HWSDA loop of Sec. 3.2 (Steps 1-7), one instance.
+ *   X[NP*ld]   out: final population (FP32 genes)
+ *   fcur[NP]   out: FP64 fitness of the final population
+ *   lockstep:  if non-NULL, selection and leader decisions are taken from these
+ *              FP32 fitness values instead of the oracle's own FP64 ones, so that
+ *              an FP32 implementation can be followed bit for bit:
+ *              lockstep[0 .. NP)                       fitness after init
+ *              lockstep[NP*(1+2g) .. NP*(2+2g))        trial fitness of generation g
+ *              lockstep[NP*(2+2g) .. NP*(3+2g))        GWO candidate fitness of gen g
+ *   trace64:   if non-NULL, same layout, filled with the oracle's FP64 fitness
+ *   Returns 0. */
+ORC_API int orc_hwsda_run(const orc_cfg *c, double kappa1, double kappa2, int Q, float *X,
+                          double *fcur, const float *lockstep, double *trace64) {
+  ensure_rule(Q);
+  int32_t NP = c->NP;
+  int64_t sz = (int64_t)NP * c->ld;
+  float *U = (float *)calloc((size_t)sz, sizeof(float));
+  double *ft = (double *)malloc(sizeof(double) * NP);
+  float *fdec = (float *)malloc(sizeof(float) * NP); /* decision fitness */
+  double *f64 = fcur;
+  orc_init_population(c, X);
+  eval_rows(c, kappa1, kappa2, Q, X, NULL, f64);
+  if (trace64) memcpy(trace64, f64, sizeof(double) * NP);
+  for (int32_t i = 0; i < NP; ++i) fdec[i] = lockstep ? lockstep[i] : (float)f64[i];
+  double *fdec64 = (double *)malloc(sizeof(double) * NP);
+  for (int32_t i = 0; i < NP; ++i) fdec64[i] = f64[i];
+  for (int32_t g = 0; g < c->G; ++g) {
+    /* Step 2: mutation, crossover, selection over all NP individuals */
+    orc_de_trials(c, (uint32_t)g, X, U);
+    eval_rows(c, kappa1, kappa2, Q, U, NULL, ft);
+    const float *lt = lockstep ? lockstep + (int64_t)NP * (1 + 2 * g) : NULL;
+    if (trace64) memcpy(trace64 + (int64_t)NP * (1 + 2 * g), ft, sizeof(double) * NP);
+    for (int32_t i = 0; i < NP; ++i) {
+      int accept = lockstep ? (lt[i] >= fdec[i]) : (ft[i] >= fdec64[i]);
+      if (accept) {
+        memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
+        f64[i] = ft[i];
+        fdec64[i] = ft[i];
+        if (lockstep) fdec[i] = lt[i];
+      }
+    }
+    /* Step 3: leaders */
+    int32_t lead[3];
+    if (lockstep) {
+      orc_top3(NP, fdec, lead);
+    } else {
+      /* FP64 decisions: same rule on the FP64 values */
+      for (int k = 0; k < 3; ++k) lead[k] = -1;
+      for (int32_t i = 0; i < NP; ++i)
+        for (int k = 0; k < 3; ++k)
+          if (lead[k] < 0 || fdec64[i] > fdec64[lead[k]]) {
+            for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+            lead[k] = i;
+            break;
+          }
+    }
+    /* Step 4: move the omega wolves; Step 5: greedy selection again */
+    orc_gwo_candidates(c, (uint32_t)g, X, lead, U);
+    uint8_t *mask = (uint8_t *)malloc((size_t)NP);
+    for (int32_t i = 0; i < NP; ++i) mask[i] = !(i == lead[0] || i == lead[1] || i == lead[2]);
+    eval_rows(c, kappa1, kappa2, Q, U, mask, ft);
+    const float *lc = lockstep ? lockstep + (int64_t)NP * (2 + 2 * g) : NULL;
+    if (trace64) memcpy(trace64 + (int64_t)NP * (2 + 2 * g), ft, sizeof(double) * NP);
+    for (int32_t i = 0; i < NP; ++i) {
+      if (!mask[i]) continue;
+      int accept = lockstep ? (lc[i] >= fdec[i]) : (ft[i] >= fdec64[i]);
+      if (accept) {
+        memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
+        f64[i] = ft[i];
+        fdec64[i] = ft[i];
+        if (lockstep) fdec[i] = lc[i];
+      }
+    }
+    free(mask);
+    /* Step 6: F and CR stay constant; a is recomputed from g at the next pass */
+  }
+  free(U); free(ft); free(fdec); free(fdec64);
+  return 0;
+}
+
+ORC_API int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,238 @@
+"""Pins for the oracle's random numbers, DE/GWO updates, leader choice, HWSDA loop
+and relaxed gradient -- CPU only.
+
+  * Philox4x32-10 against curand's host generator (a library implementation of
+    the same published generator) on counter words 0-2 and both key words;
+  * DE donor indices: distinct, never the target, uniformly spread;
+  * DE rand/1 + binomial crossover (Sec. 2.2.1) special cases: CR = 0 leaves only
+    the forced dimension from the mutant, CR = 1 takes the whole mutant, F = 0
+    copies donor r1; every trial gene is either the target's or the textbook
+    rand/1 mutant's; the crossover rate matches CR;
+  * GWO (Sec. 2.2.2) distributions: with all leaders at 1/2 and the wolf at 0,
+    mean and variance of the candidate follow from A = 2a r1 - a, C = 2 r2;
+  * top-3 equals a stable sort (numpy lexsort);
+  * the HWSDA loop (Sec. 3.2) never loses its best and reaches the exhaustive
+    optimum's neighbourhood on a 16-domain problem;
+  * the relaxed gradient equals central finite differences and obeys Euler's
+    identity for a quadratic form.
+"""
+import ctypes
+import ctypes.util
+import json
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _curand():
+    for p in ("/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")):
+        if p and os.path.exists(p) or (p and not p.startswith("/")):
+            try:
+                return ctypes.CDLL(p)
+            except OSError:
+                pass
+    return None
+
+
+def test_philox_matches_curand_host_generator(orc):
+    cur = _curand()
+    if cur is None:
+        pytest.skip("libcurand not found")
+    seed = 0x0123456789ABCDEF
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    # curand's host PHILOX4_32_10 generator emits block b of its stream from
+    # counter (word0, word1) = (b + offset/4) // 65536 as a 64-bit value, word2 = b % 65536
+    for offset in (0, 2 ** 50 + 4 * 65536 * 3):
+        gen = ctypes.c_void_p()
+        assert cur.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0
+        assert cur.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert cur.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
+        n = 4 * 65536 * 2
+        out = np.zeros(n, dtype=np.uint32)
+        assert cur.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+        cur.curandDestroyGenerator(gen)
+        blocks = out.reshape(-1, 4)
+        base = offset // 4
+        for b in (0, 1, 5, 65535, 65536, 65536 + 77, 131071):
+            pos = base + b
+            hi = pos // 65536
+            ctr = [hi & 0xFFFFFFFF, hi >> 32, b % 65536, 0]
+            assert np.array_equal(orc.philox(ctr, key), blocks[b]), (offset, b)
+
+
+def test_uniform_and_index_ranges(orc):
+    us = np.array([orc.uniform(7, 0, 2, 3, i, j) for i in range(4) for j in range(64)])
+    assert us.min() >= 0.0 and us.max() < 1.0
+    assert np.all(us * 2 ** 24 == np.floor(us * 2 ** 24))  # 24-bit grid, exact in FP32
+    NP, N = 9, 13
+    r1s = []
+    for g in range(400):
+        for i in range(NP):
+            r1, r2, r3, jr = orc.de_indices(5, 1, g, i, NP, N)
+            assert len({i, r1, r2, r3}) == 4
+            assert 0 <= min(r1, r2, r3) and max(r1, r2, r3) < NP
+            assert 0 <= jr < N
+            r1s.append((r1 - i) % NP)
+    # r1 is spread evenly over the NP-1 other individuals (chi-square, 8 dof)
+    cnt = np.bincount(r1s, minlength=NP)[1:]
+    exp = len(r1s) / (NP - 1)
+    chi2 = np.sum((cnt - exp) ** 2 / exp)
+    assert cnt.min() > 0 and chi2 < 30.0
+
+
+def _cfg(orc, NP=12, N=40, G=10, F=0.5, CR=0.9, seed=3, inst=0, combine=0):
+    return orc.make_cfg(NP, N, G, F, CR, seed, inst, combine)
+
+
+def test_init_population_uniform(orc):
+    c = _cfg(orc, NP=64, N=256)
+    X = orc.init_population(c)
+    assert X.min() >= -1.0 and X.max() < 1.0
+    assert abs(X.mean()) < 0.02 and abs(X.var() - 1.0 / 3.0) < 0.02
+    # x = 2U - 1 with U on the 24-bit grid
+    assert np.all((X + 1) * 2 ** 23 == np.floor((X + 1) * 2 ** 23))
+
+
+def test_de_trial_structure(orc):
+    c = _cfg(orc, NP=16, N=64, F=0.5, CR=0.9)
+    X = orc.init_population(c)
+    U = orc.de_trials(c, 4, X)
+    taken = 0
+    for i in range(c.NP):
+        r1, r2, r3, jr = orc.de_indices(c.seed, c.inst, 4, i, c.NP, c.N)
+        v = np.clip(X[r1] + np.float32(c.F) * (X[r2] - X[r3]), -1, 1).astype(np.float32)
+        from_v = U[i] == v
+        from_x = U[i] == X[i]
+        assert np.all(from_v | from_x)
+        assert U[i][jr] == v[jr]
+        taken += np.sum(from_v & ~from_x)
+    frac = taken / (c.NP * c.N)
+    assert 0.8 < frac < 0.97  # about CR
+
+
+def test_de_trial_special_cases(orc):
+    X = orc.init_population(_cfg(orc, NP=10, N=50))
+    c0 = _cfg(orc, NP=10, N=50, CR=0.0)
+    U = orc.de_trials(c0, 2, X)
+    for i in range(10):
+        jr = orc.de_indices(c0.seed, 0, 2, i, 10, 50)[3]
+        diff = np.nonzero(U[i] != X[i])[0]
+        assert set(diff.tolist()) <= {jr}
+    c1 = _cfg(orc, NP=10, N=50, CR=1.0, F=0.0)
+    U = orc.de_trials(c1, 2, X)
+    for i in range(10):
+        r1 = orc.de_indices(c1.seed, 0, 2, i, 10, 50)[0]
+        assert np.array_equal(U[i], X[r1])  # F = 0: mutant is donor r1
+
+
+def test_gwo_candidate_moments(orc):
+    NP, N, G = 8, 20000, 100
+    c = _cfg(orc, NP=NP, N=N, G=G)
+    X = np.zeros((NP, N), dtype=np.float32)
+    X[:3] = 0.5  # leaders alpha, beta, gamma at 1/2; omega wolves at 0
+    g = 90
+    a = orc.a_of(g, G)
+    assert a == np.float32(0.2)
+    Y = orc.gwo_candidates(c, g, X, np.array([0, 1, 2]))
+    y = Y[3:].ravel().astype(np.float64)
+    assert np.array_equal(Y[:3], X[:3])
+    # Y_k = 1/2 - A |C/2| with E[A] = 0, E[A^2] = a^2/3, E[C^2] = 4/3 -> var(y) = a^2/27
+    assert abs(y.mean() - 0.5) < 4 * np.sqrt(a * a / 27 / y.size)
+    assert abs(y.var() / (a * a / 27) - 1.0) < 0.04
+    assert y.min() >= 0.5 - a and y.max() <= 0.5 + a
+
+
+def test_gwo_a_schedule(orc):
+    G = 2000
+    a = np.array([orc.a_of(g, G) for g in range(G)])
+    assert a[0] == 2.0 and np.all(np.diff(a) < 0) and abs(a[-1] - 2.0 / G) < 1e-7
+
+
+def test_gwo_weighted_combination_reduces_to_mean(orc):
+    # with identical leaders and the wolf on them, A d = A |C-1| |x| for every k, and the
+    # |X_k|-weighted combination of equal-sign X_k is (sum X_k^2 / sum |X_k|) / 3
+    NP, N = 6, 512
+    X = np.full((NP, N), 0.25, dtype=np.float32)
+    cm = _cfg(orc, NP=NP, N=N, G=10, combine=0)
+    cw = _cfg(orc, NP=NP, N=N, G=10, combine=1)
+    Ym = orc.gwo_candidates(cm, 9, X, np.array([0, 1, 2]))
+    Yw = orc.gwo_candidates(cw, 9, X, np.array([0, 1, 2]))
+    # a = 0.2: every X_k is positive; weighted/3 is about 1/3 of the mean
+    assert np.all(Yw[3:] > 0)
+    ratio = Yw[3:].mean() / Ym[3:].mean()
+    assert abs(ratio - 1.0 / 3.0) < 0.01
+
+
+def test_top3_matches_stable_sort(orc):
+    rng = np.random.default_rng(5)
+    for NP in (4, 5, 31, 300):
+        f = rng.integers(0, 6, NP).astype(np.float32)  # many ties
+        lead = orc.top3(f)
+        ref = np.lexsort((np.arange(NP), -f))[:3]
+        assert np.array_equal(lead, ref)
+
+
+def test_hwsda_greedy_selection_never_loses_fitness(orc):
+    # one-to-one greedy selection (Sec. 2.2.1 step 4, Sec. 3.2 Step 5): every
+    # individual ends at least as fit as it started, and at least as fit as every
+    # trial and candidate it was offered in its last generation
+    k1, k2 = 2 * np.pi / 7.0, 2 * np.pi / 1.6
+    c = _cfg(orc, NP=16, N=16, G=40)
+    X, f, tr = orc.hwsda_run(c, k1, k2, want_trace=True)
+    NP = c.NP
+    assert np.all(f >= tr[:NP])
+    last_trial = tr[NP * (1 + 2 * (c.G - 1)):NP * (2 + 2 * (c.G - 1))]
+    last_cand = tr[NP * (2 + 2 * (c.G - 1)):NP * (3 + 2 * (c.G - 1))]
+    assert np.all(f >= last_trial)
+    ok = ~np.isnan(last_cand)
+    assert np.all(f[ok] >= last_cand[ok]) and np.sum(~ok) == 3
+    # the final fitness is that of the final genes
+    assert np.allclose(f, np.abs(orc.deff_genes(X, k1, k2)) ** 2, rtol=1e-13)
+
+
+def test_hwsda_reaches_bruteforce_optimum_small(orc):
+    """N = 16 domains, dk1 w = 2pi/7, dk2 w = 2pi/1.6, NP = 32, 200 generations."""
+    with open(os.path.join(GOLDEN, "bruteforce_n16.json")) as fh:
+        gold = json.load(fh)
+    k1, k2 = gold["kappa1"], gold["kappa2"]
+    best, mask, allf = orc.bruteforce(16, k1, k2, want_all=True)
+    assert abs(best - gold["best_f"]) <= 1e-12 * best and mask == gold["best_mask"]
+    c = _cfg(orc, NP=32, N=16, G=200, F=0.5, CR=0.9, seed=1)
+    X, f = orc.hwsda_run(c, k1, k2)
+    # reaching the exhaustive optimum is an empirical outcome of the heuristic, not a
+    # property of the method: require a design in the top 0.1 % of all 65536 patterns
+    # and no value above the optimum (the gap for seed 1 is 1.5 %)
+    assert f.max() <= best * (1 + 1e-12)
+    assert f.max() >= np.quantile(allf, 0.999), (f.max(), best)
+
+
+def test_lockstep_replay_equals_free_run_when_decisions_agree(orc):
+    k1, k2 = 2 * np.pi / 7.0, 2 * np.pi / 1.6
+    c = _cfg(orc, NP=10, N=24, G=15, seed=9)
+    X, f, tr = orc.hwsda_run(c, k1, k2, want_trace=True)
+    # feed the oracle's own fitness back as FP32 decision values: same trajectory unless
+    # rounding to FP32 merges two FP64 values (not the case here)
+    ls = tr.astype(np.float32)
+    ls[np.isnan(tr)] = np.nan
+    X2, f2 = orc.hwsda_run(c, k1, k2, lockstep=ls)
+    assert np.array_equal(X, X2)
+
+
+def test_relaxed_gradient_matches_finite_differences(orc):
+    rng = np.random.default_rng(21)
+    N = 96
+    theta = rng.normal(size=N)
+    k1, k2 = 2 * np.pi / 6.9, 2 * np.pi / 1.55
+    g, D = orc.grad_relaxed(theta, k1, k2)
+    fd = orc.fd_grad(theta, k1, k2, np.arange(N), h=1e-6)
+    scale = np.abs(fd).max()
+    assert np.max(np.abs(g - fd)) <= 1e-6 * scale
+    f, D2 = orc.fit_relaxed(theta, k1, k2)
+    assert abs(D - D2) <= 1e-12 * abs(D) and abs(f - abs(D) ** 2) <= 1e-12 * f
+    # Euler: f is homogeneous of degree 4 in d, so sum_k d_k df/dd_k = 4 f
+    d = np.tanh(theta)
+    dfdd = g / (1 - d * d)
+    assert abs(np.sum(d * dfdd) - 4 * f) <= 1e-9 * f
