@@ -1,0 +1,165 @@
+/*
+ * qpm.h -- C ABI of the GB300 (sm_103a) library for quasi-phase-matching crystal
+ * design by the hybrid wolf-swarm differential algorithm (HWSDA: differential
+ * evolution + grey-wolf optimiser) of arXiv 2511.01255.
+ *
+ * Conventions shared by every entry point
+ *   - Lengths are in units of the domain width w.  A problem is N domains of width
+ *     w with phase mismatches dk1 (SHG) and dk2 (SFG); the library takes
+ *     kappa1 = dk1*w and kappa2 = dk2*w in radians.  The returned d_eff is in
+ *     units of w^2 (multiply by w^2 for physical units).
+ *   - d_eff is the double integral of Sec. 2.1 (the expression that ends the
+ *     derivation of the cascaded third-harmonic field):
+ *         d_eff = int_0^L d(z) e^{-i dk2 z} ( int_0^z d(x) e^{-i dk1 x} dx ) dz
+ *     evaluated exactly for piecewise-constant d(z).  The fitness is
+ *     f = |d_eff|^2, which the optimiser maximises (Sec. 2.1 asks for the
+ *     largest d_eff).
+ *   - Domain signs: a real gene x maps to d = (x < 0) ? -1 : +1 (Sec. 3.1.2's
+ *     continuous-to-(+1/-1) mapping); in packed form bit (j % 32) of word j / 32
+ *     set means d_j = -1.
+ *   - Complex values are two consecutive floats (re, im), i.e. float2 layout.
+ *   - Every pointer named "device" is CUDA device memory owned by the caller;
+ *     the library never frees it and never keeps it past the call.  Host
+ *     pointers are named "host".
+ *   - Every call that takes a stream enqueues its work on that stream
+ *     (NULL = the legacy default stream) and returns without synchronising,
+ *     unless stated otherwise.
+ *   - Every call returns a qpm_status.  On failure nothing is enqueued (argument
+ *     errors) or the CUDA error is reported (QPM_ERR_CUDA); qpm_last_error()
+ *     gives a message for the calling thread.  No exception crosses the ABI.
+ *     There is no CPU fallback: without a usable sm_103a device every call that
+ *     computes returns QPM_ERR_CUDA.
+ */
+#ifndef QPM_H_
+#define QPM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qpm_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  QPM_OK = 0,
+  QPM_ERR_ARG = 1,         /* invalid argument (size, alignment, NULL pointer) */
+  QPM_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  QPM_ERR_TIMEOUT = 3,     /* a bounded device-side wait gave up (persistent kernel) */
+  QPM_ERR_UNSUPPORTED = 4, /* request outside what this build supports */
+  QPM_ERR_STATE = 5        /* call out of order (e.g. step before init) */
+} qpm_status;
+
+/* One design problem: N domains, kappa = dk * w in radians. */
+typedef struct {
+  int32_t N;
+  double kappa1; /* SHG mismatch dk1 * w */
+  double kappa2; /* SFG mismatch dk2 * w */
+} qpm_problem;
+
+/* HWSDA parameters (Sec. 2.2.1, 2.2.2, 3.2). */
+typedef struct {
+  int32_t NP;          /* population size, >= 4 (rand/1 needs 3 donors != target) */
+  int32_t G;           /* generations; a decays linearly 2 -> 0 over them */
+  float F;             /* DE scale factor, [0, 2] */
+  float CR;            /* crossover rate, [0, 1] */
+  uint64_t seed;       /* Philox4x32-10 key */
+  int32_t gwo_combine; /* 0: (X1+X2+X3)/3; 1: |X_k|-weighted, per dimension */
+  int32_t compensated; /* 0: plain FP32 scan; 1: Kahan-compensated FP32 scan */
+} qpm_params;
+
+/* Execution modes of qpm_run. */
+enum {
+  QPM_RUN_LAUNCHES = 0,   /* two kernels per generation, launched one by one */
+  QPM_RUN_GRAPH = 1,      /* the same launches captured once into a CUDA graph */
+  QPM_RUN_PERSISTENT = 2  /* one cooperative persistent kernel for all generations */
+};
+
+const char *qpm_last_error(void);
+const char *qpm_status_string(qpm_status s);
+int32_t qpm_abi_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Fitness (Sec. 2.1): d_eff and f = |d_eff|^2 of NP sign sequences.
+ *   genes   device, float [NP][ld], row-major, ld >= N; only the sign is used
+ *   signs   device, uint32 [NP][ld_words], ld_words >= ceil(N / 32)
+ *   d_eff   device, float2 [NP] (re, im), units of w^2
+ *   fit     device, float [NP] = |d_eff|^2 (may be NULL)
+ *   compensated: 0 plain FP32 scan, 1 Kahan-compensated
+ * The per-problem phasor table is built on first use of (device, N, kappa1,
+ * kappa2) and cached by the library (library-owned device memory, released by
+ * qpm_release_caches); the scan's partial results use a library-owned scratch
+ * buffer grown on demand.  Errors: N < 1, NP < 1, ld < N -> QPM_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld, int32_t NP,
+                    float *d_eff, float *fit, int32_t compensated, qpm_stream_t stream);
+qpm_status qpm_eval_packed(const qpm_problem *prob, const uint32_t *signs, int64_t ld_words,
+                           int32_t NP, float *d_eff, float *fit, int32_t compensated,
+                           qpm_stream_t stream);
+
+/* Free the cached phasor tables and scratch of the current device (synchronises it). */
+qpm_status qpm_release_caches(void);
+
+/* ---------------------------------------------------------------------------
+ * Optimiser state: n_inst independent HWSDA instances (uneven N, kappa, NP
+ * allowed), all resident on the current device.
+ *   qpm_create   allocates the state (library-owned device memory) and returns
+ *                it in *out; synchronous; nothing is launched.
+ *   qpm_init     Step 1 of Sec. 3.2: phasor tables, x_ij = U(-1,1) (Sec. 2.2.1
+ *                step 1) and the fitness of every individual; generation := 0.
+ *   qpm_step     one generation (Sec. 3.2 Steps 2-6) of every instance.
+ *   qpm_run      `generations` generations in the given QPM_RUN_* mode.
+ *                QPM_RUN_PERSISTENT returns QPM_ERR_TIMEOUT if a bounded
+ *                device-side wait gave up (checked after synchronising the stream).
+ *   qpm_destroy  frees the state (synchronises the device first).
+ * Errors: NP < 4, N < 1, G < 1, F outside [0, 2] or CR outside [0, 1] -> QPM_ERR_ARG;
+ * qpm_step/qpm_run before qpm_init -> QPM_ERR_STATE; running past G -> QPM_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+typedef struct qpm_state qpm_state;
+
+qpm_status qpm_create(const qpm_problem *probs, const qpm_params *params, int32_t n_inst,
+                      qpm_state **out);
+qpm_status qpm_init(qpm_state *st, qpm_stream_t stream);
+qpm_status qpm_step(qpm_state *st, qpm_stream_t stream);
+qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode, qpm_stream_t stream);
+qpm_status qpm_destroy(qpm_state *st);
+
+/* generation counter of the state as seen by the host (host int32 out) */
+qpm_status qpm_generation(const qpm_state *st, int32_t *g_out);
+
+/* Current population of instance `inst`, in natural order:
+ *   genes_out device float [NP][ld] (ld >= N), fit_out device float [NP] (may be NULL),
+ *   d_eff_out device float2 [NP] (may be NULL).  Enqueued on `stream`. */
+qpm_status qpm_get_population(qpm_state *st, int32_t inst, float *genes_out, int64_t ld,
+                              float *fit_out, float *d_eff_out, qpm_stream_t stream);
+
+/* Best individual of instance `inst` (largest f, lowest index on ties) with its
+ * d_eff re-evaluated in FP64 on the device:
+ *   genes_out device float [N], d_eff64_out device double [2], fit_out device float [1]
+ *   (each may be NULL), index_out device int32 [1] (may be NULL). */
+qpm_status qpm_get_best(qpm_state *st, int32_t inst, float *genes_out, double *d_eff64_out,
+                        float *fit_out, int32_t *index_out, qpm_stream_t stream);
+
+/* Test hook: record FP32 fitness values of instance `inst` into trace (device,
+ * float [NP * (1 + 2G)]): [0, NP) after init, then for generation g the trial
+ * fitness at NP*(1+2g) and the GWO candidate fitness at NP*(2+2g) (NaN for the
+ * three leaders, which do not move).  NULL disables.  Must be set before qpm_init. */
+qpm_status qpm_set_trace(qpm_state *st, int32_t inst, float *trace);
+
+/* Upper bound, in nanoseconds, on every device-side wait of the persistent kernel
+ * (grid barriers; default 5 s).  A wait that reaches it makes the kernel record
+ * QPM_ERR_TIMEOUT and return; qpm_run then reports QPM_ERR_TIMEOUT.  No GPU
+ * trap is ever raised.  Test hook and safety valve; host-only, takes effect at
+ * the next qpm_run. */
+qpm_status qpm_set_wait_timeout_ns(qpm_state *st, uint64_t ns);
+
+/* End to end with host buffers: create, init, run all G generations (mode as in
+ * qpm_run), copy the best genes (host float [N]) and its FP64 d_eff (host
+ * double [2]) back, destroy.  Synchronous.  best_fit (host float [1]) may be NULL. */
+qpm_status qpm_solve(const qpm_problem *prob, const qpm_params *params, int32_t mode,
+                     float *best_genes_host, double *best_deff64_host, float *best_fit_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QPM_H_ */

@@ -55,6 +55,8 @@ def lib():
         L.orc_a_of.argtypes = [i32, i32]
         L.orc_a_of.restype = ctypes.c_float
         L.orc_gwo_candidates.argtypes = [P, u32, P, P, P]
+        L.orc_hwsda_generation.argtypes = [P, dbl, dbl, ctypes.c_int, i32, P, P, P, P, P, P, P, P, P]
+        L.orc_hwsda_generation.restype = ctypes.c_int
         L.orc_hwsda_run.argtypes = [P, dbl, dbl, ctypes.c_int, P, P, P, P]
         L.orc_hwsda_run.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
@@ -191,6 +193,29 @@ def gwo_candidates(cfg, g, X, lead):
     Y = X.copy()
     lib().orc_gwo_candidates(ctypes.byref(cfg), g, _p(X), _p(lead), _p(Y))
     return Y
+
+
+def hwsda_generation(cfg, kappa1, kappa2, g, X, fdec, f64=None, lock_trial=None,
+                     lock_cand=None, eval_mask=None, Q=Q_DEFAULT):
+    """One generation (Sec. 3.2 Steps 2-6) from population X.
+
+    Returns (X_next, fdec_next, f64_next, trial_f64, cand_f64, leaders).  In lockstep
+    mode (lock_trial/lock_cand given) the FP32 values decide; eval_mask limits
+    which rows get an FP64 fitness (NaN elsewhere)."""
+    X = np.array(X, dtype=np.float32, order="C", copy=True)
+    fdec = np.array(fdec, dtype=np.float32, copy=True)
+    f64 = np.zeros(cfg.NP) if f64 is None else np.array(f64, dtype=np.float64, copy=True)
+    lt = None if lock_trial is None else np.ascontiguousarray(lock_trial, dtype=np.float32)
+    lc = None if lock_cand is None else np.ascontiguousarray(lock_cand, dtype=np.float32)
+    em = None if eval_mask is None else np.ascontiguousarray(eval_mask, dtype=np.uint8)
+    tt = np.zeros(cfg.NP)
+    tc = np.zeros(cfg.NP)
+    lead = np.zeros(3, dtype=np.int32)
+    rc = lib().orc_hwsda_generation(ctypes.byref(cfg), kappa1, kappa2, Q, g, _p(X), _p(fdec),
+                                    _p(f64), _p(lt), _p(lc), _p(em), _p(tt), _p(tc), _p(lead))
+    if rc != 0:
+        raise ValueError("orc_hwsda_generation: eval_mask needs lockstep mode")
+    return X, fdec, f64, tt, tc, lead
 
 
 def hwsda_run(cfg, kappa1, kappa2, lockstep=None, want_trace=False, Q=Q_DEFAULT):

@@ -535,6 +535,78 @@ static void eval_rows(const orc_cfg *c, double kappa1, double kappa2, int Q, con
   }
 }
 
+/* One generation of the HWSDA loop (Sec. 3.2 Steps 2-6) from population X.
+ *   X[NP*ld]      in/out FP32 genes
+ *   fdec[NP]      in/out FP32 fitness used for the decisions (lockstep mode)
+ *   f64[NP]       in/out FP64 fitness of the current individuals (may be stale
+ *                 for individuals whose new fitness was not evaluated)
+ *   lock_trial, lock_cand: if non-NULL (lockstep), FP32 fitness of this
+ *                 generation's trials / GWO candidates that decide selection
+ *                 and leaders; otherwise the oracle's own FP64 values decide
+ *   eval_mask[NP]: if non-NULL, only rows with a non-zero entry get their FP64
+ *                 fitness computed (lockstep only; decisions do not need them)
+ *   tr_trial, tr_cand: if non-NULL, receive the FP64 fitness of trials and
+ *                 candidates (NaN where not evaluated)
+ *   lead_out[3]:  if non-NULL, receives the leaders of this generation */
+ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2, int Q, int32_t g,
+                                 float *X, float *fdec, double *f64, const float *lock_trial,
+                                 const float *lock_cand, const uint8_t *eval_mask,
+                                 double *tr_trial, double *tr_cand, int32_t *lead_out) {
+  ensure_rule(Q);
+  const int lock = (lock_trial != NULL);
+  if (!lock && eval_mask) return -1;
+  int32_t NP = c->NP;
+  int64_t sz = (int64_t)NP * c->ld;
+  float *U = (float *)calloc((size_t)sz, sizeof(float));
+  double *ft = (double *)malloc(sizeof(double) * NP);
+  uint8_t *mask = (uint8_t *)malloc((size_t)NP);
+  /* Step 2: mutation, crossover and selection over all NP individuals */
+  orc_de_trials(c, (uint32_t)g, X, U);
+  eval_rows(c, kappa1, kappa2, Q, U, eval_mask, ft);
+  if (tr_trial) memcpy(tr_trial, ft, sizeof(double) * NP);
+  for (int32_t i = 0; i < NP; ++i) {
+    int accept = lock ? (lock_trial[i] >= fdec[i]) : (ft[i] >= f64[i]);
+    if (accept) {
+      memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
+      f64[i] = ft[i];
+      fdec[i] = lock ? lock_trial[i] : (float)ft[i];
+    }
+  }
+  /* Step 3: the three leaders */
+  int32_t lead[3];
+  if (lock) {
+    orc_top3(NP, fdec, lead);
+  } else {
+    for (int k = 0; k < 3; ++k) lead[k] = -1;
+    for (int32_t i = 0; i < NP; ++i)
+      for (int k = 0; k < 3; ++k)
+        if (lead[k] < 0 || f64[i] > f64[lead[k]]) {
+          for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+          lead[k] = i;
+          break;
+        }
+  }
+  if (lead_out) { lead_out[0] = lead[0]; lead_out[1] = lead[1]; lead_out[2] = lead[2]; }
+  /* Step 4: move the omega wolves; Step 5: greedy selection again */
+  orc_gwo_candidates(c, (uint32_t)g, X, lead, U);
+  for (int32_t i = 0; i < NP; ++i)
+    mask[i] = !(i == lead[0] || i == lead[1] || i == lead[2]) && (!eval_mask || eval_mask[i]);
+  eval_rows(c, kappa1, kappa2, Q, U, mask, ft);
+  if (tr_cand) memcpy(tr_cand, ft, sizeof(double) * NP);
+  for (int32_t i = 0; i < NP; ++i) {
+    if (i == lead[0] || i == lead[1] || i == lead[2]) continue;
+    int accept = lock ? (lock_cand[i] >= fdec[i]) : (ft[i] >= f64[i]);
+    if (accept) {
+      memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
+      f64[i] = ft[i];
+      fdec[i] = lock ? lock_cand[i] : (float)ft[i];
+    }
+  }
+  /* Step 6: F and CR stay constant; a follows from g in the next generation */
+  free(U); free(ft); free(mask);
+  return 0;
+}
+
 /* The HWSDA loop of Sec. 3.2 (Steps 1-7), one instance.
  *   X[NP*ld]   out: final population (FP32 genes)
  *   fcur[NP]   out: FP64 fitness of the final population
@@ -550,68 +622,19 @@ ORC_API int orc_hwsda_run(const orc_cfg *c, double kappa1, double kappa2, int Q,
                           double *fcur, const float *lockstep, double *trace64) {
   ensure_rule(Q);
   int32_t NP = c->NP;
-  int64_t sz = (int64_t)NP * c->ld;
-  float *U = (float *)calloc((size_t)sz, sizeof(float));
-  double *ft = (double *)malloc(sizeof(double) * NP);
-  float *fdec = (float *)malloc(sizeof(float) * NP); /* decision fitness */
-  double *f64 = fcur;
+  float *fdec = (float *)malloc(sizeof(float) * NP);
   orc_init_population(c, X);
-  eval_rows(c, kappa1, kappa2, Q, X, NULL, f64);
-  if (trace64) memcpy(trace64, f64, sizeof(double) * NP);
-  for (int32_t i = 0; i < NP; ++i) fdec[i] = lockstep ? lockstep[i] : (float)f64[i];
-  double *fdec64 = (double *)malloc(sizeof(double) * NP);
-  for (int32_t i = 0; i < NP; ++i) fdec64[i] = f64[i];
+  eval_rows(c, kappa1, kappa2, Q, X, NULL, fcur);
+  if (trace64) memcpy(trace64, fcur, sizeof(double) * NP);
+  for (int32_t i = 0; i < NP; ++i) fdec[i] = lockstep ? lockstep[i] : (float)fcur[i];
   for (int32_t g = 0; g < c->G; ++g) {
-    /* Step 2: mutation, crossover, selection over all NP individuals */
-    orc_de_trials(c, (uint32_t)g, X, U);
-    eval_rows(c, kappa1, kappa2, Q, U, NULL, ft);
     const float *lt = lockstep ? lockstep + (int64_t)NP * (1 + 2 * g) : NULL;
-    if (trace64) memcpy(trace64 + (int64_t)NP * (1 + 2 * g), ft, sizeof(double) * NP);
-    for (int32_t i = 0; i < NP; ++i) {
-      int accept = lockstep ? (lt[i] >= fdec[i]) : (ft[i] >= fdec64[i]);
-      if (accept) {
-        memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
-        f64[i] = ft[i];
-        fdec64[i] = ft[i];
-        if (lockstep) fdec[i] = lt[i];
-      }
-    }
-    /* Step 3: leaders */
-    int32_t lead[3];
-    if (lockstep) {
-      orc_top3(NP, fdec, lead);
-    } else {
-      /* FP64 decisions: same rule on the FP64 values */
-      for (int k = 0; k < 3; ++k) lead[k] = -1;
-      for (int32_t i = 0; i < NP; ++i)
-        for (int k = 0; k < 3; ++k)
-          if (lead[k] < 0 || fdec64[i] > fdec64[lead[k]]) {
-            for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
-            lead[k] = i;
-            break;
-          }
-    }
-    /* Step 4: move the omega wolves; Step 5: greedy selection again */
-    orc_gwo_candidates(c, (uint32_t)g, X, lead, U);
-    uint8_t *mask = (uint8_t *)malloc((size_t)NP);
-    for (int32_t i = 0; i < NP; ++i) mask[i] = !(i == lead[0] || i == lead[1] || i == lead[2]);
-    eval_rows(c, kappa1, kappa2, Q, U, mask, ft);
     const float *lc = lockstep ? lockstep + (int64_t)NP * (2 + 2 * g) : NULL;
-    if (trace64) memcpy(trace64 + (int64_t)NP * (2 + 2 * g), ft, sizeof(double) * NP);
-    for (int32_t i = 0; i < NP; ++i) {
-      if (!mask[i]) continue;
-      int accept = lockstep ? (lc[i] >= fdec[i]) : (ft[i] >= fdec64[i]);
-      if (accept) {
-        memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
-        f64[i] = ft[i];
-        fdec64[i] = ft[i];
-        if (lockstep) fdec[i] = lc[i];
-      }
-    }
-    free(mask);
-    /* Step 6: F and CR stay constant; a is recomputed from g at the next pass */
+    double *tt = trace64 ? trace64 + (int64_t)NP * (1 + 2 * g) : NULL;
+    double *tc = trace64 ? trace64 + (int64_t)NP * (2 + 2 * g) : NULL;
+    orc_hwsda_generation(c, kappa1, kappa2, Q, g, X, fdec, fcur, lt, lc, NULL, tt, tc, NULL);
   }
-  free(U); free(ft); free(fdec); free(fdec64);
+  free(fdec);
   return 0;
 }
 

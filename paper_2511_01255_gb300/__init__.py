@@ -1,0 +1,250 @@
+"""GB300 (sm_103a) quasi-phase-matching crystal design by HWSDA (arXiv 2511.01255).
+
+Thin Python binding over the C ABI in ``include/qpm.h`` (library
+``_build/libqpm.so``, built by ``build_lib.py``).  The functions keep the C
+names; they only marshal arguments (torch CUDA tensors -> device pointers,
+the current torch stream -> ``cudaStream_t``) and raise ``QpmError`` on a
+non-zero status.  Every computation runs in the library's CUDA kernels; there is
+no CPU path: if the library cannot be loaded, importing the binding's functions
+raises.
+"""
+import ctypes
+import os
+
+from . import build_lib
+
+__all__ = [
+    "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_release_caches",
+    "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation",
+    "qpm_get_population", "qpm_get_best", "qpm_set_trace", "qpm_set_wait_timeout_ns",
+    "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT",
+]
+
+RUN_LAUNCHES, RUN_GRAPH, RUN_PERSISTENT = 0, 1, 2
+STATUS = {0: "QPM_OK", 1: "QPM_ERR_ARG", 2: "QPM_ERR_CUDA", 3: "QPM_ERR_TIMEOUT",
+          4: "QPM_ERR_UNSUPPORTED", 5: "QPM_ERR_STATE"}
+
+
+class QpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("kappa1", ctypes.c_double), ("kappa2", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("NP", ctypes.c_int32), ("G", ctypes.c_int32), ("F", ctypes.c_float),
+                ("CR", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("gwo_combine", ctypes.c_int32), ("compensated", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib(build=True):
+    """Load libqpm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = build_lib.build() if build else build_lib.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libqpm.so not found at {path}")
+        L = ctypes.CDLL(path)
+        i32, i64, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        sig = {
+            "qpm_last_error": ([], ctypes.c_char_p),
+            "qpm_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "qpm_abi_version": ([], i32),
+            "qpm_eval": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
+            "qpm_eval_packed": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
+            "qpm_release_caches": ([], ctypes.c_int),
+            "qpm_create": ([_P, _P, i32, _P], ctypes.c_int),
+            "qpm_init": ([_P, _P], ctypes.c_int),
+            "qpm_step": ([_P, _P], ctypes.c_int),
+            "qpm_run": ([_P, i32, i32, _P], ctypes.c_int),
+            "qpm_destroy": ([_P], ctypes.c_int),
+            "qpm_generation": ([_P, _P], ctypes.c_int),
+            "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
+            "qpm_get_best": ([_P, i32, _P, _P, _P, _P, _P], ctypes.c_int),
+            "qpm_set_trace": ([_P, i32, _P], ctypes.c_int),
+            "qpm_set_wait_timeout_ns": ([_P, u64], ctypes.c_int),
+            "qpm_solve": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise QpmError(status, lib().qpm_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor, None for None."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _rows(t, what):
+    """(rows, leading dimension) of a row-major 2-D tensor with unit column stride."""
+    if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise ValueError(f"{what}: need a 2-D tensor with contiguous rows")
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.stride(0), t.shape[1])
+    return t.shape[0], ld
+
+
+def _problem(N, kappa1, kappa2):
+    return Problem(int(N), float(kappa1), float(kappa2))
+
+
+def qpm_eval(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, stream=None):
+    """d_eff (float32 [NP, 2]) and fit of the rows of genes (float32 CUDA [NP, ld])."""
+    p = _problem(N, kappa1, kappa2)
+    NP, ld = _rows(genes, "genes")
+    _check(lib().qpm_eval(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),
+                          int(compensated), _stream(stream)))
+
+
+def qpm_eval_packed(N, kappa1, kappa2, signs, d_eff, fit=None, compensated=0, stream=None):
+    """Same from packed signs (int32/uint32 CUDA [NP, ld_words], bit set -> d = -1)."""
+    p = _problem(N, kappa1, kappa2)
+    NP, ld = _rows(signs, "signs")
+    _check(lib().qpm_eval_packed(ctypes.byref(p), _ptr(signs), ld, NP, _ptr(d_eff), _ptr(fit),
+                                 int(compensated), _stream(stream)))
+
+
+def qpm_release_caches():
+    _check(lib().qpm_release_caches())
+
+
+def qpm_create(problems, params):
+    """problems: list of (N, kappa1, kappa2); params: list of Params (same length)."""
+    n = len(problems)
+    pa = (Problem * n)(*[_problem(*p) for p in problems])
+    qa = (Params * n)(*params)
+    h = ctypes.c_void_p()
+    _check(lib().qpm_create(pa, qa, n, ctypes.byref(h)))
+    return h
+
+
+def qpm_init(st, stream=None):
+    _check(lib().qpm_init(st, _stream(stream)))
+
+
+def qpm_step(st, stream=None):
+    _check(lib().qpm_step(st, _stream(stream)))
+
+
+def qpm_run(st, generations, mode=RUN_GRAPH, stream=None):
+    _check(lib().qpm_run(st, int(generations), int(mode), _stream(stream)))
+
+
+def qpm_destroy(st):
+    _check(lib().qpm_destroy(st))
+
+
+def qpm_generation(st):
+    g = ctypes.c_int32()
+    _check(lib().qpm_generation(st, ctypes.byref(g)))
+    return g.value
+
+
+def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):
+    ld = _rows(genes_out, "genes_out")[1] if genes_out is not None else 0
+    _check(lib().qpm_get_population(st, int(inst), _ptr(genes_out), ld, _ptr(fit_out),
+                                    _ptr(d_eff_out), _stream(stream)))
+
+
+def qpm_get_best(st, inst, genes_out=None, d_eff64_out=None, fit_out=None, index_out=None,
+                 stream=None):
+    _check(lib().qpm_get_best(st, int(inst), _ptr(genes_out), _ptr(d_eff64_out), _ptr(fit_out),
+                              _ptr(index_out), _stream(stream)))
+
+
+def qpm_set_trace(st, inst, trace):
+    _check(lib().qpm_set_trace(st, int(inst), _ptr(trace)))
+
+
+def qpm_set_wait_timeout_ns(st, ns):
+    _check(lib().qpm_set_wait_timeout_ns(st, int(ns)))
+
+
+def qpm_solve(N, kappa1, kappa2, params, mode, best_genes_host, best_deff64_host,
+              best_fit_host=None):
+    """End to end with host (CPU) tensors; synchronous."""
+    p = _problem(N, kappa1, kappa2)
+    _check(lib().qpm_solve(ctypes.byref(p), ctypes.byref(params), int(mode),
+                           _ptr(best_genes_host), _ptr(best_deff64_host), _ptr(best_fit_host)))
+
+
+class State:
+    """Owning wrapper of a qpm_state (destroyed with the object or on close())."""
+
+    def __init__(self, problems, params):
+        self.problems = list(problems)
+        self.params = list(params)
+        self.h = qpm_create(self.problems, self.params)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            qpm_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, stream=None):
+        qpm_init(self.h, stream)
+
+    def step(self, stream=None):
+        qpm_step(self.h, stream)
+
+    def run(self, generations, mode=RUN_GRAPH, stream=None):
+        qpm_run(self.h, generations, mode, stream)
+
+    @property
+    def generation(self):
+        return qpm_generation(self.h)
+
+    def population(self, inst=0):
+        import torch
+        N = self.problems[inst][0]
+        NP = self.params[inst].NP
+        X = torch.empty((NP, N), dtype=torch.float32, device="cuda")
+        f = torch.empty(NP, dtype=torch.float32, device="cuda")
+        D = torch.empty((NP, 2), dtype=torch.float32, device="cuda")
+        qpm_get_population(self.h, inst, X, f, D)
+        return X, f, D
+
+    def best(self, inst=0):
+        import torch
+        N = self.problems[inst][0]
+        x = torch.empty(N, dtype=torch.float32, device="cuda")
+        d64 = torch.empty(2, dtype=torch.float64, device="cuda")
+        f = torch.empty(1, dtype=torch.float32, device="cuda")
+        idx = torch.empty(1, dtype=torch.int32, device="cuda")
+        qpm_get_best(self.h, inst, x, d64, f, idx)
+        return x, d64, f, idx

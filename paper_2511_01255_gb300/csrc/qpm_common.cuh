@@ -1,0 +1,242 @@
+// qpm_common.cuh -- device building blocks shared by the sm_103a kernels.
+//
+// Fitness (Sec. 2.1).  For piecewise-constant d over unit domains the double
+// integral closes exactly:
+//   d_eff = phi1 phi2 * sum_j a_j (sum_{m<j} b_m) + psi * sum_j d_j^2 p1_j p2_j
+// with p1_m = e^{-i k1 m}, p2_m = e^{-i k2 m}, b_m = d_m p1_m, a_j = d_j p2_j,
+// phi(k) = int_0^1 e^{-iks} ds, psi = int_0^1 e^{-i k2 s} int_0^s e^{-i k1 t} dt ds.
+// The double sum is a reduction over the monoid of triples (A, B, C) =
+// (sum a, sum b, sum_{m<j} a_j b_m) with
+//   (A, B, C) (+) (A', B', C') = (A + A', B + B', C + C' + A' B),
+// which is associative but not commutative, so every tree below keeps the
+// left operand on the lower domain indices.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qpm {
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Random-number contract: key = seed, counter = (j/4, i, g, instance<<8 | tag);
+// word j%4 of the output serves gene j.
+enum : uint32_t { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3, TAG_THETA = 16 };
+
+__device__ __forceinline__ uint4 rng4(uint2 key, uint32_t inst, uint32_t tag, uint32_t g,
+                                      uint32_t i, uint32_t jgroup) {
+  return philox10(make_uint4(jgroup, i, g, (inst << 8) | tag), key);
+}
+// U in [0, 1) on the 24-bit grid (exact in FP32)
+__device__ __forceinline__ float u24(uint32_t w) {
+  return __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+}
+// index in [0, m): Lemire's multiply-shift
+__device__ __forceinline__ uint32_t lemire(uint32_t w, uint32_t m) { return __umulhi(w, m); }
+
+// DE rand/1 donors r1, r2, r3 (distinct, != i) and the forced crossover index jrand.
+// Each draw is mapped onto the values not yet excluded by skipping the excluded
+// ones in ascending order (a bijection, so every allowed value is equally likely).
+__device__ __forceinline__ int4 de_indices(uint2 key, uint32_t inst, uint32_t g, int i, int NP,
+                                           int N) {
+  const uint4 w = rng4(key, inst, TAG_DEIDX, g, (uint32_t)i, 0u);
+  int r1 = (int)lemire(w.x, (uint32_t)(NP - 1));
+  r1 += (r1 >= i);
+  int e0 = min(i, r1), e1 = max(i, r1);
+  int r2 = (int)lemire(w.y, (uint32_t)(NP - 2));
+  r2 += (r2 >= e0);
+  r2 += (r2 >= e1);
+  // sorted triple of excluded values
+  int s0 = e0, s1 = e1, s2 = r2;
+  if (s2 < s1) { int t = s1; s1 = s2; s2 = t; }
+  if (s1 < s0) { int t = s0; s0 = s1; s1 = t; }
+  int r3 = (int)lemire(w.z, (uint32_t)(NP - 3));
+  r3 += (r3 >= s0);
+  r3 += (r3 >= s1);
+  r3 += (r3 >= s2);
+  return make_int4(r1, r2, r3, (int)lemire(w.w, (uint32_t)N));
+}
+
+__device__ __forceinline__ float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
+
+// ------------------------------------------------------------------ the monoid
+struct Mono {
+  float2 A, B, C;
+};
+__device__ __forceinline__ Mono mono_zero() {
+  Mono m;
+  m.A = m.B = m.C = make_float2(0.f, 0.f);
+  return m;
+}
+// L (+) R, L on the lower indices
+__device__ __forceinline__ Mono mono_combine(const Mono &L, const Mono &R) {
+  Mono o;
+  o.A = make_float2(L.A.x + R.A.x, L.A.y + R.A.y);
+  o.B = make_float2(L.B.x + R.B.x, L.B.y + R.B.y);
+  float cr = L.C.x + R.C.x, ci = L.C.y + R.C.y;
+  cr = fmaf(R.A.x, L.B.x, cr);
+  cr = fmaf(-R.A.y, L.B.y, cr);
+  ci = fmaf(R.A.x, L.B.y, ci);
+  ci = fmaf(R.A.y, L.B.x, ci);
+  o.C = make_float2(cr, ci);
+  return o;
+}
+
+// append one domain with sign d (+-1.0f) and phasors p = (p1.re, p1.im, p2.re, p2.im)
+__device__ __forceinline__ void mono_push(Mono &m, float d, const float4 &p) {
+  const float ar = d * p.z, ai = d * p.w;  // a = d p2
+  m.C.x = fmaf(ar, m.B.x, m.C.x);
+  m.C.x = fmaf(-ai, m.B.y, m.C.x);
+  m.C.y = fmaf(ar, m.B.y, m.C.y);
+  m.C.y = fmaf(ai, m.B.x, m.C.y);
+  m.A.x += ar;
+  m.A.y += ai;
+  m.B.x = fmaf(d, p.x, m.B.x);  // b = d p1, added after its use: strict prefix
+  m.B.y = fmaf(d, p.y, m.B.y);
+}
+
+// Kahan-compensated variant: every running sum carries its compensation term
+struct MonoK {
+  Mono s;
+  float2 eA, eB, eC;
+};
+__device__ __forceinline__ MonoK monok_zero() {
+  MonoK m;
+  m.s = mono_zero();
+  m.eA = m.eB = m.eC = make_float2(0.f, 0.f);
+  return m;
+}
+__device__ __forceinline__ void kahan_add(float &s, float &e, float x) {
+  const float y = __fsub_rn(x, e);
+  const float t = __fadd_rn(s, y);
+  e = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+__device__ __forceinline__ void monok_push(MonoK &m, float d, const float4 &p) {
+  const float ar = d * p.z, ai = d * p.w;
+  const float br = __fsub_rn(m.s.B.x, m.eB.x), bi = __fsub_rn(m.s.B.y, m.eB.y);
+  const float pr = __fsub_rn(__fmul_rn(ar, br), __fmul_rn(ai, bi));
+  const float pi = __fadd_rn(__fmul_rn(ar, bi), __fmul_rn(ai, br));
+  kahan_add(m.s.C.x, m.eC.x, pr);
+  kahan_add(m.s.C.y, m.eC.y, pi);
+  kahan_add(m.s.A.x, m.eA.x, ar);
+  kahan_add(m.s.A.y, m.eA.y, ai);
+  kahan_add(m.s.B.x, m.eB.x, d * p.x);
+  kahan_add(m.s.B.y, m.eB.y, d * p.y);
+}
+__device__ __forceinline__ Mono monok_fold(const MonoK &m) {
+  Mono o;
+  o.A = make_float2(__fsub_rn(m.s.A.x, m.eA.x), __fsub_rn(m.s.A.y, m.eA.y));
+  o.B = make_float2(__fsub_rn(m.s.B.x, m.eB.x), __fsub_rn(m.s.B.y, m.eB.y));
+  o.C = make_float2(__fsub_rn(m.s.C.x, m.eC.x), __fsub_rn(m.s.C.y, m.eC.y));
+  return o;
+}
+
+__device__ __forceinline__ Mono mono_shfl_down(const Mono &m, int s) {
+  Mono o;
+  o.A.x = __shfl_down_sync(0xffffffffu, m.A.x, s);
+  o.A.y = __shfl_down_sync(0xffffffffu, m.A.y, s);
+  o.B.x = __shfl_down_sync(0xffffffffu, m.B.x, s);
+  o.B.y = __shfl_down_sync(0xffffffffu, m.B.y, s);
+  o.C.x = __shfl_down_sync(0xffffffffu, m.C.x, s);
+  o.C.y = __shfl_down_sync(0xffffffffu, m.C.y, s);
+  return o;
+}
+
+// ordered reduction over the 32 lanes of a warp (lane 0 gets lanes 0..31 combined)
+__device__ __forceinline__ Mono warp_reduce(Mono m) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const Mono r = mono_shfl_down(m, s);
+    if ((lane & (2 * s - 1)) == 0) m = mono_combine(m, r);
+  }
+  return m;
+}
+
+// ordered reduction over the whole CTA (threads in index order); the result is
+// valid in every thread.  `sh` must hold blockDim.x/32 + 1 entries.
+__device__ __forceinline__ Mono block_reduce(Mono m, Mono *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  m = warp_reduce(m);
+  if (nw == 1) {
+    if (lane == 0) sh[0] = m;
+    __syncthreads();
+    const Mono r = sh[0];
+    __syncthreads();
+    return r;
+  }
+  if (lane == 0) sh[warp] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Mono acc = sh[0];
+    for (int w = 1; w < nw; ++w) acc = mono_combine(acc, sh[w]);
+    sh[nw] = acc;
+  }
+  __syncthreads();
+  const Mono r = sh[nw];
+  __syncthreads();
+  return r;
+}
+
+// d_eff = phi1 phi2 C + cdiag  (cdiag = psi sum_j p1_j p2_j for +-1 domains)
+__device__ __forceinline__ float2 deff_from(const Mono &m, float2 phi12, float2 cdiag) {
+  return make_float2(fmaf(phi12.x, m.C.x, fmaf(-phi12.y, m.C.y, cdiag.x)),
+                     fmaf(phi12.x, m.C.y, fmaf(phi12.y, m.C.x, cdiag.y)));
+}
+__device__ __forceinline__ float fit_of(float2 D) { return fmaf(D.x, D.x, D.y * D.y); }
+
+// leader keys: larger key = larger f, ties -> lower index
+__device__ __forceinline__ unsigned long long lead_key(float f, int i) {
+  return ((unsigned long long)__float_as_uint(f) << 32) | (0xFFFFFFFFu - (uint32_t)i);
+}
+__device__ __forceinline__ int key_index(unsigned long long k) {
+  return (int)(0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull));
+}
+__device__ __forceinline__ void top3_insert(unsigned long long &k0, unsigned long long &k1,
+                                            unsigned long long &k2, unsigned long long x) {
+  if (x > k0) { k2 = k1; k1 = k0; k0 = x; }
+  else if (x > k1) { k2 = k1; k1 = x; }
+  else if (x > k2) { k2 = x; }
+}
+
+// ----------------------------------------------- FP64 phase argument reduction
+// r = x - 2 pi n with n = rint(x / 2pi), 2pi split into a double-double
+__device__ __forceinline__ double reduce_2pi(double x) {
+  const double TWO_PI_HI = 6.283185307179586232;
+  const double TWO_PI_LO = 2.4492935982947064e-16;
+  const double INV_TWO_PI = 0.15915494309189533577;
+  const double n = rint(x * INV_TWO_PI);
+  double r = fma(-n, TWO_PI_HI, x);
+  r = fma(-n, TWO_PI_LO, r);
+  return r;
+}
+
+// ------------------------------------------------------- bounded device waits
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace qpm

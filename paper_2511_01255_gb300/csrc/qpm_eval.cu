@@ -1,0 +1,293 @@
+// qpm_eval.cu -- fitness of caller-supplied sign sequences (Sec. 2.1).
+//
+// Work split: lane = individual, so the phasor of domain m is one warp-uniform
+// (broadcast) load shared by 32 individuals; the domains of a row are cut into
+// S segments handled by different warps, each producing the monoid partial
+// (A, B, C) of its segment; a second kernel combines the S partials of every
+// row in index order and closes d_eff = phi1 phi2 C + cdiag.
+#include <math.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "qpm_common.cuh"
+#include "qpm_internal.h"
+
+namespace qpm {
+
+static constexpr int EV_WARPS = 8;  // warps per CTA; the CTA's warps share a segment
+
+struct EvalShape {
+  int NP, N, S, L;  // S segments of L domains (L a multiple of 32)
+  int groups;       // ceil(NP / 32)
+  int NPpad;        // groups * 32
+};
+
+// partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
+template <int KIND, bool COMP>  // KIND 0: float genes (vector loads), 1: float genes (scalar), 2: packed bits
+static __global__ void __launch_bounds__(EV_WARPS * 32)
+    k_eval_seg(const void *__restrict__ src, int64_t ld, EvalShape sh,
+               const float4 *__restrict__ table, float2 *__restrict__ part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x;
+  const int grp = blockIdx.y * EV_WARPS + warp;
+  if (grp >= sh.groups) return;
+  const int i = grp * 32 + lane;
+  const int irow = i < sh.NP ? i : sh.NP - 1;  // spare lanes recompute the last row
+  const int m0 = s * sh.L;
+  const int m1 = min(sh.N, m0 + sh.L);
+  Mono acc = mono_zero();
+  MonoK acck = monok_zero();
+  if (KIND == 2) {
+    const uint32_t *row = (const uint32_t *)src + (int64_t)irow * ld;
+    for (int mb = m0; mb < m1; mb += 32) {
+      const uint32_t w = __ldg(row + (mb >> 5));
+      const int n = min(32, m1 - mb);
+#pragma unroll 8
+      for (int e = 0; e < n; ++e) {
+        const float4 p = __ldg(table + mb + e);
+        const float d = ((w >> e) & 1u) ? -1.0f : 1.0f;
+        if (COMP) monok_push(acck, d, p); else mono_push(acc, d, p);
+      }
+    }
+  } else if (KIND == 0) {
+    const float *row = (const float *)src + (int64_t)irow * ld;
+    int m = m0;
+    for (; m + 4 <= m1; m += 4) {
+      const float4 x = __ldg((const float4 *)(row + m));
+      const float4 p0 = __ldg(table + m), p1 = __ldg(table + m + 1);
+      const float4 p2 = __ldg(table + m + 2), p3 = __ldg(table + m + 3);
+      const float d0 = x.x < 0.f ? -1.f : 1.f, d1 = x.y < 0.f ? -1.f : 1.f;
+      const float d2 = x.z < 0.f ? -1.f : 1.f, d3 = x.w < 0.f ? -1.f : 1.f;
+      if (COMP) {
+        monok_push(acck, d0, p0); monok_push(acck, d1, p1);
+        monok_push(acck, d2, p2); monok_push(acck, d3, p3);
+      } else {
+        mono_push(acc, d0, p0); mono_push(acc, d1, p1);
+        mono_push(acc, d2, p2); mono_push(acc, d3, p3);
+      }
+    }
+    for (; m < m1; ++m) {
+      const float d = __ldg(row + m) < 0.f ? -1.f : 1.f;
+      if (COMP) monok_push(acck, d, __ldg(table + m)); else mono_push(acc, d, __ldg(table + m));
+    }
+  } else {
+    const float *row = (const float *)src + (int64_t)irow * ld;
+    for (int m = m0; m < m1; ++m) {
+      const float d = __ldg(row + m) < 0.f ? -1.f : 1.f;
+      if (COMP) monok_push(acck, d, __ldg(table + m)); else mono_push(acc, d, __ldg(table + m));
+    }
+  }
+  if (COMP) acc = monok_fold(acck);
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  const size_t o = (size_t)s * sh.NPpad + i;
+  part[o] = acc.A;
+  part[stride + o] = acc.B;
+  part[2 * stride + o] = acc.C;
+}
+
+template <bool COMP>
+static __global__ void k_eval_combine(EvalShape sh, const float2 *__restrict__ part,
+                                      const float2 *__restrict__ konst, float2 *__restrict__ deff,
+                                      float *__restrict__ fit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sh.NP) return;
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  Mono acc = mono_zero();
+  float2 eB = make_float2(0.f, 0.f), eC = make_float2(0.f, 0.f);
+  for (int s = 0; s < sh.S; ++s) {
+    const size_t o = (size_t)s * sh.NPpad + i;
+    Mono r;
+    r.A = part[o];
+    r.B = part[stride + o];
+    r.C = part[2 * stride + o];
+    if (COMP) {
+      // C += C' + A' B and B += B' with Kahan compensation on C and B
+      const float br = __fsub_rn(acc.B.x, eB.x), bi = __fsub_rn(acc.B.y, eB.y);
+      const float xr = __fadd_rn(r.C.x, __fsub_rn(__fmul_rn(r.A.x, br), __fmul_rn(r.A.y, bi)));
+      const float xi = __fadd_rn(r.C.y, __fadd_rn(__fmul_rn(r.A.x, bi), __fmul_rn(r.A.y, br)));
+      kahan_add(acc.C.x, eC.x, xr);
+      kahan_add(acc.C.y, eC.y, xi);
+      kahan_add(acc.B.x, eB.x, r.B.x);
+      kahan_add(acc.B.y, eB.y, r.B.y);
+      acc.A.x += r.A.x;
+      acc.A.y += r.A.y;
+    } else {
+      acc = mono_combine(acc, r);
+    }
+  }
+  if (COMP) acc.C = make_float2(__fsub_rn(acc.C.x, eC.x), __fsub_rn(acc.C.y, eC.y));
+  const float2 D = deff_from(acc, konst[0], konst[1]);
+  deff[i] = D;
+  if (fit) fit[i] = fit_of(D);
+}
+
+// ------------------------------------------------------------- caches (host)
+namespace {
+struct TableEntry {
+  float4 *table = nullptr;
+  double2 *part = nullptr;
+  float2 *konst = nullptr;
+  cudaEvent_t ready = nullptr;
+};
+struct ScratchEntry {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_mu;
+std::map<std::tuple<int, int32_t, double, double>, TableEntry> g_tables;
+std::map<std::pair<int, cudaStream_t>, ScratchEntry> g_scratch;
+constexpr size_t MAX_TABLES = 64;
+
+qpm_status release_device_caches(int dev) {
+  QPM_CUDA(cudaDeviceSynchronize());
+  for (auto it = g_tables.begin(); it != g_tables.end();) {
+    if (std::get<0>(it->first) == dev) {
+      cudaFree(it->second.table);
+      cudaFree(it->second.part);
+      cudaFree(it->second.konst);
+      cudaEventDestroy(it->second.ready);
+      it = g_tables.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = g_scratch.begin(); it != g_scratch.end();) {
+    if (it->first.first == dev) {
+      cudaFree(it->second.ptr);
+      it = g_scratch.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return QPM_OK;
+}
+
+// phasor table in natural order for (device, problem); built on `stream` on a miss
+qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
+                     const float2 **konst) {
+  int dev = 0;
+  QPM_CUDA(cudaGetDevice(&dev));
+  auto key = std::make_tuple(dev, p->N, p->kappa1, p->kappa2);
+  auto it = g_tables.find(key);
+  if (it == g_tables.end()) {
+    if (g_tables.size() >= MAX_TABLES) {
+      qpm_status st = release_device_caches(dev);
+      if (st != QPM_OK) return st;
+    }
+    TableEntry e;
+    const int32_t Npad = (p->N + 3) & ~3;
+    QPM_CUDA(cudaMalloc(&e.table, sizeof(float4) * (size_t)Npad));
+    QPM_CUDA(cudaMalloc(&e.part, sizeof(double2) * (size_t)table_part_count(Npad)));
+    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 2));
+    QPM_CUDA(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+    TableSpec s{p->N, Npad, 1, Npad, p->kappa1, p->kappa2};
+    qpm_status st = launch_table(s, e.table, e.part, e.konst, nullptr, stream);
+    if (st != QPM_OK) return st;
+    QPM_CUDA(cudaEventRecord(e.ready, stream));
+    it = g_tables.emplace(key, e).first;
+  } else {
+    QPM_CUDA(cudaStreamWaitEvent(stream, it->second.ready, 0));
+  }
+  *table = it->second.table;
+  *konst = it->second.konst;
+  return QPM_OK;
+}
+
+qpm_status get_scratch(cudaStream_t stream, size_t bytes, void **ptr) {
+  int dev = 0;
+  QPM_CUDA(cudaGetDevice(&dev));
+  ScratchEntry &e = g_scratch[std::make_pair(dev, stream)];
+  if (e.bytes < bytes) {
+    if (e.ptr) {
+      QPM_CUDA(cudaStreamSynchronize(stream));
+      QPM_CUDA(cudaFree(e.ptr));
+      e.ptr = nullptr;
+      e.bytes = 0;
+    }
+    QPM_CUDA(cudaMalloc(&e.ptr, bytes));
+    e.bytes = bytes;
+  }
+  *ptr = e.ptr;
+  return QPM_OK;
+}
+}  // namespace
+
+static EvalShape eval_shape(int NP, int N) {
+  EvalShape sh;
+  sh.NP = NP;
+  sh.N = N;
+  sh.groups = (NP + 31) / 32;
+  sh.NPpad = sh.groups * 32;
+  const int target_warps = sm_count() * 24;
+  int S = (target_warps + sh.groups - 1) / sh.groups;
+  const int maxS = (N + 63) / 64;  // at least 64 domains per segment
+  if (S > maxS) S = maxS;
+  if (S < 1) S = 1;
+  int L = (N + S - 1) / S;
+  L = (L + 31) & ~31;
+  sh.S = (N + L - 1) / L;
+  sh.L = L;
+  return sh;
+}
+
+static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t ld, int32_t NP,
+                              int kind, float *d_eff, float *fit, int32_t comp,
+                              cudaStream_t stream) {
+  if (!prob || !src || !d_eff) return fail(QPM_ERR_ARG, "qpm_eval: NULL pointer");
+  if (prob->N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval: need N >= 1 and NP >= 1");
+  if (prob->N > (1 << 28)) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: N too large");
+  if (kind == 2 ? (ld < (prob->N + 31) / 32) : (ld < prob->N))
+    return fail(QPM_ERR_ARG, "qpm_eval: leading dimension smaller than the row");
+  std::lock_guard<std::mutex> lock(g_mu);
+  const float4 *table;
+  const float2 *konst;
+  qpm_status st = get_table(prob, stream, &table, &konst);
+  if (st != QPM_OK) return st;
+  const EvalShape sh = eval_shape(NP, prob->N);
+  void *scratch;
+  st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
+  if (st != QPM_OK) return st;
+  float2 *part = (float2 *)scratch;
+  dim3 grid(sh.S, (sh.groups + EV_WARPS - 1) / EV_WARPS);
+  if (kind != 2 && (ld % 4 == 0) && (((uintptr_t)src & 15) == 0)) kind = 0;
+  else if (kind != 2) kind = 1;
+#define QPM_EV(K, C) k_eval_seg<K, C><<<grid, EV_WARPS * 32, 0, stream>>>(src, ld, sh, table, part)
+  if (kind == 0) { if (comp) QPM_EV(0, true); else QPM_EV(0, false); }
+  else if (kind == 1) { if (comp) QPM_EV(1, true); else QPM_EV(1, false); }
+  else { if (comp) QPM_EV(2, true); else QPM_EV(2, false); }
+#undef QPM_EV
+  QPM_CUDA(cudaGetLastError());
+  const int cb = 128;
+  if (comp)
+    k_eval_combine<true><<<(NP + cb - 1) / cb, cb, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
+  else
+    k_eval_combine<false><<<(NP + cb - 1) / cb, cb, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+}  // namespace qpm
+
+extern "C" qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld,
+                               int32_t NP, float *d_eff, float *fit, int32_t compensated,
+                               qpm_stream_t stream) {
+  return qpm::eval_common(prob, genes, ld, NP, 1, d_eff, fit, compensated,
+                          (cudaStream_t)stream);
+}
+
+extern "C" qpm_status qpm_eval_packed(const qpm_problem *prob, const uint32_t *signs,
+                                      int64_t ld_words, int32_t NP, float *d_eff, float *fit,
+                                      int32_t compensated, qpm_stream_t stream) {
+  return qpm::eval_common(prob, signs, ld_words, NP, 2, d_eff, fit, compensated,
+                          (cudaStream_t)stream);
+}
+
+extern "C" qpm_status qpm_release_caches(void) {
+  std::lock_guard<std::mutex> lock(qpm::g_mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return qpm::cuda_fail(e, "cudaGetDevice");
+  return qpm::release_device_caches(dev);
+}

@@ -1,0 +1,899 @@
+// qpm_hwsda.cu -- the HWSDA generation step (Sec. 3.2, Steps 1-7) on sm_103a.
+//
+// One CTA is the team for one individual at a time: its T threads split the
+// N domains into contiguous chunks of c domains (c a multiple of 4), every thread
+// builds its chunk of the new vector (DE trial or GWO candidate) straight from
+// the generator and the parent rows, scans it into a monoid partial, and the CTA
+// combines the partials in index order to d_eff.  The population is stored in
+// the matching permuted order, so that every warp-wide float4 access to a row
+// (target, donors, leaders, new vector, phasor table) is one contiguous 512 B
+// segment.
+//
+// Every individual owns two row slots; the new vector is always written to the
+// slot that is not current and survives by flipping a per-individual slot
+// selector, so no row is ever copied.  DE reads selectors of generation parity
+// p and writes those of parity p^1; GWO works in place on parity p^1 (it only
+// moves omega wolves and only reads the leaders).
+//
+// Per generation: k_de (all NP trials + greedy selection + leader choice by the
+// last CTA) and k_gwo (omega wolves + greedy selection + generation counter by
+// the last CTA); or one cooperative persistent kernel that runs both phases for
+// many generations with bounded grid barriers in between.
+#include <math.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "qpm_common.cuh"
+#include "qpm_internal.h"
+
+namespace qpm {
+
+struct InstDev {
+  int32_t N, Npad, NP, T, c, G;
+  int32_t combine, compensated;
+  float F, CR;
+  uint32_t inst;
+  uint2 key;
+  double kappa1, kappa2;
+  float *pop;            // [NP][2][Npad], permuted rows
+  int32_t *sel0, *sel1;  // slot selectors, parity 0 / 1
+  float *fit;            // [NP]
+  float2 *dval;          // [NP]
+  float4 *table;         // [Npad], permuted
+  double2 *tpart;        // table reduction scratch
+  float2 *konst;         // phi1 phi2, cdiag
+  double2 *konst64;      // phi1 phi2, cdiag, psi (FP64)
+  int32_t *lead;         // [3]
+  unsigned long long *topk;  // [NP * 3] partial leader keys
+  unsigned *ctr;         // [4] CTA-completion counters
+  int32_t *gen;          // [1] completed generations
+  int32_t *best;         // [1] best index (get_best)
+  float *trace;          // optional fitness trace
+};
+
+template <bool NC>
+__device__ __forceinline__ float4 ld4(const float *p) {
+  if (NC) return __ldg((const float4 *)p);
+  return *(const float4 *)p;
+}
+__device__ __forceinline__ float4 ldt(const float4 *p) { return __ldg(p); }
+
+template <bool COMP>
+struct Acc {
+  Mono m;
+  MonoK k;
+  __device__ __forceinline__ void zero() {
+    if (COMP) k = monok_zero(); else m = mono_zero();
+  }
+  __device__ __forceinline__ void push(float d, const float4 &p) {
+    if (COMP) monok_push(k, d, p); else mono_push(m, d, p);
+  }
+  __device__ __forceinline__ Mono get() const { return COMP ? monok_fold(k) : m; }
+};
+
+__device__ __forceinline__ float sgn(float x) { return x < 0.f ? -1.f : 1.f; }
+
+// push the 4 domains of group k4 of this thread's chunk
+template <bool COMP>
+__device__ __forceinline__ void push4(Acc<COMP> &acc, const InstDev &I, int k4, int t, float4 u) {
+  const float4 *tb = I.table + (size_t)k4 * 4 * I.T + t;
+  acc.push(sgn(u.x), ldt(tb));
+  acc.push(sgn(u.y), ldt(tb + I.T));
+  acc.push(sgn(u.z), ldt(tb + 2 * I.T));
+  acc.push(sgn(u.w), ldt(tb + 3 * I.T));
+}
+
+__device__ __forceinline__ float *row_ptr(const InstDev &I, int i, int slot) {
+  return I.pop + ((size_t)2 * i + slot) * I.Npad;
+}
+
+// ---------------------------------------------------- Step 1: initialisation
+template <bool COMP>
+__device__ void init_individual(const InstDev &I, int i, Mono *sh) {
+  const int t = threadIdx.x;
+  float *row = row_ptr(I, i, 0);
+  Acc<COMP> acc;
+  acc.zero();
+  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+    const int j0 = t * I.c + 4 * k4;
+    const uint4 w = rng4(I.key, I.inst, TAG_INIT, 0u, (uint32_t)i, (uint32_t)(j0 >> 2));
+    float4 x;
+    x.x = __fsub_rn(__fmul_rn(2.0f, u24(w.x)), 1.0f);
+    x.y = __fsub_rn(__fmul_rn(2.0f, u24(w.y)), 1.0f);
+    x.z = __fsub_rn(__fmul_rn(2.0f, u24(w.z)), 1.0f);
+    x.w = __fsub_rn(__fmul_rn(2.0f, u24(w.w)), 1.0f);
+    *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
+    push4(acc, I, k4, t, x);
+  }
+  const Mono m = block_reduce(acc.get(), sh);
+  if (t == 0) {
+    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
+    const float f = fit_of(D);
+    I.fit[i] = f;
+    I.dval[i] = D;
+    I.sel0[i] = 0;
+    I.sel1[i] = 0;
+    if (I.trace) I.trace[i] = f;
+  }
+}
+
+template <bool COMP>
+static __global__ void k_init(InstDev I) {
+  extern __shared__ Mono sh[];
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) init_individual<COMP>(I, i, sh);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *I.gen = 0;
+    for (int k = 0; k < 4; ++k) I.ctr[k] = 0u;
+  }
+}
+
+// ------------------------------------------ Step 2: DE rand/1/bin + selection
+// returns (in thread 0) the key of the survivor for the leader choice
+template <bool COMP, bool NC>
+__device__ unsigned long long de_individual(const InstDev &I, int g, int i, const int32_t *sel_in,
+                                            int32_t *sel_out, Mono *sh) {
+  const int t = threadIdx.x;
+  const int4 r = de_indices(I.key, I.inst, (uint32_t)g, i, I.NP, I.N);
+  const int si = sel_in[i];
+  const float *xi = row_ptr(I, i, si);
+  const float *x1 = row_ptr(I, r.x, sel_in[r.x]);
+  const float *x2 = row_ptr(I, r.y, sel_in[r.y]);
+  const float *x3 = row_ptr(I, r.z, sel_in[r.z]);
+  float *out = row_ptr(I, i, si ^ 1);
+  const float F = I.F, CR = I.CR;
+  Acc<COMP> acc;
+  acc.zero();
+  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const float4 a = ld4<NC>(xi + off), b = ld4<NC>(x1 + off);
+    const float4 p = ld4<NC>(x2 + off), q = ld4<NC>(x3 + off);
+    const int j0 = t * I.c + 4 * k4;
+    const uint4 w = rng4(I.key, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
+    float4 u;
+    // v = x_r1 + F (x_r2 - x_r3), clamped; u = v if U <= CR or j == jrand, else x
+#define QPM_DE1(C, W, J)                                                              \
+    {                                                                                 \
+      const float v = clamp1(__fadd_rn(b.C, __fmul_rn(F, __fsub_rn(p.C, q.C))));      \
+      u.C = (u24(w.W) <= CR || (J) == r.w) ? v : a.C;                                 \
+    }
+    QPM_DE1(x, x, j0)
+    QPM_DE1(y, y, j0 + 1)
+    QPM_DE1(z, z, j0 + 2)
+    QPM_DE1(w, w, j0 + 3)
+#undef QPM_DE1
+    *(float4 *)(out + off) = u;
+    push4(acc, I, k4, t, u);
+  }
+  const Mono m = block_reduce(acc.get(), sh);
+  unsigned long long key = 0ull;
+  if (t == 0) {
+    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
+    const float f = fit_of(D);
+    const float fx = I.fit[i];
+    const bool accept = f >= fx;  // greedy one-to-one selection, maximising
+    sel_out[i] = accept ? (si ^ 1) : si;
+    if (accept) {
+      I.fit[i] = f;
+      I.dval[i] = D;
+    }
+    if (I.trace) I.trace[(size_t)I.NP * (1 + 2 * (size_t)g) + i] = f;
+    key = lead_key(accept ? f : fx, i);
+  }
+  return key;
+}
+
+// ------------------------------------------------ Step 4-5: GWO + selection
+template <bool COMP, bool NC>
+__device__ void gwo_individual(const InstDev &I, int g, int i, int32_t *sel, const float *XA,
+                               const float *XB, const float *XD, Mono *sh) {
+  const int t = threadIdx.x;
+  const int si = sel[i];
+  const float *xi = row_ptr(I, i, si);
+  float *out = row_ptr(I, i, si ^ 1);
+  const float a = __fdiv_rn((float)(2 * (I.G - g)), (float)I.G);
+  const float two_a = __fmul_rn(2.0f, a);
+  Acc<COMP> acc;
+  acc.zero();
+  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const float4 x = ld4<NC>(xi + off);
+    const float4 L0 = ld4<NC>(XA + off), L1 = ld4<NC>(XB + off), L2 = ld4<NC>(XD + off);
+    const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
+    uint4 w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = rng4(I.key, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
+    float4 y;
+#define QPM_PULL(Xp, xv, r1w, r2w, out_)                                               \
+    {                                                                                  \
+      const float A = __fsub_rn(__fmul_rn(two_a, u24(r1w)), a);                         \
+      const float C = __fmul_rn(2.0f, u24(r2w));                                        \
+      const float dist = fabsf(__fsub_rn(__fmul_rn(C, Xp), xv));                        \
+      out_ = __fsub_rn(Xp, __fmul_rn(A, dist));                                         \
+    }
+#define QPM_GWO1(CMP)                                                                  \
+    {                                                                                  \
+      float Y0, Y1, Y2;                                                                \
+      QPM_PULL(L0.CMP, x.CMP, w[0].CMP, w[1].CMP, Y0)                                  \
+      QPM_PULL(L1.CMP, x.CMP, w[2].CMP, w[3].CMP, Y1)                                  \
+      QPM_PULL(L2.CMP, x.CMP, w[4].CMP, w[5].CMP, Y2)                                  \
+      float v;                                                                         \
+      if (I.combine == 0) {                                                            \
+        v = __fdiv_rn(__fadd_rn(__fadd_rn(Y0, Y1), Y2), 3.0f);                          \
+      } else {                                                                         \
+        const float m0 = fabsf(Y0), m1 = fabsf(Y1), m2 = fabsf(Y2);                    \
+        const float s = __fadd_rn(__fadd_rn(m0, m1), m2);                              \
+        const float num = __fadd_rn(__fadd_rn(__fmul_rn(m0, Y0), __fmul_rn(m1, Y1)),   \
+                                    __fmul_rn(m2, Y2));                                \
+        v = (s == 0.0f) ? 0.0f : __fdiv_rn(num, __fmul_rn(3.0f, s));                   \
+      }                                                                                \
+      y.CMP = clamp1(v);                                                               \
+    }
+    QPM_GWO1(x)
+    QPM_GWO1(y)
+    QPM_GWO1(z)
+    QPM_GWO1(w)
+#undef QPM_GWO1
+#undef QPM_PULL
+    *(float4 *)(out + off) = y;
+    push4(acc, I, k4, t, y);
+  }
+  const Mono m = block_reduce(acc.get(), sh);
+  if (t == 0) {
+    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
+    const float f = fit_of(D);
+    const bool accept = f >= I.fit[i];
+    if (accept) {
+      sel[i] = si ^ 1;
+      I.fit[i] = f;
+      I.dval[i] = D;
+    }
+    if (I.trace) I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + i] = f;
+  }
+}
+
+// top-3 merge over the CTA: every thread passes its sorted triple, thread 0 gets the result
+__device__ void block_top3(unsigned long long &k0, unsigned long long &k1, unsigned long long &k2,
+                           unsigned long long *sh) {
+  for (int s = 16; s > 0; s >>= 1) {
+    const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
+    const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
+    const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
+    top3_insert(k0, k1, k2, p0);
+    top3_insert(k0, k1, k2, p1);
+    top3_insert(k0, k1, k2, p2);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[3 * warp] = k0;
+    sh[3 * warp + 1] = k1;
+    sh[3 * warp + 2] = k2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      top3_insert(k0, k1, k2, sh[3 * w]);
+      top3_insert(k0, k1, k2, sh[3 * w + 1]);
+      top3_insert(k0, k1, k2, sh[3 * w + 2]);
+    }
+  }
+  __syncthreads();
+}
+
+// merge all per-CTA partial triples in topk[0 .. 3*nparts) into lead[3] (thread 0 writes)
+__device__ void merge_leaders(const unsigned long long *topk, int nparts, int32_t *lead,
+                              unsigned long long *sh, int32_t *lead_sh) {
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  for (int e = threadIdx.x; e < 3 * nparts; e += blockDim.x) top3_insert(k0, k1, k2, topk[e]);
+  block_top3(k0, k1, k2, sh);
+  if (threadIdx.x == 0) {
+    const int l0 = key_index(k0), l1 = key_index(k1), l2 = key_index(k2);
+    if (lead) { lead[0] = l0; lead[1] = l1; lead[2] = l2; }
+    if (lead_sh) { lead_sh[0] = l0; lead_sh[1] = l1; lead_sh[2] = l2; }
+  }
+  __syncthreads();
+}
+
+// true in every thread of the last CTA to finish (classic fence + counter pattern)
+__device__ bool last_cta(unsigned *ctr) {
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(ctr, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+template <bool COMP>
+static __global__ void k_de(InstDev I) {
+  extern __shared__ Mono sh[];
+  __shared__ unsigned long long shk[3 * 32];
+  const int g = *I.gen;
+  const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
+  int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    const unsigned long long key = de_individual<COMP, true>(I, g, i, sel_in, sel_out, sh);
+    if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
+  }
+  if (threadIdx.x == 0) {
+    I.topk[3 * blockIdx.x] = k0;
+    I.topk[3 * blockIdx.x + 1] = k1;
+    I.topk[3 * blockIdx.x + 2] = k2;
+  }
+  if (last_cta(&I.ctr[0])) {
+    merge_leaders(I.topk, gridDim.x, I.lead, shk, nullptr);  // Step 3
+    if (threadIdx.x == 0) I.ctr[0] = 0u;
+  }
+}
+
+template <bool COMP>
+static __global__ void k_gwo(InstDev I) {
+  extern __shared__ Mono sh[];
+  const int g = *I.gen;
+  int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
+  const int la = I.lead[0], lb = I.lead[1], ld = I.lead[2];
+  const float *XA = row_ptr(I, la, sel[la]);
+  const float *XB = row_ptr(I, lb, sel[lb]);
+  const float *XD = row_ptr(I, ld, sel[ld]);
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    if (i == la || i == lb || i == ld) continue;  // the leaders do not move
+    gwo_individual<COMP, true>(I, g, i, sel, XA, XB, XD, sh);
+  }
+  if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
+    const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
+    I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
+  }
+  if (last_cta(&I.ctr[1])) {
+    if (threadIdx.x == 0) {
+      *I.gen = g + 1;  // Step 6/7: next generation (a is derived from g)
+      I.ctr[1] = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------ persistent kernel
+struct Barrier {
+  unsigned *count;   // arrivals
+  unsigned *flag;    // release epoch
+  int32_t *err;      // 0 ok, else a qpm_status
+  unsigned long long timeout_ns;
+};
+
+// grid-wide barrier with a bounded wait; false when any CTA has failed
+__device__ bool grid_sync(const Barrier &b, unsigned &epoch) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = epoch + 1;
+    __threadfence();
+    const unsigned prev = atomicAdd(b.count, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      st_release(b.flag, target);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire(b.flag) != target) {
+        if (*(volatile int32_t *)b.err != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > b.timeout_ns) {
+          atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (*(volatile int32_t *)b.err != 0) ok = 0;
+    __threadfence();
+    epoch = target;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+template <bool COMP>
+static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
+  extern __shared__ Mono sh[];
+  __shared__ unsigned long long shk[3 * 32];
+  __shared__ int32_t lead_sh[3];
+  unsigned epoch = 0;
+  int g = *I.gen;
+  if (!grid_sync(bar, epoch)) return;  // every CTA has read the start generation
+  for (; g < g_end; ++g) {
+    const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
+    int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
+    unsigned long long k0 = 0, k1 = 0, k2 = 0;
+    for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+      const unsigned long long key = de_individual<COMP, false>(I, g, i, sel_in, sel_out, sh);
+      if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
+    }
+    if (threadIdx.x == 0) {
+      I.topk[3 * blockIdx.x] = k0;
+      I.topk[3 * blockIdx.x + 1] = k1;
+      I.topk[3 * blockIdx.x + 2] = k2;
+    }
+    if (!grid_sync(bar, epoch)) return;
+    // every CTA merges the partial leader keys itself (no extra barrier)
+    merge_leaders(I.topk, gridDim.x, blockIdx.x == 0 ? I.lead : nullptr, shk, lead_sh);
+    const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
+    const float *XA = row_ptr(I, la, sel_out[la]);
+    const float *XB = row_ptr(I, lb, sel_out[lb]);
+    const float *XD = row_ptr(I, ld, sel_out[ld]);
+    for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+      if (i == la || i == lb || i == ld) continue;
+      gwo_individual<COMP, false>(I, g, i, sel_out, XA, XB, XD, sh);
+    }
+    if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
+      const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
+      I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
+    }
+    // the partial leader keys are rewritten in the next DE phase: all CTAs must
+    // have merged them before any CTA passes this barrier
+    if (!grid_sync(bar, epoch)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *I.gen = g_end;
+}
+
+// ------------------------------------------------ outputs: best, FP64, layout
+static __global__ void k_best(InstDev I, int32_t *index_out) {
+  __shared__ unsigned long long shk[3 * 32];
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) top3_insert(k0, k1, k2, lead_key(I.fit[i], i));
+  block_top3(k0, k1, k2, shk);
+  if (threadIdx.x == 0) {
+    *I.best = key_index(k0);
+    if (index_out) *index_out = key_index(k0);
+  }
+}
+
+__device__ __forceinline__ size_t perm_pos(const InstDev &I, int j) {
+  const int t = j / I.c, e = j - t * I.c;
+  return ((size_t)(e >> 2) * I.T + t) * 4 + (e & 3);
+}
+
+static __global__ void k_unpermute(InstDev I, int i_fixed, float *out, int64_t ld) {
+  const int i = i_fixed >= 0 ? i_fixed : (i_fixed == -2 ? *I.best : (int)blockIdx.x);
+  const int32_t *sel = (*I.gen & 1) ? I.sel1 : I.sel0;
+  const float *row = row_ptr(I, i, sel[i]);
+  float *o = out + (i_fixed == -1 ? (int64_t)i * ld : 0);
+  for (int j = threadIdx.x; j < I.N; j += blockDim.x) o[j] = row[perm_pos(I, j)];
+}
+
+static __global__ void k_copy_fit(InstDev I, float *fit_out, float2 *d_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= I.NP) return;
+  if (fit_out) fit_out[i] = I.fit[i];
+  if (d_out) d_out[i] = I.dval[i];
+}
+
+struct Mono64 {
+  double2 A, B, C;
+};
+__device__ __forceinline__ Mono64 m64_combine(const Mono64 &L, const Mono64 &R) {
+  Mono64 o;
+  o.A = make_double2(L.A.x + R.A.x, L.A.y + R.A.y);
+  o.B = make_double2(L.B.x + R.B.x, L.B.y + R.B.y);
+  o.C = make_double2(L.C.x + R.C.x + (R.A.x * L.B.x - R.A.y * L.B.y),
+                     L.C.y + R.C.y + (R.A.x * L.B.y + R.A.y * L.B.x));
+  return o;
+}
+
+// A11: FP64 re-evaluation of the best individual's d_eff (closed form, FP64 phasors)
+static __global__ void k_recheck64(InstDev I, double *d64_out, float *fit_out) {
+  __shared__ Mono64 sh[256];
+  const int i = *I.best;
+  const int32_t *sel = (*I.gen & 1) ? I.sel1 : I.sel0;
+  const float *row = row_ptr(I, i, sel[i]);
+  const int nt = blockDim.x, t = threadIdx.x;
+  const int per = (I.N + nt - 1) / nt;
+  const int j0 = min(I.N, t * per), j1 = min(I.N, j0 + per);
+  Mono64 m;
+  m.A = m.B = m.C = make_double2(0.0, 0.0);
+  for (int j = j0; j < j1; ++j) {
+    const double d = row[perm_pos(I, j)] < 0.f ? -1.0 : 1.0;
+    double s1, c1, s2, c2;
+    sincos(reduce_2pi((double)j * I.kappa1), &s1, &c1);
+    sincos(reduce_2pi((double)j * I.kappa2), &s2, &c2);
+    const double ar = d * c2, ai = -d * s2;  // a = d p2
+    m.C.x += ar * m.B.x - ai * m.B.y;
+    m.C.y += ar * m.B.y + ai * m.B.x;
+    m.A.x += ar;
+    m.A.y += ai;
+    m.B.x += d * c1;  // b = d p1
+    m.B.y -= d * s1;
+  }
+  sh[t] = m;
+  __syncthreads();
+  if (t == 0) {
+    Mono64 acc = sh[0];
+    for (int k = 1; k < nt; ++k) acc = m64_combine(acc, sh[k]);
+    const double2 p12 = I.konst64[0], cd = I.konst64[1];
+    const double re = p12.x * acc.C.x - p12.y * acc.C.y + cd.x;
+    const double im = p12.x * acc.C.y + p12.y * acc.C.x + cd.y;
+    if (d64_out) {
+      d64_out[0] = re;
+      d64_out[1] = im;
+    }
+    if (fit_out) fit_out[0] = I.fit[i];
+  }
+}
+
+}  // namespace qpm
+
+// =========================================================== host: the state
+using qpm::InstDev;
+
+struct qpm_state {
+  int dev = 0;
+  int n = 0;
+  std::vector<InstDev> h;
+  std::vector<qpm_problem> probs;
+  std::vector<qpm_params> params;
+  std::vector<int> grid_plain, grid_persist;
+  void *arena = nullptr;
+  int g = 0;
+  int G_min = 0;
+  bool inited = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_n = -1;
+  unsigned *bar = nullptr;  // [0] count, [1] flag, [2] err
+  unsigned long long timeout_ns = 5000000000ull;
+};
+
+namespace qpm {
+
+static int choose_team(int N) {
+  int T = 32;
+  while (T < 256 && N > T * 8) T *= 2;
+  return T;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static size_t smem_bytes(int T) { return sizeof(Mono) * (size_t)(T / 32 + 1); }
+
+template <bool COMP>
+static qpm_status occupancy(int T, int *plain, int *persist) {
+  int a = 0, b = 0;
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_de<COMP>, T, smem_bytes(T)));
+  int a2 = 0;
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_gwo<COMP>, T, smem_bytes(T)));
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_persist<COMP>, T, smem_bytes(T)));
+  *plain = std::max(1, std::min(a, a2));
+  *persist = std::max(1, b);
+  return QPM_OK;
+}
+
+static qpm_status enqueue_step(qpm_state *st, cudaStream_t s) {
+  for (int k = 0; k < st->n; ++k) {
+    const InstDev &I = st->h[k];
+    const int grid = st->grid_plain[k];
+    const size_t sm = smem_bytes(I.T);
+    if (I.compensated) {
+      k_de<true><<<grid, I.T, sm, s>>>(I);
+      k_gwo<true><<<grid, I.T, sm, s>>>(I);
+    } else {
+      k_de<false><<<grid, I.T, sm, s>>>(I);
+      k_gwo<false><<<grid, I.T, sm, s>>>(I);
+    }
+  }
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+static qpm_status check_state(qpm_state *st, int gens) {
+  if (!st) return fail(QPM_ERR_ARG, "NULL state");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  if (gens < 0) return fail(QPM_ERR_ARG, "negative generation count");
+  if (st->g + gens > st->G_min)
+    return fail(QPM_ERR_ARG, "running past the last generation G of an instance");
+  int dev = -1;
+  QPM_CUDA(cudaGetDevice(&dev));
+  if (dev != st->dev) return fail(QPM_ERR_STATE, "state belongs to another device");
+  return QPM_OK;
+}
+
+}  // namespace qpm
+
+using namespace qpm;
+
+extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *params,
+                                 int32_t n_inst, qpm_state **out) {
+  if (!probs || !params || !out) return fail(QPM_ERR_ARG, "qpm_create: NULL pointer");
+  if (n_inst < 1) return fail(QPM_ERR_ARG, "qpm_create: n_inst < 1");
+  *out = nullptr;
+  for (int k = 0; k < n_inst; ++k) {
+    const qpm_problem &p = probs[k];
+    const qpm_params &q = params[k];
+    if (p.N < 1) return fail(QPM_ERR_ARG, "qpm_create: N < 1");
+    if (p.N > (1 << 26)) return fail(QPM_ERR_UNSUPPORTED, "qpm_create: N too large");
+    if (q.NP < 4) return fail(QPM_ERR_ARG, "qpm_create: NP < 4 (rand/1 needs three donors)");
+    if (q.G < 1) return fail(QPM_ERR_ARG, "qpm_create: G < 1");
+    if (!(q.F >= 0.f && q.F <= 2.f)) return fail(QPM_ERR_ARG, "qpm_create: F outside [0, 2]");
+    if (!(q.CR >= 0.f && q.CR <= 1.f)) return fail(QPM_ERR_ARG, "qpm_create: CR outside [0, 1]");
+    if (q.gwo_combine != 0 && q.gwo_combine != 1)
+      return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0 or 1");
+    if (!std::isfinite(p.kappa1) || !std::isfinite(p.kappa2))
+      return fail(QPM_ERR_ARG, "qpm_create: kappa must be finite");
+  }
+  qpm_state *st = new qpm_state();
+  cudaError_t e = cudaGetDevice(&st->dev);
+  if (e != cudaSuccess) { delete st; return cuda_fail(e, "cudaGetDevice"); }
+  st->n = n_inst;
+  st->probs.assign(probs, probs + n_inst);
+  st->params.assign(params, params + n_inst);
+  st->h.resize(n_inst);
+  st->grid_plain.resize(n_inst);
+  st->grid_persist.resize(n_inst);
+  st->G_min = params[0].G;
+  const int nsm = sm_count();
+  size_t total = 0;
+  std::vector<size_t> base(n_inst);
+  for (int k = 0; k < n_inst; ++k) {
+    const qpm_problem &p = probs[k];
+    const qpm_params &q = params[k];
+    InstDev &I = st->h[k];
+    memset(&I, 0, sizeof(I));
+    I.N = p.N;
+    I.T = choose_team(p.N);
+    I.Npad = (int32_t)align_up((size_t)p.N, 4 * (size_t)I.T);
+    I.c = I.Npad / I.T;
+    I.NP = q.NP;
+    I.G = q.G;
+    I.combine = q.gwo_combine;
+    I.compensated = q.compensated ? 1 : 0;
+    I.F = q.F;
+    I.CR = q.CR;
+    I.inst = (uint32_t)k;
+    I.key = make_uint2((uint32_t)q.seed, (uint32_t)(q.seed >> 32));
+    I.kappa1 = p.kappa1;
+    I.kappa2 = p.kappa2;
+    st->G_min = std::min(st->G_min, q.G);
+    int occ_plain = 1, occ_persist = 1;
+    qpm_status s2 = I.compensated ? occupancy<true>(I.T, &occ_plain, &occ_persist)
+                                  : occupancy<false>(I.T, &occ_plain, &occ_persist);
+    if (s2 != QPM_OK) { delete st; return s2; }
+    st->grid_plain[k] = std::min(I.NP, occ_plain * nsm);
+    st->grid_persist[k] = std::min(I.NP, occ_persist * nsm);
+    base[k] = total;
+    const size_t NP = (size_t)I.NP, Np = (size_t)I.Npad;
+    total += align_up(2 * NP * Np * sizeof(float), 256);
+    total += 2 * align_up(NP * sizeof(int32_t), 256);
+    total += align_up(NP * sizeof(float), 256) + align_up(NP * sizeof(float2), 256);
+    total += align_up(Np * sizeof(float4), 256);
+    total += align_up((size_t)table_part_count(I.Npad) * sizeof(double2), 256);
+    total += 256 + 256 + 256;  // konst, konst64, lead
+    total += align_up(3 * NP * sizeof(unsigned long long), 256);
+    total += 256 + 256 + 256;  // ctr, gen, best
+  }
+  total += 256;  // barrier words
+  e = cudaMalloc(&st->arena, total);
+  if (e != cudaSuccess) { delete st; return cuda_fail(e, "cudaMalloc(state arena)"); }
+  e = cudaMemset(st->arena, 0, total);
+  if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaMemset"); }
+  for (int k = 0; k < n_inst; ++k) {
+    InstDev &I = st->h[k];
+    char *p = (char *)st->arena + base[k];
+    auto take = [&](size_t bytes) { char *r = p; p += align_up(bytes, 256); return (void *)r; };
+    const size_t NP = (size_t)I.NP, Np = (size_t)I.Npad;
+    I.pop = (float *)take(2 * NP * Np * sizeof(float));
+    I.sel0 = (int32_t *)take(NP * sizeof(int32_t));
+    I.sel1 = (int32_t *)take(NP * sizeof(int32_t));
+    I.fit = (float *)take(NP * sizeof(float));
+    I.dval = (float2 *)take(NP * sizeof(float2));
+    I.table = (float4 *)take(Np * sizeof(float4));
+    I.tpart = (double2 *)take((size_t)table_part_count(I.Npad) * sizeof(double2));
+    I.konst = (float2 *)take(2 * sizeof(float2));
+    I.konst64 = (double2 *)take(3 * sizeof(double2));
+    I.lead = (int32_t *)take(3 * sizeof(int32_t));
+    I.topk = (unsigned long long *)take(3 * NP * sizeof(unsigned long long));
+    I.ctr = (unsigned *)take(4 * sizeof(unsigned));
+    I.gen = (int32_t *)take(sizeof(int32_t));
+    I.best = (int32_t *)take(sizeof(int32_t));
+  }
+  st->bar = (unsigned *)((char *)st->arena + total - 256);
+  e = cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaStreamCreate"); }
+  *out = st;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_set_trace(qpm_state *st, int32_t inst, float *trace) {
+  if (!st || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "qpm_set_trace: bad instance");
+  st->h[inst].trace = trace;
+  if (st->gexec) {
+    cudaGraphExecDestroy(st->gexec);
+    st->gexec = nullptr;
+    st->graph_n = -1;
+  }
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_init(qpm_state *st, qpm_stream_t stream) {
+  if (!st) return fail(QPM_ERR_ARG, "NULL state");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int k = 0; k < st->n; ++k) {
+    const InstDev &I = st->h[k];
+    TableSpec ts{I.N, I.Npad, I.T, I.c, I.kappa1, I.kappa2};
+    qpm_status r = launch_table(ts, I.table, I.tpart, I.konst, I.konst64, s);
+    if (r != QPM_OK) return r;
+    const size_t sm = smem_bytes(I.T);
+    if (I.compensated) k_init<true><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    else k_init<false><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    QPM_CUDA(cudaGetLastError());
+  }
+  st->g = 0;
+  st->inited = true;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_step(qpm_state *st, qpm_stream_t stream) {
+  qpm_status r = check_state(st, 1);
+  if (r != QPM_OK) return r;
+  r = enqueue_step(st, (cudaStream_t)stream);
+  if (r == QPM_OK) st->g += 1;
+  return r;
+}
+
+extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
+                              qpm_stream_t stream) {
+  qpm_status r = check_state(st, generations);
+  if (r != QPM_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (generations == 0) return QPM_OK;
+  if (mode == QPM_RUN_LAUNCHES) {
+    for (int g = 0; g < generations; ++g) {
+      r = enqueue_step(st, s);
+      if (r != QPM_OK) return r;
+    }
+  } else if (mode == QPM_RUN_GRAPH) {
+    if (st->graph_n != generations || !st->gexec) {
+      if (st->gexec) {
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+      }
+      QPM_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeThreadLocal));
+      for (int g = 0; g < generations; ++g) {
+        r = enqueue_step(st, st->cap_stream);
+        if (r != QPM_OK) {
+          cudaGraph_t junk;
+          cudaStreamEndCapture(st->cap_stream, &junk);
+          if (junk) cudaGraphDestroy(junk);
+          return r;
+        }
+      }
+      cudaGraph_t graph;
+      QPM_CUDA(cudaStreamEndCapture(st->cap_stream, &graph));
+      cudaError_t e = cudaGraphInstantiate(&st->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      st->graph_n = generations;
+    }
+    QPM_CUDA(cudaGraphLaunch(st->gexec, s));
+  } else if (mode == QPM_RUN_PERSISTENT) {
+    QPM_CUDA(cudaMemsetAsync(st->bar, 0, 3 * sizeof(unsigned), s));
+    Barrier b{st->bar, st->bar + 1, (int32_t *)(st->bar + 2), st->timeout_ns};
+    for (int k = 0; k < st->n; ++k) {
+      InstDev I = st->h[k];
+      int g_end = st->g + generations;
+      void *args[] = {&I, &g_end, &b};
+      const void *fn = I.compensated ? (const void *)k_persist<true> : (const void *)k_persist<false>;
+      QPM_CUDA(cudaLaunchCooperativeKernel(fn, st->grid_persist[k], I.T, args, smem_bytes(I.T), s));
+    }
+    int32_t err = 0;
+    QPM_CUDA(cudaMemcpyAsync(&err, st->bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    QPM_CUDA(cudaStreamSynchronize(s));
+    if (err != 0) {
+      st->g += generations;
+      return fail(QPM_ERR_TIMEOUT, "persistent kernel: a bounded grid-barrier wait gave up");
+    }
+  } else {
+    return fail(QPM_ERR_ARG, "qpm_run: unknown mode");
+  }
+  st->g += generations;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_generation(const qpm_state *st, int32_t *g_out) {
+  if (!st || !g_out) return fail(QPM_ERR_ARG, "NULL pointer");
+  *g_out = st->g;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_get_population(qpm_state *st, int32_t inst, float *genes_out, int64_t ld,
+                                         float *fit_out, float *d_eff_out, qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad state or instance");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  const InstDev &I = st->h[inst];
+  if (genes_out && ld < I.N) return fail(QPM_ERR_ARG, "ld < N");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (genes_out) k_unpermute<<<I.NP, 256, 0, s>>>(I, -1, genes_out, ld);
+  if (fit_out || d_eff_out)
+    k_copy_fit<<<(I.NP + 255) / 256, 256, 0, s>>>(I, fit_out, (float2 *)d_eff_out);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_get_best(qpm_state *st, int32_t inst, float *genes_out,
+                                   double *d_eff64_out, float *fit_out, int32_t *index_out,
+                                   qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad state or instance");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  const InstDev &I = st->h[inst];
+  cudaStream_t s = (cudaStream_t)stream;
+  k_best<<<1, 256, 0, s>>>(I, index_out);
+  if (d_eff64_out || fit_out) k_recheck64<<<1, 256, 0, s>>>(I, d_eff64_out, fit_out);
+  if (genes_out) k_unpermute<<<1, 256, 0, s>>>(I, -2, genes_out, 0);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_destroy(qpm_state *st) {
+  if (!st) return QPM_OK;
+  cudaDeviceSynchronize();
+  if (st->gexec) cudaGraphExecDestroy(st->gexec);
+  if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
+  cudaFree(st->arena);
+  delete st;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_set_wait_timeout_ns(qpm_state *st, uint64_t ns) {
+  if (!st) return fail(QPM_ERR_ARG, "NULL state");
+  st->timeout_ns = ns;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_solve(const qpm_problem *prob, const qpm_params *params, int32_t mode,
+                                float *best_genes_host, double *best_deff64_host,
+                                float *best_fit_host) {
+  if (!prob || !params) return fail(QPM_ERR_ARG, "qpm_solve: NULL pointer");
+  qpm_state *st = nullptr;
+  qpm_status r = qpm_create(prob, params, 1, &st);
+  if (r != QPM_OK) return r;
+  cudaStream_t s = st->cap_stream;
+  float *dgenes = nullptr;
+  double *dd = nullptr;
+  float *df = nullptr;
+  cudaError_t e = cudaMalloc(&dgenes, sizeof(float) * (size_t)prob->N + 64);
+  if (e == cudaSuccess) e = cudaMalloc(&dd, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&df, sizeof(float));
+  if (e != cudaSuccess) r = cuda_fail(e, "cudaMalloc");
+  if (r == QPM_OK && mode == QPM_RUN_GRAPH) mode = QPM_RUN_LAUNCHES;  // one pass: nothing to reuse
+  if (r == QPM_OK) r = qpm_init(st, (qpm_stream_t)s);
+  if (r == QPM_OK) r = qpm_run(st, params->G, mode, (qpm_stream_t)s);
+  if (r == QPM_OK) r = qpm_get_best(st, 0, dgenes, dd, df, nullptr, (qpm_stream_t)s);
+  if (r == QPM_OK && best_genes_host) {
+    e = cudaMemcpyAsync(best_genes_host, dgenes, sizeof(float) * (size_t)prob->N,
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaMemcpyAsync");
+  }
+  if (r == QPM_OK && best_deff64_host) {
+    e = cudaMemcpyAsync(best_deff64_host, dd, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaMemcpyAsync");
+  }
+  if (r == QPM_OK && best_fit_host) {
+    e = cudaMemcpyAsync(best_fit_host, df, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaMemcpyAsync");
+  }
+  if (r == QPM_OK) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  cudaFree(dgenes);
+  cudaFree(dd);
+  cudaFree(df);
+  qpm_destroy(st);
+  return r;
+}

@@ -1,0 +1,39 @@
+// qpm_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "qpm.h"
+
+namespace qpm {
+
+void set_error(const std::string &msg);
+qpm_status fail(qpm_status s, const std::string &msg);
+qpm_status cuda_fail(cudaError_t e, const char *what);
+
+#define QPM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::qpm::cuda_fail(e_, #call); \
+  } while (0)
+
+// Phasor table layout: dimension m of a row split over T threads of c dims each
+// (c a multiple of 4) lives at float4 index ((k4 * 4 + q) * T + t) with t = m / c,
+// k4 = (m % c) / 4, q = m % 4.  T = 1, c = Npad is the natural order.
+struct TableSpec {
+  int32_t N, Npad, T, c;
+  double kappa1, kappa2;
+};
+
+// float2 konst[2] = {phi1*phi2, cdiag}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
+// part: scratch of table_part_count(Npad) double2
+int table_part_count(int32_t Npad);
+qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
+                        double2 *konst64, cudaStream_t stream);
+
+// current device's SM count (cached per device)
+int sm_count();
+
+}  // namespace qpm

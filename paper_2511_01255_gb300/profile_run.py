@@ -1,0 +1,65 @@
+"""Run one workload of the library for a profiler (ncu) or a quick timing.
+
+  python -m paper_2511_01255_gb300.profile_run --workload paper --form launches --gens 40
+
+workloads: small (N=16, NP=32), paper (N=1000, NP=256, compensated),
+precision (N=1e5, NP=1024, compensated), eval (qpm_eval of 1024 random rows
+of N=1e5).  forms: launches, graph, persistent.  Prints the mean time per
+repetition measured with CUDA events.
+"""
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    import torch
+
+    import paper_2511_01255_gb300 as q
+    from paper_2511_01255_gb300 import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="paper", choices=["small", "paper", "precision", "eval"])
+    ap.add_argument("--form", default="launches", choices=["launches", "graph", "persistent"])
+    ap.add_argument("--gens", type=int, default=20)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--comp", type=int, default=-1, help="override the compensated flag")
+    a = ap.parse_args()
+    q.lib()
+    if a.workload == "eval":
+        N, NP = 100000, 1024
+        X = torch.rand((NP, N), device="cuda") * 2 - 1
+        D = torch.empty((NP, 2), device="cuda")
+        comp = 0 if a.comp < 0 else a.comp
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q.qpm_eval(N, 1.0, 2.0, X, D, None, comp)
+        e0.record()
+        for _ in range(a.reps):
+            q.qpm_eval(N, 1.0, 2.0, X, D, None, comp)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"eval N={N} NP={NP}: {e0.elapsed_time(e1) / a.reps:.3f} ms per call")
+        return
+    c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
+    comp = c["compensated"] if a.comp < 0 else a.comp
+    prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp)
+    form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT}[a.form]
+    st = q.State([(c["N"], c["kappa1"], c["kappa2"])], [prm])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(a.reps):
+        st.init()
+        e0.record()
+        st.run(a.gens, form)
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    st.close()
+    print(f"{c['name']} form={a.form} comp={comp}: {a.gens} generations in "
+          f"{tot / a.reps:.3f} ms ({tot / a.reps / a.gens * 1e3:.2f} us/generation)")
+
+
+if __name__ == "__main__":
+    main()

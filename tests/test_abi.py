@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/qpm.h; argument errors are reported as status codes before any device
+work (CPU only: no computing call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(qpm_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def qlib():
+    import paper_2511_01255_gb300 as q
+    return q.lib()
+
+
+def test_every_declared_symbol_is_exported(qlib):
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(qlib, n), n
+
+
+def test_status_strings_and_version(qlib):
+    assert qlib.qpm_status_string(0) == b"QPM_OK"
+    assert qlib.qpm_status_string(3) == b"QPM_ERR_TIMEOUT"
+    assert qlib.qpm_abi_version() >= 1
+
+
+def test_argument_errors_without_device(qlib):
+    import paper_2511_01255_gb300 as q
+    # NULL problem
+    assert qlib.qpm_eval(None, None, 0, 1, None, None, 0, None) == 1
+    p = q.Problem(0, 1.0, 1.0)
+    assert qlib.qpm_eval(ctypes.byref(p), ctypes.c_void_p(16), 1, 1, ctypes.c_void_p(16), None, 0, None) == 1
+    assert b"N >= 1" in qlib.qpm_last_error()
+    st = ctypes.c_void_p()
+    p = q.Problem(16, 1.0, 2.0)
+    bad = [q.Params(3, 10, 0.5, 0.9, 1, 0, 0), q.Params(8, 0, 0.5, 0.9, 1, 0, 0),
+           q.Params(8, 10, 2.5, 0.9, 1, 0, 0), q.Params(8, 10, 0.5, 1.5, 1, 0, 0),
+           q.Params(8, 10, 0.5, 0.9, 1, 2, 0)]
+    for prm in bad:
+        assert qlib.qpm_create(ctypes.byref(p), ctypes.byref(prm), 1, ctypes.byref(st)) == 1
+        assert not st.value
+    assert qlib.qpm_create(ctypes.byref(p), ctypes.byref(bad[0]), 1, ctypes.byref(st)) == 1
+    assert b"NP < 4" in qlib.qpm_last_error()
+    assert qlib.qpm_step(None, None) == 1
+    assert qlib.qpm_destroy(None) == 0
+
+
+def test_workload_generators_are_seeded():
+    from paper_2511_01255_gb300 import workloads as W
+    import numpy as np
+    a = W.random_genes(4, 33, seed=5)
+    b = W.random_genes(4, 33, seed=5)
+    assert np.array_equal(a, b) and a.dtype == np.float32
+    words = W.pack_signs(a, 33)
+    assert words.shape == (4, 2)
+    for i in range(4):
+        for j in range(33):
+            assert ((int(words[i, j // 32]) >> (j % 32)) & 1) == int(a[i, j] < 0)
+    inst = W.batched_instances(512)
+    assert len(inst) == 512 and min(x["N"] for x in inst) >= 500 and max(x["N"] for x in inst) <= 8000

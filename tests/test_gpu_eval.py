@@ -1,0 +1,99 @@
+"""GPU parity of qpm_eval / qpm_eval_packed (Sec. 2.1 d_eff) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import TOL_D, deff_err
+
+pytestmark = pytest.mark.gpu
+
+K1, K2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01255_gb300 as q
+    q.lib()
+    return q
+
+
+def run_eval(q, X, N, k1, k2, comp=0, packed=False):
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    NP = X.shape[0]
+    D = torch.empty((NP, 2), dtype=torch.float32, device="cuda")
+    f = torch.empty(NP, dtype=torch.float32, device="cuda")
+    if packed:
+        words = torch.from_numpy(W.pack_signs(X, N).view(np.int32)).cuda()
+        q.qpm_eval_packed(N, k1, k2, words, D, f, comp)
+    else:
+        q.qpm_eval(N, k1, k2, torch.from_numpy(X).cuda(), D, f, comp)
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), f.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [1, 3, 4, 31, 32, 33, 100, 1000, 4097])
+@pytest.mark.parametrize("NP", [1, 5, 33])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_eval_random_genes(q, orc, N, NP, comp):
+    from paper_2511_01255_gb300 import workloads as W
+    X = W.random_genes(NP, N, seed=N * 7 + NP)
+    D, f = run_eval(q, X, N, K1, K2, comp)
+    ref = orc.deff_genes(X, K1, K2)
+    assert deff_err(D, ref, N).max() < TOL_D
+    assert np.allclose(f, D[:, 0] ** 2 + D[:, 1] ** 2, rtol=1e-6, atol=0)
+    Dp, fp = run_eval(q, X, N, K1, K2, comp, packed=True)
+    assert np.array_equal(D, Dp)  # same scan order from genes and from packed bits
+
+
+def test_eval_strided_rows_and_random_kappa(q, orc):
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    rng = np.random.default_rng(3)
+    for N, ld in ((77, 81), (500, 503), (1024, 1030)):
+        X = W.random_genes(9, N, seed=N, ld=ld)
+        k1, k2 = rng.uniform(-4, 4, 2)
+        D = torch.empty((9, 2), dtype=torch.float32, device="cuda")
+        q.qpm_eval(N, k1, k2, torch.from_numpy(X).cuda(), D, None, 0)
+        torch.cuda.synchronize()
+        ref = orc.deff_genes(np.ascontiguousarray(X[:, :N]), k1, k2)
+        assert deff_err(D.cpu().numpy(), ref, N).max() < TOL_D
+
+
+@pytest.mark.parametrize("N", [1, 16, 1000, 4096])
+def test_closed_forms_on_gpu(q, N):
+    ones = np.ones((1, N), dtype=np.float32)
+    D, _ = run_eval(q, ones, N, 0.0, 0.0)
+    assert abs(complex(*D[0]) - N * N / 2) <= 1e-6 * N * N / 2
+    alt = np.where(np.arange(N) % 2 == 0, 1.0, -1.0).astype(np.float32)[None]
+    D, _ = run_eval(q, alt, N, math.pi, math.pi)
+    exact = -(2 / math.pi) ** 2 * N * N / 2
+    assert abs(complex(*D[0]) - exact) <= TOL_D * abs(exact)
+
+
+def test_sign_flip_exact_on_gpu(q):
+    from paper_2511_01255_gb300 import workloads as W
+    X = W.random_genes(8, 3001, seed=9)
+    X[X == 0] = 0.5
+    D1, _ = run_eval(q, X, 3001, K1, K2)
+    D2, _ = run_eval(q, -X, 3001, K1, K2)
+    assert np.array_equal(D1, D2)
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_eval_full_size_sampled(q, orc, comp):
+    """N = 1e5 domains, 1024 sequences: every row on the GPU, 6 rows re-done by the oracle."""
+    from paper_2511_01255_gb300 import workloads as W
+    N, NP = 100000, 1024
+    X = W.random_genes(NP, N, seed=11)
+    X[5] = 1.0  # one perfectly unpoled row and one alternating row among the samples
+    X[6] = W.alternating(N)
+    D, f = run_eval(q, X, N, K1, K2, comp)
+    rows = [0, 5, 6, 511, 777, 1023]
+    ref = orc.deff_genes(X[rows], K1, K2)
+    err = deff_err(D[rows], ref, N)
+    assert err.max() < TOL_D, err

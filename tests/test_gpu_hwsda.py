@@ -1,0 +1,213 @@
+"""GPU parity of the HWSDA generation step (Sec. 3.2) against the oracle.
+
+Bit-exact: the initial population, every DE trial / GWO candidate that survives,
+the leaders, and therefore whole trajectories, when the oracle takes its
+selection decisions from the GPU's FP32 fitness (lockstep).  Within tolerance:
+every FP32 fitness the GPU computed, against the oracle's FP64 quadrature.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import TOL_D, deff_err, fit_err, lockstep_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01255_gb300 as q
+    q.lib()
+    return q
+
+
+def make(q, N, k1, k2, NP, G, F=0.5, CR=0.9, seed=1, combine=0, comp=0, trace=True):
+    import torch
+    prm = q.Params(NP, G, F, CR, seed, combine, comp)
+    st = q.State([(N, k1, k2)], [prm])
+    tr = None
+    if trace:
+        tr = torch.full((NP * (1 + 2 * G),), float("nan"), dtype=torch.float32, device="cuda")
+        q.qpm_set_trace(st.h, 0, tr)
+    return st, tr
+
+
+def snapshot(st):
+    import torch
+    X, f, D = st.population()
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), f.cpu().numpy(), D.cpu().numpy()
+
+
+def test_init_population_bit_exact(q, orc):
+    N, NP = 333, 20
+    k1, k2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+    st, tr = make(q, N, k1, k2, NP, 5, seed=77)
+    st.init()
+    X, f, D = snapshot(st)
+    cfg = orc.make_cfg(NP, N, 5, 0.5, 0.9, 77)
+    assert np.array_equal(X, orc.init_population(cfg))
+    ref = orc.deff_genes(X, k1, k2)
+    assert deff_err(D, ref, N).max() < TOL_D
+    st.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_small_config_full_run_lockstep(q, orc, mode):
+    """N = 16, kappa1 = 2pi/7, kappa2 = 2pi/1.6, NP = 32, 200 generations."""
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.SMALL
+    st, tr = make(q, c["N"], c["kappa1"], c["kappa2"], c["NP"], c["G"], seed=c["seed"])
+    st.init()
+    st.run(c["G"], mode)
+    X, f, D = snapshot(st)
+    x_best, d64, fb, idx = st.best()
+    import torch
+    torch.cuda.synchronize()
+    trace = tr.cpu().numpy()
+    cfg = orc.make_cfg(c["NP"], c["N"], c["G"], c["F"], c["CR"], c["seed"])
+    Xo, fo, tro = orc.hwsda_run(cfg, c["kappa1"], c["kappa2"], lockstep=trace, want_trace=True)
+    assert np.array_equal(X, Xo)
+    assert lockstep_errors(trace, tro, c["N"]).max() < 2 * TOL_D
+    # best individual, its FP64 re-check, and the gap to the exhaustive optimum
+    i = int(idx.cpu().item())
+    assert i == int(orc.top3(f)[0])
+    assert np.array_equal(x_best.cpu().numpy(), X[i])
+    ref = orc.deff_genes(X[i:i + 1], c["kappa1"], c["kappa2"])[0]
+    d = d64.cpu().numpy()
+    assert abs(complex(d[0], d[1]) - ref) <= 1e-9 * abs(ref)
+    best, _ = orc.bruteforce(c["N"], c["kappa1"], c["kappa2"])
+    assert abs(ref) ** 2 <= best * (1 + 1e-9)
+    st.close()
+
+
+@pytest.mark.parametrize("combine", [0, 1])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_modes_agree_and_match_oracle_ragged(q, orc, combine, comp):
+    """N = 333 (ragged against every team width), NP = 24: the three execution modes
+    give bit-identical populations and the oracle's lockstep replay."""
+    import torch
+    N, NP, G = 333, 24, 12
+    k1, k2 = 2 * math.pi / 7.3, 2 * math.pi / 1.4
+    res = []
+    for mode in (0, 1, 2):
+        st, tr = make(q, N, k1, k2, NP, G, seed=5, combine=combine, comp=comp)
+        st.init()
+        st.run(4, mode)
+        st.run(G - 4, mode)
+        X, f, D = snapshot(st)
+        res.append((X, f, tr.cpu().numpy()))
+        st.close()
+    for X, f, trace in res[1:]:
+        assert np.array_equal(X, res[0][0]) and np.array_equal(f, res[0][1])
+        assert np.array_equal(np.isnan(trace), np.isnan(res[0][2]))
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 5, 0, combine)
+    Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=res[0][2], want_trace=True)
+    assert np.array_equal(res[0][0], Xo)
+    assert lockstep_errors(res[0][2], tro, N).max() < 2 * TOL_D
+
+
+def test_paper_scale_step_sampled(q, orc):
+    """N = 1000, NP = 256, compensated scan: after 600 persistent generations one more
+    generation is replayed by the oracle from the GPU's population (bit-exact result,
+    FP64 fitness of 48 sampled trials and candidates)."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.PAPER_SCALE
+    N, NP, G = c["N"], c["NP"], c["G"]
+    st, tr = make(q, N, c["kappa1"], c["kappa2"], NP, G, seed=c["seed"], comp=1)
+    st.init()
+    g0 = 600
+    st.run(g0, q.RUN_PERSISTENT)
+    X0, f0, _ = snapshot(st)
+    st.run(1, q.RUN_GRAPH)
+    X1, f1, _ = snapshot(st)
+    trace = tr.cpu().numpy()
+    lt = trace[NP * (1 + 2 * g0):NP * (2 + 2 * g0)]
+    lc = trace[NP * (2 + 2 * g0):NP * (3 + 2 * g0)]
+    cfg = orc.make_cfg(NP, N, G, c["F"], c["CR"], c["seed"])
+    mask = np.zeros(NP, dtype=np.uint8)
+    mask[np.random.default_rng(0).choice(NP, 48, replace=False)] = 1
+    Xn, fdec, _, t64, c64, lead = orc.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g0, X0, f0,
+                                                       lock_trial=lt, lock_cand=lc, eval_mask=mask)
+    assert np.array_equal(X1, Xn)
+    assert np.array_equal(f1, fdec)
+    sel = mask.astype(bool)
+    assert fit_err(lt[sel], t64[sel], N).max() < 2 * TOL_D
+    ok = sel & ~np.isnan(c64)
+    assert fit_err(lc[ok], c64[ok], N).max() < 2 * TOL_D
+    # the final population of the whole run is still a valid FP64-checked design
+    st.run(G - g0 - 1, q.RUN_PERSISTENT)
+    x, d64, fb, idx = st.best()
+    torch.cuda.synchronize()
+    xb = x.cpu().numpy()[None]
+    ref = orc.deff_genes(xb, c["kappa1"], c["kappa2"])[0]
+    d = d64.cpu().numpy()
+    assert abs(complex(d[0], d[1]) - ref) <= 1e-9 * abs(ref)
+    assert abs(float(fb.cpu()) - abs(ref) ** 2) <= 2 * TOL_D * abs(ref) ** 2
+    st.close()
+
+
+def test_precision_scale_step_sampled(q, orc):
+    """N = 1e5 domains, NP = 1024: two generations, then the third replayed by the
+    oracle from the GPU's population; FP64 fitness of 4 sampled rows."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.PRECISION
+    N, NP, G = c["N"], c["NP"], c["G"]
+    st, tr = make(q, N, c["kappa1"], c["kappa2"], NP, G, seed=c["seed"], comp=1)
+    st.init()
+    st.run(2, q.RUN_PERSISTENT)
+    X0, f0, _ = snapshot(st)
+    st.run(1, q.RUN_LAUNCHES)
+    X1, f1, _ = snapshot(st)
+    trace = tr.cpu().numpy()
+    g0 = 2
+    lt = trace[NP * (1 + 2 * g0):NP * (2 + 2 * g0)]
+    lc = trace[NP * (2 + 2 * g0):NP * (3 + 2 * g0)]
+    cfg = orc.make_cfg(NP, N, G, c["F"], c["CR"], c["seed"])
+    mask = np.zeros(NP, dtype=np.uint8)
+    mask[[3, 400, 1000]] = 1
+    Xn, fdec, _, t64, c64, lead = orc.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g0, X0, f0,
+                                                       lock_trial=lt, lock_cand=lc, eval_mask=mask)
+    assert np.array_equal(X1, Xn)
+    sel = mask.astype(bool)
+    assert fit_err(lt[sel], t64[sel], N).max() < 2 * TOL_D
+    st.close()
+    del X0, X1, Xn
+
+
+def test_persistent_wait_timeout_reports_status(q):
+    """A device-side wait that runs out ends the kernel with QPM_ERR_TIMEOUT (no trap);
+    the context stays usable."""
+    import torch
+    st, _ = make(q, 4000, 1.0, 2.0, 512, 10, trace=False)
+    st.init()
+    q.qpm_set_wait_timeout_ns(st.h, 0)
+    with pytest.raises(q.QpmError) as e:
+        st.run(3, q.RUN_PERSISTENT)
+    assert e.value.status == 3
+    st.close()
+    X = torch.ones((2, 64), device="cuda")
+    D = torch.empty((2, 2), device="cuda")
+    q.qpm_eval(64, 0.0, 0.0, X, D)
+    torch.cuda.synchronize()
+    assert abs(D[0, 0].item() - 64 * 64 / 2) < 1e-3
+
+
+def test_state_errors(q):
+    st, _ = make(q, 64, 1.0, 2.0, 8, 3, trace=False)
+    with pytest.raises(q.QpmError) as e:
+        st.step()
+    assert e.value.status == 5
+    st.init()
+    st.run(3)
+    with pytest.raises(q.QpmError) as e:
+        st.step()
+    assert e.value.status == 1
+    assert st.generation == 3
+    st.close()
