@@ -60,7 +60,12 @@ __device__ __forceinline__ float4 ld4(const float *p) {
   if (NC) return __ldg((const float4 *)p);
   return *(const float4 *)p;
 }
-__device__ __forceinline__ float4 ldt(const float4 *p) { return __ldg(p); }
+// phasor table entry: from shared memory (TS) or through the read-only path
+template <bool TS>
+__device__ __forceinline__ float4 ldt(const float4 *p) {
+  if (TS) return *p;
+  return __ldg(p);
+}
 
 template <bool COMP>
 struct Acc {
@@ -78,17 +83,30 @@ struct Acc {
 __device__ __forceinline__ float sgn(float x) { return x < 0.f ? -1.f : 1.f; }
 
 // push the 4 domains of group k4 of this thread's chunk
-template <bool COMP>
-__device__ __forceinline__ void push4(Acc<COMP> &acc, const InstDev &I, int k4, int t, float4 u) {
-  const float4 *tb = I.table + (size_t)k4 * 4 * I.T + t;
-  acc.push(sgn(u.x), ldt(tb));
-  acc.push(sgn(u.y), ldt(tb + I.T));
-  acc.push(sgn(u.z), ldt(tb + 2 * I.T));
-  acc.push(sgn(u.w), ldt(tb + 3 * I.T));
+template <bool COMP, bool TS>
+__device__ __forceinline__ void push4(Acc<COMP> &acc, const float4 *tbl, int T, int k4, int t,
+                                      float4 u) {
+  const float4 *tb = tbl + (size_t)k4 * 4 * T + t;
+  acc.push(sgn(u.x), ldt<TS>(tb));
+  acc.push(sgn(u.y), ldt<TS>(tb + T));
+  acc.push(sgn(u.z), ldt<TS>(tb + 2 * T));
+  acc.push(sgn(u.w), ldt<TS>(tb + 3 * T));
 }
 
 __device__ __forceinline__ float *row_ptr(const InstDev &I, int i, int slot) {
   return I.pop + ((size_t)2 * i + slot) * I.Npad;
+}
+
+// float4 group `off` of individual i's current row.  DUAL: both slots are read
+// together with the selector, which takes the selector load off the critical path.
+template <bool NC, bool DUAL>
+__device__ __forceinline__ float4 ld_cur(const InstDev &I, int i, int slot, size_t off) {
+  if (DUAL) {
+    const float *r0 = I.pop + (size_t)2 * i * I.Npad + off;
+    const float4 v0 = ld4<NC>(r0), v1 = ld4<NC>(r0 + I.Npad);
+    return slot ? v1 : v0;
+  }
+  return ld4<NC>(row_ptr(I, i, slot) + off);
 }
 
 // ---------------------------------------------------- Step 1: initialisation
@@ -107,7 +125,7 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
     x.z = __fsub_rn(__fmul_rn(2.0f, u24(w.z)), 1.0f);
     x.w = __fsub_rn(__fmul_rn(2.0f, u24(w.w)), 1.0f);
     *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
-    push4(acc, I, k4, t, x);
+    push4<COMP, false>(acc, I.table, I.T, k4, t, x);
   }
   const Mono m = block_reduce(acc.get(), sh);
   if (t == 0) {
@@ -133,24 +151,21 @@ static __global__ void k_init(InstDev I) {
 
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
-template <bool COMP, bool NC>
-__device__ unsigned long long de_individual(const InstDev &I, int g, int i, const int32_t *sel_in,
-                                            int32_t *sel_out, Mono *sh) {
+template <bool COMP, bool NC, bool TS, bool DUAL>
+__device__ unsigned long long de_individual(const InstDev &I, const float4 *tbl, int g, int i,
+                                            const int32_t *sel_in, int32_t *sel_out, Mono *sh) {
   const int t = threadIdx.x;
+  const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   const int4 r = de_indices(I.key, I.inst, (uint32_t)g, i, I.NP, I.N);
-  const int si = sel_in[i];
-  const float *xi = row_ptr(I, i, si);
-  const float *x1 = row_ptr(I, r.x, sel_in[r.x]);
-  const float *x2 = row_ptr(I, r.y, sel_in[r.y]);
-  const float *x3 = row_ptr(I, r.z, sel_in[r.z]);
+  const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
   const float F = I.F, CR = I.CR;
   Acc<COMP> acc;
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
-    const float4 a = ld4<NC>(xi + off), b = ld4<NC>(x1 + off);
-    const float4 p = ld4<NC>(x2 + off), q = ld4<NC>(x3 + off);
+    const float4 a = ld_cur<NC, DUAL>(I, i, si, off), b = ld_cur<NC, DUAL>(I, r.x, s1, off);
+    const float4 p = ld_cur<NC, DUAL>(I, r.y, s2, off), q = ld_cur<NC, DUAL>(I, r.z, s3, off);
     const int j0 = t * I.c + 4 * k4;
     const uint4 w = rng4(I.key, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 u;
@@ -166,14 +181,13 @@ __device__ unsigned long long de_individual(const InstDev &I, int g, int i, cons
     QPM_DE1(w, w, j0 + 3)
 #undef QPM_DE1
     *(float4 *)(out + off) = u;
-    push4(acc, I, k4, t, u);
+    push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
   }
   const Mono m = block_reduce(acc.get(), sh);
   unsigned long long key = 0ull;
   if (t == 0) {
     const float2 D = deff_from(m, I.konst[0], I.konst[1]);
     const float f = fit_of(D);
-    const float fx = I.fit[i];
     const bool accept = f >= fx;  // greedy one-to-one selection, maximising
     sel_out[i] = accept ? (si ^ 1) : si;
     if (accept) {
@@ -187,12 +201,12 @@ __device__ unsigned long long de_individual(const InstDev &I, int g, int i, cons
 }
 
 // ------------------------------------------------ Step 4-5: GWO + selection
-template <bool COMP, bool NC>
-__device__ void gwo_individual(const InstDev &I, int g, int i, int32_t *sel, const float *XA,
-                               const float *XB, const float *XD, Mono *sh) {
+template <bool COMP, bool NC, bool TS, bool DUAL>
+__device__ void gwo_individual(const InstDev &I, const float4 *tbl, int g, int i, int32_t *sel,
+                               int la, int lb, int ld, Mono *sh) {
   const int t = threadIdx.x;
-  const int si = sel[i];
-  const float *xi = row_ptr(I, i, si);
+  const float fx = (t == 0) ? I.fit[i] : 0.f;
+  const int si = sel[i], sa = sel[la], sb = sel[lb], sd = sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
   const float a = __fdiv_rn((float)(2 * (I.G - g)), (float)I.G);
   const float two_a = __fmul_rn(2.0f, a);
@@ -200,8 +214,9 @@ __device__ void gwo_individual(const InstDev &I, int g, int i, int32_t *sel, con
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
-    const float4 x = ld4<NC>(xi + off);
-    const float4 L0 = ld4<NC>(XA + off), L1 = ld4<NC>(XB + off), L2 = ld4<NC>(XD + off);
+    const float4 x = ld_cur<NC, DUAL>(I, i, si, off);
+    const float4 L0 = ld_cur<NC, DUAL>(I, la, sa, off), L1 = ld_cur<NC, DUAL>(I, lb, sb, off);
+    const float4 L2 = ld_cur<NC, DUAL>(I, ld, sd, off);
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
     uint4 w[6];
 #pragma unroll
@@ -239,13 +254,13 @@ __device__ void gwo_individual(const InstDev &I, int g, int i, int32_t *sel, con
 #undef QPM_GWO1
 #undef QPM_PULL
     *(float4 *)(out + off) = y;
-    push4(acc, I, k4, t, y);
+    push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
   }
   const Mono m = block_reduce(acc.get(), sh);
   if (t == 0) {
     const float2 D = deff_from(m, I.konst[0], I.konst[1]);
     const float f = fit_of(D);
-    const bool accept = f >= I.fit[i];
+    const bool accept = f >= fx;
     if (accept) {
       sel[i] = si ^ 1;
       I.fit[i] = f;
@@ -312,7 +327,7 @@ __device__ bool last_cta(unsigned *ctr) {
   return is_last;
 }
 
-template <bool COMP>
+template <bool COMP, bool DUAL>
 static __global__ void k_de(InstDev I) {
   extern __shared__ Mono sh[];
   __shared__ unsigned long long shk[3 * 32];
@@ -321,7 +336,8 @@ static __global__ void k_de(InstDev I) {
   int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
-    const unsigned long long key = de_individual<COMP, true>(I, g, i, sel_in, sel_out, sh);
+    const unsigned long long key =
+        de_individual<COMP, true, false, DUAL>(I, I.table, g, i, sel_in, sel_out, sh);
     if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
   }
   if (threadIdx.x == 0) {
@@ -335,18 +351,15 @@ static __global__ void k_de(InstDev I) {
   }
 }
 
-template <bool COMP>
+template <bool COMP, bool DUAL>
 static __global__ void k_gwo(InstDev I) {
   extern __shared__ Mono sh[];
   const int g = *I.gen;
   int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
   const int la = I.lead[0], lb = I.lead[1], ld = I.lead[2];
-  const float *XA = row_ptr(I, la, sel[la]);
-  const float *XB = row_ptr(I, lb, sel[lb]);
-  const float *XD = row_ptr(I, ld, sel[ld]);
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
-    gwo_individual<COMP, true>(I, g, i, sel, XA, XB, XD, sh);
+    gwo_individual<COMP, true, false, DUAL>(I, I.table, g, i, sel, la, lb, ld, sh);
   }
   if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
     const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -362,59 +375,65 @@ static __global__ void k_gwo(InstDev I) {
 
 // ------------------------------------------------------ persistent kernel
 struct Barrier {
-  unsigned *count;   // arrivals
-  unsigned *flag;    // release epoch
+  unsigned *count;   // arrivals, monotonically increasing (zeroed before the launch)
   int32_t *err;      // 0 ok, else a qpm_status
   unsigned long long timeout_ns;
 };
 
-// grid-wide barrier with a bounded wait; false when any CTA has failed
-__device__ bool grid_sync(const Barrier &b, unsigned &epoch) {
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// grid-wide barrier with a bounded wait: every CTA adds one arrival and waits for
+// the counter to reach (barriers passed) * gridDim.x.  Returns false in every
+// thread when any CTA has failed or this wait ran out (the error is recorded).
+__device__ bool grid_sync(const Barrier &b, unsigned &target) {
   __shared__ int ok_sh;
   __syncthreads();
+  target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned target = epoch + 1;
     __threadfence();
-    const unsigned prev = atomicAdd(b.count, 1u);
-    if (prev == gridDim.x - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      st_release(b.flag, target);
-    } else {
-      const unsigned long long t0 = globaltimer_ns();
-      while (ld_acquire(b.flag) != target) {
-        if (*(volatile int32_t *)b.err != 0) { ok = 0; break; }
-        if (globaltimer_ns() - t0 > b.timeout_ns) {
-          atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
+    red_release_add(b.count, 1u);
+    const unsigned long long t0 = globaltimer_ns();
+    while ((int)(ld_acquire(b.count) - target) < 0) {
+      if (*(volatile int32_t *)b.err != 0) { ok = 0; break; }
+      if (globaltimer_ns() - t0 > b.timeout_ns) {
+        atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+        ok = 0;
+        break;
       }
     }
     if (*(volatile int32_t *)b.err != 0) ok = 0;
     __threadfence();
-    epoch = target;
     ok_sh = ok;
   }
   __syncthreads();
   return ok_sh != 0;
 }
 
-template <bool COMP>
+// All generations [*gen, g_end) in one cooperative launch; every CTA keeps the
+// same individuals, the phasor table sits in shared memory when it fits (TS).
+template <bool COMP, bool TS, bool DUAL>
 static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
-  extern __shared__ Mono sh[];
+  extern __shared__ float4 dyn[];
   __shared__ unsigned long long shk[3 * 32];
   __shared__ int32_t lead_sh[3];
-  unsigned epoch = 0;
+  Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
+  if (TS) {
+    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
+    __syncthreads();
+  }
+  const float4 *tbl = TS ? (const float4 *)dyn : I.table;
+  unsigned target = 0;
   int g = *I.gen;
-  if (!grid_sync(bar, epoch)) return;  // every CTA has read the start generation
   for (; g < g_end; ++g) {
     const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
     int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
     unsigned long long k0 = 0, k1 = 0, k2 = 0;
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
-      const unsigned long long key = de_individual<COMP, false>(I, g, i, sel_in, sel_out, sh);
+      const unsigned long long key =
+          de_individual<COMP, false, TS, DUAL>(I, tbl, g, i, sel_in, sel_out, sh);
       if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
     }
     if (threadIdx.x == 0) {
@@ -422,16 +441,13 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
       I.topk[3 * blockIdx.x + 1] = k1;
       I.topk[3 * blockIdx.x + 2] = k2;
     }
-    if (!grid_sync(bar, epoch)) return;
+    if (!grid_sync(bar, target)) return;
     // every CTA merges the partial leader keys itself (no extra barrier)
     merge_leaders(I.topk, gridDim.x, blockIdx.x == 0 ? I.lead : nullptr, shk, lead_sh);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
-    const float *XA = row_ptr(I, la, sel_out[la]);
-    const float *XB = row_ptr(I, lb, sel_out[lb]);
-    const float *XD = row_ptr(I, ld, sel_out[ld]);
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
-      gwo_individual<COMP, false>(I, g, i, sel_out, XA, XB, XD, sh);
+      gwo_individual<COMP, false, TS, DUAL>(I, tbl, g, i, sel_out, la, lb, ld, sh);
     }
     if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -439,7 +455,7 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
     }
     // the partial leader keys are rewritten in the next DE phase: all CTAs must
     // have merged them before any CTA passes this barrier
-    if (!grid_sync(bar, epoch)) return;
+    if (!grid_sync(bar, target)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *I.gen = g_end;
 }
@@ -553,9 +569,11 @@ struct qpm_state {
 
 namespace qpm {
 
+// threads per individual: the smallest power of two in [32, 256] giving at most
+// 4 domains per thread; beyond 1024 domains the 256 threads take more each
 static int choose_team(int N) {
   int T = 32;
-  while (T < 256 && N > T * 8) T *= 2;
+  while (T < 256 && N > 4 * T) T *= 2;
   return T;
 }
 
@@ -563,13 +581,44 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static size_t smem_bytes(int T) { return sizeof(Mono) * (size_t)(T / 32 + 1); }
 
-template <bool COMP>
-static qpm_status occupancy(int T, int *plain, int *persist) {
-  int a = 0, b = 0;
-  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_de<COMP>, T, smem_bytes(T)));
-  int a2 = 0;
-  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, k_gwo<COMP>, T, smem_bytes(T)));
-  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_persist<COMP>, T, smem_bytes(T)));
+// kernel variants of one instance
+struct Variant {
+  const void *de, *gwo, *persist;
+  size_t smem, persist_smem;
+};
+
+static constexpr int TS_MAX_NPAD = 4096;  // phasor table in shared memory up to 64 KB
+
+template <bool COMP, bool DUAL>
+static Variant variant2(const InstDev &I) {
+  Variant v;
+  v.de = (const void *)k_de<COMP, DUAL>;
+  v.gwo = (const void *)k_gwo<COMP, DUAL>;
+  v.smem = smem_bytes(I.T);
+  if (I.Npad <= TS_MAX_NPAD) {
+    v.persist = (const void *)k_persist<COMP, true, DUAL>;
+    v.persist_smem = smem_bytes(I.T) + sizeof(float4) * (size_t)I.Npad;
+  } else {
+    v.persist = (const void *)k_persist<COMP, false, DUAL>;
+    v.persist_smem = smem_bytes(I.T);
+  }
+  return v;
+}
+
+static Variant variant_of(const InstDev &I) {
+  const bool dual = I.c <= 8;
+  if (I.compensated) return dual ? variant2<true, true>(I) : variant2<true, false>(I);
+  return dual ? variant2<false, true>(I) : variant2<false, false>(I);
+}
+
+static qpm_status occupancy(const InstDev &I, int *plain, int *persist) {
+  const Variant v = variant_of(I);
+  int a = 0, a2 = 0, b = 0;
+  QPM_CUDA(cudaFuncSetAttribute(v.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)v.persist_smem));
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, I.T, v.smem));
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, v.gwo, I.T, v.smem));
+  QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.persist, I.T, v.persist_smem));
   *plain = std::max(1, std::min(a, a2));
   *persist = std::max(1, b);
   return QPM_OK;
@@ -577,18 +626,13 @@ static qpm_status occupancy(int T, int *plain, int *persist) {
 
 static qpm_status enqueue_step(qpm_state *st, cudaStream_t s) {
   for (int k = 0; k < st->n; ++k) {
-    const InstDev &I = st->h[k];
-    const int grid = st->grid_plain[k];
-    const size_t sm = smem_bytes(I.T);
-    if (I.compensated) {
-      k_de<true><<<grid, I.T, sm, s>>>(I);
-      k_gwo<true><<<grid, I.T, sm, s>>>(I);
-    } else {
-      k_de<false><<<grid, I.T, sm, s>>>(I);
-      k_gwo<false><<<grid, I.T, sm, s>>>(I);
-    }
+    InstDev I = st->h[k];
+    const Variant v = variant_of(I);
+    void *args[] = {&I};
+    const dim3 grid(st->grid_plain[k]), block(I.T);
+    QPM_CUDA(cudaLaunchKernel(v.de, grid, block, args, v.smem, s));
+    QPM_CUDA(cudaLaunchKernel(v.gwo, grid, block, args, v.smem, s));
   }
-  QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }
 
@@ -661,8 +705,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.kappa2 = p.kappa2;
     st->G_min = std::min(st->G_min, q.G);
     int occ_plain = 1, occ_persist = 1;
-    qpm_status s2 = I.compensated ? occupancy<true>(I.T, &occ_plain, &occ_persist)
-                                  : occupancy<false>(I.T, &occ_plain, &occ_persist);
+    qpm_status s2 = occupancy(I, &occ_plain, &occ_persist);
     if (s2 != QPM_OK) { delete st; return s2; }
     st->grid_plain[k] = std::min(I.NP, occ_plain * nsm);
     st->grid_persist[k] = std::min(I.NP, occ_persist * nsm);
@@ -783,13 +826,16 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     QPM_CUDA(cudaGraphLaunch(st->gexec, s));
   } else if (mode == QPM_RUN_PERSISTENT) {
     QPM_CUDA(cudaMemsetAsync(st->bar, 0, 3 * sizeof(unsigned), s));
-    Barrier b{st->bar, st->bar + 1, (int32_t *)(st->bar + 2), st->timeout_ns};
     for (int k = 0; k < st->n; ++k) {
       InstDev I = st->h[k];
+      const Variant v = variant_of(I);
       int g_end = st->g + generations;
+      // each instance gets a fresh arrival counter; the error word is shared
+      QPM_CUDA(cudaMemsetAsync(st->bar, 0, sizeof(unsigned), s));
+      Barrier b{st->bar, (int32_t *)(st->bar + 2), st->timeout_ns};
       void *args[] = {&I, &g_end, &b};
-      const void *fn = I.compensated ? (const void *)k_persist<true> : (const void *)k_persist<false>;
-      QPM_CUDA(cudaLaunchCooperativeKernel(fn, st->grid_persist[k], I.T, args, smem_bytes(I.T), s));
+      QPM_CUDA(cudaLaunchCooperativeKernel(v.persist, st->grid_persist[k], I.T, args,
+                                           v.persist_smem, s));
     }
     int32_t err = 0;
     QPM_CUDA(cudaMemcpyAsync(&err, st->bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
