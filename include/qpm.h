@@ -97,6 +97,28 @@ qpm_status qpm_eval_packed(const qpm_problem *prob, const uint32_t *signs, int64
                            int32_t NP, float *d_eff, float *fit, int32_t compensated,
                            qpm_stream_t stream);
 
+/* Allocation-free qpm_eval (no counterpart in the paper; it exists for callers
+ * that cannot allocate device memory: code running while a stream is being
+ * captured into a CUDA graph, host callbacks, processes whose device memory is
+ * owned by an external allocator, real-time paths that cannot afford the
+ * implicit synchronisation of cudaMalloc).  Same arguments, layouts and result
+ * as qpm_eval; it allocates nothing (no cudaMalloc/cudaFree, no allocating
+ * library routine).  Its scratch -- the phasor table and the partial sums of the
+ * scan -- lives in one fixed 8 MiB array in the library's device image, which
+ * every GPU that loads the library holds until the process exits.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make this first call
+ *     before any stream capture on that device.
+ *   - N and NP whose scratch needs exceed 8 MiB (about N = 250k domains with
+ *     the default segment split) are rejected with QPM_ERR_ARG and a message
+ *     stating the bytes needed; nothing is enqueued.
+ *   - Every call rebuilds the phasor table in the shared array, so calls that
+ *     overlap on the GPU (different streams, or graphs replayed concurrently)
+ *     race on it and must be serialised by the caller.  Nothing in the array
+ *     needs to start at zero: each call writes every word it reads. */
+qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *genes, int64_t ld, int32_t NP,
+                            float *d_eff, float *fit, int32_t compensated, qpm_stream_t stream);
+
 /* Free the cached phasor tables and scratch of the current device (synchronises it). */
 qpm_status qpm_release_caches(void);
 

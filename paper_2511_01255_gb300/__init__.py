@@ -14,7 +14,8 @@ import os
 from . import build_lib
 
 __all__ = [
-    "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_release_caches",
+    "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc",
+    "qpm_release_caches",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation",
     "qpm_get_population", "qpm_get_best", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT",
@@ -60,6 +61,7 @@ def lib(build=True):
             "qpm_abi_version": ([], i32),
             "qpm_eval": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_eval_packed": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
+            "qpm_eval_noalloc": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_release_caches": ([], ctypes.c_int),
             "qpm_create": ([_P, _P, i32, _P], ctypes.c_int),
             "qpm_init": ([_P, _P], ctypes.c_int),
@@ -125,6 +127,14 @@ def qpm_eval_packed(N, kappa1, kappa2, signs, d_eff, fit=None, compensated=0, st
     NP, ld = _rows(signs, "signs")
     _check(lib().qpm_eval_packed(ctypes.byref(p), _ptr(signs), ld, NP, _ptr(d_eff), _ptr(fit),
                                  int(compensated), _stream(stream)))
+
+
+def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, stream=None):
+    """qpm_eval without any device allocation (fixed 8 MiB scratch inside the library)."""
+    p = _problem(N, kappa1, kappa2)
+    NP, ld = _rows(genes, "genes")
+    _check(lib().qpm_eval_noalloc(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),
+                                  int(compensated), _stream(stream)))
 
 
 def qpm_release_caches():

@@ -9,6 +9,7 @@
 
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 
 #include "qpm_common.cuh"
@@ -268,7 +269,98 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   return QPM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of qpm_eval.  For callers that must not allocate
+// device memory: code running where cudaMalloc is not allowed or not wanted,
+// e.g. while a CUDA stream is being captured into a graph, inside a host
+// callback, under an external allocator that owns all device memory, or on a
+// real-time path where an allocation's implicit device synchronisation is not
+// acceptable.  Its scratch (phasor table, table reduction, segment partials)
+// lives in one file-scope device array of fixed size that every GPU loading
+// this library holds until the process exits.
+// ---------------------------------------------------------------------------
+static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[128] = {nullptr};  // device address of g_noalloc_scratch, per device
+
+// One-time set-up per device (with that device current): the host name
+// g_noalloc_scratch is only a host-side stand-in, so its device address is
+// looked up once and cached.
+qpm_status noalloc_base(void **out) {
+  int dev = 0;
+  QPM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(QPM_ERR_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QPM_OK;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
 }  // namespace qpm
+
+extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *genes, int64_t ld,
+                                       int32_t NP, float *d_eff, float *fit, int32_t compensated,
+                                       qpm_stream_t stream) {
+  using namespace qpm;
+  if (!prob || !genes || !d_eff) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: NULL pointer");
+  if (prob->N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: need N >= 1 and NP >= 1");
+  if (ld < prob->N) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: leading dimension smaller than the row");
+  if (prob->N > (1 << 28) || NP > (1 << 26))
+    return fail(QPM_ERR_ARG, "qpm_eval_noalloc: problem exceeds the fixed scratch (8 MiB)");
+  const EvalShape sh = eval_shape(NP, prob->N);
+  const int32_t Npad = (prob->N + 3) & ~3;
+  const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
+  const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));
+  const size_t b_konst = 256;
+  const size_t b_part = up256(sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad);
+  const size_t need = b_table + b_tpart + b_konst + b_part;
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return fail(QPM_ERR_ARG, "qpm_eval_noalloc: N and NP need " + std::to_string(need) +
+                                 " bytes of scratch, more than the fixed 8 MiB (8388608)");
+  void *base = nullptr;
+  qpm_status st = noalloc_base(&base);
+  if (st != QPM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  char *p = (char *)base;
+  float4 *table = (float4 *)p;
+  double2 *tpart = (double2 *)(p + b_table);
+  float2 *konst = (float2 *)(p + b_table + b_tpart);
+  float2 *part = (float2 *)(p + b_table + b_tpart + b_konst);
+  // every word read below is written first in this call (table, its partial
+  // sums, every segment partial of every padded row), so nothing needs zeroing
+  TableSpec ts{prob->N, Npad, 1, Npad, prob->kappa1, prob->kappa2};
+  st = launch_table(ts, table, tpart, konst, nullptr, s);
+  if (st != QPM_OK) return st;
+  dim3 grid(sh.S, (sh.groups + EV_WARPS - 1) / EV_WARPS);
+  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
+  if (vec) {
+    if (compensated) k_eval_seg<0, true><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
+    else k_eval_seg<0, false><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
+  } else {
+    if (compensated) k_eval_seg<1, true><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
+    else k_eval_seg<1, false><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
+  }
+  QPM_CUDA(cudaGetLastError());
+  const int cb = 128;
+  if (compensated)
+    k_eval_combine<true><<<(NP + cb - 1) / cb, cb, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
+  else
+    k_eval_combine<false><<<(NP + cb - 1) / cb, cb, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
 
 extern "C" qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld,
                                int32_t NP, float *d_eff, float *fit, int32_t compensated,
