@@ -66,6 +66,7 @@ typedef struct {
   uint64_t seed;       /* Philox4x32-10 key */
   int32_t gwo_combine; /* 0: (X1+X2+X3)/3; 1: |X_k|-weighted, per dimension */
   int32_t compensated; /* 0: plain FP32 scan; 1: Kahan-compensated FP32 scan */
+  int32_t team;        /* threads per individual: 0 = automatic, else 32, 64, 128 or 256 */
 } qpm_params;
 
 /* Execution modes of qpm_run. */
@@ -161,6 +162,9 @@ qpm_status qpm_get_population(qpm_state *st, int32_t inst, float *genes_out, int
  *   (each may be NULL), index_out device int32 [1] (may be NULL). */
 qpm_status qpm_get_best(qpm_state *st, int32_t inst, float *genes_out, double *d_eff64_out,
                         float *fit_out, int32_t *index_out, qpm_stream_t stream);
+
+/* Threads per individual the state uses for instance `inst` (host int32 out). */
+qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out);
 
 /* Test hook: record FP32 fitness values of instance `inst` into trace (device,
  * float [NP * (1 + 2G)]): [0, NP) after init, then for generation g the trial

@@ -16,7 +16,7 @@ from . import build_lib
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc",
     "qpm_release_caches",
-    "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation",
+    "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_get_population", "qpm_get_best", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT",
 ]
@@ -39,7 +39,8 @@ class Problem(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("NP", ctypes.c_int32), ("G", ctypes.c_int32), ("F", ctypes.c_float),
                 ("CR", ctypes.c_float), ("seed", ctypes.c_uint64),
-                ("gwo_combine", ctypes.c_int32), ("compensated", ctypes.c_int32)]
+                ("gwo_combine", ctypes.c_int32), ("compensated", ctypes.c_int32),
+                ("team", ctypes.c_int32)]
 
 
 _lib = None
@@ -69,6 +70,7 @@ def lib(build=True):
             "qpm_run": ([_P, i32, i32, _P], ctypes.c_int),
             "qpm_destroy": ([_P], ctypes.c_int),
             "qpm_generation": ([_P, _P], ctypes.c_int),
+            "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
             "qpm_get_best": ([_P, i32, _P, _P, _P, _P, _P], ctypes.c_int),
             "qpm_set_trace": ([_P, i32, _P], ctypes.c_int),
@@ -171,6 +173,12 @@ def qpm_generation(st):
     g = ctypes.c_int32()
     _check(lib().qpm_generation(st, ctypes.byref(g)))
     return g.value
+
+
+def qpm_team_of(st, inst=0):
+    t = ctypes.c_int32()
+    _check(lib().qpm_team_of(st, int(inst), ctypes.byref(t)))
+    return t.value
 
 
 def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):

@@ -18,15 +18,27 @@ namespace qpm {
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds, multipliers 0xD2511F53 and
-// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.  The round keys
+// depend on the seed only, so a thread builds them once and reuses them.
+struct PhiloxKey {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKey philox_schedule(uint2 key) {
+  PhiloxKey K;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    k.x += 0x9E3779B9u;
-    k.y += 0xBB67AE85u;
+    K.k0[r] = key.x + (uint32_t)r * 0x9E3779B9u;
+    K.k1[r] = key.y + (uint32_t)r * 0xBB67AE85u;
+  }
+  return K;
+}
+__device__ __forceinline__ uint4 philox10(uint4 c, const PhiloxKey &K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[r], (uint32_t)p0);
   }
   return c;
 }
@@ -35,9 +47,9 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 // word j%4 of the output serves gene j.
 enum : uint32_t { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3, TAG_THETA = 16 };
 
-__device__ __forceinline__ uint4 rng4(uint2 key, uint32_t inst, uint32_t tag, uint32_t g,
+__device__ __forceinline__ uint4 rng4(const PhiloxKey &K, uint32_t inst, uint32_t tag, uint32_t g,
                                       uint32_t i, uint32_t jgroup) {
-  return philox10(make_uint4(jgroup, i, g, (inst << 8) | tag), key);
+  return philox10(make_uint4(jgroup, i, g, (inst << 8) | tag), K);
 }
 // U in [0, 1) on the 24-bit grid (exact in FP32)
 __device__ __forceinline__ float u24(uint32_t w) {
@@ -49,9 +61,9 @@ __device__ __forceinline__ uint32_t lemire(uint32_t w, uint32_t m) { return __um
 // DE rand/1 donors r1, r2, r3 (distinct, != i) and the forced crossover index jrand.
 // Each draw is mapped onto the values not yet excluded by skipping the excluded
 // ones in ascending order (a bijection, so every allowed value is equally likely).
-__device__ __forceinline__ int4 de_indices(uint2 key, uint32_t inst, uint32_t g, int i, int NP,
-                                           int N) {
-  const uint4 w = rng4(key, inst, TAG_DEIDX, g, (uint32_t)i, 0u);
+__device__ __forceinline__ int4 de_indices(const PhiloxKey &K, uint32_t inst, uint32_t g, int i,
+                                           int NP, int N) {
+  const uint4 w = rng4(K, inst, TAG_DEIDX, g, (uint32_t)i, 0u);
   int r1 = (int)lemire(w.x, (uint32_t)(NP - 1));
   r1 += (r1 >= i);
   int e0 = min(i, r1), e1 = max(i, r1);
@@ -107,7 +119,7 @@ __device__ __forceinline__ void mono_push(Mono &m, float d, const float4 &p) {
   m.B.y = fmaf(d, p.y, m.B.y);
 }
 
-// Kahan-compensated variant: every running sum carries its compensation term
+// compensated running triple: every running sum carries its Kahan compensation term
 struct MonoK {
   Mono s;
   float2 eA, eB, eC;
@@ -124,24 +136,26 @@ __device__ __forceinline__ void kahan_add(float &s, float &e, float x) {
   e = __fsub_rn(__fsub_rn(t, s), y);
   s = t;
 }
-__device__ __forceinline__ void monok_push(MonoK &m, float d, const float4 &p) {
-  const float ar = d * p.z, ai = d * p.w;
-  const float br = __fsub_rn(m.s.B.x, m.eB.x), bi = __fsub_rn(m.s.B.y, m.eB.y);
-  const float pr = __fsub_rn(__fmul_rn(ar, br), __fmul_rn(ai, bi));
-  const float pi = __fadd_rn(__fmul_rn(ar, bi), __fmul_rn(ai, br));
-  kahan_add(m.s.C.x, m.eC.x, pr);
-  kahan_add(m.s.C.y, m.eC.y, pi);
-  kahan_add(m.s.A.x, m.eA.x, ar);
-  kahan_add(m.s.A.y, m.eA.y, ai);
-  kahan_add(m.s.B.x, m.eB.x, d * p.x);
-  kahan_add(m.s.B.y, m.eB.y, d * p.y);
-}
 __device__ __forceinline__ Mono monok_fold(const MonoK &m) {
   Mono o;
   o.A = make_float2(__fsub_rn(m.s.A.x, m.eA.x), __fsub_rn(m.s.A.y, m.eA.y));
   o.B = make_float2(__fsub_rn(m.s.B.x, m.eB.x), __fsub_rn(m.s.B.y, m.eB.y));
   o.C = make_float2(__fsub_rn(m.s.C.x, m.eC.x), __fsub_rn(m.s.C.y, m.eC.y));
   return o;
+}
+
+// Kahan-fold a plain partial R (the next domains) into the compensated running
+// monoid m: C += C_R + A_R B, B += B_R, A += A_R, each sum with its compensation
+__device__ __forceinline__ void monok_fold_in(MonoK &m, const Mono &R) {
+  const float br = __fsub_rn(m.s.B.x, m.eB.x), bi = __fsub_rn(m.s.B.y, m.eB.y);
+  const float xr = __fadd_rn(R.C.x, __fsub_rn(__fmul_rn(R.A.x, br), __fmul_rn(R.A.y, bi)));
+  const float xi = __fadd_rn(R.C.y, __fadd_rn(__fmul_rn(R.A.x, bi), __fmul_rn(R.A.y, br)));
+  kahan_add(m.s.C.x, m.eC.x, xr);
+  kahan_add(m.s.C.y, m.eC.y, xi);
+  kahan_add(m.s.B.x, m.eB.x, R.B.x);
+  kahan_add(m.s.B.y, m.eB.y, R.B.y);
+  kahan_add(m.s.A.x, m.eA.x, R.A.x);
+  kahan_add(m.s.A.y, m.eA.y, R.A.y);
 }
 
 __device__ __forceinline__ Mono mono_shfl_down(const Mono &m, int s) {

@@ -38,6 +38,8 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
   const int irow = i < sh.NP ? i : sh.NP - 1;  // spare lanes recompute the last row
   const int m0 = s * sh.L;
   const int m1 = min(sh.N, m0 + sh.L);
+  // plain: FP32 running sums; compensated: plain blocks of 8 domains Kahan-folded
+  // into a compensated running triple (blocked Kahan summation)
   Mono acc = mono_zero();
   MonoK acck = monok_zero();
   if (KIND == 2) {
@@ -49,8 +51,10 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
       for (int e = 0; e < n; ++e) {
         const float4 p = __ldg(table + mb + e);
         const float d = ((w >> e) & 1u) ? -1.0f : 1.0f;
-        if (COMP) monok_push(acck, d, p); else mono_push(acc, d, p);
+        mono_push(acc, d, p);
+        if (COMP && (e & 7) == 7) { monok_fold_in(acck, acc); acc = mono_zero(); }
       }
+      if (COMP && (n & 7)) { monok_fold_in(acck, acc); acc = mono_zero(); }
     }
   } else if (KIND == 0) {
     const float *row = (const float *)src + (int64_t)irow * ld;
@@ -59,28 +63,24 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
       const float4 x = __ldg((const float4 *)(row + m));
       const float4 p0 = __ldg(table + m), p1 = __ldg(table + m + 1);
       const float4 p2 = __ldg(table + m + 2), p3 = __ldg(table + m + 3);
-      const float d0 = x.x < 0.f ? -1.f : 1.f, d1 = x.y < 0.f ? -1.f : 1.f;
-      const float d2 = x.z < 0.f ? -1.f : 1.f, d3 = x.w < 0.f ? -1.f : 1.f;
-      if (COMP) {
-        monok_push(acck, d0, p0); monok_push(acck, d1, p1);
-        monok_push(acck, d2, p2); monok_push(acck, d3, p3);
-      } else {
-        mono_push(acc, d0, p0); mono_push(acc, d1, p1);
-        mono_push(acc, d2, p2); mono_push(acc, d3, p3);
-      }
+      mono_push(acc, x.x < 0.f ? -1.f : 1.f, p0);
+      mono_push(acc, x.y < 0.f ? -1.f : 1.f, p1);
+      mono_push(acc, x.z < 0.f ? -1.f : 1.f, p2);
+      mono_push(acc, x.w < 0.f ? -1.f : 1.f, p3);
+      if (COMP && ((m - m0) & 4)) { monok_fold_in(acck, acc); acc = mono_zero(); }
     }
-    for (; m < m1; ++m) {
-      const float d = __ldg(row + m) < 0.f ? -1.f : 1.f;
-      if (COMP) monok_push(acck, d, __ldg(table + m)); else mono_push(acc, d, __ldg(table + m));
-    }
+    for (; m < m1; ++m) mono_push(acc, __ldg(row + m) < 0.f ? -1.f : 1.f, __ldg(table + m));
   } else {
     const float *row = (const float *)src + (int64_t)irow * ld;
     for (int m = m0; m < m1; ++m) {
-      const float d = __ldg(row + m) < 0.f ? -1.f : 1.f;
-      if (COMP) monok_push(acck, d, __ldg(table + m)); else mono_push(acc, d, __ldg(table + m));
+      mono_push(acc, __ldg(row + m) < 0.f ? -1.f : 1.f, __ldg(table + m));
+      if (COMP && ((m - m0) & 7) == 7) { monok_fold_in(acck, acc); acc = mono_zero(); }
     }
   }
-  if (COMP) acc = monok_fold(acck);
+  if (COMP) {
+    monok_fold_in(acck, acc);
+    acc = monok_fold(acck);
+  }
   const size_t stride = (size_t)sh.S * sh.NPpad;
   const size_t o = (size_t)s * sh.NPpad + i;
   part[o] = acc.A;

@@ -67,17 +67,32 @@ __device__ __forceinline__ float4 ldt(const float4 *p) {
   return __ldg(p);
 }
 
+// Running monoid of a thread's chunk.  Plain: FP32 sums.  Compensated: the
+// domains are summed plainly in blocks of 8 and every block is Kahan-folded into
+// the running triple (blocked Kahan summation: error of order 8 eps instead of c eps).
 template <bool COMP>
 struct Acc {
-  Mono m;
-  MonoK k;
+  Mono m;   // plain sums / current block
+  MonoK k;  // compensated running triple
   __device__ __forceinline__ void zero() {
-    if (COMP) k = monok_zero(); else m = mono_zero();
+    m = mono_zero();
+    if (COMP) k = monok_zero();
   }
-  __device__ __forceinline__ void push(float d, const float4 &p) {
-    if (COMP) monok_push(k, d, p); else mono_push(m, d, p);
+  __device__ __forceinline__ void push(float d, const float4 &p) { mono_push(m, d, p); }
+  // end of a block of domains
+  __device__ __forceinline__ void fold() {
+    if (COMP) {
+      monok_fold_in(k, m);
+      m = mono_zero();
+    }
   }
-  __device__ __forceinline__ Mono get() const { return COMP ? monok_fold(k) : m; }
+  __device__ __forceinline__ Mono get() {
+    if (COMP) {
+      fold();
+      return monok_fold(k);
+    }
+    return m;
+  }
 };
 
 __device__ __forceinline__ float sgn(float x) { return x < 0.f ? -1.f : 1.f; }
@@ -113,12 +128,13 @@ __device__ __forceinline__ float4 ld_cur(const InstDev &I, int i, int slot, size
 template <bool COMP>
 __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
   const int t = threadIdx.x;
+  const PhiloxKey K = philox_schedule(I.key);
   float *row = row_ptr(I, i, 0);
   Acc<COMP> acc;
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const int j0 = t * I.c + 4 * k4;
-    const uint4 w = rng4(I.key, I.inst, TAG_INIT, 0u, (uint32_t)i, (uint32_t)(j0 >> 2));
+    const uint4 w = rng4(K, I.inst, TAG_INIT, 0u, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 x;
     x.x = __fsub_rn(__fmul_rn(2.0f, u24(w.x)), 1.0f);
     x.y = __fsub_rn(__fmul_rn(2.0f, u24(w.y)), 1.0f);
@@ -126,6 +142,7 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
     x.w = __fsub_rn(__fmul_rn(2.0f, u24(w.w)), 1.0f);
     *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
     push4<COMP, false>(acc, I.table, I.T, k4, t, x);
+    if (k4 & 1) acc.fold();
   }
   const Mono m = block_reduce(acc.get(), sh);
   if (t == 0) {
@@ -152,11 +169,12 @@ static __global__ void k_init(InstDev I) {
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
 template <bool COMP, bool NC, bool TS, bool DUAL>
-__device__ unsigned long long de_individual(const InstDev &I, const float4 *tbl, int g, int i,
+__device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
+                                            const float4 *tbl, int g, int i,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh) {
   const int t = threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
-  const int4 r = de_indices(I.key, I.inst, (uint32_t)g, i, I.NP, I.N);
+  const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
   const float F = I.F, CR = I.CR;
@@ -167,7 +185,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const float4 *tbl,
     const float4 a = ld_cur<NC, DUAL>(I, i, si, off), b = ld_cur<NC, DUAL>(I, r.x, s1, off);
     const float4 p = ld_cur<NC, DUAL>(I, r.y, s2, off), q = ld_cur<NC, DUAL>(I, r.z, s3, off);
     const int j0 = t * I.c + 4 * k4;
-    const uint4 w = rng4(I.key, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
+    const uint4 w = rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 u;
     // v = x_r1 + F (x_r2 - x_r3), clamped; u = v if U <= CR or j == jrand, else x
 #define QPM_DE1(C, W, J)                                                              \
@@ -182,6 +200,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const float4 *tbl,
 #undef QPM_DE1
     *(float4 *)(out + off) = u;
     push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
+    if (k4 & 1) acc.fold();
   }
   const Mono m = block_reduce(acc.get(), sh);
   unsigned long long key = 0ull;
@@ -202,8 +221,8 @@ __device__ unsigned long long de_individual(const InstDev &I, const float4 *tbl,
 
 // ------------------------------------------------ Step 4-5: GWO + selection
 template <bool COMP, bool NC, bool TS, bool DUAL>
-__device__ void gwo_individual(const InstDev &I, const float4 *tbl, int g, int i, int32_t *sel,
-                               int la, int lb, int ld, Mono *sh) {
+__device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
+                               int i, int32_t *sel, int la, int lb, int ld, Mono *sh) {
   const int t = threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
   const int si = sel[i], sa = sel[la], sb = sel[lb], sd = sel[ld];
@@ -220,7 +239,7 @@ __device__ void gwo_individual(const InstDev &I, const float4 *tbl, int g, int i
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
     uint4 w[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = rng4(I.key, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
+    for (int k = 0; k < 6; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
     float4 y;
 #define QPM_PULL(Xp, xv, r1w, r2w, out_)                                               \
     {                                                                                  \
@@ -255,6 +274,7 @@ __device__ void gwo_individual(const InstDev &I, const float4 *tbl, int g, int i
 #undef QPM_PULL
     *(float4 *)(out + off) = y;
     push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
+    if (k4 & 1) acc.fold();
   }
   const Mono m = block_reduce(acc.get(), sh);
   if (t == 0) {
@@ -299,16 +319,26 @@ __device__ void block_top3(unsigned long long &k0, unsigned long long &k1, unsig
   __syncthreads();
 }
 
-// merge all per-CTA partial triples in topk[0 .. 3*nparts) into lead[3] (thread 0 writes)
+// merge all per-CTA partial triples in topk[0 .. 3*nparts) into the leaders; warp 0
+// does the work, every thread returns after the CTA barrier (thread 0 writes lead)
 __device__ void merge_leaders(const unsigned long long *topk, int nparts, int32_t *lead,
-                              unsigned long long *sh, int32_t *lead_sh) {
-  unsigned long long k0 = 0, k1 = 0, k2 = 0;
-  for (int e = threadIdx.x; e < 3 * nparts; e += blockDim.x) top3_insert(k0, k1, k2, topk[e]);
-  block_top3(k0, k1, k2, sh);
-  if (threadIdx.x == 0) {
-    const int l0 = key_index(k0), l1 = key_index(k1), l2 = key_index(k2);
-    if (lead) { lead[0] = l0; lead[1] = l1; lead[2] = l2; }
-    if (lead_sh) { lead_sh[0] = l0; lead_sh[1] = l1; lead_sh[2] = l2; }
+                              int32_t *lead_sh) {
+  if (threadIdx.x < 32) {
+    unsigned long long k0 = 0, k1 = 0, k2 = 0;
+    for (int e = threadIdx.x; e < 3 * nparts; e += 32) top3_insert(k0, k1, k2, topk[e]);
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
+      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
+      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
+      top3_insert(k0, k1, k2, p0);
+      top3_insert(k0, k1, k2, p1);
+      top3_insert(k0, k1, k2, p2);
+    }
+    if (threadIdx.x == 0) {
+      const int l0 = key_index(k0), l1 = key_index(k1), l2 = key_index(k2);
+      if (lead) { lead[0] = l0; lead[1] = l1; lead[2] = l2; }
+      if (lead_sh) { lead_sh[0] = l0; lead_sh[1] = l1; lead_sh[2] = l2; }
+    }
   }
   __syncthreads();
 }
@@ -330,14 +360,14 @@ __device__ bool last_cta(unsigned *ctr) {
 template <bool COMP, bool DUAL>
 static __global__ void k_de(InstDev I) {
   extern __shared__ Mono sh[];
-  __shared__ unsigned long long shk[3 * 32];
   const int g = *I.gen;
+  const PhiloxKey K = philox_schedule(I.key);
   const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
   int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     const unsigned long long key =
-        de_individual<COMP, true, false, DUAL>(I, I.table, g, i, sel_in, sel_out, sh);
+        de_individual<COMP, true, false, DUAL>(I, K, I.table, g, i, sel_in, sel_out, sh);
     if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
   }
   if (threadIdx.x == 0) {
@@ -346,7 +376,7 @@ static __global__ void k_de(InstDev I) {
     I.topk[3 * blockIdx.x + 2] = k2;
   }
   if (last_cta(&I.ctr[0])) {
-    merge_leaders(I.topk, gridDim.x, I.lead, shk, nullptr);  // Step 3
+    merge_leaders(I.topk, gridDim.x, I.lead, nullptr);  // Step 3
     if (threadIdx.x == 0) I.ctr[0] = 0u;
   }
 }
@@ -355,11 +385,12 @@ template <bool COMP, bool DUAL>
 static __global__ void k_gwo(InstDev I) {
   extern __shared__ Mono sh[];
   const int g = *I.gen;
+  const PhiloxKey K = philox_schedule(I.key);
   int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
   const int la = I.lead[0], lb = I.lead[1], ld = I.lead[2];
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
-    gwo_individual<COMP, true, false, DUAL>(I, I.table, g, i, sel, la, lb, ld, sh);
+    gwo_individual<COMP, true, false, DUAL>(I, K, I.table, g, i, sel, la, lb, ld, sh);
   }
   if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
     const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -393,7 +424,8 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
   target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
+    // the release orders this CTA's writes (made visible to thread 0 by the CTA
+    // barrier above) before the arrival; the acquiring polls order what follows
     red_release_add(b.count, 1u);
     const unsigned long long t0 = globaltimer_ns();
     while ((int)(ld_acquire(b.count) - target) < 0) {
@@ -405,7 +437,6 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
       }
     }
     if (*(volatile int32_t *)b.err != 0) ok = 0;
-    __threadfence();
     ok_sh = ok;
   }
   __syncthreads();
@@ -417,7 +448,6 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
 template <bool COMP, bool TS, bool DUAL>
 static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
   extern __shared__ float4 dyn[];
-  __shared__ unsigned long long shk[3 * 32];
   __shared__ int32_t lead_sh[3];
   Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
   if (TS) {
@@ -425,6 +455,7 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
     __syncthreads();
   }
   const float4 *tbl = TS ? (const float4 *)dyn : I.table;
+  const PhiloxKey K = philox_schedule(I.key);
   unsigned target = 0;
   int g = *I.gen;
   for (; g < g_end; ++g) {
@@ -433,7 +464,7 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
     unsigned long long k0 = 0, k1 = 0, k2 = 0;
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       const unsigned long long key =
-          de_individual<COMP, false, TS, DUAL>(I, tbl, g, i, sel_in, sel_out, sh);
+          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_in, sel_out, sh);
       if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
     }
     if (threadIdx.x == 0) {
@@ -443,11 +474,11 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
     }
     if (!grid_sync(bar, target)) return;
     // every CTA merges the partial leader keys itself (no extra barrier)
-    merge_leaders(I.topk, gridDim.x, blockIdx.x == 0 ? I.lead : nullptr, shk, lead_sh);
+    merge_leaders(I.topk, gridDim.x, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
-      gwo_individual<COMP, false, TS, DUAL>(I, tbl, g, i, sel_out, la, lb, ld, sh);
+      gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh);
     }
     if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -668,6 +699,8 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (!(q.CR >= 0.f && q.CR <= 1.f)) return fail(QPM_ERR_ARG, "qpm_create: CR outside [0, 1]");
     if (q.gwo_combine != 0 && q.gwo_combine != 1)
       return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0 or 1");
+    if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256)
+      return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128 or 256");
     if (!std::isfinite(p.kappa1) || !std::isfinite(p.kappa2))
       return fail(QPM_ERR_ARG, "qpm_create: kappa must be finite");
   }
@@ -690,7 +723,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     InstDev &I = st->h[k];
     memset(&I, 0, sizeof(I));
     I.N = p.N;
-    I.T = choose_team(p.N);
+    I.T = q.team ? q.team : choose_team(p.N);
     I.Npad = (int32_t)align_up((size_t)p.N, 4 * (size_t)I.T);
     I.c = I.Npad / I.T;
     I.NP = q.NP;
@@ -848,6 +881,12 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     return fail(QPM_ERR_ARG, "qpm_run: unknown mode");
   }
   st->g += generations;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out) {
+  if (!st || !team_out || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad arguments");
+  *team_out = st->h[inst].T;
   return QPM_OK;
 }
 

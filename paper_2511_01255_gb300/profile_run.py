@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--gens", type=int, default=20)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--comp", type=int, default=-1, help="override the compensated flag")
+    ap.add_argument("--team", type=int, default=0, help="threads per individual (0 = automatic)")
     a = ap.parse_args()
     q.lib()
     if a.workload == "eval":
@@ -44,7 +45,7 @@ def main():
         return
     c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
     comp = c["compensated"] if a.comp < 0 else a.comp
-    prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp)
+    prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
     form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT}[a.form]
     st = q.State([(c["N"], c["kappa1"], c["kappa2"])], [prm])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -57,7 +58,7 @@ def main():
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
     st.close()
-    print(f"{c['name']} form={a.form} comp={comp}: {a.gens} generations in "
+    print(f"{c['name']} form={a.form} comp={comp} team={a.team or 'auto'}: {a.gens} generations in "
           f"{tot / a.reps:.3f} ms ({tot / a.reps / a.gens * 1e3:.2f} us/generation)")
 
 

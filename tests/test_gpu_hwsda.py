@@ -25,9 +25,9 @@ def q():
     return q
 
 
-def make(q, N, k1, k2, NP, G, F=0.5, CR=0.9, seed=1, combine=0, comp=0, trace=True):
+def make(q, N, k1, k2, NP, G, F=0.5, CR=0.9, seed=1, combine=0, comp=0, trace=True, team=0):
     import torch
-    prm = q.Params(NP, G, F, CR, seed, combine, comp)
+    prm = q.Params(NP, G, F, CR, seed, combine, comp, team)
     st = q.State([(N, k1, k2)], [prm])
     tr = None
     if trace:
@@ -109,6 +109,25 @@ def test_modes_agree_and_match_oracle_ragged(q, orc, combine, comp):
     Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=res[0][2], want_trace=True)
     assert np.array_equal(res[0][0], Xo)
     assert lockstep_errors(res[0][2], tro, N).max() < 2 * TOL_D
+
+
+@pytest.mark.parametrize("team", [32, 64, 256])
+def test_team_widths_lockstep(q, orc, team):
+    """Every team width (threads per individual) follows the oracle bit for bit."""
+    N, NP, G = 1000, 16, 6
+    k1, k2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+    for mode in (1, 2):
+        st, tr = make(q, N, k1, k2, NP, G, seed=3, comp=1, team=team)
+        assert q.qpm_team_of(st.h) == team
+        st.init()
+        st.run(G, mode)
+        X, f, D = snapshot(st)
+        trace = tr.cpu().numpy()
+        st.close()
+        cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 3)
+        Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+        assert np.array_equal(X, Xo)
+        assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
 def test_paper_scale_step_sampled(q, orc):
