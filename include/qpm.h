@@ -73,7 +73,10 @@ typedef struct {
 enum {
   QPM_RUN_LAUNCHES = 0,   /* two kernels per generation, launched one by one */
   QPM_RUN_GRAPH = 1,      /* the same launches captured once into a CUDA graph */
-  QPM_RUN_PERSISTENT = 2  /* one cooperative persistent kernel for all generations */
+  QPM_RUN_PERSISTENT = 2, /* one cooperative persistent kernel for all generations */
+  QPM_RUN_BATCHED = 3     /* many instances in one launch (captured in a CUDA graph): each
+                             CTA runs whole instances from a largest-first queue; needs
+                             team = 32, the default when n_inst > 1 */
 };
 
 const char *qpm_last_error(void);
@@ -124,6 +127,30 @@ qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *genes, int64_t
 qpm_status qpm_release_caches(void);
 
 /* ---------------------------------------------------------------------------
+ * Relaxed fitness and its adjoint (no counterpart in the paper's method, which
+ * works on +-1 domains; used to polish the GWO leaders and exposed for
+ * gradient-based design).  Each row theta_r[0..N) defines real domain values
+ * d_j = tanh(theta_j); d_eff is the Sec. 2.1 integral for that piecewise-
+ * constant d (exact for real d: phi1 phi2 sum_j a_j P_j + psi sum_j d_j^2 p1_j p2_j).
+ *   theta      device float [B][ld], ld >= N
+ *   d_eff      device float2 [B] (fwd out, bwd in)
+ *   fit        device float [B] = |d_eff|^2 (fwd, may be NULL)
+ *   sum_a      device float2 [B] = sum_j d_j e^{-i kappa2 j} (fwd out, may be NULL;
+ *              the backward needs it)
+ *   grad_fit   device float [B] upstream gradient dL/df (NULL = all ones)
+ *   grad_theta device float [B][ld_grad] out: dL/dtheta = grad_fit * df/dtheta
+ * Phasor table as for qpm_eval (cached per problem).  Errors: N < 1, B < 1,
+ * ld < N, NULL outputs -> QPM_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float *theta, int64_t ld,
+                                int32_t B, float *d_eff, float *fit, float *sum_a,
+                                qpm_stream_t stream);
+qpm_status qpm_deff_relaxed_bwd(const qpm_problem *prob, const float *theta, int64_t ld,
+                                int32_t B, const float *d_eff, const float *sum_a,
+                                const float *grad_fit, float *grad_theta, int64_t ld_grad,
+                                qpm_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Optimiser state: n_inst independent HWSDA instances (uneven N, kappa, NP
  * allowed), all resident on the current device.
  *   qpm_create   allocates the state (library-owned device memory) and returns
@@ -131,7 +158,8 @@ qpm_status qpm_release_caches(void);
  *   qpm_init     Step 1 of Sec. 3.2: phasor tables, x_ij = U(-1,1) (Sec. 2.2.1
  *                step 1) and the fitness of every individual; generation := 0.
  *   qpm_step     one generation (Sec. 3.2 Steps 2-6) of every instance.
- *   qpm_run      `generations` generations in the given QPM_RUN_* mode.
+ *   qpm_run      `generations` generations in the given QPM_RUN_* mode (every
+ *                instance advances by the same count).
  *                QPM_RUN_PERSISTENT returns QPM_ERR_TIMEOUT if a bounded
  *                device-side wait gave up (checked after synchronising the stream).
  *   qpm_destroy  frees the state (synchronises the device first).
@@ -162,6 +190,17 @@ qpm_status qpm_get_population(qpm_state *st, int32_t inst, float *genes_out, int
  *   (each may be NULL), index_out device int32 [1] (may be NULL). */
 qpm_status qpm_get_best(qpm_state *st, int32_t inst, float *genes_out, double *d_eff64_out,
                         float *fit_out, int32_t *index_out, qpm_stream_t stream);
+
+/* Gradient polish of the three best individuals of instance `inst` (build
+ * add-on; the paper has no counterpart): theta = tau x, `steps` ascent steps
+ * theta += lr g / max_j |g_j| with g the adjoint of the relaxed fitness
+ * (qpm_deff_relaxed_*), then x' = clamp(theta / tau, -1, 1); x' replaces x only if
+ * its +-1 fitness is >= the current one.  accepted_out (device int32 [3], may be
+ * NULL) receives 1 where a leader was replaced.  Allocates a small state-owned
+ * scratch on first use (call once before any stream capture).  Errors: steps < 0,
+ * lr < 0 or tau <= 0 -> QPM_ERR_ARG. */
+qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t steps, float lr, float tau,
+                              int32_t *accepted_out, qpm_stream_t stream);
 
 /* Threads per individual the state uses for instance `inst` (host int32 out). */
 qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out);

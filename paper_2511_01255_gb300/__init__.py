@@ -15,13 +15,13 @@ from . import build_lib
 
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc",
-    "qpm_release_caches",
+    "qpm_release_caches", "qpm_deff_relaxed_fwd", "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
-    "qpm_get_population", "qpm_get_best", "qpm_set_trace", "qpm_set_wait_timeout_ns",
-    "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT",
+    "qpm_get_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
+    "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
 ]
 
-RUN_LAUNCHES, RUN_GRAPH, RUN_PERSISTENT = 0, 1, 2
+RUN_LAUNCHES, RUN_GRAPH, RUN_PERSISTENT, RUN_BATCHED = 0, 1, 2, 3
 STATUS = {0: "QPM_OK", 1: "QPM_ERR_ARG", 2: "QPM_ERR_CUDA", 3: "QPM_ERR_TIMEOUT",
           4: "QPM_ERR_UNSUPPORTED", 5: "QPM_ERR_STATE"}
 
@@ -64,6 +64,8 @@ def lib(build=True):
             "qpm_eval_packed": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_eval_noalloc": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_release_caches": ([], ctypes.c_int),
+            "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
+            "qpm_deff_relaxed_bwd": ([_P, _P, i64, i32, _P, _P, _P, _P, i64, _P], ctypes.c_int),
             "qpm_create": ([_P, _P, i32, _P], ctypes.c_int),
             "qpm_init": ([_P, _P], ctypes.c_int),
             "qpm_step": ([_P, _P], ctypes.c_int),
@@ -76,6 +78,8 @@ def lib(build=True):
             "qpm_set_trace": ([_P, i32, _P], ctypes.c_int),
             "qpm_set_wait_timeout_ns": ([_P, u64], ctypes.c_int),
             "qpm_solve": ([_P, _P, i32, _P, _P, _P], ctypes.c_int),
+            "qpm_polish_leaders": ([_P, i32, i32, ctypes.c_float, ctypes.c_float, _P, _P],
+                                   ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -139,6 +143,65 @@ def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, s
                                   int(compensated), _stream(stream)))
 
 
+def qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, d_eff, fit=None, sum_a=None, stream=None):
+    p = _problem(N, kappa1, kappa2)
+    B, ld = _rows(theta, "theta")
+    _check(lib().qpm_deff_relaxed_fwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff), _ptr(fit),
+                                      _ptr(sum_a), _stream(stream)))
+
+
+def qpm_deff_relaxed_bwd(N, kappa1, kappa2, theta, d_eff, sum_a, grad_fit, grad_theta,
+                         stream=None):
+    p = _problem(N, kappa1, kappa2)
+    B, ld = _rows(theta, "theta")
+    _, ldg = _rows(grad_theta, "grad_theta")
+    _check(lib().qpm_deff_relaxed_bwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff),
+                                      _ptr(sum_a), _ptr(grad_fit), _ptr(grad_theta), ldg,
+                                      _stream(stream)))
+
+
+def _relaxed_function():
+    import torch
+
+    class QpmDeff(torch.autograd.Function):
+        """f = |d_eff|^2 of each row of theta (d = tanh(theta)); backward is the
+        library's adjoint kernel (argument marshalling only)."""
+
+        @staticmethod
+        def forward(ctx, theta, kappa1, kappa2):
+            theta = theta.contiguous()
+            B, N = theta.shape
+            D = torch.empty((B, 2), dtype=torch.float32, device=theta.device)
+            f = torch.empty(B, dtype=torch.float32, device=theta.device)
+            A = torch.empty((B, 2), dtype=torch.float32, device=theta.device)
+            qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, D, f, A)
+            ctx.save_for_backward(theta, D, A)
+            ctx.kappa = (kappa1, kappa2)
+            return f
+
+        @staticmethod
+        def backward(ctx, gf):
+            theta, D, A = ctx.saved_tensors
+            B, N = theta.shape
+            g = torch.empty_like(theta)
+            qpm_deff_relaxed_bwd(N, ctx.kappa[0], ctx.kappa[1], theta, D, A,
+                                 gf.contiguous().to(torch.float32), g)
+            return g, None, None
+
+    return QpmDeff
+
+
+_QpmDeff = None
+
+
+def deff_relaxed(theta, kappa1, kappa2):
+    """Differentiable f = |d_eff|^2 per row of theta (float32 CUDA [B, N])."""
+    global _QpmDeff
+    if _QpmDeff is None:
+        _QpmDeff = _relaxed_function()
+    return _QpmDeff.apply(theta, float(kappa1), float(kappa2))
+
+
 def qpm_release_caches():
     _check(lib().qpm_release_caches())
 
@@ -191,6 +254,11 @@ def qpm_get_best(st, inst, genes_out=None, d_eff64_out=None, fit_out=None, index
                  stream=None):
     _check(lib().qpm_get_best(st, int(inst), _ptr(genes_out), _ptr(d_eff64_out), _ptr(fit_out),
                               _ptr(index_out), _stream(stream)))
+
+
+def qpm_polish_leaders(st, inst=0, steps=8, lr=0.5, tau=3.0, accepted_out=None, stream=None):
+    _check(lib().qpm_polish_leaders(st, int(inst), int(steps), float(lr), float(tau),
+                                    _ptr(accepted_out), _stream(stream)))
 
 
 def qpm_set_trace(st, inst, trace):

@@ -181,7 +181,7 @@ qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **t
     const int32_t Npad = (p->N + 3) & ~3;
     QPM_CUDA(cudaMalloc(&e.table, sizeof(float4) * (size_t)Npad));
     QPM_CUDA(cudaMalloc(&e.part, sizeof(double2) * (size_t)table_part_count(Npad)));
-    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 2));
+    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 3));
     QPM_CUDA(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
     TableSpec s{p->N, Npad, 1, Npad, p->kappa1, p->kappa2};
     qpm_status st = launch_table(s, e.table, e.part, e.konst, nullptr, stream);
@@ -360,6 +360,12 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
     k_eval_combine<false><<<(NP + cb - 1) / cb, cb, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
   return QPM_OK;
+}
+
+qpm_status qpm::cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
+                             const float2 **konst) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return get_table(p, stream, table, konst);
 }
 
 extern "C" qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld,

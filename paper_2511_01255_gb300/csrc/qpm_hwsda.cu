@@ -168,11 +168,12 @@ static __global__ void k_init(InstDev I) {
 
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
-template <bool COMP, bool NC, bool TS, bool DUAL>
+// WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
                                             const float4 *tbl, int g, int i,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh) {
-  const int t = threadIdx.x;
+  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
@@ -202,7 +203,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
     if (k4 & 1) acc.fold();
   }
-  const Mono m = block_reduce(acc.get(), sh);
+  const Mono m = WT ? warp_reduce(acc.get()) : block_reduce(acc.get(), sh);
   unsigned long long key = 0ull;
   if (t == 0) {
     const float2 D = deff_from(m, I.konst[0], I.konst[1]);
@@ -220,10 +221,10 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 }
 
 // ------------------------------------------------ Step 4-5: GWO + selection
-template <bool COMP, bool NC, bool TS, bool DUAL>
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
 __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
                                int i, int32_t *sel, int la, int lb, int ld, Mono *sh) {
-  const int t = threadIdx.x;
+  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
   const int si = sel[i], sa = sel[la], sb = sel[lb], sd = sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
@@ -276,7 +277,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
     push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
     if (k4 & 1) acc.fold();
   }
-  const Mono m = block_reduce(acc.get(), sh);
+  const Mono m = WT ? warp_reduce(acc.get()) : block_reduce(acc.get(), sh);
   if (t == 0) {
     const float2 D = deff_from(m, I.konst[0], I.konst[1]);
     const float f = fit_of(D);
@@ -491,6 +492,90 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *I.gen = g_end;
 }
 
+// ------------------------------------------------------------ batched form
+// Many independent instances in one launch.  Each CTA takes whole instances from
+// a queue (largest first) and runs them for the requested generations by itself:
+// every warp is the team of one individual (instances use T = 32), and the two
+// dependencies of a generation are CTA barriers.  No CTA ever waits for another.
+static constexpr int BATCH_WARPS = 16;
+
+// one instance, generations [*gen, min(*gen + gens, G)), by the whole CTA
+template <bool COMP, bool TS>
+__device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned long long *wk,
+                               int32_t *lead_sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (TS) {
+    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
+  }
+  const float4 *tbl = TS ? (const float4 *)dyn : I.table;
+  const PhiloxKey K = philox_schedule(I.key);
+  int g = *I.gen;
+  const int g_end = min(g + gens, I.G);
+  __syncthreads();
+  for (; g < g_end; ++g) {
+    const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
+    int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
+    unsigned long long k0 = 0, k1 = 0, k2 = 0;
+    for (int i = warp; i < I.NP; i += nw) {
+      const unsigned long long key =
+          de_individual<COMP, false, TS, false, true>(I, K, tbl, g, i, sel_in, sel_out, nullptr);
+      if (lane == 0) top3_insert(k0, k1, k2, key);
+    }
+    if (lane == 0) {
+      wk[3 * warp] = k0;
+      wk[3 * warp + 1] = k1;
+      wk[3 * warp + 2] = k2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // Step 3: leaders of this instance
+      for (int w = 1; w < nw; ++w) {
+        top3_insert(k0, k1, k2, wk[3 * w]);
+        top3_insert(k0, k1, k2, wk[3 * w + 1]);
+        top3_insert(k0, k1, k2, wk[3 * w + 2]);
+      }
+      lead_sh[0] = key_index(k0);
+      lead_sh[1] = key_index(k1);
+      lead_sh[2] = key_index(k2);
+      I.lead[0] = lead_sh[0];
+      I.lead[1] = lead_sh[1];
+      I.lead[2] = lead_sh[2];
+    }
+    __syncthreads();
+    const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
+    for (int i = warp; i < I.NP; i += nw) {
+      if (i == la || i == lb || i == ld) continue;
+      gwo_individual<COMP, false, TS, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld, nullptr);
+    }
+    if (I.trace && threadIdx.x < 3) {
+      const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
+      I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *I.gen = g_end;
+  __syncthreads();
+}
+
+template <bool TS>
+static __global__ void __launch_bounds__(BATCH_WARPS * 32, 1)
+    k_batch(const InstDev *__restrict__ insts, const int32_t *__restrict__ order, int n_inst,
+            unsigned *queue, int gens) {
+  extern __shared__ float4 dyn[];
+  __shared__ unsigned long long wk[3 * BATCH_WARPS];
+  __shared__ int32_t lead_sh[3];
+  __shared__ int job_sh;
+  for (;;) {
+    if (threadIdx.x == 0) job_sh = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int job = job_sh;
+    __syncthreads();
+    if (job >= n_inst) break;
+    const InstDev I = insts[order[job]];
+    if (I.compensated) batch_instance<true, TS>(I, gens, dyn, wk, lead_sh);
+    else batch_instance<false, TS>(I, gens, dyn, wk, lead_sh);
+  }
+}
+
 // ------------------------------------------------ outputs: best, FP64, layout
 static __global__ void k_best(InstDev I, int32_t *index_out) {
   __shared__ unsigned long long shk[3 * 32];
@@ -575,6 +660,95 @@ static __global__ void k_recheck64(InstDev I, double *d64_out, float *fit_out) {
   }
 }
 
+// ------------------------------------------------------------ leader polish
+// The three best individuals are polished on the relaxed fitness: theta = tau x,
+// `steps` ascent steps theta += lr g / max|g| (g = df/dtheta from the adjoint
+// kernels), then x' = clamp(theta / tau, -1, 1) is re-mapped to +-1 and kept
+// only if its +-1 fitness is at least the current one (the same greedy rule as
+// Sec. 2.2.1 step 4).
+static __global__ void k_polish_pick(InstDev I, int32_t *lead_out) {
+  __shared__ unsigned long long shk[3 * 32];
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) top3_insert(k0, k1, k2, lead_key(I.fit[i], i));
+  block_top3(k0, k1, k2, shk);
+  if (threadIdx.x == 0) {
+    lead_out[0] = key_index(k0);
+    lead_out[1] = key_index(k1);
+    lead_out[2] = key_index(k2);
+  }
+}
+
+__device__ __forceinline__ size_t perm_pos_of(const InstDev &I, int j) {
+  const int t = j / I.c, e = j - t * I.c;
+  return ((size_t)(e >> 2) * I.T + t) * 4 + (e & 3);
+}
+
+static __global__ void k_polish_theta(InstDev I, const int32_t *lead, float tau, float *theta) {
+  const int k = blockIdx.x, i = lead[k];
+  const int32_t *sel = (*I.gen & 1) ? I.sel1 : I.sel0;
+  const float *row = row_ptr(I, i, sel[i]);
+  for (int j = threadIdx.x; j < I.N; j += blockDim.x)
+    theta[(size_t)k * I.Npad + j] = __fmul_rn(tau, row[perm_pos_of(I, j)]);
+}
+
+static __global__ void k_polish_step(int N, int64_t ld, float lr, float *theta, const float *grad) {
+  __shared__ float red[32];
+  const float *g = grad + (size_t)blockIdx.x * ld;
+  float *th = theta + (size_t)blockIdx.x * ld;
+  float m = 0.f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) m = fmaxf(m, fabsf(g[j]));
+  for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    red[0] = m;
+  }
+  __syncthreads();
+  m = red[0];
+  if (m > 0.f && isfinite(m)) {
+    const float s = lr / m;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) th[j] = fmaf(s, g[j], th[j]);
+  }
+}
+
+// one CTA (team of T threads) per leader
+template <bool COMP>
+static __global__ void k_polish_accept(InstDev I, const int32_t *lead, float tau,
+                                       const float *theta, int32_t *accepted) {
+  extern __shared__ Mono sh[];
+  const int k = blockIdx.x, i = lead[k], t = threadIdx.x;
+  int32_t *sel = (*I.gen & 1) ? I.sel1 : I.sel0;
+  const int si = sel[i];
+  float *out = row_ptr(I, i, si ^ 1);
+  const float *th = theta + (size_t)k * I.Npad;
+  Acc<COMP> acc;
+  acc.zero();
+  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+    const int j0 = t * I.c + 4 * k4;
+    float4 x;
+    x.x = j0 < I.N ? clamp1(__fdiv_rn(th[j0], tau)) : 0.f;
+    x.y = j0 + 1 < I.N ? clamp1(__fdiv_rn(th[j0 + 1], tau)) : 0.f;
+    x.z = j0 + 2 < I.N ? clamp1(__fdiv_rn(th[j0 + 2], tau)) : 0.f;
+    x.w = j0 + 3 < I.N ? clamp1(__fdiv_rn(th[j0 + 3], tau)) : 0.f;
+    *(float4 *)(out + ((size_t)k4 * I.T + t) * 4) = x;
+    push4<COMP, false>(acc, I.table, I.T, k4, t, x);
+    if (k4 & 1) acc.fold();
+  }
+  const Mono m = block_reduce(acc.get(), sh);
+  if (t == 0) {
+    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
+    const float f = fit_of(D);
+    const bool accept = f >= I.fit[i];
+    if (accept) {
+      sel[i] = si ^ 1;
+      I.fit[i] = f;
+      I.dval[i] = D;
+    }
+    if (accepted) accepted[k] = accept ? 1 : 0;
+  }
+}
+
 }  // namespace qpm
 
 // =========================================================== host: the state
@@ -594,8 +768,16 @@ struct qpm_state {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_n = -1;
-  unsigned *bar = nullptr;  // [0] count, [1] flag, [2] err
+  unsigned *bar = nullptr;  // [0] count, [1] unused, [2] err, [3] batch queue
   unsigned long long timeout_ns = 5000000000ull;
+  InstDev *d_insts = nullptr;  // device copy of the descriptors (batched form)
+  int32_t *d_order = nullptr;  // instances by decreasing work
+  size_t batch_smem = 0;       // 0: table read from global memory
+  int grid_batch = 0;
+  cudaGraphExec_t gexec_b = nullptr;
+  int graph_b_n = -1;
+  void *polish = nullptr;  // leader-polish scratch (allocated on first use)
+  size_t polish_bytes = 0;
 };
 
 namespace qpm {
@@ -619,6 +801,7 @@ struct Variant {
 };
 
 static constexpr int TS_MAX_NPAD = 4096;  // phasor table in shared memory up to 64 KB
+static constexpr size_t BATCH_TS_MAX_BYTES = 160 * 1024;  // batched form: table in smem up to 160 KB
 
 template <bool COMP, bool DUAL>
 static Variant variant2(const InstDev &I) {
@@ -642,11 +825,18 @@ static Variant variant_of(const InstDev &I) {
   return dual ? variant2<false, true>(I) : variant2<false, false>(I);
 }
 
+// the shared-memory attribute of a persistent variant is the same for every
+// instance (the largest any instance can need), so occupancy figures computed
+// for one instance stay valid after another instance is set up
+static size_t persist_smem_cap(bool ts) {
+  return smem_bytes(256) + (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
+}
+
 static qpm_status occupancy(const InstDev &I, int *plain, int *persist) {
   const Variant v = variant_of(I);
   int a = 0, a2 = 0, b = 0;
   QPM_CUDA(cudaFuncSetAttribute(v.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)v.persist_smem));
+                                (int)persist_smem_cap(I.Npad <= TS_MAX_NPAD)));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, I.T, v.smem));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, v.gwo, I.T, v.smem));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.persist, I.T, v.persist_smem));
@@ -723,7 +913,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     InstDev &I = st->h[k];
     memset(&I, 0, sizeof(I));
     I.N = p.N;
-    I.T = q.team ? q.team : choose_team(p.N);
+    I.T = q.team ? q.team : (n_inst > 1 ? 32 : choose_team(p.N));
     I.Npad = (int32_t)align_up((size_t)p.N, 4 * (size_t)I.T);
     I.c = I.Npad / I.T;
     I.NP = q.NP;
@@ -753,6 +943,10 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += align_up(3 * NP * sizeof(unsigned long long), 256);
     total += 256 + 256 + 256;  // ctr, gen, best
   }
+  const size_t desc_off = total;
+  total += align_up(sizeof(InstDev) * (size_t)n_inst, 256);
+  const size_t order_off = total;
+  total += align_up(sizeof(int32_t) * (size_t)n_inst, 256);
   total += 256;  // barrier words
   e = cudaMalloc(&st->arena, total);
   if (e != cudaSuccess) { delete st; return cuda_fail(e, "cudaMalloc(state arena)"); }
@@ -770,7 +964,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.dval = (float2 *)take(NP * sizeof(float2));
     I.table = (float4 *)take(Np * sizeof(float4));
     I.tpart = (double2 *)take((size_t)table_part_count(I.Npad) * sizeof(double2));
-    I.konst = (float2 *)take(2 * sizeof(float2));
+    I.konst = (float2 *)take(3 * sizeof(float2));
     I.konst64 = (double2 *)take(3 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(3 * NP * sizeof(unsigned long long));
@@ -779,6 +973,31 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.best = (int32_t *)take(sizeof(int32_t));
   }
   st->bar = (unsigned *)((char *)st->arena + total - 256);
+  st->d_insts = (InstDev *)((char *)st->arena + desc_off);
+  st->d_order = (int32_t *)((char *)st->arena + order_off);
+  {
+    // largest instances first (longest-processing-time order for the batch queue)
+    std::vector<int32_t> order(n_inst);
+    for (int k = 0; k < n_inst; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return (long long)st->h[a].NP * st->h[a].Npad > (long long)st->h[b].NP * st->h[b].Npad;
+    });
+    e = cudaMemcpy(st->d_order, order.data(), sizeof(int32_t) * n_inst, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(st->d_insts, st->h.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaMemcpy"); }
+    int maxpad = 0;
+    for (int k = 0; k < n_inst; ++k) maxpad = std::max(maxpad, st->h[k].Npad);
+    st->batch_smem = ((size_t)maxpad * sizeof(float4) <= BATCH_TS_MAX_BYTES)
+                         ? (size_t)maxpad * sizeof(float4) : 0;
+    const void *kb = st->batch_smem ? (const void *)k_batch<true> : (const void *)k_batch<false>;
+    e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->batch_smem);
+    int occ = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb, BATCH_WARPS * 32, st->batch_smem);
+    if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "batch set-up"); }
+    st->grid_batch = std::max(1, occ) * nsm;
+  }
   e = cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaStreamCreate"); }
   *out = st;
@@ -793,6 +1012,8 @@ extern "C" qpm_status qpm_set_trace(qpm_state *st, int32_t inst, float *trace) {
     st->gexec = nullptr;
     st->graph_n = -1;
   }
+  cudaError_t e = cudaMemcpy(st->d_insts + inst, &st->h[inst], sizeof(InstDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(descriptor)");
   return QPM_OK;
 }
 
@@ -877,6 +1098,37 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
       st->g += generations;
       return fail(QPM_ERR_TIMEOUT, "persistent kernel: a bounded grid-barrier wait gave up");
     }
+  } else if (mode == QPM_RUN_BATCHED) {
+    for (int k = 0; k < st->n; ++k)
+      if (st->h[k].T != 32)
+        return fail(QPM_ERR_UNSUPPORTED, "batched form needs 32 threads per individual (team 32)");
+    if (st->graph_b_n != generations || !st->gexec_b) {
+      if (st->gexec_b) {
+        cudaGraphExecDestroy(st->gexec_b);
+        st->gexec_b = nullptr;
+      }
+      QPM_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaMemsetAsync(st->bar + 3, 0, sizeof(unsigned), st->cap_stream);
+      if (e == cudaSuccess) {
+        int n = st->n, gens = generations;
+        unsigned *queue = st->bar + 3;
+        void *args[] = {&st->d_insts, &st->d_order, &n, &queue, &gens};
+        const void *kb = st->batch_smem ? (const void *)k_batch<true> : (const void *)k_batch<false>;
+        e = cudaLaunchKernel(kb, dim3(st->grid_batch), dim3(BATCH_WARPS * 32), args, st->batch_smem,
+                             st->cap_stream);
+      }
+      cudaGraph_t graph = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(st->cap_stream, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(e != cudaSuccess ? e : e2, "capturing the batched launch");
+      }
+      e = cudaGraphInstantiate(&st->gexec_b, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      st->graph_b_n = generations;
+    }
+    QPM_CUDA(cudaGraphLaunch(st->gexec_b, s));
   } else {
     return fail(QPM_ERR_ARG, "qpm_run: unknown mode");
   }
@@ -928,6 +1180,8 @@ extern "C" qpm_status qpm_destroy(qpm_state *st) {
   if (!st) return QPM_OK;
   cudaDeviceSynchronize();
   if (st->gexec) cudaGraphExecDestroy(st->gexec);
+  if (st->gexec_b) cudaGraphExecDestroy(st->gexec_b);
+  if (st->polish) cudaFree(st->polish);
   if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
   cudaFree(st->arena);
   delete st;
@@ -937,6 +1191,51 @@ extern "C" qpm_status qpm_destroy(qpm_state *st) {
 extern "C" qpm_status qpm_set_wait_timeout_ns(qpm_state *st, uint64_t ns) {
   if (!st) return fail(QPM_ERR_ARG, "NULL state");
   st->timeout_ns = ns;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t steps, float lr,
+                                         float tau, int32_t *accepted_out, qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad state or instance");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  if (steps < 0 || !(lr >= 0.f) || !(tau > 0.f))
+    return fail(QPM_ERR_ARG, "qpm_polish_leaders: need steps >= 0, lr >= 0, tau > 0");
+  const InstDev &I = st->h[inst];
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t Np = (size_t)I.Npad;
+  const size_t need = 256 + align_up(3 * Np * sizeof(float), 256) * 2 + 256 * 3;
+  if (st->polish_bytes < need) {
+    if (st->polish) {
+      QPM_CUDA(cudaDeviceSynchronize());
+      QPM_CUDA(cudaFree(st->polish));
+      st->polish = nullptr;
+      st->polish_bytes = 0;
+    }
+    QPM_CUDA(cudaMalloc(&st->polish, need));
+    st->polish_bytes = need;
+  }
+  char *p = (char *)st->polish;
+  int32_t *lead = (int32_t *)p;
+  float *theta = (float *)(p + 256);
+  float *grad = (float *)(p + 256 + align_up(3 * Np * sizeof(float), 256));
+  float *D = (float *)(p + 256 + 2 * align_up(3 * Np * sizeof(float), 256));
+  float *A = D + 256 / sizeof(float);
+  k_polish_pick<<<1, 256, 0, s>>>(I, lead);
+  k_polish_theta<<<3, 256, 0, s>>>(I, lead, tau, theta);
+  QPM_CUDA(cudaGetLastError());
+  const qpm_problem prob = st->probs[inst];
+  for (int k = 0; k < steps; ++k) {
+    qpm_status r = qpm_deff_relaxed_fwd(&prob, theta, (int64_t)Np, 3, D, nullptr, A, stream);
+    if (r != QPM_OK) return r;
+    r = qpm_deff_relaxed_bwd(&prob, theta, (int64_t)Np, 3, D, A, nullptr, grad, (int64_t)Np, stream);
+    if (r != QPM_OK) return r;
+    k_polish_step<<<3, 256, 0, s>>>(I.N, (int64_t)Np, lr, theta, grad);
+  }
+  if (I.compensated)
+    k_polish_accept<true><<<3, I.T, smem_bytes(I.T), s>>>(I, lead, tau, theta, accepted_out);
+  else
+    k_polish_accept<false><<<3, I.T, smem_bytes(I.T), s>>>(I, lead, tau, theta, accepted_out);
+  QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }
 

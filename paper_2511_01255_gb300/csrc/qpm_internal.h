@@ -27,11 +27,16 @@ struct TableSpec {
   double kappa1, kappa2;
 };
 
-// float2 konst[2] = {phi1*phi2, cdiag}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
+// float2 konst[3] = {phi1*phi2, cdiag, psi}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
 // part: scratch of table_part_count(Npad) double2
 int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
                         double2 *konst64, cudaStream_t stream);
+
+// natural-order phasor table and FP32 constants of a problem, cached per
+// (device, N, kappa1, kappa2); built on `stream` on a miss (caller holds no lock)
+qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
+                        const float2 **konst);
 
 // current device's SM count (cached per device)
 int sm_count();

@@ -92,6 +92,7 @@ static __global__ void k_table_finalize(int nparts, const double2 *__restrict__ 
   const double2 cdiag = make_double2(ps.x * sr - ps.y * si, ps.x * si + ps.y * sr);
   konst[0] = make_float2((float)phi12.x, (float)phi12.y);
   konst[1] = make_float2((float)cdiag.x, (float)cdiag.y);
+  konst[2] = make_float2((float)ps.x, (float)ps.y);
   if (konst64) {
     konst64[0] = phi12;
     konst64[1] = cdiag;

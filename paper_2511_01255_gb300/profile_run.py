@@ -21,8 +21,10 @@ def main():
     from paper_2511_01255_gb300 import workloads as W
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="paper", choices=["small", "paper", "precision", "eval"])
-    ap.add_argument("--form", default="launches", choices=["launches", "graph", "persistent"])
+    ap.add_argument("--workload", default="paper",
+                    choices=["small", "paper", "precision", "eval", "batch"])
+    ap.add_argument("--form", default="launches",
+                    choices=["launches", "graph", "persistent", "batched"])
     ap.add_argument("--gens", type=int, default=20)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--comp", type=int, default=-1, help="override the compensated flag")
@@ -43,11 +45,20 @@ def main():
         torch.cuda.synchronize()
         print(f"eval N={N} NP={NP}: {e0.elapsed_time(e1) / a.reps:.3f} ms per call")
         return
-    c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
-    comp = c["compensated"] if a.comp < 0 else a.comp
-    prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
-    form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT}[a.form]
-    st = q.State([(c["N"], c["kappa1"], c["kappa2"])], [prm])
+    form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT,
+            "batched": q.RUN_BATCHED}[a.form]
+    if a.workload == "batch":
+        inst = W.batched_instances(512)
+        comp = 0 if a.comp < 0 else a.comp
+        st = q.State([(c["N"], c["kappa1"], c["kappa2"]) for c in inst],
+                      [q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
+                       for c in inst])
+        c = {"name": "batch512_g1000"}
+    else:
+        c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
+        comp = c["compensated"] if a.comp < 0 else a.comp
+        prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
+        st = q.State([(c["N"], c["kappa1"], c["kappa2"])], [prm])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tot = 0.0
     for _ in range(a.reps):

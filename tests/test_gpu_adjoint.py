@@ -1,0 +1,133 @@
+"""GPU parity of the relaxed fitness and its hand-written adjoint, and of the
+leader polish built on them.
+
+Relaxed rows: d = tanh(theta); f = |d_eff|^2 (Sec. 2.1 integral for real d).
+Gradient tolerance (FP32 against FP64): |g - g_ref| <= 1e-4 * max(|g_ref|,
+max over the compared coordinates of |g_ref|).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import TOL_D, deff_err, fit_err
+
+pytestmark = pytest.mark.gpu
+
+K1, K2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+TOL_G = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01255_gb300 as q
+    q.lib()
+    return q
+
+
+def fwd_bwd(q, theta_np, k1, k2, gf=None):
+    import torch
+    th = torch.from_numpy(theta_np).cuda()
+    B, N = th.shape
+    D = torch.empty((B, 2), device="cuda")
+    f = torch.empty(B, device="cuda")
+    A = torch.empty((B, 2), device="cuda")
+    q.qpm_deff_relaxed_fwd(N, k1, k2, th, D, f, A)
+    g = torch.empty_like(th)
+    gft = None if gf is None else torch.from_numpy(gf.astype(np.float32)).cuda()
+    q.qpm_deff_relaxed_bwd(N, k1, k2, th, D, A, gft, g)
+    torch.cuda.synchronize()
+    return D.cpu().numpy(), f.cpu().numpy(), g.cpu().numpy()
+
+
+def grad_err(g, ref):
+    scale = np.maximum(np.abs(ref), np.abs(ref).max())
+    return np.max(np.abs(g - ref) / scale)
+
+
+@pytest.mark.parametrize("N", [1, 5, 255, 256, 257, 1000, 4096])
+def test_relaxed_fwd_bwd_against_oracle(q, orc, N):
+    from paper_2511_01255_gb300 import workloads as W
+    B = 5
+    theta = W.relaxed_theta(B, N, seed=N)
+    D, f, g = fwd_bwd(q, theta, K1, K2)
+    for r in range(B):
+        ref_g, ref_D = orc.grad_relaxed(theta[r].astype(np.float64), K1, K2)
+        assert deff_err(D[r:r + 1], np.array([ref_D]), N).max() < TOL_D
+        assert grad_err(g[r], ref_g) < TOL_G
+
+
+def test_finite_differences_and_euler_full_size(q, orc):
+    """B = 4096 rows of N = 4096, theta ~ N(0, 1): all rows on the GPU; FP64 central
+    differences (h = 1e-6) on 64 random coordinates of two rows, the oracle's exact
+    gradient on four rows, Euler's identity on every row."""
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.RELAXED
+    B, N = c["B"], c["N"]
+    theta = W.relaxed_theta(B, N, seed=c["seed"])
+    D, f, g = fwd_bwd(q, theta, c["kappa1"], c["kappa2"])
+    rng = np.random.default_rng(5)
+    for r in (0, B - 1):
+        idx = np.sort(rng.choice(N, 64, replace=False))
+        fd = orc.fd_grad(theta[r].astype(np.float64), c["kappa1"], c["kappa2"], idx, h=1e-6)
+        assert grad_err(g[r, idx], fd) < TOL_G
+    for r in (1, 777, 2048, 4000):
+        ref_g, ref_D = orc.grad_relaxed(theta[r].astype(np.float64), c["kappa1"], c["kappa2"])
+        assert grad_err(g[r], ref_g) < TOL_G
+        assert fit_err(f[r:r + 1], np.array([abs(ref_D) ** 2]), N).max() < 2 * TOL_D
+    # f is homogeneous of degree 4 in d: sum_k d_k df/dd_k = 4 f (FP64 sum of FP32 terms)
+    d = np.tanh(theta.astype(np.float64))
+    euler = np.sum(d * g / (1.0 - d * d), axis=1)
+    scale = np.abs(d * g / (1.0 - d * d)).sum(axis=1)
+    assert np.max(np.abs(euler - 4 * f) / np.maximum(scale, 4 * f)) < 1e-4
+
+
+def test_autograd_function(q, orc):
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    N = 700
+    theta = W.relaxed_theta(3, N, seed=2)
+    th = torch.from_numpy(theta).cuda().requires_grad_(True)
+    w = torch.tensor([0.5, -2.0, 1.0], device="cuda")
+    loss = (q.deff_relaxed(th, K1, K2) * w).sum()
+    loss.backward()
+    g = th.grad.cpu().numpy()
+    for r in range(3):
+        ref_g, _ = orc.grad_relaxed(theta[r].astype(np.float64), K1, K2)
+        assert grad_err(g[r], float(w[r]) * ref_g) < TOL_G
+
+
+def test_polish_leaders(q, orc):
+    """After polishing, every leader's fitness is at least what it was, its new genes
+    evaluate (oracle, FP64) to the stored fitness, and nobody else changed."""
+    import torch
+    N, NP = 1000, 32
+    prm = q.Params(NP, 50, 0.5, 0.9, 4, 0, 1)
+    with q.State([(N, K1, K2)], [prm]) as st:
+        st.init()
+        st.run(10, q.RUN_GRAPH)
+        X0, f0, _ = st.population()
+        acc = torch.zeros(3, dtype=torch.int32, device="cuda")
+        q.qpm_polish_leaders(st.h, 0, steps=8, lr=0.5, tau=3.0, accepted_out=acc)
+        X1, f1, _ = st.population()
+        torch.cuda.synchronize()
+        X0, f0, X1, f1 = X0.cpu().numpy(), f0.cpu().numpy(), X1.cpu().numpy(), f1.cpu().numpy()
+        lead = orc.top3(f0)
+        others = np.setdiff1d(np.arange(NP), lead)
+        assert np.array_equal(X0[others], X1[others]) and np.array_equal(f0[others], f1[others])
+        assert np.all(f1[lead] >= f0[lead])
+        ref = np.abs(orc.deff_genes(X1[lead], K1, K2)) ** 2
+        assert fit_err(f1[lead], ref, N).max() < 2 * TOL_D
+        a = acc.cpu().numpy()
+        assert set(np.unique(a)) <= {0, 1}
+        for k in range(3):
+            if not a[k]:  # rejected: the leader is untouched
+                assert np.array_equal(X0[lead[k]], X1[lead[k]]) and f1[lead[k]] == f0[lead[k]]
+        # the run carries on from the polished population
+        st.run(5, q.RUN_PERSISTENT)
+        X2, f2, _ = st.population()
+        torch.cuda.synchronize()
+        assert f2.cpu().numpy().max() >= f1.max()
