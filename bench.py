@@ -102,8 +102,27 @@ class ClockSampler:
 def algorithmic_lane_ops_per_gene_gen(compensated):
     """Lane instructions the method needs per gene and generation (documented in
     the design doc): Philox4x32-10 at 1.75 calls (80 ops each), 7 uniforms (3 ops),
-    DE update (7), GWO update (30), two fitness domain-evals (10 plain / 32 Kahan)."""
-    return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (32 if compensated else 10)
+    DE update (7), GWO update (30), two fitness domain-evals (10 plain; 14.25 with
+    Kahan compensation folded in every 8 domains)."""
+    return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
+
+
+def _time_cuda(fn, reps, flush=None):
+    """Mean seconds per call of fn() with CUDA events on the current stream."""
+    import torch
+    st = torch.cuda.current_stream()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1) / 1e3
+    return tot / reps
 
 
 def run_gpu(args):
@@ -119,6 +138,10 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     q.lib()
+    pk, pk_src = peaks()
+    nsm = torch.cuda.get_device_properties(lrank).multi_processor_count
+    peak_alu = nsm * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
+    peak_hbm = pk.get("hbm_gbs", 6800.0)
     c = W.PAPER_SCALE
     N, NP, G = c["N"], c["NP"], c["G"]
     # independent replicas: each rank designs its own crystal (seed = 1 + rank)
@@ -135,8 +158,9 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # ---------------------------------------------------------- headline workload
     results = {}
-    for mode_name, mode in (("plain_graph", q.RUN_GRAPH), ("persistent", q.RUN_PERSISTENT)):
+    for mode_name, mode in (("persistent", q.RUN_PERSISTENT), ("plain_graph", q.RUN_GRAPH)):
         st = q.State([prob], [prm])
         for _ in range(args.warmup):
             st.init()
@@ -173,30 +197,121 @@ def run_gpu(args):
         results[mode_name] = dict(s_per_step=t, wall=wall, clocks=clocks, best_f=best_f,
                                   launches_per_step=(3 + (2 * G if mode == q.RUN_GRAPH else 1)))
 
-    # dominant-kernel timing on its own stream: the persistent kernel alone
+    # dominant kernel: the persistent generation kernel alone, on its stream
     st = q.State([prob], [prm])
-    st.init()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     dur = []
     for _ in range(max(3, args.steps)):
         st.init()
-        flush.fill_(1.0)
-        e0.record(stream)
-        st.run(G, q.RUN_PERSISTENT)
-        e1.record(stream)
-        e1.synchronize()
-        dur.append(e0.elapsed_time(e1) / 1e3)
+        dur.append(_time_cuda(lambda: st.run(G, q.RUN_PERSISTENT), 1, flush))
     st.close()
     kdur = statistics.median(dur)
+    ops_gene_gen = algorithmic_lane_ops_per_gene_gen(c["compensated"])
+    achieved = ops_gene_gen * gene_gens / kdur / 1e12
+    best_mode = min(results, key=lambda k: results[k]["s_per_step"])
 
-    # end to end through the C ABI with host buffers (qpm_solve: create, init, run,
-    # best genes + FP64 d_eff back to the host)
+    # ------------------------------------------------ batched: 512 instances
+    inst = W.batched_instances(512)
+    probs_b = [(ci["N"], ci["kappa1"], ci["kappa2"]) for ci in inst]
+    prms_b = [q.Params(ci["NP"], ci["G"], ci["F"], ci["CR"], ci["seed"] + rank, 0, ci["compensated"])
+              for ci in inst]
+    Gb = inst[0]["G"]
+    gg_b = sum(ci["NP"] * ci["N"] for ci in inst) * Gb
+    ev_b = sum((2 * ci["NP"] - 3) * ci["N"] for ci in inst) * Gb + sum(ci["NP"] * ci["N"] for ci in inst)
+    stb = q.State(probs_b, prms_b)
+    stb.init()
+    stb.run(3, q.RUN_BATCHED)  # warm-up (graph instantiation, caches)
+    tb = []
+    for _ in range(min(2, args.steps)):
+        def one():
+            stb.init()
+            stb.run(Gb, q.RUN_BATCHED)
+        tb.append(_time_cuda(one, 1, flush))
+    t_batched = min(tb)
+    # the same batch in the per-instance persistent form, timed over 3 generations
+    stb.init()
+    stb.run(1, q.RUN_PERSISTENT)
+    t_inst3 = _time_cuda(lambda: stb.run(3, q.RUN_PERSISTENT), 1, flush)
+    stb.close()
+    batched = {
+        "workload": "512 instances, N~U[500,8000], NP in {64,128,256,512}, G=1000, plain FP32 scan",
+        "s_per_run": t_batched, "domain_evals_per_s": ev_b / t_batched,
+        "gene_gens_per_s": gg_b / t_batched,
+        "per_instance_persistent_s_per_gen": t_inst3 / 3,
+        "speedup_vs_per_instance_persistent": (t_inst3 / 3 * Gb) / t_batched,
+        "roofline": {"bound": "alu", "achieved": algorithmic_lane_ops_per_gene_gen(0) * gg_b / t_batched / 1e12,
+                     "peak": peak_alu, "unit": "T lane-ops/s",
+                     "frac": algorithmic_lane_ops_per_gene_gen(0) * gg_b / t_batched / 1e12 / peak_alu},
+    }
+
+    # --------------------------------------- precision: N = 1e5, NP = 1024, G = 500
+    cp = W.PRECISION
+    prec = {}
+    for comp in (1, 0):
+        pr = q.Params(cp["NP"], cp["G"], cp["F"], cp["CR"], cp["seed"] + rank, 0, comp)
+        stp = q.State([(cp["N"], cp["kappa1"], cp["kappa2"])], [pr])
+        stp.init()
+        stp.run(2, q.RUN_PERSISTENT)
+        stp.init()
+        tp = _time_cuda(lambda: stp.run(cp["G"], q.RUN_PERSISTENT), 1, None)
+        stp.close()
+        ggp = cp["NP"] * cp["N"] * cp["G"]
+        prec["compensated" if comp else "plain"] = {
+            "s_per_run": tp, "gene_gens_per_s": ggp / tp,
+            "domain_evals_per_s": (2 * cp["NP"] - 3) * cp["N"] * cp["G"] / tp,
+            "alu_frac": algorithmic_lane_ops_per_gene_gen(comp) * ggp / tp / 1e12 / peak_alu}
+    prec["workload"] = cp["name"]
+
+    # ---------------------------------- adjoint: B = 4096 rows of N = 4096, fwd + bwd
+    cr = W.RELAXED
+    th = torch.from_numpy(W.relaxed_theta(cr["B"], cr["N"], seed=cr["seed"])).cuda()
+    Dr = torch.empty((cr["B"], 2), device="cuda")
+    Ar = torch.empty((cr["B"], 2), device="cuda")
+    fr = torch.empty(cr["B"], device="cuda")
+    gr = torch.empty_like(th)
+
+    def fwd():
+        q.qpm_deff_relaxed_fwd(cr["N"], cr["kappa1"], cr["kappa2"], th, Dr, fr, Ar)
+
+    def bwd():
+        q.qpm_deff_relaxed_bwd(cr["N"], cr["kappa1"], cr["kappa2"], th, Dr, Ar, None, gr)
+
+    for _ in range(3):
+        fwd()
+        bwd()
+    t_f = _time_cuda(fwd, 10, flush)
+    t_b = _time_cuda(bwd, 10, flush)
+    elems = cr["B"] * cr["N"]
+    adjoint = {"workload": cr["name"], "fwd_us": t_f * 1e6, "bwd_us": t_b * 1e6,
+               "elements_per_s": elems / (t_f + t_b),
+               "roofline": {"bound": "hbm", "achieved": 12 * elems / (t_f + t_b) / 1e9,
+                            "peak": peak_hbm, "unit": "GB/s",
+                            "frac": 12 * elems / (t_f + t_b) / 1e9 / peak_hbm,
+                            "bytes_per_element": 12}}
+
+    # ------------------------------ qpm_eval: 1024 rows of N = 1e5 (genes, packed)
+    Ne, NPe = 100000, 1024
+    Xe = torch.rand((NPe, Ne), device="cuda") * 2 - 1
+    We = torch.randint(-2 ** 31, 2 ** 31 - 1, (NPe, (Ne + 31) // 32), dtype=torch.int32, device="cuda")
+    De = torch.empty((NPe, 2), device="cuda")
+    q.qpm_eval(Ne, 1.0, 2.0, Xe, De)
+    q.qpm_eval_packed(Ne, 1.0, 2.0, We, De)
+    t_g = _time_cuda(lambda: q.qpm_eval(Ne, 1.0, 2.0, Xe, De), 10, flush)
+    t_p = _time_cuda(lambda: q.qpm_eval_packed(Ne, 1.0, 2.0, We, De), 10, flush)
+    ev = NPe * Ne
+    evaluate = {"workload": "1024 rows x 1e5 domains, plain scan",
+                "genes": {"domain_evals_per_s": ev / t_g, "us": t_g * 1e6,
+                          "roofline": {"bound": "hbm", "achieved": 4 * ev / t_g / 1e9, "peak": peak_hbm,
+                                       "unit": "GB/s", "frac": 4 * ev / t_g / 1e9 / peak_hbm}},
+                "packed": {"domain_evals_per_s": ev / t_p, "us": t_p * 1e6,
+                           "roofline": {"bound": "alu", "achieved": 10 * ev / t_p / 1e12,
+                                        "peak": peak_alu, "unit": "T lane-ops/s",
+                                        "frac": 10 * ev / t_p / 1e12 / peak_alu}}}
+    del Xe, We
+
+    # ---------------------------------------------- end to end through qpm_solve
     best_host = torch.empty(N, dtype=torch.float32).pin_memory()
     d64_host = torch.empty(2, dtype=torch.float64).pin_memory()
     f_host = torch.empty(1, dtype=torch.float32).pin_memory()
-    best_mode = min(results, key=lambda k: results[k]["s_per_step"])
     mode_id = q.RUN_PERSISTENT if best_mode == "persistent" else q.RUN_GRAPH
     for _ in range(args.warmup):
         q.qpm_solve(N, c["kappa1"], c["kappa2"], prm, mode_id, best_host, d64_host, f_host)
@@ -210,16 +325,10 @@ def run_gpu(args):
         e2e.append(time.perf_counter() - t0)
     e2e_t = sum(e2e) / len(e2e)
 
-    pk, pk_src = peaks()
-    nsm = torch.cuda.get_device_properties(lrank).multi_processor_count
-    sm_mhz = results[best_mode]["clocks"].get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    peak_max = nsm * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
-    ops = algorithmic_lane_ops_per_gene_gen(c["compensated"]) * gene_gens
-    achieved = ops / kdur / 1e12
-
     if rank != 0:
         return
     best = results[best_mode]
+    sm_mhz = best["clocks"].get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     value = world * evals_per_run / best["s_per_step"]
     line = {
         "metric": METRIC,
@@ -245,13 +354,17 @@ def run_gpu(args):
                       "gen_per_s": world * G / v["s_per_step"],
                       "best_f": v["best_f"]} for k, v in results.items()},
         "roofline": {"bound": "alu", "kernel": "k_persist",
-                     "achieved": achieved, "peak": peak_max, "unit": "T lane-ops/s",
-                     "frac": achieved / peak_max, "traffic": None,
+                     "achieved": achieved, "peak": peak_alu, "unit": "T lane-ops/s",
+                     "frac": achieved / peak_alu, "traffic": None,
                      "peak_note": f"{nsm} SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
                                   f"(issue limit, derived; clocks {pk_src})",
                      "frac_at_median_clock": achieved / (nsm * 128 * sm_mhz * 1e6 / 1e12),
-                     "ops_per_gene_gen": algorithmic_lane_ops_per_gene_gen(c["compensated"]),
-                     "launch_ms": kdur * 1e3},
+                     "ops_per_gene_gen": ops_gene_gen, "launch_ms": kdur * 1e3,
+                     "us_per_generation": kdur / G * 1e6},
+        "batched": batched,
+        "precision": prec,
+        "adjoint": adjoint,
+        "eval": evaluate,
         "e2e": {"value": world * evals_per_run / e2e_t, "unit": "domain-evals/s",
                 "h2d_bytes_per_step": 24 + 40, "d2h_bytes_per_step": 4 * N + 16 + 4,
                 "api": "qpm_solve (host buffers)", "form": best_mode},

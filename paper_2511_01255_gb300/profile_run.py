@@ -22,15 +22,31 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="paper",
-                    choices=["small", "paper", "precision", "eval", "batch"])
+                    choices=["small", "paper", "precision", "eval", "batch", "relaxed"])
     ap.add_argument("--form", default="launches",
                     choices=["launches", "graph", "persistent", "batched"])
     ap.add_argument("--gens", type=int, default=20)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--comp", type=int, default=-1, help="override the compensated flag")
     ap.add_argument("--team", type=int, default=0, help="threads per individual (0 = automatic)")
+    ap.add_argument("--instances", type=int, default=512, help="instances of the batch workload")
     a = ap.parse_args()
     q.lib()
+    if a.workload == "relaxed":
+        c = W.RELAXED
+        th = torch.from_numpy(W.relaxed_theta(c["B"], c["N"], seed=c["seed"])).cuda()
+        D = torch.empty((c["B"], 2), device="cuda")
+        A = torch.empty((c["B"], 2), device="cuda")
+        g = torch.empty_like(th)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.reps):
+            q.qpm_deff_relaxed_fwd(c["N"], c["kappa1"], c["kappa2"], th, D, None, A)
+            q.qpm_deff_relaxed_bwd(c["N"], c["kappa1"], c["kappa2"], th, D, A, None, g)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"relaxed B={c['B']} N={c['N']}: {e0.elapsed_time(e1) / a.reps:.3f} ms per fwd+bwd")
+        return
     if a.workload == "eval":
         N, NP = 100000, 1024
         X = torch.rand((NP, N), device="cuda") * 2 - 1
@@ -48,7 +64,7 @@ def main():
     form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT,
             "batched": q.RUN_BATCHED}[a.form]
     if a.workload == "batch":
-        inst = W.batched_instances(512)
+        inst = W.batched_instances(a.instances)
         comp = 0 if a.comp < 0 else a.comp
         st = q.State([(c["N"], c["kappa1"], c["kappa2"]) for c in inst],
                       [q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
