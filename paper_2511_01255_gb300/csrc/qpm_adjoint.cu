@@ -13,10 +13,12 @@
 //
 // Work split: one warp per row; the row is cut into tiles of 256 domains, lane l
 // owns the 8 contiguous domains [8l, 8l+8) of every tile (two coalesced float4
-// accesses per tile).  Partial sums of a tile are combined across lanes in index
-// order (butterfly with the lower lane on the left), so every lane holds the
-// running totals.  The phasor table is staged once per CTA in shared memory in
-// a [tile][e][lane] layout, which makes every table read conflict-free.
+// accesses per tile).  Because C = sum_j a_j P_j is bilinear, each lane keeps its
+// own share of C, of A and of E across the whole row; only the prefix of b
+// entering each lane's 8 domains needs a warp exclusive scan per tile, and the
+// shares are summed once per row.  The phasor table (p1, p2) and q = p1 p2 are
+// staged once per CTA in shared memory in a [tile][e][lane] layout, which makes
+// every table read conflict-free.
 #include <math.h>
 
 #include <algorithm>
@@ -35,39 +37,6 @@ struct RelaxShape {
   int64_t ld;
   bool vec;  // 16-byte aligned rows with ld % 4 == 0
 };
-
-// relaxed monoid: the (A, B, C) triple plus E = sum d^2 q (additive)
-struct MonoR {
-  Mono m;
-  float2 E;
-};
-
-__device__ __forceinline__ MonoR monor_combine(const MonoR &L, const MonoR &R) {
-  MonoR o;
-  o.m = mono_combine(L.m, R.m);
-  o.E = make_float2(L.E.x + R.E.x, L.E.y + R.E.y);
-  return o;
-}
-
-// ordered all-reduce over the warp: lane l combines with lane l^s keeping the
-// lower lane's operand on the left, so every lane ends with lanes 0..31 in order
-__device__ __forceinline__ MonoR warp_allreduce(MonoR v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 1; s < 32; s <<= 1) {
-    MonoR o;
-    o.m.A.x = __shfl_xor_sync(0xffffffffu, v.m.A.x, s);
-    o.m.A.y = __shfl_xor_sync(0xffffffffu, v.m.A.y, s);
-    o.m.B.x = __shfl_xor_sync(0xffffffffu, v.m.B.x, s);
-    o.m.B.y = __shfl_xor_sync(0xffffffffu, v.m.B.y, s);
-    o.m.C.x = __shfl_xor_sync(0xffffffffu, v.m.C.x, s);
-    o.m.C.y = __shfl_xor_sync(0xffffffffu, v.m.C.y, s);
-    o.E.x = __shfl_xor_sync(0xffffffffu, v.E.x, s);
-    o.E.y = __shfl_xor_sync(0xffffffffu, v.E.y, s);
-    v = (lane & s) ? monor_combine(o, v) : monor_combine(v, o);
-  }
-  return v;
-}
 
 // table entry of (tile, lane, e) in the staged layout
 __device__ __forceinline__ const float4 &tab(const float4 *sm, int tile, int e, int lane) {
@@ -107,59 +76,23 @@ __device__ __forceinline__ void store8(float *row, int m0, int N, const float v[
   }
 }
 
-// stage the natural-order table into shared memory ([tile][e][lane], zero padded)
-__device__ void stage_table(float4 *sm, const float4 *gtab, int N, int ntiles) {
+// stage the natural-order table into shared memory ([tile][e][lane], zero padded),
+// with q = p1 p2 beside it in `sq` (same layout)
+__device__ void stage_table(float4 *sm, float2 *sq, const float4 *gtab, int N, int ntiles) {
   for (int m = threadIdx.x; m < ntiles * RX_TILE; m += blockDim.x) {
     const int tile = m / RX_TILE, r = m - tile * RX_TILE, lane = r >> 3, e = r & 7;
-    sm[((size_t)tile * 8 + e) * 32 + lane] = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 p = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const size_t o = ((size_t)tile * 8 + e) * 32 + lane;
+    sm[o] = p;
+    sq[o] = make_float2(p.x * p.z - p.y * p.w, p.x * p.w + p.y * p.z);
   }
   __syncthreads();
 }
 
-template <bool VEC, bool SMT>
-static __global__ void __launch_bounds__(RX_WARPS * 32)
-    k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
-                  const float2 *__restrict__ konst, float2 *__restrict__ Dout,
-                  float *__restrict__ fout, float2 *__restrict__ Aout) {
-  extern __shared__ float4 smt[];
-  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  const float2 phi12 = konst[0], psi = konst[2];
-  for (int r = gw; r < sh.B; r += nw) {
-    const float *row = theta + (int64_t)r * sh.ld;
-    MonoR run;
-    run.m = mono_zero();
-    run.E = make_float2(0.f, 0.f);
-    for (int tile = 0; tile < sh.ntiles; ++tile) {
-      const int m0 = tile * RX_TILE + lane * 8;
-      float th[8];
-      load8<VEC>(row, m0, sh.N, th);
-      MonoR loc;
-      loc.m = mono_zero();
-      loc.E = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const float d = tanhf(th[e]);
-        const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
-        mono_push(loc.m, d, p);
-        const float qr = p.x * p.z - p.y * p.w, qi = p.x * p.w + p.y * p.z;  // q = p1 p2
-        const float d2 = d * d;
-        loc.E.x = fmaf(d2, qr, loc.E.x);
-        loc.E.y = fmaf(d2, qi, loc.E.y);
-      }
-      run = monor_combine(run, warp_allreduce(loc));
-    }
-    if (lane == 0) {
-      const float2 D = make_float2(
-          phi12.x * run.m.C.x - phi12.y * run.m.C.y + (psi.x * run.E.x - psi.y * run.E.y),
-          phi12.x * run.m.C.y + phi12.y * run.m.C.x + (psi.x * run.E.y + psi.y * run.E.x));
-      Dout[r] = D;
-      if (fout) fout[r] = fit_of(D);
-      if (Aout) Aout[r] = run.m.A;
-    }
-  }
+template <bool SMT>
+__device__ __forceinline__ float2 q_get(const float2 *sq, const float4 &p, int tile, int e, int lane) {
+  if (SMT) return sq[((size_t)tile * 8 + e) * 32 + lane];
+  return make_float2(p.x * p.z - p.y * p.w, p.x * p.w + p.y * p.z);
 }
 
 // exclusive prefix over lanes of a float2 (lane 0 gets 0); total in `tot`
@@ -180,6 +113,67 @@ __device__ __forceinline__ float2 warp_excl_scan2(float2 v, float2 &tot) {
   return make_float2(inc.x - v.x, inc.y - v.y);
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+  return v;
+}
+
+template <bool VEC, bool SMT>
+static __global__ void __launch_bounds__(RX_WARPS * 32)
+    k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
+                  const float2 *__restrict__ konst, float2 *__restrict__ Dout,
+                  float *__restrict__ fout, float2 *__restrict__ Aout) {
+  extern __shared__ float4 smt[];
+  float2 *sq = (float2 *)(smt + (size_t)sh.ntiles * RX_TILE);
+  if (SMT) stage_table(smt, sq, gtab, sh.N, sh.ntiles);
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const float2 phi12 = konst[0], psi = konst[2];
+  for (int r = gw; r < sh.B; r += nw) {
+    const float *row = theta + (int64_t)r * sh.ld;
+    float2 Cl = make_float2(0.f, 0.f), Al = Cl, El = Cl;  // this lane's shares
+    float2 Brun = make_float2(0.f, 0.f);                   // sum of b before this tile
+    for (int tile = 0; tile < sh.ntiles; ++tile) {
+      const int m0 = tile * RX_TILE + lane * 8;
+      float th[8];
+      load8<VEC>(row, m0, sh.N, th);
+      Mono loc = mono_zero();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float d = tanhf(th[e]);
+        const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
+        mono_push(loc, d, p);
+        const float2 q = q_get<SMT>(sq, p, tile, e, lane);
+        const float d2 = d * d;
+        El.x = fmaf(d2, q.x, El.x);
+        El.y = fmaf(d2, q.y, El.y);
+      }
+      float2 Bt;
+      const float2 Bex = warp_excl_scan2(loc.B, Bt);
+      // C share: the lane's own pairs plus its a-sum times every b before the lane
+      const float br = Brun.x + Bex.x, bi = Brun.y + Bex.y;
+      Cl.x += loc.C.x + (loc.A.x * br - loc.A.y * bi);
+      Cl.y += loc.C.y + (loc.A.x * bi + loc.A.y * br);
+      Al.x += loc.A.x;
+      Al.y += loc.A.y;
+      Brun.x += Bt.x;
+      Brun.y += Bt.y;
+    }
+    const float Cr = warp_sum(Cl.x), Ci = warp_sum(Cl.y);
+    const float Er = warp_sum(El.x), Ei = warp_sum(El.y);
+    const float Ar = warp_sum(Al.x), Ai = warp_sum(Al.y);
+    if (lane == 0) {
+      const float2 D = make_float2(phi12.x * Cr - phi12.y * Ci + (psi.x * Er - psi.y * Ei),
+                                   phi12.x * Ci + phi12.y * Cr + (psi.x * Ei + psi.y * Er));
+      Dout[r] = D;
+      if (fout) fout[r] = fit_of(D);
+      if (Aout) Aout[r] = make_float2(Ar, Ai);
+    }
+  }
+}
+
 template <bool VEC, bool SMT>
 static __global__ void __launch_bounds__(RX_WARPS * 32)
     k_relaxed_bwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
@@ -187,7 +181,8 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
                   const float2 *__restrict__ Ain, const float *__restrict__ gf,
                   float *__restrict__ grad, int64_t ldg) {
   extern __shared__ float4 smt[];
-  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
+  float2 *sq = (float2 *)(smt + (size_t)sh.ntiles * RX_TILE);
+  if (SMT) stage_table(smt, sq, gtab, sh.N, sh.ntiles);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (blockDim.x >> 5);
@@ -233,8 +228,8 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
         // w = p2 P + p1 R
         const float wr = p.z * P.x - p.w * P.y + (p.x * Rr - p.y * Ri);
         const float wi = p.z * P.y + p.w * P.x + (p.x * Ri + p.y * Rr);
-        const float qr = p.x * p.z - p.y * p.w, qi = p.x * p.w + p.y * p.z;
-        const float s = (ur * wr - ui * wi) + d[e] * (vr * qr - vi * qi);
+        const float2 q = q_get<SMT>(sq, p, tile, e, lane);
+        const float s = (ur * wr - ui * wi) + d[e] * (vr * q.x - vi * q.y);
         out[e] = s * (1.f - d[e] * d[e]);
         P.x = fmaf(d[e], p.x, P.x);
         P.y = fmaf(d[e], p.y, P.y);
@@ -261,7 +256,7 @@ static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int
   sh->ntiles = (prob->N + RX_TILE - 1) / RX_TILE;
   sh->ld = ld;
   sh->vec = (ld % 4 == 0) && (((uintptr_t)theta & 15) == 0);
-  const size_t need = sizeof(float4) * (size_t)sh->ntiles * RX_TILE;
+  const size_t need = (sizeof(float4) + sizeof(float2)) * (size_t)sh->ntiles * RX_TILE;
   *smem = need <= RX_SMEM_MAX ? need : 0;
   const int per_sm = *smem ? (int)std::max<size_t>(1, (228 * 1024) / (*smem + 1024)) : 4;
   *grid = sm_count() * std::min(per_sm, 4);

@@ -1,10 +1,13 @@
 // qpm_eval.cu -- fitness of caller-supplied sign sequences (Sec. 2.1).
 //
-// Work split: lane = individual, so the phasor of domain m is one warp-uniform
-// (broadcast) load shared by 32 individuals; the domains of a row are cut into
-// S segments handled by different warps, each producing the monoid partial
-// (A, B, C) of its segment; a second kernel combines the S partials of every
-// row in index order and closes d_eff = phi1 phi2 C + cdiag.
+// Work split: a CTA takes 32 rows and one segment of the domains.  It walks the
+// segment in steps of 256 domains: the 32 x 256 genes (or their sign words) are
+// copied into shared memory with fully coalesced loads, the 256 phasors beside
+// them, then warp w scans domains [32w, 32w + 32) of the step for all 32 rows
+// (lane = row, so each phasor read is a broadcast) and the 8 warp partials are
+// combined in index order into the CTA's running monoid (A, B, C).  A second
+// kernel combines the S segment partials of every row in index order and closes
+// d_eff = phi1 phi2 C + cdiag.
 #include <math.h>
 
 #include <map>
@@ -17,75 +20,109 @@
 
 namespace qpm {
 
-static constexpr int EV_WARPS = 8;  // warps per CTA; the CTA's warps share a segment
+static constexpr int EV_WARPS = 8;
+static constexpr int EV_STEP = 256;  // domains staged per step (32 per warp)
 
 struct EvalShape {
-  int NP, N, S, L;  // S segments of L domains (L a multiple of 32)
+  int NP, N, S, L;  // S segments of L domains (L a multiple of EV_STEP)
   int groups;       // ceil(NP / 32)
   int NPpad;        // groups * 32
 };
+
+// gene (row, domain d of the step) in the swizzled [domain][row] tile: the float4
+// column d/4 xor-permutes the row, so that both the coalesced stores (32 columns,
+// one row) and the transposed reads (one domain, 32 rows) hit 32 different banks
+__device__ __forceinline__ int tile_idx(int d, int row) { return d * 32 + (row ^ ((d >> 2) & 31)); }
 
 // partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
 template <int KIND, bool COMP>  // KIND 0: float genes (vector loads), 1: float genes (scalar), 2: packed bits
 static __global__ void __launch_bounds__(EV_WARPS * 32)
     k_eval_seg(const void *__restrict__ src, int64_t ld, EvalShape sh,
                const float4 *__restrict__ table, float2 *__restrict__ part) {
+  __shared__ float tile[EV_STEP * 32];              // genes, or sign words for KIND 2
+  __shared__ float4 tb[EV_STEP];                    // phasors of the step
+  __shared__ Mono wpart[EV_WARPS][32];              // per-warp partials of the step
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int s = blockIdx.x;
-  const int grp = blockIdx.y * EV_WARPS + warp;
-  if (grp >= sh.groups) return;
-  const int i = grp * 32 + lane;
-  const int irow = i < sh.NP ? i : sh.NP - 1;  // spare lanes recompute the last row
+  const int s = blockIdx.x, grp = blockIdx.y;
+  const int r0 = grp * 32;
   const int m0 = s * sh.L;
   const int m1 = min(sh.N, m0 + sh.L);
-  // plain: FP32 running sums; compensated: plain blocks of 8 domains Kahan-folded
-  // into a compensated running triple (blocked Kahan summation)
-  Mono acc = mono_zero();
-  MonoK acck = monok_zero();
-  if (KIND == 2) {
-    const uint32_t *row = (const uint32_t *)src + (int64_t)irow * ld;
-    for (int mb = m0; mb < m1; mb += 32) {
-      const uint32_t w = __ldg(row + (mb >> 5));
-      const int n = min(32, m1 - mb);
-#pragma unroll 8
-      for (int e = 0; e < n; ++e) {
-        const float4 p = __ldg(table + mb + e);
-        const float d = ((w >> e) & 1u) ? -1.0f : 1.0f;
-        mono_push(acc, d, p);
-        if (COMP && (e & 7) == 7) { monok_fold_in(acck, acc); acc = mono_zero(); }
+  Mono run = mono_zero();   // running monoid of the segment (warp 0, lane = row)
+  MonoK runk = monok_zero();
+  for (int ms = m0; ms < m1; ms += EV_STEP) {
+    __syncthreads();  // the previous step's tile and partials have been consumed
+    // ---- stage phasors
+    {
+      const int m = ms + threadIdx.x;
+      tb[threadIdx.x] = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // ---- stage genes / sign words
+    if (KIND == 2) {
+      uint32_t *tw = (uint32_t *)tile;  // [row][8 words]
+      const int row = threadIdx.x >> 3, wd = threadIdx.x & 7;
+      const int gr = r0 + row;
+      const int word = (ms >> 5) + wd;
+      uint32_t v = 0u;
+      if (gr < sh.NP && ms + wd * 32 < sh.N) v = __ldg((const uint32_t *)src + (int64_t)gr * ld + word);
+      tw[row * 8 + wd] = v;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int f = threadIdx.x + k * EV_WARPS * 32;  // float4 slot: 32 rows x 64 columns
+        const int row = f >> 6, c4 = f & 63;
+        const int gr = r0 + row, m = ms + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gr < sh.NP) {
+          const float *rp = (const float *)src + (int64_t)gr * ld;
+          if (KIND == 0 && m + 4 <= sh.N) {
+            v = __ldg((const float4 *)(rp + m));
+          } else {
+            if (m < sh.N) v.x = __ldg(rp + m);
+            if (m + 1 < sh.N) v.y = __ldg(rp + m + 1);
+            if (m + 2 < sh.N) v.z = __ldg(rp + m + 2);
+            if (m + 3 < sh.N) v.w = __ldg(rp + m + 3);
+          }
+        }
+        const int d = 4 * c4;
+        tile[tile_idx(d, row)] = v.x;
+        tile[tile_idx(d + 1, row)] = v.y;
+        tile[tile_idx(d + 2, row)] = v.z;
+        tile[tile_idx(d + 3, row)] = v.w;
       }
-      if (COMP && (n & 7)) { monok_fold_in(acck, acc); acc = mono_zero(); }
     }
-  } else if (KIND == 0) {
-    const float *row = (const float *)src + (int64_t)irow * ld;
-    int m = m0;
-    for (; m + 4 <= m1; m += 4) {
-      const float4 x = __ldg((const float4 *)(row + m));
-      const float4 p0 = __ldg(table + m), p1 = __ldg(table + m + 1);
-      const float4 p2 = __ldg(table + m + 2), p3 = __ldg(table + m + 3);
-      mono_push(acc, x.x < 0.f ? -1.f : 1.f, p0);
-      mono_push(acc, x.y < 0.f ? -1.f : 1.f, p1);
-      mono_push(acc, x.z < 0.f ? -1.f : 1.f, p2);
-      mono_push(acc, x.w < 0.f ? -1.f : 1.f, p3);
-      if (COMP && ((m - m0) & 4)) { monok_fold_in(acck, acc); acc = mono_zero(); }
+    __syncthreads();
+    // ---- warp w: domains [32w, 32w + 32) of the step for rows r0 + lane
+    Mono acc = mono_zero();
+    const int d0 = warp * 32;
+    if (KIND == 2) {
+      const uint32_t w = ((const uint32_t *)tile)[lane * 8 + warp];
+#pragma unroll 8
+      for (int e = 0; e < 32; ++e) mono_push(acc, ((w >> e) & 1u) ? -1.0f : 1.0f, tb[d0 + e]);
+    } else {
+#pragma unroll 8
+      for (int e = 0; e < 32; ++e) {
+        const float x = tile[tile_idx(d0 + e, lane)];
+        mono_push(acc, x < 0.f ? -1.f : 1.f, tb[d0 + e]);
+      }
     }
-    for (; m < m1; ++m) mono_push(acc, __ldg(row + m) < 0.f ? -1.f : 1.f, __ldg(table + m));
-  } else {
-    const float *row = (const float *)src + (int64_t)irow * ld;
-    for (int m = m0; m < m1; ++m) {
-      mono_push(acc, __ldg(row + m) < 0.f ? -1.f : 1.f, __ldg(table + m));
-      if (COMP && ((m - m0) & 7) == 7) { monok_fold_in(acck, acc); acc = mono_zero(); }
+    wpart[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int w = 0; w < EV_WARPS; ++w) {
+        if (COMP) monok_fold_in(runk, wpart[w][lane]);
+        else run = mono_combine(run, wpart[w][lane]);
+      }
     }
   }
-  if (COMP) {
-    monok_fold_in(acck, acc);
-    acc = monok_fold(acck);
+  if (warp == 0) {
+    if (COMP) run = monok_fold(runk);
+    const size_t stride = (size_t)sh.S * sh.NPpad;
+    const size_t o = (size_t)s * sh.NPpad + r0 + lane;
+    part[o] = run.A;
+    part[stride + o] = run.B;
+    part[2 * stride + o] = run.C;
   }
-  const size_t stride = (size_t)sh.S * sh.NPpad;
-  const size_t o = (size_t)s * sh.NPpad + i;
-  part[o] = acc.A;
-  part[stride + o] = acc.B;
-  part[2 * stride + o] = acc.C;
 }
 
 template <bool COMP>
@@ -221,13 +258,13 @@ static EvalShape eval_shape(int NP, int N) {
   sh.N = N;
   sh.groups = (NP + 31) / 32;
   sh.NPpad = sh.groups * 32;
-  const int target_warps = sm_count() * 24;
-  int S = (target_warps + sh.groups - 1) / sh.groups;
-  const int maxS = (N + 63) / 64;  // at least 64 domains per segment
+  const int target_ctas = sm_count() * 6;
+  int S = (target_ctas + sh.groups - 1) / sh.groups;
+  const int maxS = (N + EV_STEP - 1) / EV_STEP;  // at least one step per segment
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
   int L = (N + S - 1) / S;
-  L = (L + 31) & ~31;
+  L = (L + EV_STEP - 1) / EV_STEP * EV_STEP;
   sh.S = (N + L - 1) / L;
   sh.L = L;
   return sh;
@@ -251,7 +288,7 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
   if (st != QPM_OK) return st;
   float2 *part = (float2 *)scratch;
-  dim3 grid(sh.S, (sh.groups + EV_WARPS - 1) / EV_WARPS);
+  dim3 grid(sh.S, sh.groups);
   if (kind != 2 && (ld % 4 == 0) && (((uintptr_t)src & 15) == 0)) kind = 0;
   else if (kind != 2) kind = 1;
 #define QPM_EV(K, C) k_eval_seg<K, C><<<grid, EV_WARPS * 32, 0, stream>>>(src, ld, sh, table, part)
@@ -343,7 +380,7 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   TableSpec ts{prob->N, Npad, 1, Npad, prob->kappa1, prob->kappa2};
   st = launch_table(ts, table, tpart, konst, nullptr, s);
   if (st != QPM_OK) return st;
-  dim3 grid(sh.S, (sh.groups + EV_WARPS - 1) / EV_WARPS);
+  dim3 grid(sh.S, sh.groups);
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   if (vec) {
     if (compensated) k_eval_seg<0, true><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);

@@ -48,7 +48,7 @@ struct InstDev {
   float2 *konst;         // phi1 phi2, cdiag
   double2 *konst64;      // phi1 phi2, cdiag, psi (FP64)
   int32_t *lead;         // [3]
-  unsigned long long *topk;  // [NP * 3] partial leader keys
+  unsigned long long *topk;  // [2][NP * 3] partial leader keys (by generation parity)
   unsigned *ctr;         // [4] CTA-completion counters
   int32_t *gen;          // [1] completed generations
   int32_t *best;         // [1] best index (get_best)
@@ -169,13 +169,13 @@ static __global__ void k_init(InstDev I) {
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
 // WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
+// r = (r1, r2, r3, jrand) from de_indices
 template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
-                                            const float4 *tbl, int g, int i,
+                                            const float4 *tbl, int g, int i, const int4 r,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh) {
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
-  const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
   const float F = I.F, CR = I.CR;
@@ -221,9 +221,14 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 }
 
 // ------------------------------------------------ Step 4-5: GWO + selection
-template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
+// PRE: the six GWO random words of the thread's first group of 4 domains were
+// drawn earlier (while waiting at the grid barrier) and are passed in wpre
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool PRE = false>
 __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
-                               int i, int32_t *sel, int la, int lb, int ld, Mono *sh) {
+                               int i, int32_t *sel, int la, int lb, int ld, Mono *sh,
+                               const uint4 *wpre = nullptr,
+                               float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f),
+                               float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f)) {
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
   const int si = sel[i], sa = sel[la], sb = sel[lb], sd = sel[ld];
@@ -234,13 +239,18 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
-    const float4 x = ld_cur<NC, DUAL>(I, i, si, off);
+    const float4 x = (PRE && k4 == 0) ? (si ? own1 : own0) : ld_cur<NC, DUAL>(I, i, si, off);
     const float4 L0 = ld_cur<NC, DUAL>(I, la, sa, off), L1 = ld_cur<NC, DUAL>(I, lb, sb, off);
     const float4 L2 = ld_cur<NC, DUAL>(I, ld, sd, off);
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
     uint4 w[6];
+    if (PRE && k4 == 0) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
+      for (int k = 0; k < 6; ++k) w[k] = wpre[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
+    }
     float4 y;
 #define QPM_PULL(Xp, xv, r1w, r2w, out_)                                               \
     {                                                                                  \
@@ -344,6 +354,30 @@ __device__ void merge_leaders(const unsigned long long *topk, int nparts, int32_
   __syncthreads();
 }
 
+// leaders straight from the fitness array (warp 0 scans all NP values; every
+// thread returns after the CTA barrier with lead_sh set)
+__device__ void leaders_from_fit(const float *fit, int NP, int32_t *lead, int32_t *lead_sh) {
+  if (threadIdx.x < 32) {
+    unsigned long long k0 = 0, k1 = 0, k2 = 0;
+    for (int i = threadIdx.x; i < NP; i += 32) top3_insert(k0, k1, k2, lead_key(fit[i], i));
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
+      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
+      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
+      top3_insert(k0, k1, k2, p0);
+      top3_insert(k0, k1, k2, p1);
+      top3_insert(k0, k1, k2, p2);
+    }
+    if (threadIdx.x == 0) {
+      lead_sh[0] = key_index(k0);
+      lead_sh[1] = key_index(k1);
+      lead_sh[2] = key_index(k2);
+      if (lead) { lead[0] = lead_sh[0]; lead[1] = lead_sh[1]; lead[2] = lead_sh[2]; }
+    }
+  }
+  __syncthreads();
+}
+
 // true in every thread of the last CTA to finish (classic fence + counter pattern)
 __device__ bool last_cta(unsigned *ctr) {
   __shared__ bool is_last;
@@ -368,7 +402,8 @@ static __global__ void k_de(InstDev I) {
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     const unsigned long long key =
-        de_individual<COMP, true, false, DUAL>(I, K, I.table, g, i, sel_in, sel_out, sh);
+        de_individual<COMP, true, false, DUAL>(
+            I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh);
     if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
   }
   if (threadIdx.x == 0) {
@@ -416,38 +451,50 @@ __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// grid-wide barrier with a bounded wait: every CTA adds one arrival and waits for
-// the counter to reach (barriers passed) * gridDim.x.  Returns false in every
-// thread when any CTA has failed or this wait ran out (the error is recorded).
-__device__ bool grid_sync(const Barrier &b, unsigned &target) {
-  __shared__ int ok_sh;
+// bounded wait (thread 0) until *p >= need; false when it ran out or another CTA failed
+__device__ bool wait_geq(const Barrier &b, const unsigned *p, unsigned need) {
+  const unsigned long long t0 = globaltimer_ns();
+  while ((int)(ld_acquire(p) - need) < 0) {
+    if (*(volatile int32_t *)b.err != 0) return false;
+    if (globaltimer_ns() - t0 > b.timeout_ns) {
+      atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return *(volatile int32_t *)b.err == 0;
+}
+
+// grid-wide barrier split into arrival and wait, so that independent work can
+// run in between.  Every CTA adds one arrival (release) and then waits for the
+// counter to reach (barriers passed) * gridDim.x (acquire).
+__device__ __forceinline__ void grid_arrive(const Barrier &b, unsigned &target) {
   __syncthreads();
   target += gridDim.x;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    // the release orders this CTA's writes (made visible to thread 0 by the CTA
-    // barrier above) before the arrival; the acquiring polls order what follows
-    red_release_add(b.count, 1u);
-    const unsigned long long t0 = globaltimer_ns();
-    while ((int)(ld_acquire(b.count) - target) < 0) {
-      if (*(volatile int32_t *)b.err != 0) { ok = 0; break; }
-      if (globaltimer_ns() - t0 > b.timeout_ns) {
-        atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
-        ok = 0;
-        break;
-      }
-    }
-    if (*(volatile int32_t *)b.err != 0) ok = 0;
-    ok_sh = ok;
-  }
+  // the release orders this CTA's writes (made visible to thread 0 by the CTA
+  // barrier above) before the arrival
+  if (threadIdx.x == 0) red_release_add(b.count, 1u);
+}
+
+__device__ bool grid_wait(const Barrier &b, unsigned target) {
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) ok_sh = wait_geq(b, b.count, target) ? 1 : 0;
   __syncthreads();
   return ok_sh != 0;
 }
 
+__device__ bool grid_sync(const Barrier &b, unsigned &target) {
+  grid_arrive(b, target);
+  return grid_wait(b, target);
+}
+
 // All generations [*gen, g_end) in one cooperative launch; every CTA keeps the
-// same individuals, the phasor table sits in shared memory when it fits (TS).
+// same individuals (i = blockIdx.x + k gridDim.x), the phasor table sits in
+// shared memory when it fits (TS).  Two grid barriers per generation: after DE
+// (the leaders need every DE survivor) and after GWO (the next donors are any
+// individuals).  With one individual per CTA and 4 domains per thread, the GWO
+// random words are drawn between the arrival at the first barrier and the wait.
 template <bool COMP, bool TS, bool DUAL>
-static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
+static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end, Barrier bar) {
   extern __shared__ float4 dyn[];
   __shared__ int32_t lead_sh[3];
   Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
@@ -457,38 +504,53 @@ static __global__ void k_persist(InstDev I, int g_end, Barrier bar) {
   }
   const float4 *tbl = TS ? (const float4 *)dyn : I.table;
   const PhiloxKey K = philox_schedule(I.key);
+  const bool pre = DUAL && (I.c == 4) && (gridDim.x == (unsigned)I.NP);
   unsigned target = 0;
   int g = *I.gen;
   for (; g < g_end; ++g) {
     const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
     int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
-    unsigned long long k0 = 0, k1 = 0, k2 = 0;
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
-      const unsigned long long key =
-          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_in, sel_out, sh);
-      if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
+      const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
+      de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh);
     }
-    if (threadIdx.x == 0) {
-      I.topk[3 * blockIdx.x] = k0;
-      I.topk[3 * blockIdx.x + 1] = k1;
-      I.topk[3 * blockIdx.x + 2] = k2;
+    grid_arrive(bar, target);
+    uint4 wpre[6];
+    if (pre) {
+      const uint32_t jg = (uint32_t)((threadIdx.x * I.c) >> 2);
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        wpre[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)blockIdx.x, jg);
     }
-    if (!grid_sync(bar, target)) return;
-    // every CTA merges the partial leader keys itself (no extra barrier)
-    merge_leaders(I.topk, gridDim.x, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
+    if (!grid_wait(bar, target)) return;
+    // the own row (both slots) is requested before the leaders are known, so that
+    // its latency overlaps the leader search
+    float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f), own1 = own0;
+    if (pre) {
+      const float *r0 = I.pop + (size_t)2 * blockIdx.x * I.Npad + (size_t)threadIdx.x * 4;
+      own0 = *(const float4 *)r0;
+      own1 = *(const float4 *)(r0 + I.Npad);
+    }
+    // every CTA finds the leaders itself (Sec. 3.2 Step 3) from the fitness array
+    leaders_from_fit(I.fit, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
-      gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh);
+      if (pre)
+        gwo_individual<COMP, false, TS, DUAL, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld,
+                                                           sh, wpre, own0, own1);
+      else
+        gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh);
     }
     if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
       I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
     }
-    // the partial leader keys are rewritten in the next DE phase: all CTAs must
-    // have merged them before any CTA passes this barrier
+    // the next DE phase reads any individual: every CTA must have finished GWO
     if (!grid_sync(bar, target)) return;
   }
+  // every CTA read the start generation before its first barrier; later kernels
+  // see the new value after this launch completes
   if (blockIdx.x == 0 && threadIdx.x == 0) *I.gen = g_end;
 }
 
@@ -518,7 +580,9 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
     unsigned long long k0 = 0, k1 = 0, k2 = 0;
     for (int i = warp; i < I.NP; i += nw) {
       const unsigned long long key =
-          de_individual<COMP, false, TS, false, true>(I, K, tbl, g, i, sel_in, sel_out, nullptr);
+          de_individual<COMP, false, TS, false, true>(
+              I, K, tbl, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out,
+              nullptr);
       if (lane == 0) top3_insert(k0, k1, k2, key);
     }
     if (lane == 0) {
@@ -940,7 +1004,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += align_up(Np * sizeof(float4), 256);
     total += align_up((size_t)table_part_count(I.Npad) * sizeof(double2), 256);
     total += 256 + 256 + 256;  // konst, konst64, lead
-    total += align_up(3 * NP * sizeof(unsigned long long), 256);
+    total += align_up(6 * NP * sizeof(unsigned long long), 256);
     total += 256 + 256 + 256;  // ctr, gen, best
   }
   const size_t desc_off = total;
@@ -967,7 +1031,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.konst = (float2 *)take(3 * sizeof(float2));
     I.konst64 = (double2 *)take(3 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
-    I.topk = (unsigned long long *)take(3 * NP * sizeof(unsigned long long));
+    I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
     I.ctr = (unsigned *)take(4 * sizeof(unsigned));
     I.gen = (int32_t *)take(sizeof(int32_t));
     I.best = (int32_t *)take(sizeof(int32_t));
