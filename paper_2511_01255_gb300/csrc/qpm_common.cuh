@@ -181,28 +181,19 @@ __device__ __forceinline__ Mono warp_reduce(Mono m) {
 }
 
 // ordered reduction over the whole CTA (threads in index order); the result is
-// valid in every thread.  `sh` must hold blockDim.x/32 + 1 entries.
+// valid in thread 0 only.  Each warp reduces by shuffles, lane 0 parks the warp
+// total in sh[warp] (blockDim.x/32 entries) and thread 0 folds them in order.
+// `sh` is reused by the next call: a caller that reduces again before any other
+// CTA barrier must put a __syncthreads() in between.
 __device__ __forceinline__ Mono block_reduce(Mono m, Mono *sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   m = warp_reduce(m);
-  if (nw == 1) {
-    if (lane == 0) sh[0] = m;
-    __syncthreads();
-    const Mono r = sh[0];
-    __syncthreads();
-    return r;
-  }
+  if (nw == 1) return m;
   if (lane == 0) sh[warp] = m;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Mono acc = sh[0];
-    for (int w = 1; w < nw; ++w) acc = mono_combine(acc, sh[w]);
-    sh[nw] = acc;
-  }
-  __syncthreads();
-  const Mono r = sh[nw];
-  __syncthreads();
-  return r;
+  if (threadIdx.x == 0)
+    for (int w = 1; w < nw; ++w) m = mono_combine(m, sh[w]);
+  return m;
 }
 
 // d_eff = phi1 phi2 C + cdiag  (cdiag = psi sum_j p1_j p2_j for +-1 domains)

@@ -159,7 +159,10 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
 template <bool COMP>
 static __global__ void k_init(InstDev I) {
   extern __shared__ Mono sh[];
-  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) init_individual<COMP>(I, i, sh);
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
+    init_individual<COMP>(I, i, sh);
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *I.gen = 0;
     for (int k = 0; k < 4; ++k) I.ctr[k] = 0u;
@@ -401,6 +404,7 @@ static __global__ void k_de(InstDev I) {
   int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
     const unsigned long long key =
         de_individual<COMP, true, false, DUAL>(
             I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh);
@@ -426,6 +430,7 @@ static __global__ void k_gwo(InstDev I) {
   const int la = I.lead[0], lb = I.lead[1], ld = I.lead[2];
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
+    __syncthreads();  // the reduction scratch is reused
     gwo_individual<COMP, true, false, DUAL>(I, K, I.table, g, i, sel, la, lb, ld, sh);
   }
   if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
@@ -511,6 +516,7 @@ static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end,
     const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
     int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+      if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
       de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh);
     }
@@ -536,6 +542,7 @@ static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end,
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
+      if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       if (pre)
         gwo_individual<COMP, false, TS, DUAL, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld,
                                                            sh, wpre, own0, own1);
