@@ -16,9 +16,10 @@
 // accesses per tile).  Because C = sum_j a_j P_j is bilinear, each lane keeps its
 // own share of C, of A and of E across the whole row; only the prefix of b
 // entering each lane's 8 domains needs a warp exclusive scan per tile, and the
-// shares are summed once per row.  The phasor table (p1, p2) and q = p1 p2 are
-// staged once per CTA in shared memory in a [tile][e][lane] layout, which makes
-// every table read conflict-free.
+// shares are summed once per row.  The phasor table (p1, p2) is staged once per
+// CTA in shared memory in a [tile][e][lane] layout, which makes every table read
+// conflict-free; the next tile's theta is requested before the current one is
+// processed, so one tile of loads is always in flight per warp.
 #include <math.h>
 
 #include <algorithm>
@@ -76,22 +77,18 @@ __device__ __forceinline__ void store8(float *row, int m0, int N, const float v[
   }
 }
 
-// stage the natural-order table into shared memory ([tile][e][lane], zero padded),
-// with q = p1 p2 beside it in `sq` (same layout)
-__device__ void stage_table(float4 *sm, float2 *sq, const float4 *gtab, int N, int ntiles) {
-  for (int m = threadIdx.x; m < ntiles * RX_TILE; m += blockDim.x) {
-    const int tile = m / RX_TILE, r = m - tile * RX_TILE, lane = r >> 3, e = r & 7;
-    const float4 p = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const size_t o = ((size_t)tile * 8 + e) * 32 + lane;
-    sm[o] = p;
-    sq[o] = make_float2(p.x * p.z - p.y * p.w, p.x * p.w + p.y * p.z);
+// stage the natural-order table into shared memory ([tile][e][lane], zero padded);
+// consecutive threads write consecutive shared-memory slots
+__device__ void stage_table(float4 *sm, const float4 *gtab, int N, int ntiles) {
+  for (int o = threadIdx.x; o < ntiles * RX_TILE; o += blockDim.x) {
+    const int tile = o / RX_TILE, rem = o - tile * RX_TILE, e = rem >> 5, lane = rem & 31;
+    const int m = tile * RX_TILE + lane * 8 + e;
+    sm[o] = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
 }
 
-template <bool SMT>
-__device__ __forceinline__ float2 q_get(const float2 *sq, const float4 &p, int tile, int e, int lane) {
-  if (SMT) return sq[((size_t)tile * 8 + e) * 32 + lane];
+__device__ __forceinline__ float2 q_of(const float4 &p) {  // q = p1 p2
   return make_float2(p.x * p.z - p.y * p.w, p.x * p.w + p.y * p.z);
 }
 
@@ -119,33 +116,69 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// this warp's work list: rows r = gw, gw + nw, ...; (row, tile) pairs in order.
+// next() advances and prefetches the theta of the following pair.
+template <bool VEC>
+struct RowWalker {
+  const float *theta;
+  int64_t ld;
+  int N, B, ntiles, nw;
+  int r, tile;
+  float nxt[8];
+  __device__ __forceinline__ void fetch(int rr, int tt) {
+    if (rr < B) load8<VEC>(theta + (int64_t)rr * ld, tt * RX_TILE + (threadIdx.x & 31) * 8, N, nxt);
+  }
+  __device__ __forceinline__ void start(int gw) {
+    r = gw;
+    tile = 0;
+    fetch(r, 0);
+  }
+  // copies the prefetched values of (r, tile) into v and requests the next pair
+  __device__ __forceinline__ void take(float v[8]) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = nxt[e];
+    const int nt = tile + 1 < ntiles ? tile + 1 : 0;
+    const int nr = tile + 1 < ntiles ? r : r + nw;
+    fetch(nr, nt);
+  }
+  __device__ __forceinline__ bool advance() {  // true when a new row starts
+    if (++tile < ntiles) return false;
+    tile = 0;
+    r += nw;
+    return true;
+  }
+};
+
 template <bool VEC, bool SMT>
 static __global__ void __launch_bounds__(RX_WARPS * 32)
     k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
                   const float2 *__restrict__ konst, float2 *__restrict__ Dout,
                   float *__restrict__ fout, float2 *__restrict__ Aout) {
   extern __shared__ float4 smt[];
-  float2 *sq = (float2 *)(smt + (size_t)sh.ntiles * RX_TILE);
-  if (SMT) stage_table(smt, sq, gtab, sh.N, sh.ntiles);
+  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (blockDim.x >> 5);
   const float2 phi12 = konst[0], psi = konst[2];
-  for (int r = gw; r < sh.B; r += nw) {
-    const float *row = theta + (int64_t)r * sh.ld;
+  RowWalker<VEC> w{theta, sh.ld, sh.N, sh.B, sh.ntiles, nw, 0, 0, {}};
+  w.start(gw);
+  while (w.r < sh.B) {
+    const int r = w.r;
     float2 Cl = make_float2(0.f, 0.f), Al = Cl, El = Cl;  // this lane's shares
     float2 Brun = make_float2(0.f, 0.f);                   // sum of b before this tile
-    for (int tile = 0; tile < sh.ntiles; ++tile) {
+    bool row_done = false;
+    while (!row_done) {
+      const int tile = w.tile;
       const int m0 = tile * RX_TILE + lane * 8;
       float th[8];
-      load8<VEC>(row, m0, sh.N, th);
+      w.take(th);
       Mono loc = mono_zero();
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float d = tanhf(th[e]);
         const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
         mono_push(loc, d, p);
-        const float2 q = q_get<SMT>(sq, p, tile, e, lane);
+        const float2 q = q_of(p);
         const float d2 = d * d;
         El.x = fmaf(d2, q.x, El.x);
         El.y = fmaf(d2, q.y, El.y);
@@ -160,6 +193,7 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
       Al.y += loc.A.y;
       Brun.x += Bt.x;
       Brun.y += Bt.y;
+      row_done = w.advance();
     }
     const float Cr = warp_sum(Cl.x), Ci = warp_sum(Cl.y);
     const float Er = warp_sum(El.x), Ei = warp_sum(El.y);
@@ -181,14 +215,15 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
                   const float2 *__restrict__ Ain, const float *__restrict__ gf,
                   float *__restrict__ grad, int64_t ldg) {
   extern __shared__ float4 smt[];
-  float2 *sq = (float2 *)(smt + (size_t)sh.ntiles * RX_TILE);
-  if (SMT) stage_table(smt, sq, gtab, sh.N, sh.ntiles);
+  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (blockDim.x >> 5);
   const float2 phi12 = konst[0], psi = konst[2];
-  for (int r = gw; r < sh.B; r += nw) {
-    const float *row = theta + (int64_t)r * sh.ld;
+  RowWalker<VEC> wk{theta, sh.ld, sh.N, sh.B, sh.ntiles, nw, 0, 0, {}};
+  wk.start(gw);
+  while (wk.r < sh.B) {
+    const int r = wk.r;
     float *grow = grad + (int64_t)r * ldg;
     const float2 D = Din[r];
     const float2 Atot = Ain[r];
@@ -200,10 +235,12 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
     const float vr = 4.f * g * (D.x * psi.x + D.y * psi.y);
     const float vi = 4.f * g * (D.x * psi.y - D.y * psi.x);
     float2 Brun = make_float2(0.f, 0.f), Arun = make_float2(0.f, 0.f);
-    for (int tile = 0; tile < sh.ntiles; ++tile) {
+    bool row_done = false;
+    while (!row_done) {
+      const int tile = wk.tile;
       const int m0 = tile * RX_TILE + lane * 8;
       float th[8], d[8];
-      load8<VEC>(row, m0, sh.N, th);
+      wk.take(th);
       float2 la = make_float2(0.f, 0.f), lb = make_float2(0.f, 0.f);
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
@@ -216,7 +253,7 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
       }
       float2 ta, tb;
       const float2 ea = warp_excl_scan2(la, ta), eb = warp_excl_scan2(lb, tb);
-      float2 P = make_float2(Brun.x + eb.x, Brun.y + eb.y);  // sum of b before this lane
+      float2 P = make_float2(Brun.x + eb.x, Brun.y + eb.y);   // sum of b before this lane
       float2 Ap = make_float2(Arun.x + ea.x, Arun.y + ea.y);  // sum of a before this lane
       float out[8];
 #pragma unroll
@@ -228,9 +265,9 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
         // w = p2 P + p1 R
         const float wr = p.z * P.x - p.w * P.y + (p.x * Rr - p.y * Ri);
         const float wi = p.z * P.y + p.w * P.x + (p.x * Ri + p.y * Rr);
-        const float2 q = q_get<SMT>(sq, p, tile, e, lane);
-        const float s = (ur * wr - ui * wi) + d[e] * (vr * q.x - vi * q.y);
-        out[e] = s * (1.f - d[e] * d[e]);
+        const float2 q = q_of(p);
+        const float sv = (ur * wr - ui * wi) + d[e] * (vr * q.x - vi * q.y);
+        out[e] = sv * (1.f - d[e] * d[e]);
         P.x = fmaf(d[e], p.x, P.x);
         P.y = fmaf(d[e], p.y, P.y);
       }
@@ -239,6 +276,7 @@ static __global__ void __launch_bounds__(RX_WARPS * 32)
       Brun.y += tb.y;
       Arun.x += ta.x;
       Arun.y += ta.y;
+      row_done = wk.advance();
     }
   }
 }
@@ -256,7 +294,7 @@ static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int
   sh->ntiles = (prob->N + RX_TILE - 1) / RX_TILE;
   sh->ld = ld;
   sh->vec = (ld % 4 == 0) && (((uintptr_t)theta & 15) == 0);
-  const size_t need = (sizeof(float4) + sizeof(float2)) * (size_t)sh->ntiles * RX_TILE;
+  const size_t need = sizeof(float4) * (size_t)sh->ntiles * RX_TILE;
   *smem = need <= RX_SMEM_MAX ? need : 0;
   const int per_sm = *smem ? (int)std::max<size_t>(1, (228 * 1024) / (*smem + 1024)) : 4;
   *grid = sm_count() * std::min(per_sm, 4);

@@ -34,6 +34,49 @@ struct EvalShape {
 // one row) and the transposed reads (one domain, 32 rows) hit 32 different banks
 __device__ __forceinline__ int tile_idx(int d, int row) { return d * 32 + (row ^ ((d >> 2) & 31)); }
 
+// the genes (or sign word) of step `ms` that this thread stages, loaded into
+// registers ahead of time
+template <int KIND>
+struct StepRegs {
+  float4 v[8];
+  uint32_t w;
+  float4 p;
+};
+
+template <int KIND>
+__device__ __forceinline__ void load_step(const void *src, int64_t ld, const EvalShape &sh,
+                                          const float4 *table, int r0, int ms, StepRegs<KIND> &R) {
+  const int m = ms + threadIdx.x;
+  R.p = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (KIND == 2) {
+    const int row = threadIdx.x >> 3, wd = threadIdx.x & 7;
+    const int gr = r0 + row;
+    R.w = 0u;
+    if (gr < sh.NP && ms + wd * 32 < sh.N)
+      R.w = __ldg((const uint32_t *)src + (int64_t)gr * ld + (ms >> 5) + wd);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int f = threadIdx.x + k * EV_WARPS * 32;  // float4 slot: 32 rows x 64 columns
+      const int row = f >> 6, c4 = f & 63;
+      const int gr = r0 + row, mm = ms + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < sh.NP) {
+        const float *rp = (const float *)src + (int64_t)gr * ld;
+        if (KIND == 0 && mm + 4 <= sh.N) {
+          v = __ldg((const float4 *)(rp + mm));
+        } else {
+          if (mm < sh.N) v.x = __ldg(rp + mm);
+          if (mm + 1 < sh.N) v.y = __ldg(rp + mm + 1);
+          if (mm + 2 < sh.N) v.z = __ldg(rp + mm + 2);
+          if (mm + 3 < sh.N) v.w = __ldg(rp + mm + 3);
+        }
+      }
+      R.v[k] = v;
+    }
+  }
+}
+
 // partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
 template <int KIND, bool COMP>  // KIND 0: float genes (vector loads), 1: float genes (scalar), 2: packed bits
 static __global__ void __launch_bounds__(EV_WARPS * 32)
@@ -49,48 +92,27 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
   const int m1 = min(sh.N, m0 + sh.L);
   Mono run = mono_zero();   // running monoid of the segment (warp 0, lane = row)
   MonoK runk = monok_zero();
+  StepRegs<KIND> R;
+  if (m0 < m1) load_step<KIND>(src, ld, sh, table, r0, m0, R);
   for (int ms = m0; ms < m1; ms += EV_STEP) {
     __syncthreads();  // the previous step's tile and partials have been consumed
-    // ---- stage phasors
-    {
-      const int m = ms + threadIdx.x;
-      tb[threadIdx.x] = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // ---- stage genes / sign words
+    tb[threadIdx.x] = R.p;
     if (KIND == 2) {
-      uint32_t *tw = (uint32_t *)tile;  // [row][8 words]
-      const int row = threadIdx.x >> 3, wd = threadIdx.x & 7;
-      const int gr = r0 + row;
-      const int word = (ms >> 5) + wd;
-      uint32_t v = 0u;
-      if (gr < sh.NP && ms + wd * 32 < sh.N) v = __ldg((const uint32_t *)src + (int64_t)gr * ld + word);
-      tw[row * 8 + wd] = v;
+      ((uint32_t *)tile)[threadIdx.x] = R.w;  // [row][8 words]
     } else {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const int f = threadIdx.x + k * EV_WARPS * 32;  // float4 slot: 32 rows x 64 columns
-        const int row = f >> 6, c4 = f & 63;
-        const int gr = r0 + row, m = ms + 4 * c4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gr < sh.NP) {
-          const float *rp = (const float *)src + (int64_t)gr * ld;
-          if (KIND == 0 && m + 4 <= sh.N) {
-            v = __ldg((const float4 *)(rp + m));
-          } else {
-            if (m < sh.N) v.x = __ldg(rp + m);
-            if (m + 1 < sh.N) v.y = __ldg(rp + m + 1);
-            if (m + 2 < sh.N) v.z = __ldg(rp + m + 2);
-            if (m + 3 < sh.N) v.w = __ldg(rp + m + 3);
-          }
-        }
-        const int d = 4 * c4;
-        tile[tile_idx(d, row)] = v.x;
-        tile[tile_idx(d + 1, row)] = v.y;
-        tile[tile_idx(d + 2, row)] = v.z;
-        tile[tile_idx(d + 3, row)] = v.w;
+        const int f = threadIdx.x + k * EV_WARPS * 32;
+        const int row = f >> 6, d = 4 * (f & 63);
+        tile[tile_idx(d, row)] = R.v[k].x;
+        tile[tile_idx(d + 1, row)] = R.v[k].y;
+        tile[tile_idx(d + 2, row)] = R.v[k].z;
+        tile[tile_idx(d + 3, row)] = R.v[k].w;
       }
     }
     __syncthreads();
+    // the next step's loads are in flight while this step is scanned
+    if (ms + EV_STEP < m1) load_step<KIND>(src, ld, sh, table, r0, ms + EV_STEP, R);
     // ---- warp w: domains [32w, 32w + 32) of the step for rows r0 + lane
     Mono acc = mono_zero();
     const int d0 = warp * 32;
