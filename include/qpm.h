@@ -184,6 +184,17 @@ qpm_status qpm_generation(const qpm_state *st, int32_t *g_out);
 qpm_status qpm_get_population(qpm_state *st, int32_t inst, float *genes_out, int64_t ld,
                               float *fit_out, float *d_eff_out, qpm_stream_t stream);
 
+/* Checkpoint / resume: replace the population of instance `inst` (after qpm_init)
+ * by genes (device float [NP][ld], natural order, e.g. from qpm_get_population)
+ * and set the generation counter to `generation`.  Fitness is recomputed with the
+ * library's own scan, so it equals the value the saved run held bit for bit; since
+ * every random number is a function of (seed, instance, generation, individual,
+ * gene), continuing from a checkpoint reproduces the uninterrupted run exactly.
+ * Single-instance states, or states whose instances are all at `generation`.
+ * Errors: generation outside [0, G], ld < N -> QPM_ERR_ARG. */
+qpm_status qpm_set_population(qpm_state *st, int32_t inst, const float *genes, int64_t ld,
+                              int32_t generation, qpm_stream_t stream);
+
 /* Best individual of instance `inst` (largest f, lowest index on ties) with its
  * d_eff re-evaluated in FP64 on the device:
  *   genes_out device float [N], d_eff64_out device double [2], fit_out device float [1]

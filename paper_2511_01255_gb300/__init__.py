@@ -17,7 +17,7 @@ __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc",
     "qpm_release_caches", "qpm_deff_relaxed_fwd", "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
-    "qpm_get_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
+    "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
 ]
 
@@ -74,6 +74,7 @@ def lib(build=True):
             "qpm_generation": ([_P, _P], ctypes.c_int),
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
+            "qpm_set_population": ([_P, i32, _P, i64, i32, _P], ctypes.c_int),
             "qpm_get_best": ([_P, i32, _P, _P, _P, _P, _P], ctypes.c_int),
             "qpm_set_trace": ([_P, i32, _P], ctypes.c_int),
             "qpm_set_wait_timeout_ns": ([_P, u64], ctypes.c_int),
@@ -248,6 +249,12 @@ def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, s
     ld = _rows(genes_out, "genes_out")[1] if genes_out is not None else 0
     _check(lib().qpm_get_population(st, int(inst), _ptr(genes_out), ld, _ptr(fit_out),
                                     _ptr(d_eff_out), _stream(stream)))
+
+
+def qpm_set_population(st, inst, genes, generation, stream=None):
+    _, ld = _rows(genes, "genes")
+    _check(lib().qpm_set_population(st, int(inst), _ptr(genes), ld, int(generation),
+                                    _stream(stream)))
 
 
 def qpm_get_best(st, inst, genes_out=None, d_eff64_out=None, fit_out=None, index_out=None,

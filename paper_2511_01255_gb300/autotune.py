@@ -1,0 +1,99 @@
+"""Autotuner for the threads-per-individual (team width) of a workload.
+
+The library's automatic choice (qpm_params.team = 0) is a fixed rule: the
+smallest power of two in [32, 256] giving at most 4 domains per thread.  This
+module measures the candidates instead, through the C ABI, for a given problem
+size, population and execution form, and caches the fastest in a JSON file
+keyed by (device name, N bucket, NP, compensated, form).  Pass the result as
+qpm_params.team.
+"""
+import json
+import os
+import time
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+CANDIDATES = (32, 64, 128, 256)
+
+
+def n_bucket(N):
+    """Problems whose N rounds to the same power of two (in quarters) share an entry."""
+    b = 1
+    while b * 2 <= N:
+        b *= 2
+    q = (N - b) * 4 // b
+    return f"{b}+{q}/4"
+
+
+def _key(device, N, NP, compensated, form):
+    return f"{device}|N{n_bucket(N)}|NP{NP}|c{int(bool(compensated))}|f{form}"
+
+
+def load_cache(path=CACHE):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache, path=CACHE):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def choose(timings):
+    """Fastest candidate; ties go to the smaller team (fewer threads per row)."""
+    return min(sorted(timings), key=lambda t: timings[t])
+
+
+def measure_team(N, kappa1, kappa2, NP, team, compensated=0, form=None, gens=40, reps=3):
+    """Seconds per generation of one instance with the given team width."""
+    import torch
+
+    import paper_2511_01255_gb300 as q
+    form = q.RUN_PERSISTENT if form is None else form
+    G = gens * (reps + 1) + 1
+    prm = q.Params(NP, G, 0.5, 0.9, 1, 0, int(compensated), int(team))
+    with q.State([(N, kappa1, kappa2)], [prm]) as st:
+        st.init()
+        st.run(gens, form)  # warm-up (graph instantiation, caches)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.run(gens, form)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3 / gens)
+    return best
+
+
+def autotune_team(N, kappa1, kappa2, NP, compensated=0, form=None, gens=40,
+                  candidates=CANDIDATES, use_cache=True, path=CACHE, measure=None):
+    """Return the fastest team width for this workload (cached)."""
+    import torch
+
+    import paper_2511_01255_gb300 as q
+    form = q.RUN_PERSISTENT if form is None else form
+    device = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    key = _key(device, N, NP, compensated, form)
+    cache = load_cache(path) if use_cache else {}
+    if key in cache:
+        return cache[key]["team"]
+    measure = measure or measure_team
+    timings = {}
+    for t in candidates:
+        if t > 32 and N <= 4 * (t // 2):
+            continue  # more threads than 4 domains each would leave most of them idle
+        timings[t] = measure(N, kappa1, kappa2, NP, t, compensated, form, gens)
+    best = choose(timings)
+    cache[key] = {"team": best, "s_per_generation": {str(k): v for k, v in timings.items()},
+                  "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    if use_cache:
+        save_cache(cache, path)
+    return best

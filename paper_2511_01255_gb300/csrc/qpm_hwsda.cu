@@ -820,6 +820,47 @@ static __global__ void k_polish_accept(InstDev I, const int32_t *lead, float tau
   }
 }
 
+// ------------------------------------------------------ checkpoint / resume
+// Natural-order genes [NP][ld] -> slot 0 of every row (permuted), both selectors
+// 0, fitness recomputed with the same scan as every other evaluation (so it is
+// bit-identical to the value the run had), generation counter set.
+template <bool COMP>
+static __global__ void k_load_population(InstDev I, const float *__restrict__ genes, int64_t ld,
+                                         int generation) {
+  extern __shared__ Mono sh[];
+  const int t = threadIdx.x;
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
+    float *row = row_ptr(I, i, 0);
+    const float *src = genes + (int64_t)i * ld;
+    Acc<COMP> acc;
+    acc.zero();
+    for (int k4 = 0; k4 < I.c / 4; ++k4) {
+      const int j0 = t * I.c + 4 * k4;
+      float4 x;
+      x.x = j0 < I.N ? src[j0] : 0.f;
+      x.y = j0 + 1 < I.N ? src[j0 + 1] : 0.f;
+      x.z = j0 + 2 < I.N ? src[j0 + 2] : 0.f;
+      x.w = j0 + 3 < I.N ? src[j0 + 3] : 0.f;
+      *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
+      push4<COMP, false>(acc, I.table, I.T, k4, t, x);
+      if (k4 & 1) acc.fold();
+    }
+    const Mono m = block_reduce(acc.get(), sh);
+    if (t == 0) {
+      const float2 D = deff_from(m, I.konst[0], I.konst[1]);
+      I.fit[i] = fit_of(D);
+      I.dval[i] = D;
+      I.sel0[i] = 0;
+      I.sel1[i] = 0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *I.gen = generation;
+    for (int k = 0; k < 4; ++k) I.ctr[k] = 0u;
+  }
+}
+
 }  // namespace qpm
 
 // =========================================================== host: the state
@@ -1216,6 +1257,27 @@ extern "C" qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *te
 extern "C" qpm_status qpm_generation(const qpm_state *st, int32_t *g_out) {
   if (!st || !g_out) return fail(QPM_ERR_ARG, "NULL pointer");
   *g_out = st->g;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_set_population(qpm_state *st, int32_t inst, const float *genes,
+                                         int64_t ld, int32_t generation, qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n || !genes) return fail(QPM_ERR_ARG, "bad arguments");
+  const InstDev &I = st->h[inst];
+  if (ld < I.N) return fail(QPM_ERR_ARG, "ld < N");
+  if (generation < 0 || generation > I.G) return fail(QPM_ERR_ARG, "generation outside [0, G]");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  for (int k = 0; k < st->n; ++k)
+    if (k != inst && generation != st->g)
+      return fail(QPM_ERR_UNSUPPORTED, "all instances of a state share one generation count");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t sm = smem_bytes(I.T);
+  if (I.compensated)
+    k_load_population<true><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+  else
+    k_load_population<false><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+  QPM_CUDA(cudaGetLastError());
+  st->g = generation;
   return QPM_OK;
 }
 

@@ -230,3 +230,33 @@ def test_state_errors(q):
     assert e.value.status == 1
     assert st.generation == 3
     st.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_checkpoint_resume_is_bit_exact(q, mode):
+    """15 generations, checkpoint through qpm_get_population, a fresh state resumed with
+    qpm_set_population at generation 15, 15 more: identical to 30 uninterrupted ones."""
+    import torch
+    N, NP, G = 700, 40, 30
+    k1, k2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+    st, _ = make(q, N, k1, k2, NP, G, seed=21, comp=1, trace=False)
+    st.init()
+    st.run(G, mode)
+    Xa, fa, Da = snapshot(st)
+    st.close()
+    st, _ = make(q, N, k1, k2, NP, G, seed=21, comp=1, trace=False)
+    st.init()
+    st.run(15, mode)
+    Xc, fc, Dc = st.population()
+    torch.cuda.synchronize()
+    st.close()
+    st2, _ = make(q, N, k1, k2, NP, G, seed=21, comp=1, trace=False)
+    st2.init()
+    q.qpm_set_population(st2.h, 0, Xc, 15)
+    assert st2.generation == 15
+    X2, f2, _ = snapshot(st2)
+    assert np.array_equal(f2, fc.cpu().numpy())  # re-evaluated fitness is bit-identical
+    st2.run(G - 15, mode)
+    Xb, fb, Db = snapshot(st2)
+    st2.close()
+    assert np.array_equal(Xa, Xb) and np.array_equal(fa, fb)
