@@ -107,6 +107,22 @@ def algorithmic_lane_ops_per_gene_gen(compensated):
     return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
 
 
+def max_over_ranks(seconds, world, device=None):
+    """Slowest rank's step time (the job's time); identity for one process."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_max, world):
+    """Whole-job throughput of independent replicas (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
 def _time_cuda(fn, reps, flush=None):
     """Mean seconds per call of fn() with CUDA events on the current stream."""
     import torch
@@ -188,12 +204,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         best_f = float(fb.cpu())
         st.close()
-        t = sum(times) / len(times)
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(sum(times) / len(times), world, device="cuda")
         results[mode_name] = dict(s_per_step=t, wall=wall, clocks=clocks, best_f=best_f,
                                   launches_per_step=(3 + (2 * G if mode == q.RUN_GRAPH else 1)))
 
@@ -329,7 +340,7 @@ def run_gpu(args):
         return
     best = results[best_mode]
     sm_mhz = best["clocks"].get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    value = world * evals_per_run / best["s_per_step"]
+    value = job_throughput(evals_per_run, best["s_per_step"], world)
     line = {
         "metric": METRIC,
         "value": value,

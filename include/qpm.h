@@ -33,6 +33,7 @@
 #ifndef QPM_H_
 #define QPM_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -100,6 +101,27 @@ qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld, int
 qpm_status qpm_eval_packed(const qpm_problem *prob, const uint32_t *signs, int64_t ld_words,
                            int32_t NP, float *d_eff, float *fit, int32_t compensated,
                            qpm_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Other objectives of the paper's designs (Sec. 2.1 and Sec. 5).
+ * qpm_eval_shg: the SHG field integral int_0^L d(z) e^{-i dk z} dz (units of w) of
+ *   each row, with dk w = prob->kappa1 (prob->kappa2 is ignored); e_shg device
+ *   float2 [NP], fit device float [NP] = |e_shg|^2 (may be NULL).
+ * qpm_eval_multi: the multi-wavelength objective of Sec. 5,
+ *     f = sum_k |G0 - G_k| + beta (G_max - G_min),  G_k = |d_eff(probs[k])|,
+ *   to be minimised, for K <= 4 problems of equal N sharing one read of the
+ *   genes.  d_eff device float2 [NP][K] (may be NULL), objective device float [NP].
+ *   scratch: caller-owned device memory of at least
+ *   qpm_eval_multi_scratch_bytes(K, N, NP) bytes (segment partials).
+ * Phasor tables as for qpm_eval.  Errors: K outside [1, 4], unequal N, N < 1,
+ * NP < 1, ld < N, small scratch -> QPM_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+qpm_status qpm_eval_shg(const qpm_problem *prob, const float *genes, int64_t ld, int32_t NP,
+                        float *e_shg, float *fit, qpm_stream_t stream);
+qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const float *genes, int64_t ld,
+                          int32_t NP, float G0, float beta, float *d_eff, float *objective,
+                          void *scratch, size_t scratch_bytes, qpm_stream_t stream);
+size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP);
 
 /* Allocation-free qpm_eval (no counterpart in the paper; it exists for callers
  * that cannot allocate device memory: code running while a stream is being

@@ -41,6 +41,9 @@ def lib():
         L.orc_deff_genes.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, dbl, P, ctypes.c_int, P]
         L.orc_bruteforce.argtypes = [ctypes.c_int, dbl, dbl, ctypes.c_int, P, P]
         L.orc_bruteforce.restype = dbl
+        L.orc_shg_genes.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, P, ctypes.c_int, P]
+        L.orc_multi_objective.argtypes = [ctypes.c_int, ctypes.c_int, i64, ctypes.c_int, P, P, P,
+                                          dbl, dbl, ctypes.c_int, P, P]
         L.orc_grad_relaxed.argtypes = [ctypes.c_int, dbl, dbl, P, ctypes.c_int, P, P]
         L.orc_fit_relaxed.argtypes = [ctypes.c_int, dbl, dbl, P, ctypes.c_int, P]
         L.orc_fit_relaxed.restype = dbl
@@ -99,6 +102,28 @@ def deff_genes(X, kappa1, kappa2, Q=Q_DEFAULT):
     out = np.zeros((NP, 2))
     lib().orc_deff_genes(NP, N, N, kappa1, kappa2, _p(X), Q, _p(out))
     return out[:, 0] + 1j * out[:, 1]
+
+
+def shg_genes(X, kappa, Q=Q_DEFAULT):
+    """SHG field integral int_0^L d(z) e^{-i k z} dz (units of w) of each gene row."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    NP, N = X.shape
+    out = np.zeros((NP, 2))
+    lib().orc_shg_genes(NP, N, N, kappa, _p(X), Q, _p(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def multi_objective(X, kappas, G0, beta, Q=Q_DEFAULT):
+    """(d_eff [NP, K], objective [NP]) for the list of (kappa1, kappa2) pairs."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    NP, N = X.shape
+    K = len(kappas)
+    k1 = np.ascontiguousarray([k[0] for k in kappas], dtype=np.float64)
+    k2 = np.ascontiguousarray([k[1] for k in kappas], dtype=np.float64)
+    D = np.zeros((NP, K, 2))
+    obj = np.zeros(NP)
+    lib().orc_multi_objective(NP, N, N, K, _p(k1), _p(k2), _p(X), G0, beta, Q, _p(D), _p(obj))
+    return D[..., 0] + 1j * D[..., 1], obj
 
 
 def signs_from_bits(words, N):

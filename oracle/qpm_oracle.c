@@ -223,6 +223,73 @@ ORC_API double orc_bruteforce(int N, double kappa1, double kappa2, int Q, double
 }
 
 /* ------------------------------------------------------------------------- */
+/* SHG field integral (Sec. 2.1, first step of the derivation):              */
+/*   E2(L) prop. to int_0^L d(z) e^{-i dk z} dz = sum_j d_j int_j^{j+1} e^{-ik z} dz */
+/* each domain integrated with the Q-node Gauss-Legendre rule.                 */
+/* ------------------------------------------------------------------------- */
+static void shg_quad_one(int N, double k, const double *d, int Q, double *re, double *im) {
+  acc_t S = {0, 0, 0, 0};
+  for (int j = 0; j < N; ++j) {
+    double fr = 0.0, fi = 0.0;
+    for (int r = 0; r < Q; ++r) {
+      double x = j + 0.5 * (1.0 + g_t[r]);
+      double er, ei;
+      cis_neg(k, x, &er, &ei);
+      fr += 0.5 * g_w[r] * er;
+      fi += 0.5 * g_w[r] * ei;
+    }
+    acc_add(&S, d[j] * fr, d[j] * fi);
+  }
+  *re = acc_re(&S);
+  *im = acc_im(&S);
+}
+
+ORC_API void orc_shg_genes(int NP, int N, int64_t ld, double kappa, const float *X, int Q,
+                           double *E) {
+  ensure_rule(Q);
+#pragma omp parallel
+  {
+    double *d = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < NP; ++i) {
+      for (int j = 0; j < N; ++j) d[j] = (X[(int64_t)i * ld + j] < 0.0f) ? -1.0 : 1.0;
+      shg_quad_one(N, kappa, d, Q, &E[2 * i], &E[2 * i + 1]);
+    }
+    free(d);
+  }
+}
+
+/* Multi-wavelength objective (Sec. 5, multi-wavelength designs):
+ *   f = sum_i |G0 - G_i| + beta (G_max - G_min),  G_i = |d_eff| at (kappa1_i, kappa2_i)
+ * (to be minimised; G0 a large reference value, beta a weight).  D[2*(i*K+k)]. */
+ORC_API void orc_multi_objective(int NP, int N, int64_t ld, int K, const double *kappa1,
+                                 const double *kappa2, const float *X, double G0, double beta,
+                                 int Q, double *D, double *obj) {
+  ensure_rule(Q);
+#pragma omp parallel
+  {
+    double *d = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < NP; ++i) {
+      for (int j = 0; j < N; ++j) d[j] = (X[(int64_t)i * ld + j] < 0.0f) ? -1.0 : 1.0;
+      double f = 0.0, gmax = -1.0, gmin = 1e300;
+      for (int k = 0; k < K; ++k) {
+        double re, im;
+        deff_quad_one(N, kappa1[k], kappa2[k], d, Q, &re, &im);
+        D[2 * ((int64_t)i * K + k)] = re;
+        D[2 * ((int64_t)i * K + k) + 1] = im;
+        double G = sqrt(re * re + im * im);
+        f += fabs(G0 - G);
+        if (G > gmax) gmax = G;
+        if (G < gmin) gmin = G;
+      }
+      obj[i] = f + beta * (gmax - gmin);
+    }
+    free(d);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Relaxed gradient: d_k = tanh(theta_k), f = |D|^2.                          */
 /* D is a quadratic form in d; its derivative is taken term by term from the  */
 /* quadrature sum of deff_quad_one:                                           */

@@ -14,7 +14,7 @@ import os
 from . import build_lib
 
 __all__ = [
-    "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc",
+    "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc", "qpm_eval_shg", "qpm_eval_multi",
     "qpm_release_caches", "qpm_deff_relaxed_fwd", "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
@@ -63,6 +63,10 @@ def lib(build=True):
             "qpm_eval": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_eval_packed": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
             "qpm_eval_noalloc": ([_P, _P, i64, i32, _P, _P, i32, _P], ctypes.c_int),
+            "qpm_eval_shg": ([_P, _P, i64, i32, _P, _P, _P], ctypes.c_int),
+            "qpm_eval_multi": ([_P, i32, _P, i64, i32, ctypes.c_float, ctypes.c_float, _P, _P, _P,
+                                ctypes.c_size_t, _P], ctypes.c_int),
+            "qpm_eval_multi_scratch_bytes": ([i32, i32, i32], ctypes.c_size_t),
             "qpm_release_caches": ([], ctypes.c_int),
             "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
             "qpm_deff_relaxed_bwd": ([_P, _P, i64, i32, _P, _P, _P, _P, i64, _P], ctypes.c_int),
@@ -201,6 +205,27 @@ def deff_relaxed(theta, kappa1, kappa2):
     if _QpmDeff is None:
         _QpmDeff = _relaxed_function()
     return _QpmDeff.apply(theta, float(kappa1), float(kappa2))
+
+
+def qpm_eval_shg(N, kappa, genes, e_shg, fit=None, stream=None):
+    """SHG field integral of each gene row (dk w = kappa)."""
+    p = _problem(N, kappa, 0.0)
+    NP, ld = _rows(genes, "genes")
+    _check(lib().qpm_eval_shg(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(e_shg), _ptr(fit),
+                              _stream(stream)))
+
+
+def qpm_eval_multi(N, kappas, genes, G0, beta, objective, d_eff=None, stream=None):
+    """Multi-wavelength objective for the (kappa1, kappa2) pairs in `kappas`."""
+    import torch
+    K = len(kappas)
+    probs = (Problem * K)(*[_problem(N, k1, k2) for k1, k2 in kappas])
+    NP, ld = _rows(genes, "genes")
+    nbytes = lib().qpm_eval_multi_scratch_bytes(K, N, NP)
+    scratch = torch.empty(max(1, nbytes), dtype=torch.uint8, device=genes.device)
+    _check(lib().qpm_eval_multi(probs, K, _ptr(genes), ld, NP, float(G0), float(beta),
+                                _ptr(d_eff), _ptr(objective), _ptr(scratch), nbytes,
+                                _stream(stream)))
 
 
 def qpm_release_caches():

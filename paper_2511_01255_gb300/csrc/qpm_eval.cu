@@ -23,16 +23,11 @@ namespace qpm {
 static constexpr int EV_WARPS = 8;
 static constexpr int EV_STEP = 256;  // domains staged per step (32 per warp)
 
-struct EvalShape {
-  int NP, N, S, L;  // S segments of L domains (L a multiple of EV_STEP)
-  int groups;       // ceil(NP / 32)
-  int NPpad;        // groups * 32
-};
-
-// gene (row, domain d of the step) in the swizzled [domain][row] tile: the float4
-// column d/4 xor-permutes the row, so that both the coalesced stores (32 columns,
-// one row) and the transposed reads (one domain, 32 rows) hit 32 different banks
-__device__ __forceinline__ int tile_idx(int d, int row) { return d * 32 + (row ^ ((d >> 2) & 31)); }
+// genes of the step as float4 [column c4 = d/4][row], the row xor-swizzled by the
+// low 3 bits of the column: 8 consecutive columns of one row (a quarter-warp of
+// the coalesced staging stores) and 8 rows of one column (a quarter-warp of the
+// scan reads) both fall into 8 different 16-byte bank groups
+__device__ __forceinline__ int tile4_idx(int c4, int row) { return c4 * 32 + (row ^ (c4 & 7)); }
 
 // the genes (or sign word) of step `ms` that this thread stages, loaded into
 // registers ahead of time
@@ -82,7 +77,7 @@ template <int KIND, bool COMP>  // KIND 0: float genes (vector loads), 1: float 
 static __global__ void __launch_bounds__(EV_WARPS * 32)
     k_eval_seg(const void *__restrict__ src, int64_t ld, EvalShape sh,
                const float4 *__restrict__ table, float2 *__restrict__ part) {
-  __shared__ float tile[EV_STEP * 32];              // genes, or sign words for KIND 2
+  __shared__ float4 tile4[EV_STEP / 4 * 32];         // genes, or sign words for KIND 2
   __shared__ float4 tb[EV_STEP];                    // phasors of the step
   __shared__ Mono wpart[EV_WARPS][32];              // per-warp partials of the step
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -98,16 +93,12 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
     __syncthreads();  // the previous step's tile and partials have been consumed
     tb[threadIdx.x] = R.p;
     if (KIND == 2) {
-      ((uint32_t *)tile)[threadIdx.x] = R.w;  // [row][8 words]
+      ((uint32_t *)tile4)[threadIdx.x] = R.w;  // [row][8 words]
     } else {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int f = threadIdx.x + k * EV_WARPS * 32;
-        const int row = f >> 6, d = 4 * (f & 63);
-        tile[tile_idx(d, row)] = R.v[k].x;
-        tile[tile_idx(d + 1, row)] = R.v[k].y;
-        tile[tile_idx(d + 2, row)] = R.v[k].z;
-        tile[tile_idx(d + 3, row)] = R.v[k].w;
+        tile4[tile4_idx(f & 63, f >> 6)] = R.v[k];
       }
     }
     __syncthreads();
@@ -117,14 +108,19 @@ static __global__ void __launch_bounds__(EV_WARPS * 32)
     Mono acc = mono_zero();
     const int d0 = warp * 32;
     if (KIND == 2) {
-      const uint32_t w = ((const uint32_t *)tile)[lane * 8 + warp];
+      const uint32_t w = ((const uint32_t *)tile4)[lane * 8 + warp];
 #pragma unroll 8
       for (int e = 0; e < 32; ++e) mono_push(acc, ((w >> e) & 1u) ? -1.0f : 1.0f, tb[d0 + e]);
     } else {
-#pragma unroll 8
-      for (int e = 0; e < 32; ++e) {
-        const float x = tile[tile_idx(d0 + e, lane)];
-        mono_push(acc, x < 0.f ? -1.f : 1.f, tb[d0 + e]);
+#pragma unroll 2
+      for (int e4 = 0; e4 < 8; ++e4) {
+        const int c4 = (d0 >> 2) + e4;
+        const float4 x = tile4[tile4_idx(c4, lane)];
+        const float4 *pp = tb + 4 * c4;
+        mono_push(acc, x.x < 0.f ? -1.f : 1.f, pp[0]);
+        mono_push(acc, x.y < 0.f ? -1.f : 1.f, pp[1]);
+        mono_push(acc, x.z < 0.f ? -1.f : 1.f, pp[2]);
+        mono_push(acc, x.w < 0.f ? -1.f : 1.f, pp[3]);
       }
     }
     wpart[warp][lane] = acc;
@@ -240,7 +236,7 @@ qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **t
     const int32_t Npad = (p->N + 3) & ~3;
     QPM_CUDA(cudaMalloc(&e.table, sizeof(float4) * (size_t)Npad));
     QPM_CUDA(cudaMalloc(&e.part, sizeof(double2) * (size_t)table_part_count(Npad)));
-    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 3));
+    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 4));
     QPM_CUDA(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
     TableSpec s{p->N, Npad, 1, Npad, p->kappa1, p->kappa2};
     qpm_status st = launch_table(s, e.table, e.part, e.konst, nullptr, stream);
@@ -274,7 +270,7 @@ qpm_status get_scratch(cudaStream_t stream, size_t bytes, void **ptr) {
 }
 }  // namespace
 
-static EvalShape eval_shape(int NP, int N) {
+EvalShape eval_shape(int NP, int N) {
   EvalShape sh;
   sh.NP = NP;
   sh.N = N;

@@ -1076,7 +1076,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.dval = (float2 *)take(NP * sizeof(float2));
     I.table = (float4 *)take(Np * sizeof(float4));
     I.tpart = (double2 *)take((size_t)table_part_count(I.Npad) * sizeof(double2));
-    I.konst = (float2 *)take(3 * sizeof(float2));
+    I.konst = (float2 *)take(4 * sizeof(float2));
     I.konst64 = (double2 *)take(3 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));

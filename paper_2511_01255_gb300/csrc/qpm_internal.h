@@ -27,7 +27,7 @@ struct TableSpec {
   double kappa1, kappa2;
 };
 
-// float2 konst[3] = {phi1*phi2, cdiag, psi}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
+// float2 konst[4] = {phi1*phi2, cdiag, psi, phi1}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
 // part: scratch of table_part_count(Npad) double2
 int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
@@ -37,6 +37,15 @@ qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2
 // (device, N, kappa1, kappa2); built on `stream` on a miss (caller holds no lock)
 qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
                         const float2 **konst);
+
+// split of qpm_eval-style work: S segments of L domains (L a multiple of 256),
+// rows in groups of 32
+struct EvalShape {
+  int NP, N, S, L;
+  int groups;  // ceil(NP / 32)
+  int NPpad;   // groups * 32
+};
+EvalShape eval_shape(int NP, int N);
 
 // current device's SM count (cached per device)
 int sm_count();

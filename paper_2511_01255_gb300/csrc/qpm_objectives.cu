@@ -1,0 +1,289 @@
+// qpm_objectives.cu -- the other objectives of the paper's designs.
+//
+// SHG field (Sec. 2.1, the single integral before the cascade):
+//   E2 prop. to int_0^L d(z) e^{-i dk z} dz = phi(kappa) sum_j d_j e^{-i kappa j},
+// used by the multi-wavelength SHG designs of Sec. 5.  A plain complex sum per
+// row: each CTA takes 8 rows, each thread 4-domain groups spaced by the CTA width
+// (coalesced float4 loads), so one phasor read serves the 8 rows.
+//
+// Multi-wavelength objective (Sec. 5): f = sum_k |G0 - G_k| + beta (G_max - G_min)
+// with G_k = |d_eff(kappa1_k, kappa2_k)|, to be minimised.  The K cascaded scans
+// share one staged copy of the genes: 32 rows x 256 domains per step are copied
+// into shared memory once, and every warp runs its 32 domains through the K
+// phasor tables of the step.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qpm_common.cuh"
+#include "qpm_internal.h"
+
+namespace qpm {
+
+// ------------------------------------------------------------------ SHG field
+static constexpr int SHG_ROWS = 8;
+static constexpr int SHG_THREADS = 256;
+
+template <bool VEC>
+static __global__ void __launch_bounds__(SHG_THREADS)
+    k_shg(const float *__restrict__ genes, int64_t ld, int NP, int N,
+          const float4 *__restrict__ table, const float2 *__restrict__ konst,
+          float2 *__restrict__ eout, float *__restrict__ fout) {
+  __shared__ float2 red[SHG_THREADS / 32][SHG_ROWS];
+  const int r0 = blockIdx.x * SHG_ROWS;
+  float2 S[SHG_ROWS];
+#pragma unroll
+  for (int r = 0; r < SHG_ROWS; ++r) S[r] = make_float2(0.f, 0.f);
+  for (int m = 4 * threadIdx.x; m < N; m += 4 * SHG_THREADS) {
+    float2 p[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = m + q < N ? __ldg(table + m + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      p[q] = make_float2(t.x, t.y);  // e^{-i kappa m}
+    }
+#pragma unroll
+    for (int r = 0; r < SHG_ROWS; ++r) {
+      if (r0 + r >= NP) break;
+      const float *row = genes + (int64_t)(r0 + r) * ld;
+      float x[4];
+      if (VEC && m + 4 <= N) {
+        const float4 v = __ldg((const float4 *)(row + m));
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = m + q < N ? __ldg(row + m + q) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float d = x[q] < 0.f ? -1.f : 1.f;
+        S[r].x = fmaf(d, p[q].x, S[r].x);
+        S[r].y = fmaf(d, p[q].y, S[r].y);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < SHG_ROWS; ++r) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      S[r].x += __shfl_xor_sync(0xffffffffu, S[r].x, s);
+      S[r].y += __shfl_xor_sync(0xffffffffu, S[r].y, s);
+    }
+    if (lane == 0) red[warp][r] = S[r];
+  }
+  __syncthreads();
+  if (threadIdx.x < SHG_ROWS && r0 + (int)threadIdx.x < NP) {
+    const int r = threadIdx.x;
+    float2 t = red[0][r];
+    for (int w = 1; w < SHG_THREADS / 32; ++w) {
+      t.x += red[w][r].x;
+      t.y += red[w][r].y;
+    }
+    const float2 ph = konst[3];  // phi(kappa)
+    const float2 E = make_float2(ph.x * t.x - ph.y * t.y, ph.x * t.y + ph.y * t.x);
+    eout[r0 + r] = E;
+    if (fout) fout[r0 + r] = fit_of(E);
+  }
+}
+
+// ------------------------------------------------- multi-wavelength objective
+static constexpr int MW_STEP = 256;
+static constexpr int MW_WARPS = 8;
+static constexpr int MW_KMAX = 4;
+
+struct MultiTables {
+  const float4 *t[MW_KMAX];
+  const float2 *konst[MW_KMAX];
+};
+
+__device__ __forceinline__ int mw_idx(int c4, int row) { return c4 * 32 + (row ^ (c4 & 7)); }
+
+// dynamic smem: tile [64 x 32] float4 | tables [K][256] float4 | partials [K][8][32] Mono
+template <bool VEC, int K>
+static __global__ void __launch_bounds__(MW_WARPS * 32)
+    k_multi_seg(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
+                float2 *__restrict__ part) {
+  extern __shared__ float4 mw[];
+  float4 *tile4 = mw;
+  float4 *tb = mw + MW_STEP / 4 * 32;
+  Mono *wpart = (Mono *)(tb + K * MW_STEP);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x, r0 = blockIdx.y * 32;
+  const int m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  Mono run[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) run[k] = mono_zero();
+  for (int ms = m0; ms < m1; ms += MW_STEP) {
+    __syncthreads();
+    {
+      const int m = ms + threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        tb[k * MW_STEP + threadIdx.x] = m < sh.N ? __ldg(mt.t[k] + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int f = threadIdx.x + i * MW_WARPS * 32;
+      const int row = f >> 6, c4 = f & 63;
+      const int gr = r0 + row, mm = ms + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < sh.NP) {
+        const float *rp = genes + (int64_t)gr * ld;
+        if (VEC && mm + 4 <= sh.N) {
+          v = __ldg((const float4 *)(rp + mm));
+        } else {
+          if (mm < sh.N) v.x = __ldg(rp + mm);
+          if (mm + 1 < sh.N) v.y = __ldg(rp + mm + 1);
+          if (mm + 2 < sh.N) v.z = __ldg(rp + mm + 2);
+          if (mm + 3 < sh.N) v.w = __ldg(rp + mm + 3);
+        }
+      }
+      tile4[mw_idx(c4, row)] = v;
+    }
+    __syncthreads();
+    Mono acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = mono_zero();
+    for (int e4 = 0; e4 < 8; ++e4) {
+      const int c4 = warp * 8 + e4;
+      const float4 x = tile4[mw_idx(c4, lane)];
+      const float d0 = x.x < 0.f ? -1.f : 1.f, d1 = x.y < 0.f ? -1.f : 1.f;
+      const float d2 = x.z < 0.f ? -1.f : 1.f, d3 = x.w < 0.f ? -1.f : 1.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float4 *pp = tb + k * MW_STEP + 4 * c4;
+        mono_push(acc[k], d0, pp[0]);
+        mono_push(acc[k], d1, pp[1]);
+        mono_push(acc[k], d2, pp[2]);
+        mono_push(acc[k], d3, pp[3]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) wpart[(k * MW_WARPS + warp) * 32 + lane] = acc[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        for (int w = 0; w < MW_WARPS; ++w)
+          run[k] = mono_combine(run[k], wpart[(k * MW_WARPS + w) * 32 + lane]);
+    }
+  }
+  if (warp == 0) {
+    const size_t stride = (size_t)sh.S * sh.NPpad;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + r0 + lane;
+      part[o] = run[k].A;
+      part[o + stride] = run[k].B;
+      part[o + 2 * stride] = run[k].C;
+    }
+  }
+}
+
+template <int K>
+static __global__ void k_multi_combine(EvalShape sh, const float2 *__restrict__ part, MultiTables mt,
+                                       float G0, float beta, float2 *__restrict__ deff,
+                                       float *__restrict__ obj) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sh.NP) return;
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  float f = 0.f, gmax = -1.f, gmin = 3.0e38f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    Mono acc = mono_zero();
+    for (int s = 0; s < sh.S; ++s) {
+      const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + i;
+      Mono r;
+      r.A = part[o];
+      r.B = part[o + stride];
+      r.C = part[o + 2 * stride];
+      acc = mono_combine(acc, r);
+    }
+    const float2 D = deff_from(acc, mt.konst[k][0], mt.konst[k][1]);
+    if (deff) deff[(size_t)i * K + k] = D;
+    const float G = sqrtf(fit_of(D));
+    f += fabsf(G0 - G);
+    gmax = fmaxf(gmax, G);
+    gmin = fminf(gmin, G);
+  }
+  obj[i] = f + beta * (gmax - gmin);
+}
+
+
+}  // namespace qpm
+
+using namespace qpm;
+
+extern "C" qpm_status qpm_eval_shg(const qpm_problem *prob, const float *genes, int64_t ld,
+                                   int32_t NP, float *e_shg, float *fit, qpm_stream_t stream) {
+  if (!prob || !genes || !e_shg) return fail(QPM_ERR_ARG, "qpm_eval_shg: NULL pointer");
+  if (prob->N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval_shg: need N >= 1 and NP >= 1");
+  if (ld < prob->N) return fail(QPM_ERR_ARG, "qpm_eval_shg: leading dimension smaller than the row");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float4 *table;
+  const float2 *konst;
+  qpm_status st = cached_table(prob, s, &table, &konst);
+  if (st != QPM_OK) return st;
+  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
+  const int grid = (NP + SHG_ROWS - 1) / SHG_ROWS;
+  if (vec)
+    k_shg<true><<<grid, SHG_THREADS, 0, s>>>(genes, ld, NP, prob->N, table, konst, (float2 *)e_shg, fit);
+  else
+    k_shg<false><<<grid, SHG_THREADS, 0, s>>>(genes, ld, NP, prob->N, table, konst, (float2 *)e_shg, fit);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const float *genes,
+                                     int64_t ld, int32_t NP, float G0, float beta, float *d_eff,
+                                     float *objective, void *scratch, size_t scratch_bytes,
+                                     qpm_stream_t stream) {
+  if (!probs || !genes || !objective) return fail(QPM_ERR_ARG, "qpm_eval_multi: NULL pointer");
+  if (K < 1 || K > MW_KMAX) return fail(QPM_ERR_ARG, "qpm_eval_multi: need 1 <= K <= 4");
+  const int N = probs[0].N;
+  for (int k = 1; k < K; ++k)
+    if (probs[k].N != N) return fail(QPM_ERR_ARG, "qpm_eval_multi: all problems need the same N");
+  if (N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval_multi: need N >= 1 and NP >= 1");
+  if (ld < N) return fail(QPM_ERR_ARG, "qpm_eval_multi: leading dimension smaller than the row");
+  cudaStream_t s = (cudaStream_t)stream;
+  MultiTables mt;
+  for (int k = 0; k < MW_KMAX; ++k) {
+    mt.t[k] = nullptr;
+    mt.konst[k] = nullptr;
+  }
+  for (int k = 0; k < K; ++k) {
+    qpm_status st = cached_table(&probs[k], s, &mt.t[k], &mt.konst[k]);
+    if (st != QPM_OK) return st;
+  }
+  const EvalShape sh = eval_shape(NP, N);
+  const size_t need = sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
+  if (!scratch || scratch_bytes < need)
+    return fail(QPM_ERR_ARG, "qpm_eval_multi: scratch smaller than qpm_eval_multi_scratch_bytes()");
+  float2 *part = (float2 *)scratch;
+  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
+  const dim3 grid(sh.S, sh.groups);
+  const size_t smem = sizeof(float4) * (MW_STEP / 4 * 32 + (size_t)K * MW_STEP) +
+                      sizeof(Mono) * (size_t)K * MW_WARPS * 32;
+#define QPM_MW(KK)                                                                          \
+  {                                                                                         \
+    const void *fn = vec ? (const void *)k_multi_seg<true, KK> : (const void *)k_multi_seg<false, KK>; \
+    QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    EvalShape shv = sh;                                                                     \
+    int64_t ldv = ld;                                                                       \
+    void *args[] = {(void *)&genes, &ldv, &shv, &mt, &part};                                \
+    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(MW_WARPS * 32), args, smem, s));               \
+    k_multi_combine<KK><<<(NP + 127) / 128, 128, 0, s>>>(sh, part, mt, G0, beta,            \
+                                                         (float2 *)d_eff, objective);       \
+  }
+  if (K == 1) QPM_MW(1) else if (K == 2) QPM_MW(2) else if (K == 3) QPM_MW(3) else QPM_MW(4)
+#undef QPM_MW
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
+}
+
+extern "C" size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP) {
+  if (K < 1 || N < 1 || NP < 1) return 0;
+  const EvalShape sh = eval_shape(NP, N);
+  return sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
+}

@@ -93,6 +93,7 @@ static __global__ void k_table_finalize(int nparts, const double2 *__restrict__ 
   konst[0] = make_float2((float)phi12.x, (float)phi12.y);
   konst[1] = make_float2((float)cdiag.x, (float)cdiag.y);
   konst[2] = make_float2((float)ps.x, (float)ps.y);
+  konst[3] = make_float2((float)p1.x, (float)p1.y);
   if (konst64) {
     konst64[0] = phi12;
     konst64[1] = cdiag;

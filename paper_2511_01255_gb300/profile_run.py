@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--comp", type=int, default=-1, help="override the compensated flag")
     ap.add_argument("--team", type=int, default=0, help="threads per individual (0 = automatic)")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batch workload")
+    ap.add_argument("--packed", type=int, default=0, help="eval workload: packed sign words")
     a = ap.parse_args()
     q.lib()
     if a.workload == "relaxed":
@@ -49,17 +50,23 @@ def main():
         return
     if a.workload == "eval":
         N, NP = 100000, 1024
-        X = torch.rand((NP, N), device="cuda") * 2 - 1
         D = torch.empty((NP, 2), device="cuda")
         comp = 0 if a.comp < 0 else a.comp
+        if a.packed:
+            X = torch.randint(-2 ** 31, 2 ** 31 - 1, (NP, (N + 31) // 32), dtype=torch.int32,
+                              device="cuda")
+            fn = q.qpm_eval_packed
+        else:
+            X = torch.rand((NP, N), device="cuda") * 2 - 1
+            fn = q.qpm_eval
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q.qpm_eval(N, 1.0, 2.0, X, D, None, comp)
+        fn(N, 1.0, 2.0, X, D, None, comp)
         e0.record()
         for _ in range(a.reps):
-            q.qpm_eval(N, 1.0, 2.0, X, D, None, comp)
+            fn(N, 1.0, 2.0, X, D, None, comp)
         e1.record()
         torch.cuda.synchronize()
-        print(f"eval N={N} NP={NP}: {e0.elapsed_time(e1) / a.reps:.3f} ms per call")
+        print(f"eval N={N} NP={NP} packed={a.packed}: {e0.elapsed_time(e1) / a.reps:.3f} ms per call")
         return
     form = {"launches": q.RUN_LAUNCHES, "graph": q.RUN_GRAPH, "persistent": q.RUN_PERSISTENT,
             "batched": q.RUN_BATCHED}[a.form]

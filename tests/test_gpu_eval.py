@@ -97,3 +97,55 @@ def test_eval_full_size_sampled(q, orc, comp):
     ref = orc.deff_genes(X[rows], K1, K2)
     err = deff_err(D[rows], ref, N)
     assert err.max() < TOL_D, err
+
+
+@pytest.mark.parametrize("N", [1, 7, 1000, 4097, 100000])
+def test_shg_field_against_oracle(q, orc, N):
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    NP = 19 if N < 100000 else 6
+    X = W.random_genes(NP, N, seed=N + 3)
+    X[0] = W.alternating(N)
+    E = torch.empty((NP, 2), device="cuda")
+    f = torch.empty(NP, device="cuda")
+    k = 2 * math.pi / 6.9
+    q.qpm_eval_shg(N, k, torch.from_numpy(X).cuda(), E, f)
+    torch.cuda.synchronize()
+    E = E.cpu().numpy()
+    ref = orc.shg_genes(X, k)
+    z = E[:, 0] + 1j * E[:, 1]
+    # random rows cancel: floor at 1e-3 of the all-up magnitude scale N
+    err = np.abs(z - ref) / np.maximum(np.abs(ref), 1e-3 * N)
+    assert err.max() < TOL_D
+    # first-order QPM at kappa = pi: |E| = 2N/pi
+    E2 = torch.empty((1, 2), device="cuda")
+    q.qpm_eval_shg(N, math.pi, torch.from_numpy(W.alternating(N)[None]).cuda(), E2)
+    torch.cuda.synchronize()
+    assert abs(np.hypot(*E2.cpu().numpy()[0]) - 2 * N / math.pi) <= TOL_D * 2 * N / math.pi
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+def test_multi_wavelength_objective_against_oracle(q, orc, K):
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    N, NP = 3001, 41
+    X = W.random_genes(NP, N, seed=K)
+    kap = [(2 * math.pi / (6.5 + 0.4 * k), 2 * math.pi / (1.4 + 0.1 * k)) for k in range(K)]
+    G0, beta = 2.0e4, 0.7
+    obj = torch.empty(NP, device="cuda")
+    D = torch.empty((NP, K, 2), device="cuda")
+    q.qpm_eval_multi(N, kap, torch.from_numpy(X).cuda(), G0, beta, obj, D)
+    torch.cuda.synchronize()
+    Dr, objr = orc.multi_objective(X, kap, G0, beta)
+    Dg = D.cpu().numpy()
+    for k in range(K):
+        assert deff_err(Dg[:, k], Dr[:, k], N).max() < TOL_D
+    # each |G0 - G_k| term carries the d_eff error; FP32 rounding of G0-sized sums
+    scale = K * G0 + beta * np.abs(Dr).max()
+    assert np.max(np.abs(obj.cpu().numpy() - objr)) <= TOL_D * scale
+    # one problem through the fused path equals qpm_eval
+    if K == 1:
+        D1 = torch.empty((NP, 2), device="cuda")
+        q.qpm_eval(N, kap[0][0], kap[0][1], torch.from_numpy(X).cuda(), D1)
+        torch.cuda.synchronize()
+        assert np.array_equal(D1.cpu().numpy(), Dg[:, 0])

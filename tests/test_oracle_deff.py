@@ -129,3 +129,32 @@ def test_bruteforce_enumeration(orc):
     assert best == fit.max() and mask == int(np.argmax(fit))
     # the sign-flipped twin of the optimum attains the same value
     assert fit[mask ^ ((1 << N) - 1)] == best
+
+
+def test_shg_integral_closed_forms(orc):
+    # all domains up: int_0^N e^{-ikz} dz = (1 - e^{-ikN}) / (ik)
+    for N, k in ((1, 0.7), (40, 1.3), (333, 2 * np.pi / 6.9)):
+        X = np.ones((1, N), dtype=np.float32)
+        E = orc.shg_genes(X, k)[0]
+        exact = (1 - np.exp(-1j * k * N)) / (1j * k)
+        assert abs(E - exact) <= 1e-12 * max(1.0, abs(exact))
+    # first-order QPM of SHG: alternating domains at kappa = pi give |E| = (2/pi) N
+    for N in (2, 10, 1001):
+        X = np.where(np.arange(N) % 2 == 0, 1.0, -1.0).astype(np.float32)[None]
+        E = orc.shg_genes(X, np.pi)[0]
+        assert abs(abs(E) - 2 * N / np.pi) <= 1e-12 * N
+        # the SHG field is linear in d: a global flip negates it exactly (|E| is kept)
+        assert orc.shg_genes(-X, np.pi)[0] == -E
+
+
+def test_multi_objective_against_single_problems(orc):
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, (5, 120)).astype(np.float32)
+    kap = [(2 * np.pi / 6.9, 2 * np.pi / 1.55), (2 * np.pi / 7.4, 2 * np.pi / 1.7),
+           (0.0, 0.0)]
+    D, obj = orc.multi_objective(X, kap, G0=1e4, beta=0.5)
+    for k, (k1, k2) in enumerate(kap):
+        assert np.allclose(D[:, k], orc.deff_genes(X, k1, k2), rtol=0, atol=0)
+    G = np.abs(D)
+    ref = np.sum(np.abs(1e4 - G), axis=1) + 0.5 * (G.max(axis=1) - G.min(axis=1))
+    assert np.allclose(obj, ref, rtol=1e-15, atol=0)
