@@ -68,6 +68,9 @@ typedef struct {
   int32_t gwo_combine; /* 0: (X1+X2+X3)/3; 1: |X_k|-weighted, per dimension */
   int32_t compensated; /* 0: plain FP32 scan; 1: Kahan-compensated FP32 scan */
   int32_t team;        /* threads per individual: 0 = automatic, else 32, 64, 128 or 256 */
+  int32_t f_schedule;  /* 0: F constant; 1: decaying F of Sec. 3.1.1,
+                          F_g = F (cos(pi g / 2G) + 1) / 2 (1 - 0.2 (g / G)^2),
+                          evaluated in FP64 and rounded to FP32 */
 } qpm_params;
 
 /* Execution modes of qpm_run. */

@@ -25,7 +25,7 @@ class OrcCfg(ctypes.Structure):
     _fields_ = [("NP", ctypes.c_int32), ("N", ctypes.c_int32), ("ld", ctypes.c_int64),
                 ("G", ctypes.c_int32), ("F", ctypes.c_float), ("CR", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("inst", ctypes.c_uint32),
-                ("combine", ctypes.c_int32)]
+                ("combine", ctypes.c_int32), ("f_schedule", ctypes.c_int32)]
 
 
 def lib():
@@ -55,6 +55,8 @@ def lib():
         L.orc_init_population.argtypes = [P, P]
         L.orc_de_trials.argtypes = [P, u32, P, P]
         L.orc_top3.argtypes = [i32, P, P]
+        L.orc_F_of.argtypes = [P, i32]
+        L.orc_F_of.restype = ctypes.c_float
         L.orc_a_of.argtypes = [i32, i32]
         L.orc_a_of.restype = ctypes.c_float
         L.orc_gwo_candidates.argtypes = [P, u32, P, P, P]
@@ -188,8 +190,12 @@ def a_of(g, G):
     return lib().orc_a_of(g, G)
 
 
-def make_cfg(NP, N, G, F, CR, seed, inst=0, combine=0):
-    return OrcCfg(NP, N, N, G, F, CR, seed, inst, combine)
+def make_cfg(NP, N, G, F, CR, seed, inst=0, combine=0, f_schedule=0):
+    return OrcCfg(NP, N, N, G, F, CR, seed, inst, combine, f_schedule)
+
+
+def F_of(cfg, g):
+    return lib().orc_F_of(ctypes.byref(cfg), g)
 
 
 def init_population(cfg):

@@ -490,7 +490,21 @@ typedef struct {
   uint64_t seed;
   uint32_t inst;
   int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension */
+  int32_t f_schedule; /* 0 = constant F; 1 = decaying F of Sec. 3.1.1 */
 } orc_cfg;
+
+/* F of generation g.  Sec. 3.1.1 lets F follow (cos(pi g / 2G) + 1) / 2 times a
+ * quadratic factor that falls from 1.0 to 0.8 over the run; the reading taken
+ * here is F_g = F (cos(pi g / 2G) + 1) / 2 (1 - 0.2 (g/G)^2) in FP64, rounded to
+ * FP32.  Its diversity-triggered adjustments have unstated thresholds and are not
+ * modelled. */
+ORC_API float orc_F_of(const orc_cfg *c, int32_t g) {
+  if (!c->f_schedule) return c->F;
+  const double x = (double)g / (double)c->G;
+  const double cs = 0.5 * (cos(M_PI * (double)g / (2.0 * (double)c->G)) + 1.0);
+  const double qd = 1.0 - 0.2 * x * x;
+  return (float)((double)c->F * cs * qd);
+}
 
 static inline float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
 
@@ -512,9 +526,10 @@ static void de_trial_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
   const float *x1 = X + (int64_t)r[0] * c->ld;
   const float *x2 = X + (int64_t)r[1] * c->ld;
   const float *x3 = X + (int64_t)r[2] * c->ld;
+  const float F = orc_F_of(c, (int32_t)g);
   for (int32_t j = 0; j < c->N; ++j) {
     float diff = x2[j] - x3[j];
-    float step = c->F * diff;
+    float step = F * diff;
     float v = clamp1(x1[j] + step);
     float randb = u24(rng_word(c->seed, c->inst, TAG_CR, g, (uint32_t)i, (uint32_t)j));
     u[j] = (randb <= c->CR || j == r[3]) ? v : x[j];

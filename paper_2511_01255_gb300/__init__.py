@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
     _fields_ = [("NP", ctypes.c_int32), ("G", ctypes.c_int32), ("F", ctypes.c_float),
                 ("CR", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("gwo_combine", ctypes.c_int32), ("compensated", ctypes.c_int32),
-                ("team", ctypes.c_int32)]
+                ("team", ctypes.c_int32), ("f_schedule", ctypes.c_int32)]
 
 
 _lib = None

@@ -4,7 +4,8 @@ Each .cu file is compiled to an object in parallel with
 `nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo -O3`, then linked into
 paper_2511_01255_gb300/_build/libqpm.so.  No fast-math: the DE/GWO update
 arithmetic relies on IEEE-rounded single operations and the fitness on accurate
-sincosf.
+sincosf; host code is built without floating-point contraction so that the
+F schedule computed on the host is the exact IEEE evaluation of its formula.
 """
 import concurrent.futures as cf
 import glob
@@ -19,6 +20,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqpm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", SRC]
 
 

@@ -53,6 +53,7 @@ struct InstDev {
   int32_t *gen;          // [1] completed generations
   int32_t *best;         // [1] best index (get_best)
   float *trace;          // optional fitness trace
+  const float *Fsched;   // [G] F of every generation, or NULL for constant F
 };
 
 template <bool NC>
@@ -181,7 +182,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
-  const float F = I.F, CR = I.CR;
+  const float F = I.Fsched ? I.Fsched[g] : I.F, CR = I.CR;
   Acc<COMP> acc;
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
@@ -1003,6 +1004,8 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
       return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0 or 1");
     if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256)
       return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128 or 256");
+    if (q.f_schedule != 0 && q.f_schedule != 1)
+      return fail(QPM_ERR_ARG, "qpm_create: f_schedule must be 0 or 1");
     if (!std::isfinite(p.kappa1) || !std::isfinite(p.kappa2))
       return fail(QPM_ERR_ARG, "qpm_create: kappa must be finite");
   }
@@ -1053,6 +1056,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += align_up((size_t)table_part_count(I.Npad) * sizeof(double2), 256);
     total += 256 + 256 + 256;  // konst, konst64, lead
     total += align_up(6 * NP * sizeof(unsigned long long), 256);
+    total += align_up((size_t)q.G * sizeof(float), 256);  // F schedule
     total += 256 + 256 + 256;  // ctr, gen, best
   }
   const size_t desc_off = total;
@@ -1080,6 +1084,8 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.konst64 = (double2 *)take(3 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
+    I.Fsched = st->params[k].f_schedule ? (const float *)take((size_t)I.G * sizeof(float))
+                                        : (take((size_t)I.G * sizeof(float)), nullptr);
     I.ctr = (unsigned *)take(4 * sizeof(unsigned));
     I.gen = (int32_t *)take(sizeof(int32_t));
     I.best = (int32_t *)take(sizeof(int32_t));
@@ -1094,7 +1100,21 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
       return (long long)st->h[a].NP * st->h[a].Npad > (long long)st->h[b].NP * st->h[b].Npad;
     });
-    e = cudaMemcpy(st->d_order, order.data(), sizeof(int32_t) * n_inst, cudaMemcpyHostToDevice);
+    // F schedules (Sec. 3.1.1): cosine decay times a quadratic factor 1.0 -> 0.8
+    for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
+      if (!st->h[k].Fsched) continue;
+      const int G = st->h[k].G;
+      std::vector<float> F(G);
+      for (int g = 0; g < G; ++g) {
+        const double x = (double)g / (double)G;
+        const double c = 0.5 * (std::cos(M_PI * (double)g / (2.0 * (double)G)) + 1.0);
+        const double qd = 1.0 - 0.2 * x * x;
+        F[g] = (float)((double)st->params[k].F * c * qd);
+      }
+      e = cudaMemcpy((void *)st->h[k].Fsched, F.data(), sizeof(float) * G, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpy(st->d_order, order.data(), sizeof(int32_t) * n_inst, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(st->d_insts, st->h.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaMemcpy"); }

@@ -25,9 +25,10 @@ def q():
     return q
 
 
-def make(q, N, k1, k2, NP, G, F=0.5, CR=0.9, seed=1, combine=0, comp=0, trace=True, team=0):
+def make(q, N, k1, k2, NP, G, F=0.5, CR=0.9, seed=1, combine=0, comp=0, trace=True, team=0,
+         f_schedule=0):
     import torch
-    prm = q.Params(NP, G, F, CR, seed, combine, comp, team)
+    prm = q.Params(NP, G, F, CR, seed, combine, comp, team, f_schedule)
     st = q.State([(N, k1, k2)], [prm])
     tr = None
     if trace:
@@ -109,6 +110,24 @@ def test_modes_agree_and_match_oracle_ragged(q, orc, combine, comp):
     Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=res[0][2], want_trace=True)
     assert np.array_equal(res[0][0], Xo)
     assert lockstep_errors(res[0][2], tro, N).max() < 2 * TOL_D
+
+
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_decaying_F_lockstep(q, orc, mode):
+    """The Sec. 3.1.1 F schedule (computed on the host in FP64) drives the trials bit
+    for bit like the oracle's own evaluation of the same formula."""
+    N, NP, G = 333, 24, 14
+    k1, k2 = 2 * math.pi / 7.3, 2 * math.pi / 1.4
+    st, tr = make(q, N, k1, k2, NP, G, F=0.1, seed=8, f_schedule=1, team=32)
+    st.init()
+    st.run(G, mode)
+    X, f, D = snapshot(st)
+    trace = tr.cpu().numpy()
+    st.close()
+    cfg = orc.make_cfg(NP, N, G, 0.1, 0.9, 8, 0, 0, 1)
+    Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+    assert np.array_equal(X, Xo)
+    assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
 @pytest.mark.parametrize("team", [32, 64, 256])

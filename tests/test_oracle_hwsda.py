@@ -236,3 +236,23 @@ def test_relaxed_gradient_matches_finite_differences(orc):
     d = np.tanh(theta)
     dfdd = g / (1 - d * d)
     assert abs(np.sum(d * dfdd) - 4 * f) <= 1e-9 * f
+
+
+def test_decaying_F_schedule(orc):
+    """Sec. 3.1.1: F follows (cos(pi g / 2G) + 1)/2 times a factor falling from 1.0 to 0.8."""
+    c = _cfg(orc, G=1000, F=0.1)
+    c.f_schedule = 1
+    F = np.array([orc.F_of(c, g) for g in range(c.G)], dtype=np.float64)
+    assert F[0] == np.float32(0.1)
+    assert np.all(np.diff(F) <= 0)
+    assert abs(F[500] / 0.1 - 0.5 * (np.cos(np.pi / 4) + 1) * 0.95) < 1e-6
+    assert abs(F[-1] / 0.1 - 0.4) < 2e-3          # (0 + 1)/2 * 0.8 at the end of the run
+    c.f_schedule = 0
+    assert all(orc.F_of(c, g) == np.float32(0.1) for g in (0, 10, 999))
+    # the schedule reaches the trials: F = 0 at every step reduces rand/1 to copying donor r1
+    c0 = _cfg(orc, NP=10, N=30, CR=1.0, F=0.0)
+    c0.f_schedule = 1
+    X = orc.init_population(c0)
+    U = orc.de_trials(c0, 3, X)
+    r1 = orc.de_indices(c0.seed, 0, 3, 2, 10, 30)[0]
+    assert np.array_equal(U[2], X[r1])
