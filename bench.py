@@ -276,7 +276,7 @@ def run_gpu(args):
     cr = W.RELAXED
     th = torch.from_numpy(W.relaxed_theta(cr["B"], cr["N"], seed=cr["seed"])).cuda()
     Dr = torch.empty((cr["B"], 2), device="cuda")
-    Ar = torch.empty((cr["B"], 2), device="cuda")
+    Ar = q.relaxed_saved(cr["B"], cr["N"])
     fr = torch.empty(cr["B"], device="cuda")
     gr = torch.empty_like(th)
 

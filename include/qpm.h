@@ -160,18 +160,22 @@ qpm_status qpm_release_caches(void);
  *   theta      device float [B][ld], ld >= N
  *   d_eff      device float2 [B] (fwd out, bwd in)
  *   fit        device float [B] = |d_eff|^2 (fwd, may be NULL)
- *   sum_a      device float2 [B] = sum_j d_j e^{-i kappa2 j} (fwd out, may be NULL;
- *              the backward needs it)
+ *   saved      device float [B][qpm_relaxed_saved_floats(N)], 16-byte aligned,
+ *              caller-owned: the forward fills it (it is also the forward's
+ *              workspace) and the backward reads it.  Floats 0-1 of each row
+ *              hold sum_a = sum_j d_j e^{-i kappa2 j}; the rest holds the
+ *              row's prefix sums at segment starts (about N/32 floats).
  *   grad_fit   device float [B] upstream gradient dL/df (NULL = all ones)
  *   grad_theta device float [B][ld_grad] out: dL/dtheta = grad_fit * df/dtheta
  * Phasor table as for qpm_eval (cached per problem).  Errors: N < 1, B < 1,
- * ld < N, NULL outputs -> QPM_ERR_ARG.
+ * ld < N, NULL theta, d_eff, saved or grad_theta, misaligned saved -> QPM_ERR_ARG.
  * ------------------------------------------------------------------------- */
+int64_t qpm_relaxed_saved_floats(int32_t N);
 qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float *theta, int64_t ld,
-                                int32_t B, float *d_eff, float *fit, float *sum_a,
+                                int32_t B, float *d_eff, float *fit, float *saved,
                                 qpm_stream_t stream);
 qpm_status qpm_deff_relaxed_bwd(const qpm_problem *prob, const float *theta, int64_t ld,
-                                int32_t B, const float *d_eff, const float *sum_a,
+                                int32_t B, const float *d_eff, const float *saved,
                                 const float *grad_fit, float *grad_theta, int64_t ld_grad,
                                 qpm_stream_t stream);
 

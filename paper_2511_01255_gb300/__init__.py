@@ -15,7 +15,8 @@ from . import build_lib
 
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc", "qpm_eval_shg", "qpm_eval_multi",
-    "qpm_release_caches", "qpm_deff_relaxed_fwd", "qpm_deff_relaxed_bwd", "deff_relaxed",
+    "qpm_release_caches", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
+    "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
@@ -68,6 +69,7 @@ def lib(build=True):
                                 ctypes.c_size_t, _P], ctypes.c_int),
             "qpm_eval_multi_scratch_bytes": ([i32, i32, i32], ctypes.c_size_t),
             "qpm_release_caches": ([], ctypes.c_int),
+            "qpm_relaxed_saved_floats": ([i32], i64),
             "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
             "qpm_deff_relaxed_bwd": ([_P, _P, i64, i32, _P, _P, _P, _P, i64, _P], ctypes.c_int),
             "qpm_create": ([_P, _P, i32, _P], ctypes.c_int),
@@ -148,20 +150,31 @@ def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, s
                                   int(compensated), _stream(stream)))
 
 
-def qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, d_eff, fit=None, sum_a=None, stream=None):
+def qpm_relaxed_saved_floats(N):
+    """Floats per row of the saved block the relaxed passes share."""
+    return int(lib().qpm_relaxed_saved_floats(int(N)))
+
+
+def relaxed_saved(B, N, device="cuda"):
+    """A saved block for B rows of N domains (float32 [B, qpm_relaxed_saved_floats(N)])."""
+    import torch
+    return torch.empty((B, qpm_relaxed_saved_floats(N)), dtype=torch.float32, device=device)
+
+
+def qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, d_eff, fit, saved, stream=None):
     p = _problem(N, kappa1, kappa2)
     B, ld = _rows(theta, "theta")
     _check(lib().qpm_deff_relaxed_fwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff), _ptr(fit),
-                                      _ptr(sum_a), _stream(stream)))
+                                      _ptr(saved), _stream(stream)))
 
 
-def qpm_deff_relaxed_bwd(N, kappa1, kappa2, theta, d_eff, sum_a, grad_fit, grad_theta,
+def qpm_deff_relaxed_bwd(N, kappa1, kappa2, theta, d_eff, saved, grad_fit, grad_theta,
                          stream=None):
     p = _problem(N, kappa1, kappa2)
     B, ld = _rows(theta, "theta")
     _, ldg = _rows(grad_theta, "grad_theta")
     _check(lib().qpm_deff_relaxed_bwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff),
-                                      _ptr(sum_a), _ptr(grad_fit), _ptr(grad_theta), ldg,
+                                      _ptr(saved), _ptr(grad_fit), _ptr(grad_theta), ldg,
                                       _stream(stream)))
 
 
@@ -178,18 +191,18 @@ def _relaxed_function():
             B, N = theta.shape
             D = torch.empty((B, 2), dtype=torch.float32, device=theta.device)
             f = torch.empty(B, dtype=torch.float32, device=theta.device)
-            A = torch.empty((B, 2), dtype=torch.float32, device=theta.device)
-            qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, D, f, A)
-            ctx.save_for_backward(theta, D, A)
+            S = relaxed_saved(B, N, theta.device)
+            qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, D, f, S)
+            ctx.save_for_backward(theta, D, S)
             ctx.kappa = (kappa1, kappa2)
             return f
 
         @staticmethod
         def backward(ctx, gf):
-            theta, D, A = ctx.saved_tensors
+            theta, D, S = ctx.saved_tensors
             B, N = theta.shape
             g = torch.empty_like(theta)
-            qpm_deff_relaxed_bwd(N, ctx.kappa[0], ctx.kappa[1], theta, D, A,
+            qpm_deff_relaxed_bwd(N, ctx.kappa[0], ctx.kappa[1], theta, D, S,
                                  gf.contiguous().to(torch.float32), g)
             return g, None, None
 

@@ -7,89 +7,130 @@
 // and f = |D|^2.  Its derivative with respect to d_k is
 //   dD/dd_k = phi1 phi2 (p2_k P_k + p1_k R_k) + 2 psi d_k q_k,  R_k = sum_{j>k} a_j,
 //   df/dtheta_k = 2 Re(conj(D) dD/dd_k) (1 - d_k^2).
-// The forward pass keeps D and A = sum_j a_j per row; the backward pass
-// recomputes d, sweeps the row once in index order and forms P_k as a running
-// prefix and R_k = A - (prefix of a through k).
 //
-// Work split: one warp per row; the row is cut into tiles of 256 domains, lane l
-// owns the 8 contiguous domains [8l, 8l+8) of every tile (two coalesced float4
-// accesses per tile).  Because C = sum_j a_j P_j is bilinear, each lane keeps its
-// own share of C, of A and of E across the whole row; only the prefix of b
-// entering each lane's 8 domains needs a warp exclusive scan per tile, and the
-// shares are summed once per row.  The phasor table (p1, p2) is staged once per
-// CTA in shared memory in a [tile][e][lane] layout, which makes every table read
-// conflict-free; the next tile's theta is requested before the current one is
-// processed, so one tile of loads is always in flight per warp.
+// Work split (both passes): a warp takes 32 rows (lane = row) and one segment of
+// L domains (L a multiple of 32 fixed by N alone, at most 256) and sweeps the
+// segment in index order in steps of 32 domains.  Each step's 32 x 32 theta
+// values are loaded with coalesced 16-byte loads one step ahead, transposed
+// through a per-warp shared-memory tile, and every lane then walks its own row:
+// the running prefixes of a and b are plain sequential sums and every phasor
+// read is a broadcast.  The warps of a CTA take consecutive row groups of the
+// same segment and share its staged phasors (p1, p2, q = p1 p2).
+//
+// Forward: every (row, segment) writes its partial sums (A_s, B_s, C_s, E_s) into
+// the row's saved block; the segments of a row are then combined in index order
+// (C = sum_s C_s + A_s Bpre_s with Bpre_s the b-sum of the segments before s),
+// D is closed and each segment's (A_s, B_s) is overwritten with the exclusive
+// prefixes (Apre_s, Bpre_s).  For up to RX_FUSE_S segments the combine is done by
+// the last warp to finish a row group (an arrival counter per row group, reset
+// by that warp); longer rows use a separate kernel with a warp per row.
+// Backward: each (row, segment) starts from those prefixes (P = Bpre_s,
+// R = A - Apre_s), updates P_k and R_k as it goes and writes the gradient back
+// through the same tile with coalesced stores.
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
 
 namespace qpm {
 
-static constexpr int RX_WARPS = 8;
-static constexpr int RX_TILE = 256;
-static constexpr size_t RX_SMEM_MAX = 192 * 1024;
+static constexpr int RX_STEP = 32;   // domains per step (one per lane of a tile row)
+static constexpr int RX_LMAX = 256;  // longest segment
+static constexpr int RX_WPC = 4;     // warps (row groups of 32) per CTA
+static constexpr int RX_FUSE_S = 64; // longest row (in segments) combined inside the forward
 
 struct RelaxShape {
-  int B, N, ntiles;
-  int64_t ld;
-  bool vec;  // 16-byte aligned rows with ld % 4 == 0
+  int B, N, L, S;  // rows, domains, segment length, segments
+  int64_t ld;      // theta leading dimension
+  int64_t sf;      // floats per row of the saved block
+  bool vec;        // theta rows 16-byte aligned with ld % 4 == 0
 };
 
-// table entry of (tile, lane, e) in the staged layout
-__device__ __forceinline__ const float4 &tab(const float4 *sm, int tile, int e, int lane) {
-  return sm[((size_t)tile * 8 + e) * 32 + lane];
+// segment length: S = ceil(N / L) is about 16 for short rows, L = 256 for long ones
+static int rx_seg_len(int N) { return std::min(RX_LMAX, RX_STEP * ((N + 511) / 512)); }
+static int rx_nseg(int N) { return (N + rx_seg_len(N) - 1) / rx_seg_len(N); }
+// saved block of a row: [A (2 floats), 2 unused, then per segment 8 floats]
+static int64_t rx_saved_floats(int N) { return 4 + 8 * (int64_t)rx_nseg(N); }
+
+__device__ __forceinline__ float ex2_approx(float y) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
 }
 
-template <bool SMT>
-__device__ __forceinline__ float4 tab_get(const float4 *sm, const float4 *gtab, int tile, int e,
-                                          int lane, int m, int N) {
-  if (SMT) return tab(sm, tile, e, lane);
-  return m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ float rcp_approx(float y) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y));
+  return r;
 }
 
-// the 8 values of lane `lane` in tile `tile` of a row (0 beyond N)
-template <bool VEC>
-__device__ __forceinline__ void load8(const float *row, int m0, int N, float v[8]) {
-  if (VEC && m0 + 8 <= N) {
-    const float4 x = __ldg((const float4 *)(row + m0));
-    const float4 y = __ldg((const float4 *)(row + m0 + 4));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-  } else {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = (m0 + e < N) ? __ldg(row + m0 + e) : 0.f;
-  }
-}
-
-template <bool VEC>
-__device__ __forceinline__ void store8(float *row, int m0, int N, const float v[8]) {
-  if (VEC && m0 + 8 <= N) {
-    *(float4 *)(row + m0) = make_float4(v[0], v[1], v[2], v[3]);
-    *(float4 *)(row + m0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (m0 + e < N) row[m0 + e] = v[e];
-  }
-}
-
-// stage the natural-order table into shared memory ([tile][e][lane], zero padded);
-// consecutive threads write consecutive shared-memory slots
-__device__ void stage_table(float4 *sm, const float4 *gtab, int N, int ntiles) {
-  for (int o = threadIdx.x; o < ntiles * RX_TILE; o += blockDim.x) {
-    const int tile = o / RX_TILE, rem = o - tile * RX_TILE, e = rem >> 5, lane = rem & 31;
-    const int m = tile * RX_TILE + lane * 8 + e;
-    sm[o] = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  __syncthreads();
+// d = tanh(x) from one exponential.  With r = 1 / (1 + e^{2|x|}):
+//   tanh|x| = 1 - 2r,   1 - tanh^2 x = 4 r (1 - r).
+// The second identity keeps the derivative accurate to a few ulp where d is
+// close to +-1 (1 - d*d cancels there).  d is accurate to about 3e-7 absolute
+// (the hardware 2^y and 1/y approximations, see the parity tests).
+__device__ __forceinline__ float tanh_r(float x, float &r) {
+  const float E = ex2_approx(fabsf(x) * 2.8853900817779268f);  // 2 log2(e) |x|
+  r = rcp_approx(1.f + E);
+  return copysignf(fmaf(-2.f, r, 1.f), x);
 }
 
 __device__ __forceinline__ float2 q_of(const float4 &p) {  // q = p1 p2
   return make_float2(p.x * p.z - p.y * p.w, p.x * p.w + p.y * p.z);
+}
+
+// The per-warp tile holds 32 rows x 32 domains as float4 [row][c4], the column
+// xor-swizzled by the row: 8 columns of one row (a quarter-warp of the staging
+// stores) and 8 rows of one column (a quarter-warp of the row walks) both fall
+// into 8 different 16-byte bank groups.
+__device__ __forceinline__ int tix(int row, int c4) { return row * 8 + (c4 ^ (row & 7)); }
+
+// Step registers: lane l holds float4 k * 32 + l of the 32 x 8 float4 step,
+// i.e. row 4k + l / 8, column l % 8 (4 rows x 128 contiguous bytes per load).
+template <bool VEC>
+__device__ __forceinline__ void load_step(const float *__restrict__ theta, const RelaxShape &sh,
+                                          int r0, int ms, float4 R[8]) {
+  const int lane = threadIdx.x & 31;
+  const int m = ms + 4 * (lane & 7);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int gr = r0 + 4 * k + (lane >> 3);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gr < sh.B) {
+      const float *rp = theta + (int64_t)gr * sh.ld;
+      if (VEC && m + 4 <= sh.N) {
+        v = __ldg((const float4 *)(rp + m));
+      } else {
+        if (m < sh.N) v.x = __ldg(rp + m);
+        if (m + 1 < sh.N) v.y = __ldg(rp + m + 1);
+        if (m + 2 < sh.N) v.z = __ldg(rp + m + 2);
+        if (m + 3 < sh.N) v.w = __ldg(rp + m + 3);
+      }
+    }
+    R[k] = v;
+  }
+}
+
+__device__ __forceinline__ void put_step(float4 *T, const float4 R[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) T[tix(4 * k + (lane >> 3), lane & 7)] = R[k];
+}
+
+// phasors of the CTA's segment [m0, m0 + L) (zero beyond N), then a CTA barrier
+__device__ __forceinline__ void stage_segment(float4 *sp, float2 *sq, const float4 *gtab, int m0,
+                                              int L, int N) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    const int m = m0 + i;
+    const float4 p = m < N ? __ldg(gtab + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sp[i] = p;
+    sq[i] = q_of(p);
+  }
+  __syncthreads();
 }
 
 // exclusive prefix over lanes of a float2 (lane 0 gets 0); total in `tot`
@@ -116,244 +157,365 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// this warp's work list: rows r = gw, gw + nw, ...; (row, tile) pairs in order.
-// next() advances and prefetches the theta of the following pair.
-template <bool VEC>
-struct RowWalker {
-  const float *theta;
-  int64_t ld;
-  int N, B, ntiles, nw;
-  int r, tile;
-  float nxt[8];
-  __device__ __forceinline__ void fetch(int rr, int tt) {
-    if (rr < B) load8<VEC>(theta + (int64_t)rr * ld, tt * RX_TILE + (threadIdx.x & 31) * 8, N, nxt);
-  }
-  __device__ __forceinline__ void start(int gw) {
-    r = gw;
-    tile = 0;
-    fetch(r, 0);
-  }
-  // copies the prefetched values of (r, tile) into v and requests the next pair
-  __device__ __forceinline__ void take(float v[8]) {
+// the segments of row `row` in index order (lane = row): D, f and A of the row,
+// and the exclusive prefixes (Apre_s, Bpre_s) in place of (A_s, B_s).  The
+// partials were written by other CTAs of the running grid: read past L1, four
+// segments' loads in flight before any of them is overwritten.
+__device__ __forceinline__ void combine_row(const RelaxShape &sh, const float2 *konst, float *sv,
+                                            float2 *Dout, float *fout, int row) {
+  float2 cA = make_float2(0.f, 0.f), cB = cA, C = cA, E = cA;
+  float4 *blk = (float4 *)(sv + 4);
+  for (int s0 = 0; s0 < sh.S; s0 += 4) {
+    float4 ab[4], ce[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = nxt[e];
-    const int nt = tile + 1 < ntiles ? tile + 1 : 0;
-    const int nr = tile + 1 < ntiles ? r : r + nw;
-    fetch(nr, nt);
-  }
-  __device__ __forceinline__ bool advance() {  // true when a new row starts
-    if (++tile < ntiles) return false;
-    tile = 0;
-    r += nw;
-    return true;
-  }
-};
-
-template <bool VEC, bool SMT>
-static __global__ void __launch_bounds__(RX_WARPS * 32)
-    k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
-                  const float2 *__restrict__ konst, float2 *__restrict__ Dout,
-                  float *__restrict__ fout, float2 *__restrict__ Aout) {
-  extern __shared__ float4 smt[];
-  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  const float2 phi12 = konst[0], psi = konst[2];
-  RowWalker<VEC> w{theta, sh.ld, sh.N, sh.B, sh.ntiles, nw, 0, 0, {}};
-  w.start(gw);
-  while (w.r < sh.B) {
-    const int r = w.r;
-    float2 Cl = make_float2(0.f, 0.f), Al = Cl, El = Cl;  // this lane's shares
-    float2 Brun = make_float2(0.f, 0.f);                   // sum of b before this tile
-    bool row_done = false;
-    while (!row_done) {
-      const int tile = w.tile;
-      const int m0 = tile * RX_TILE + lane * 8;
-      float th[8];
-      w.take(th);
-      Mono loc = mono_zero();
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const float d = tanhf(th[e]);
-        const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
-        mono_push(loc, d, p);
-        const float2 q = q_of(p);
-        const float d2 = d * d;
-        El.x = fmaf(d2, q.x, El.x);
-        El.y = fmaf(d2, q.y, El.y);
+    for (int k = 0; k < 4; ++k) {
+      ab[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      ce[k] = ab[k];
+      if (s0 + k < sh.S) {
+        ab[k] = __ldcg(blk + 2 * (s0 + k));
+        ce[k] = __ldcg(blk + 2 * (s0 + k) + 1);
       }
-      float2 Bt;
-      const float2 Bex = warp_excl_scan2(loc.B, Bt);
-      // C share: the lane's own pairs plus its a-sum times every b before the lane
-      const float br = Brun.x + Bex.x, bi = Brun.y + Bex.y;
-      Cl.x += loc.C.x + (loc.A.x * br - loc.A.y * bi);
-      Cl.y += loc.C.y + (loc.A.x * bi + loc.A.y * br);
-      Al.x += loc.A.x;
-      Al.y += loc.A.y;
-      Brun.x += Bt.x;
-      Brun.y += Bt.y;
-      row_done = w.advance();
     }
-    const float Cr = warp_sum(Cl.x), Ci = warp_sum(Cl.y);
-    const float Er = warp_sum(El.x), Ei = warp_sum(El.y);
-    const float Ar = warp_sum(Al.x), Ai = warp_sum(Al.y);
-    if (lane == 0) {
-      const float2 D = make_float2(phi12.x * Cr - phi12.y * Ci + (psi.x * Er - psi.y * Ei),
-                                   phi12.x * Ci + phi12.y * Cr + (psi.x * Ei + psi.y * Er));
-      Dout[r] = D;
-      if (fout) fout[r] = fit_of(D);
-      if (Aout) Aout[r] = make_float2(Ar, Ai);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      C.x += ce[k].x + (ab[k].x * cB.x - ab[k].y * cB.y);
+      C.y += ce[k].y + (ab[k].x * cB.y + ab[k].y * cB.x);
+      E.x += ce[k].z;
+      E.y += ce[k].w;
+      if (s0 + k < sh.S) __stcg(blk + 2 * (s0 + k), make_float4(cA.x, cA.y, cB.x, cB.y));
+      cA.x += ab[k].x;
+      cA.y += ab[k].y;
+      cB.x += ab[k].z;
+      cB.y += ab[k].w;
     }
+  }
+  const float2 phi12 = konst[0], psi = konst[2];
+  const float2 D = make_float2(phi12.x * C.x - phi12.y * C.y + (psi.x * E.x - psi.y * E.y),
+                               phi12.x * C.y + phi12.y * C.x + (psi.x * E.y + psi.y * E.x));
+  Dout[row] = D;
+  if (fout) fout[row] = fit_of(D);
+  sv[0] = cA.x;
+  sv[1] = cA.y;
+}
+
+// grid (ceil(row groups / RX_WPC), S), block RX_WPC warps
+template <bool VEC, bool FUSE>
+static __global__ void __launch_bounds__(RX_WPC * 32)
+    k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
+                  float *__restrict__ saved, const float2 *__restrict__ konst,
+                  unsigned *__restrict__ arrivals, float2 *__restrict__ Dout,
+                  float *__restrict__ fout) {
+  __shared__ float4 sp[RX_LMAX];
+  __shared__ float2 sq[RX_LMAX];
+  __shared__ float4 tile[RX_WPC][RX_STEP * RX_STEP / 4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = blockIdx.y, m0 = seg * sh.L;
+  const int r0 = (blockIdx.x * RX_WPC + warp) * 32;
+  const int nsteps = sh.L / RX_STEP;
+  float4 R[8];
+  if (r0 < sh.B) load_step<VEC>(theta, sh, r0, m0, R);  // in flight while the table is staged
+  stage_segment(sp, sq, gtab, m0, sh.L, sh.N);
+  if (r0 >= sh.B) return;
+  float4 *T = tile[warp];
+  Mono acc = mono_zero();
+  float2 E = make_float2(0.f, 0.f);
+  for (int t = 0; t < nsteps; ++t) {
+    __syncwarp();
+    put_step(T, R);
+    __syncwarp();
+    if (t + 1 < nsteps) load_step<VEC>(theta, sh, r0, m0 + (t + 1) * RX_STEP, R);
+    const int e0 = t * RX_STEP;
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+      const float4 x = T[tix(lane, c4)];
+      const float th[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float rc;
+        const float d = tanh_r(th[j], rc);
+        const int e = e0 + 4 * c4 + j;
+        const float4 p = sp[e];
+        const float2 q = sq[e];
+        mono_push(acc, d, p);
+        const float d2 = d * d;
+        E.x = fmaf(d2, q.x, E.x);
+        E.y = fmaf(d2, q.y, E.y);
+      }
+    }
+  }
+  const int row = r0 + lane;
+  float *sv = saved + (int64_t)row * sh.sf;
+  if (row < sh.B) {
+    float4 *o = (float4 *)(sv + 4 + 8 * (int64_t)seg);
+    o[0] = make_float4(acc.A.x, acc.A.y, acc.B.x, acc.B.y);
+    o[1] = make_float4(acc.C.x, acc.C.y, E.x, E.y);
+  }
+  if (!FUSE) return;
+  // the last of the S warps of this row group combines it
+  __threadfence();
+  __syncwarp();
+  unsigned last = 0;
+  const int group = r0 >> 5;
+  if (lane == 0) last = atomicAdd(arrivals + group, 1u) == (unsigned)(sh.S - 1);
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  __threadfence();
+  if (lane == 0) arrivals[group] = 0u;  // ready for the next call on this stream
+  if (row < sh.B) combine_row(sh, konst, sv, Dout, fout, row);
+}
+
+// one warp per row: segments in index order -> D, f, A; (A_s, B_s) -> prefixes
+static __global__ void k_relaxed_combine(RelaxShape sh, const float2 *__restrict__ konst,
+                                         float *__restrict__ saved, float2 *__restrict__ Dout,
+                                         float *__restrict__ fout) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= sh.B) return;
+  float *sv = saved + (int64_t)row * sh.sf;
+  float2 cA = make_float2(0.f, 0.f), cB = cA, Cl = cA, El = cA;
+  for (int c = 0; c < sh.S; c += 32) {
+    const int s = c + lane;
+    float4 ab = make_float4(0.f, 0.f, 0.f, 0.f), ce = ab;
+    if (s < sh.S) {
+      const float4 *in = (const float4 *)(sv + 4 + 8 * (int64_t)s);
+      ab = in[0];
+      ce = in[1];
+    }
+    float2 tA, tB;
+    const float2 xA = warp_excl_scan2(make_float2(ab.x, ab.y), tA);
+    const float2 xB = warp_excl_scan2(make_float2(ab.z, ab.w), tB);
+    const float2 Ap = make_float2(cA.x + xA.x, cA.y + xA.y);
+    const float2 Bp = make_float2(cB.x + xB.x, cB.y + xB.y);
+    // this segment's pairs plus its a-sum times every b before it
+    Cl.x += ce.x + (ab.x * Bp.x - ab.y * Bp.y);
+    Cl.y += ce.y + (ab.x * Bp.y + ab.y * Bp.x);
+    El.x += ce.z;
+    El.y += ce.w;
+    if (s < sh.S) *(float4 *)(sv + 4 + 8 * (int64_t)s) = make_float4(Ap.x, Ap.y, Bp.x, Bp.y);
+    cA.x += tA.x;
+    cA.y += tA.y;
+    cB.x += tB.x;
+    cB.y += tB.y;
+  }
+  const float Cr = warp_sum(Cl.x), Ci = warp_sum(Cl.y);
+  const float Er = warp_sum(El.x), Ei = warp_sum(El.y);
+  if (lane == 0) {
+    const float2 phi12 = konst[0], psi = konst[2];
+    const float2 D = make_float2(phi12.x * Cr - phi12.y * Ci + (psi.x * Er - psi.y * Ei),
+                                 phi12.x * Ci + phi12.y * Cr + (psi.x * Ei + psi.y * Er));
+    Dout[row] = D;
+    if (fout) fout[row] = fit_of(D);
+    sv[0] = cA.x;
+    sv[1] = cA.y;
   }
 }
 
-template <bool VEC, bool SMT>
-static __global__ void __launch_bounds__(RX_WARPS * 32)
+template <bool VEC, bool VECG>
+static __global__ void __launch_bounds__(RX_WPC * 32)
     k_relaxed_bwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
                   const float2 *__restrict__ konst, const float2 *__restrict__ Din,
-                  const float2 *__restrict__ Ain, const float *__restrict__ gf,
+                  const float *__restrict__ saved, const float *__restrict__ gf,
                   float *__restrict__ grad, int64_t ldg) {
-  extern __shared__ float4 smt[];
-  if (SMT) stage_table(smt, gtab, sh.N, sh.ntiles);
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (blockDim.x >> 5);
+  __shared__ float4 sp[RX_LMAX];
+  __shared__ float2 sq[RX_LMAX];
+  __shared__ float4 tile[RX_WPC][RX_STEP * RX_STEP / 4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int seg = blockIdx.y, m0 = seg * sh.L;
+  const int r0 = (blockIdx.x * RX_WPC + warp) * 32;
+  const int nsteps = sh.L / RX_STEP;
+  float4 R[8];
+  if (r0 < sh.B) load_step<VEC>(theta, sh, r0, m0, R);
+  stage_segment(sp, sq, gtab, m0, sh.L, sh.N);
+  if (r0 >= sh.B) return;
+  float4 *T = tile[warp];
+  const int row = r0 + lane;
+  // u = 8 g conj(D) phi1 phi2, v = 16 g conj(D) psi: df/dtheta_k =
+  //   [Re(u (p2 P + p1 R)) + d Re(v q)] r (1 - r)   with (1 - d^2) = 4 r (1 - r)
+  float2 D = make_float2(0.f, 0.f), P = D, Rs = D;
+  float g = 0.f;
+  if (row < sh.B) {
+    const float *sv = saved + (int64_t)row * sh.sf;
+    D = Din[row];
+    const float4 pre = *(const float4 *)(sv + 4 + 8 * (int64_t)seg);
+    Rs = make_float2(sv[0] - pre.x, sv[1] - pre.y);  // sum of a from the segment start on
+    P = make_float2(pre.z, pre.w);                  // sum of b before the segment
+    g = gf ? gf[row] : 1.0f;
+  }
   const float2 phi12 = konst[0], psi = konst[2];
-  RowWalker<VEC> wk{theta, sh.ld, sh.N, sh.B, sh.ntiles, nw, 0, 0, {}};
-  wk.start(gw);
-  while (wk.r < sh.B) {
-    const int r = wk.r;
-    float *grow = grad + (int64_t)r * ldg;
-    const float2 D = Din[r];
-    const float2 Atot = Ain[r];
-    const float g = gf ? gf[r] : 1.0f;
-    // u = 2 g conj(D) phi1 phi2, v = 4 g conj(D) psi: df/dtheta_k =
-    //   [Re(u (p2 P + p1 R)) + d Re(v q)] (1 - d^2)
-    const float ur = 2.f * g * (D.x * phi12.x + D.y * phi12.y);
-    const float ui = 2.f * g * (D.x * phi12.y - D.y * phi12.x);
-    const float vr = 4.f * g * (D.x * psi.x + D.y * psi.y);
-    const float vi = 4.f * g * (D.x * psi.y - D.y * psi.x);
-    float2 Brun = make_float2(0.f, 0.f), Arun = make_float2(0.f, 0.f);
-    bool row_done = false;
-    while (!row_done) {
-      const int tile = wk.tile;
-      const int m0 = tile * RX_TILE + lane * 8;
-      float th[8], d[8];
-      wk.take(th);
-      float2 la = make_float2(0.f, 0.f), lb = make_float2(0.f, 0.f);
+  const float ur = 8.f * g * (D.x * phi12.x + D.y * phi12.y);
+  const float ui = 8.f * g * (D.x * phi12.y - D.y * phi12.x);
+  const float vr = 16.f * g * (D.x * psi.x + D.y * psi.y);
+  const float vi = 16.f * g * (D.x * psi.y - D.y * psi.x);
+  for (int t = 0; t < nsteps; ++t) {
+    const int ms = m0 + t * RX_STEP;
+    __syncwarp();
+    put_step(T, R);
+    __syncwarp();
+    if (t + 1 < nsteps) load_step<VEC>(theta, sh, r0, ms + RX_STEP, R);
+    const int e0 = t * RX_STEP;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        d[e] = tanhf(th[e]);
-        const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
-        la.x = fmaf(d[e], p.z, la.x);
-        la.y = fmaf(d[e], p.w, la.y);
-        lb.x = fmaf(d[e], p.x, lb.x);
-        lb.y = fmaf(d[e], p.y, lb.y);
-      }
-      float2 ta, tb;
-      const float2 ea = warp_excl_scan2(la, ta), eb = warp_excl_scan2(lb, tb);
-      float2 P = make_float2(Brun.x + eb.x, Brun.y + eb.y);   // sum of b before this lane
-      float2 Ap = make_float2(Arun.x + ea.x, Arun.y + ea.y);  // sum of a before this lane
-      float out[8];
+    for (int c4 = 0; c4 < 8; ++c4) {
+      const float4 x = T[tix(lane, c4)];
+      const float th[4] = {x.x, x.y, x.z, x.w};
+      float out[4];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const float4 p = tab_get<SMT>(smt, gtab, tile, e, lane, m0 + e, sh.N);
-        Ap.x = fmaf(d[e], p.z, Ap.x);
-        Ap.y = fmaf(d[e], p.w, Ap.y);
-        const float Rr = Atot.x - Ap.x, Ri = Atot.y - Ap.y;  // sum of a after this domain
+      for (int j = 0; j < 4; ++j) {
+        float rc;
+        const float d = tanh_r(th[j], rc);
+        const int e = e0 + 4 * c4 + j;
+        const float4 p = sp[e];
+        const float2 q = sq[e];
+        Rs.x = fmaf(-d, p.z, Rs.x);  // R_k: sum of a after this domain
+        Rs.y = fmaf(-d, p.w, Rs.y);
         // w = p2 P + p1 R
-        const float wr = p.z * P.x - p.w * P.y + (p.x * Rr - p.y * Ri);
-        const float wi = p.z * P.y + p.w * P.x + (p.x * Ri + p.y * Rr);
-        const float2 q = q_of(p);
-        const float sv = (ur * wr - ui * wi) + d[e] * (vr * q.x - vi * q.y);
-        out[e] = sv * (1.f - d[e] * d[e]);
-        P.x = fmaf(d[e], p.x, P.x);
-        P.y = fmaf(d[e], p.y, P.y);
+        const float wr = p.z * P.x - p.w * P.y + (p.x * Rs.x - p.y * Rs.y);
+        const float wi = p.z * P.y + p.w * P.x + (p.x * Rs.y + p.y * Rs.x);
+        const float s = (ur * wr - ui * wi) + d * (vr * q.x - vi * q.y);
+        out[j] = s * fmaf(-rc, rc, rc);
+        P.x = fmaf(d, p.x, P.x);
+        P.y = fmaf(d, p.y, P.y);
       }
-      store8<VEC>(grow, m0, sh.N, out);
-      Brun.x += tb.x;
-      Brun.y += tb.y;
-      Arun.x += ta.x;
-      Arun.y += ta.y;
-      row_done = wk.advance();
+      T[tix(lane, c4)] = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    __syncwarp();
+    // the step's gradient leaves through the tile with the load pattern
+    const int m = ms + 4 * (lane & 7);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int tr = 4 * k + (lane >> 3), gr = r0 + tr;
+      if (gr < sh.B) {
+        const float4 v = T[tix(tr, lane & 7)];
+        float *gp = grad + (int64_t)gr * ldg;
+        if (VECG && m + 4 <= sh.N) {
+          *(float4 *)(gp + m) = v;
+        } else {
+          if (m < sh.N) gp[m] = v.x;
+          if (m + 1 < sh.N) gp[m + 1] = v.y;
+          if (m + 2 < sh.N) gp[m + 2] = v.z;
+          if (m + 3 < sh.N) gp[m + 3] = v.w;
+        }
+      }
     }
   }
 }
 
 static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int64_t ld,
-                                int32_t B, cudaStream_t s, RelaxShape *sh, const float4 **tab,
-                                const float2 **konst, size_t *smem, int *grid) {
-  if (!prob || !theta) return fail(QPM_ERR_ARG, "relaxed: NULL pointer");
+                                int32_t B, const void *saved, cudaStream_t s, RelaxShape *sh,
+                                const float4 **tab, const float2 **konst) {
+  if (!prob || !theta || !saved) return fail(QPM_ERR_ARG, "relaxed: NULL theta or saved block");
   if (prob->N < 1 || B < 1) return fail(QPM_ERR_ARG, "relaxed: need N >= 1 and B >= 1");
   if (ld < prob->N) return fail(QPM_ERR_ARG, "relaxed: leading dimension smaller than the row");
+  if (((uintptr_t)saved & 15) != 0) return fail(QPM_ERR_ARG, "relaxed: saved block not 16-byte aligned");
+  if (rx_nseg(prob->N) > 65535) return fail(QPM_ERR_ARG, "relaxed: N too large");
   qpm_status st = cached_table(prob, s, tab, konst);
   if (st != QPM_OK) return st;
   sh->B = B;
   sh->N = prob->N;
-  sh->ntiles = (prob->N + RX_TILE - 1) / RX_TILE;
+  sh->L = rx_seg_len(prob->N);
+  sh->S = rx_nseg(prob->N);
   sh->ld = ld;
+  sh->sf = rx_saved_floats(prob->N);
   sh->vec = (ld % 4 == 0) && (((uintptr_t)theta & 15) == 0);
-  const size_t need = sizeof(float4) * (size_t)sh->ntiles * RX_TILE;
-  *smem = need <= RX_SMEM_MAX ? need : 0;
-  const int per_sm = *smem ? (int)std::max<size_t>(1, (228 * 1024) / (*smem + 1024)) : 4;
-  *grid = sm_count() * std::min(per_sm, 4);
-  const int rows_per_cta = RX_WARPS;
-  *grid = std::max(1, std::min(*grid, (B + rows_per_cta - 1) / rows_per_cta));
   return QPM_OK;
+}
+
+// zeroed arrival counters (one per row group) for the forward's fused combine,
+// per (device, stream); the kernel leaves them at zero
+static qpm_status rx_arrivals(cudaStream_t s, int groups, unsigned **out) {
+  static std::mutex mu;
+  static std::map<std::pair<int, cudaStream_t>, std::pair<unsigned *, int>> cache;
+  int dev = 0;
+  QPM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  auto &e = cache[std::make_pair(dev, s)];
+  if (e.second < groups) {
+    if (e.first) {
+      QPM_CUDA(cudaStreamSynchronize(s));
+      QPM_CUDA(cudaFree(e.first));
+      e.first = nullptr;
+      e.second = 0;
+    }
+    const int n = std::max(groups, 256);
+    QPM_CUDA(cudaMalloc(&e.first, sizeof(unsigned) * n));
+    QPM_CUDA(cudaMemsetAsync(e.first, 0, sizeof(unsigned) * n, s));
+    e.second = n;
+  }
+  *out = e.first;
+  return QPM_OK;
+}
+
+static dim3 rx_grid(const RelaxShape &sh) {
+  const int groups = (sh.B + 31) / 32;
+  return dim3((groups + RX_WPC - 1) / RX_WPC, sh.S);
 }
 
 }  // namespace qpm
 
 using namespace qpm;
 
-#define QPM_RX_DISPATCH(KERNEL, ...)                                                       \
-  do {                                                                                     \
-    const void *fn;                                                                        \
-    if (sh.vec) fn = smem ? (const void *)KERNEL<true, true> : (const void *)KERNEL<true, false>; \
-    else fn = smem ? (const void *)KERNEL<false, true> : (const void *)KERNEL<false, false>;      \
-    if (smem) QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                            (int)RX_SMEM_MAX));                            \
-    void *args[] = {__VA_ARGS__};                                                          \
-    QPM_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(RX_WARPS * 32), args, smem, s));         \
-  } while (0)
+extern "C" int64_t qpm_relaxed_saved_floats(int32_t N) { return N < 1 ? 0 : rx_saved_floats(N); }
 
 extern "C" qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float *theta, int64_t ld,
-                                           int32_t B, float *d_eff, float *fit, float *sum_a,
+                                           int32_t B, float *d_eff, float *fit, float *saved,
                                            qpm_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (!d_eff) return fail(QPM_ERR_ARG, "qpm_deff_relaxed_fwd: NULL d_eff");
   RelaxShape sh;
   const float4 *tab;
   const float2 *konst;
-  size_t smem;
-  int grid;
-  qpm_status st = relaxed_setup(prob, theta, ld, B, s, &sh, &tab, &konst, &smem, &grid);
+  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, &sh, &tab, &konst);
   if (st != QPM_OK) return st;
-  float2 *D = (float2 *)d_eff, *A = (float2 *)sum_a;
-  QPM_RX_DISPATCH(k_relaxed_fwd, (void *)&theta, &sh, &tab, &konst, &D, &fit, &A);
+  float2 *D = (float2 *)d_eff;
+  const dim3 grid = rx_grid(sh);
+  if (sh.S <= RX_FUSE_S) {
+    unsigned *arr;
+    st = rx_arrivals(s, (B + 31) / 32, &arr);
+    if (st != QPM_OK) return st;
+    if (sh.vec)
+      k_relaxed_fwd<true, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, arr, D, fit);
+    else
+      k_relaxed_fwd<false, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, arr, D, fit);
+    QPM_CUDA(cudaGetLastError());
+    return QPM_OK;
+  }
+  if (sh.vec)
+    k_relaxed_fwd<true, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, nullptr, D, fit);
+  else
+    k_relaxed_fwd<false, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, nullptr, D, fit);
+  QPM_CUDA(cudaGetLastError());
+  k_relaxed_combine<<<(B + 7) / 8, 256, 0, s>>>(sh, konst, saved, D, fit);
+  QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }
 
 extern "C" qpm_status qpm_deff_relaxed_bwd(const qpm_problem *prob, const float *theta, int64_t ld,
-                                           int32_t B, const float *d_eff, const float *sum_a,
+                                           int32_t B, const float *d_eff, const float *saved,
                                            const float *grad_fit, float *grad_theta,
                                            int64_t ld_grad, qpm_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (!d_eff || !sum_a || !grad_theta)
-    return fail(QPM_ERR_ARG, "qpm_deff_relaxed_bwd: NULL d_eff, sum_a or grad_theta");
+  if (!d_eff || !grad_theta)
+    return fail(QPM_ERR_ARG, "qpm_deff_relaxed_bwd: NULL d_eff or grad_theta");
   if (!prob || ld_grad < prob->N)
     return fail(QPM_ERR_ARG, "qpm_deff_relaxed_bwd: gradient leading dimension smaller than the row");
   RelaxShape sh;
   const float4 *tab;
   const float2 *konst;
-  size_t smem;
-  int grid;
-  qpm_status st = relaxed_setup(prob, theta, ld, B, s, &sh, &tab, &konst, &smem, &grid);
+  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, &sh, &tab, &konst);
   if (st != QPM_OK) return st;
-  if (sh.vec && (ld_grad % 4 != 0 || ((uintptr_t)grad_theta & 15) != 0)) sh.vec = false;
-  const float2 *D = (const float2 *)d_eff, *A = (const float2 *)sum_a;
-  QPM_RX_DISPATCH(k_relaxed_bwd, (void *)&theta, &sh, &tab, &konst, (void *)&D, (void *)&A,
-                  (void *)&grad_fit, &grad_theta, &ld_grad);
+  const bool vg = (ld_grad % 4 == 0) && (((uintptr_t)grad_theta & 15) == 0);
+  const float2 *D = (const float2 *)d_eff;
+  const dim3 grid = rx_grid(sh);
+  if (sh.vec && vg)
+    k_relaxed_bwd<true, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, konst, D, saved, grad_fit,
+                                                           grad_theta, ld_grad);
+  else if (sh.vec)
+    k_relaxed_bwd<true, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, konst, D, saved,
+                                                            grad_fit, grad_theta, ld_grad);
+  else if (vg)
+    k_relaxed_bwd<false, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, konst, D, saved,
+                                                            grad_fit, grad_theta, ld_grad);
+  else
+    k_relaxed_bwd<false, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, konst, D, saved,
+                                                             grad_fit, grad_theta, ld_grad);
+  QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }

@@ -52,4 +52,4 @@ extern "C" const char *qpm_status_string(qpm_status s) {
   return "QPM_ERR_UNKNOWN";
 }
 
-extern "C" int32_t qpm_abi_version(void) { return 1; }
+extern "C" int32_t qpm_abi_version(void) { return 2; }

@@ -1356,7 +1356,8 @@ extern "C" qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t st
   const InstDev &I = st->h[inst];
   cudaStream_t s = (cudaStream_t)stream;
   const size_t Np = (size_t)I.Npad;
-  const size_t need = 256 + align_up(3 * Np * sizeof(float), 256) * 2 + 256 * 3;
+  const size_t saved_bytes = align_up(3 * (size_t)qpm_relaxed_saved_floats(I.N) * sizeof(float), 256);
+  const size_t need = 256 + align_up(3 * Np * sizeof(float), 256) * 2 + 256 + saved_bytes;
   if (st->polish_bytes < need) {
     if (st->polish) {
       QPM_CUDA(cudaDeviceSynchronize());
@@ -1372,15 +1373,16 @@ extern "C" qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t st
   float *theta = (float *)(p + 256);
   float *grad = (float *)(p + 256 + align_up(3 * Np * sizeof(float), 256));
   float *D = (float *)(p + 256 + 2 * align_up(3 * Np * sizeof(float), 256));
-  float *A = D + 256 / sizeof(float);
+  float *saved = D + 256 / sizeof(float);
   k_polish_pick<<<1, 256, 0, s>>>(I, lead);
   k_polish_theta<<<3, 256, 0, s>>>(I, lead, tau, theta);
   QPM_CUDA(cudaGetLastError());
   const qpm_problem prob = st->probs[inst];
   for (int k = 0; k < steps; ++k) {
-    qpm_status r = qpm_deff_relaxed_fwd(&prob, theta, (int64_t)Np, 3, D, nullptr, A, stream);
+    qpm_status r = qpm_deff_relaxed_fwd(&prob, theta, (int64_t)Np, 3, D, nullptr, saved, stream);
     if (r != QPM_OK) return r;
-    r = qpm_deff_relaxed_bwd(&prob, theta, (int64_t)Np, 3, D, A, nullptr, grad, (int64_t)Np, stream);
+    r = qpm_deff_relaxed_bwd(&prob, theta, (int64_t)Np, 3, D, saved, nullptr, grad, (int64_t)Np,
+                             stream);
     if (r != QPM_OK) return r;
     k_polish_step<<<3, 256, 0, s>>>(I.N, (int64_t)Np, lr, theta, grad);
   }

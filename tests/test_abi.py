@@ -60,6 +60,27 @@ def test_argument_errors_without_device(qlib):
     assert qlib.qpm_destroy(None) == 0
 
 
+def test_relaxed_saved_block_size_and_errors(qlib):
+    import paper_2511_01255_gb300 as q
+    # segments of L = min(256, 32 ceil(N / 512)) domains; 4 + 8 floats per segment
+    for N, L in ((1, 32), (5, 32), (512, 32), (513, 64), (1000, 64), (4096, 256), (100000, 256)):
+        assert qlib.qpm_relaxed_saved_floats(N) == 4 + 8 * ((N + L - 1) // L), N
+    assert qlib.qpm_relaxed_saved_floats(0) == 0
+    p = q.Problem(64, 1.0, 2.0)
+    f16 = ctypes.c_void_p(16)
+    # NULL or misaligned saved block, NULL outputs: argument errors before any device work
+    assert qlib.qpm_deff_relaxed_fwd(ctypes.byref(p), f16, 64, 2, f16, None, None, None) == 1
+    assert b"saved" in qlib.qpm_last_error()
+    assert qlib.qpm_deff_relaxed_fwd(ctypes.byref(p), f16, 64, 2, f16, None,
+                                     ctypes.c_void_p(20), None) == 1
+    assert b"aligned" in qlib.qpm_last_error()
+    assert qlib.qpm_deff_relaxed_bwd(ctypes.byref(p), f16, 64, 2, f16, f16, None, None, 64,
+                                     None) == 1
+    assert qlib.qpm_deff_relaxed_bwd(ctypes.byref(p), f16, 64, 2, f16, f16, None, f16, 63,
+                                     None) == 1
+    assert qlib.qpm_abi_version() == 2
+
+
 def test_workload_generators_are_seeded():
     from paper_2511_01255_gb300 import workloads as W
     import numpy as np

@@ -34,7 +34,7 @@ def fwd_bwd(q, theta_np, k1, k2, gf=None):
     B, N = th.shape
     D = torch.empty((B, 2), device="cuda")
     f = torch.empty(B, device="cuda")
-    A = torch.empty((B, 2), device="cuda")
+    A = q.relaxed_saved(B, N)
     q.qpm_deff_relaxed_fwd(N, k1, k2, th, D, f, A)
     g = torch.empty_like(th)
     gft = None if gf is None else torch.from_numpy(gf.astype(np.float32)).cuda()
@@ -58,6 +58,33 @@ def test_relaxed_fwd_bwd_against_oracle(q, orc, N):
         ref_g, ref_D = orc.grad_relaxed(theta[r].astype(np.float64), K1, K2)
         assert deff_err(D[r:r + 1], np.array([ref_D]), N).max() < TOL_D
         assert grad_err(g[r], ref_g) < TOL_G
+
+
+def test_tanh_and_derivative_accuracy(q):
+    """The kernels form d = tanh(theta) and 1 - d^2 from one hardware exponential
+    and reciprocal.  A one-domain row exposes both: its sum of a (the first
+    float of its saved block) is d itself (p2_0 = 1), and its gradient is 4 |psi|^2 d^3 (1 - d^2).  Checked over a dense
+    sweep of theta against FP64: d to 5e-7 absolute, 1 - d^2 to 1e-5 relative
+    (where d and the gradient are representable)."""
+    import torch
+    theta = np.concatenate([np.linspace(-30.0, 30.0, 60001),
+                            [0.0, 1e-30, -1e-30, 1e-6, -1e-6, 1e-3, -1e-3]]).astype(np.float32)
+    B = theta.size
+    _, f, g = fwd_bwd(q, theta[:, None].copy(), K1, K2)
+    th = torch.from_numpy(theta[:, None].copy()).cuda()
+    Dd = torch.empty((B, 2), device="cuda")
+    A = q.relaxed_saved(B, 1)
+    q.qpm_deff_relaxed_fwd(1, K1, K2, th, Dd, None, A)
+    torch.cuda.synchronize()
+    d = A.cpu().numpy()[:, 0].astype(np.float64)
+    ref = np.tanh(theta.astype(np.float64))
+    assert np.max(np.abs(d - ref)) <= 5e-7
+    assert np.all(np.abs(d) <= 1.0) and np.all(np.sign(d) * np.sign(theta) >= 0)
+    # f = |psi|^2 d^4 and df/dtheta = 4 |psi|^2 d^3 (1 - d^2), so g d / (4 f) = 1 - d^2
+    sech2 = 1.0 / np.cosh(theta.astype(np.float64)) ** 2
+    sel = (np.abs(d) > 1e-2) & (sech2 > 1e-30)
+    est = g[sel, 0].astype(np.float64) * d[sel] / (4.0 * f[sel].astype(np.float64))
+    assert np.max(np.abs(est - sech2[sel]) / sech2[sel]) <= 1e-5
 
 
 def test_finite_differences_and_euler_full_size(q, orc):
@@ -100,11 +127,11 @@ def test_autograd_function(q, orc):
         assert grad_err(g[r], float(w[r]) * ref_g) < TOL_G
 
 
-def test_polish_leaders(q, orc):
+@pytest.mark.parametrize("N,NP", [(1000, 32), (4096, 256)])
+def test_polish_leaders(q, orc, N, NP):
     """After polishing, every leader's fitness is at least what it was, its new genes
     evaluate (oracle, FP64) to the stored fitness, and nobody else changed."""
     import torch
-    N, NP = 1000, 32
     prm = q.Params(NP, 50, 0.5, 0.9, 4, 0, 1)
     with q.State([(N, K1, K2)], [prm]) as st:
         st.init()
