@@ -54,6 +54,7 @@ struct InstDev {
   int32_t *best;         // [1] best index (get_best)
   float *trace;          // optional fitness trace
   const float *Fsched;   // [G] F of every generation, or NULL for constant F
+  unsigned long long *dekey;  // [NP] persistent form: DE survivor keys (lead_key) for Step 3
 };
 
 template <bool NC>
@@ -358,30 +359,6 @@ __device__ void merge_leaders(const unsigned long long *topk, int nparts, int32_
   __syncthreads();
 }
 
-// leaders straight from the fitness array (warp 0 scans all NP values; every
-// thread returns after the CTA barrier with lead_sh set)
-__device__ void leaders_from_fit(const float *fit, int NP, int32_t *lead, int32_t *lead_sh) {
-  if (threadIdx.x < 32) {
-    unsigned long long k0 = 0, k1 = 0, k2 = 0;
-    for (int i = threadIdx.x; i < NP; i += 32) top3_insert(k0, k1, k2, lead_key(fit[i], i));
-    for (int s = 16; s > 0; s >>= 1) {
-      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
-      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
-      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
-      top3_insert(k0, k1, k2, p0);
-      top3_insert(k0, k1, k2, p1);
-      top3_insert(k0, k1, k2, p2);
-    }
-    if (threadIdx.x == 0) {
-      lead_sh[0] = key_index(k0);
-      lead_sh[1] = key_index(k1);
-      lead_sh[2] = key_index(k2);
-      if (lead) { lead[0] = lead_sh[0]; lead[1] = lead_sh[1]; lead[2] = lead_sh[2]; }
-    }
-  }
-  __syncthreads();
-}
-
 // true in every thread of the last CTA to finish (classic fence + counter pattern)
 __device__ bool last_cta(unsigned *ctr) {
   __shared__ bool is_last;
@@ -493,6 +470,34 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
   return grid_wait(b, target);
 }
 
+// Step 3 of the persistent form, after the grid barrier that follows DE: warp 0
+// reads the DE survivor keys of all individuals and takes the top three; every
+// thread returns after the CTA barrier with lead_sh set.  The keys are written in
+// the DE phase only, so a CTA that is still choosing leaders never sees a fitness
+// already changed by another CTA's GWO selection.
+__device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_t *lead,
+                                  int32_t *lead_sh) {
+  if (threadIdx.x < 32) {
+    unsigned long long k0 = 0, k1 = 0, k2 = 0;
+    for (int i = threadIdx.x; i < NP; i += 32) top3_insert(k0, k1, k2, keys[i]);
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
+      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
+      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
+      top3_insert(k0, k1, k2, p0);
+      top3_insert(k0, k1, k2, p1);
+      top3_insert(k0, k1, k2, p2);
+    }
+    if (threadIdx.x == 0) {
+      lead_sh[0] = key_index(k0);
+      lead_sh[1] = key_index(k1);
+      lead_sh[2] = key_index(k2);
+      if (lead) { lead[0] = lead_sh[0]; lead[1] = lead_sh[1]; lead[2] = lead_sh[2]; }
+    }
+  }
+  __syncthreads();
+}
+
 // All generations [*gen, g_end) in one cooperative launch; every CTA keeps the
 // same individuals (i = blockIdx.x + k gridDim.x), the phasor table sits in
 // shared memory when it fits (TS).  Two grid barriers per generation: after DE
@@ -519,7 +524,9 @@ static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end,
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
-      de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh);
+      const unsigned long long key =
+          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh);
+      if (threadIdx.x == 0) I.dekey[i] = key;  // ordered before the barrier's release
     }
     grid_arrive(bar, target);
     uint4 wpre[6];
@@ -538,8 +545,8 @@ static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end,
       own0 = *(const float4 *)r0;
       own1 = *(const float4 *)(r0 + I.Npad);
     }
-    // every CTA finds the leaders itself (Sec. 3.2 Step 3) from the fitness array
-    leaders_from_fit(I.fit, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
+    // every CTA finds the leaders itself (Sec. 3.2 Step 3) from the DE keys
+    leaders_from_keys(I.dekey, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
@@ -1056,6 +1063,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += align_up((size_t)table_part_count(I.Npad) * sizeof(double2), 256);
     total += 256 + 256 + 256;  // konst, konst64, lead
     total += align_up(6 * NP * sizeof(unsigned long long), 256);
+    total += align_up(NP * sizeof(unsigned long long), 256);  // DE survivor keys
     total += align_up((size_t)q.G * sizeof(float), 256);  // F schedule
     total += 256 + 256 + 256;  // ctr, gen, best
   }
@@ -1084,6 +1092,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.konst64 = (double2 *)take(3 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
+    I.dekey = (unsigned long long *)take(NP * sizeof(unsigned long long));
     I.Fsched = st->params[k].f_schedule ? (const float *)take((size_t)I.G * sizeof(float))
                                         : (take((size_t)I.G * sizeof(float)), nullptr);
     I.ctr = (unsigned *)take(4 * sizeof(unsigned));
