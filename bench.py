@@ -54,13 +54,14 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []     # (arrival time, line)
+        self.t_mark = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -69,7 +70,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        """Start of the timed region: samples that arrive earlier are dropped."""
+        self.t_mark = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
@@ -81,7 +86,9 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if self.t_mark is not None and t < self.t_mark:
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -99,6 +106,16 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- GPU arm
+# DRAM bytes (read + write) of one k_persist launch of the 1000-domain workload
+# (2000 generations), captured with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k regex:k_persist -c 1 python -m paper_2511_01255_gb300.profile_run \
+#       --workload paper --form persistent --gens 2000 --reps 1
+# on the current kernel: 1144064 read + 305664 written.  The 2 MB population and
+# the phasor table stay in L2; DRAM sees little more than the first touch.
+K_PERSIST_DRAM_BYTES = 1144064 + 305664
+
+
 def algorithmic_lane_ops_per_gene_gen(compensated):
     """Lane instructions the method needs per gene and generation (documented in
     the design doc): Philox4x32-10 at 1.75 calls (80 ops each), 7 uniforms (3 ops),
@@ -178,14 +195,15 @@ def run_gpu(args):
     results = {}
     for mode_name, mode in (("persistent", q.RUN_PERSISTENT), ("plain_graph", q.RUN_GRAPH)):
         st = q.State([prob], [prm])
+        sampler = ClockSampler(lrank)
+        sampler.start()  # running before the timed region begins
         for _ in range(args.warmup):
             st.init()
             st.run(G, mode)
         torch.cuda.synchronize()
         times = []
-        sampler = ClockSampler(lrank)
         barrier()
-        sampler.start()
+        sampler.mark()
         wall0 = time.perf_counter()
         for _ in range(args.steps):
             flush.fill_(1.0)
@@ -366,7 +384,8 @@ def run_gpu(args):
                       "best_f": v["best_f"]} for k, v in results.items()},
         "roofline": {"bound": "alu", "kernel": "k_persist",
                      "achieved": achieved, "peak": peak_alu, "unit": "T lane-ops/s",
-                     "frac": achieved / peak_alu, "traffic": None,
+                     "frac": achieved / peak_alu, "traffic": K_PERSIST_DRAM_BYTES,
+                     "traffic_unit": "DRAM bytes per launch (2000 generations)",
                      "peak_note": f"{nsm} SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
                                   f"(issue limit, derived; clocks {pk_src})",
                      "frac_at_median_clock": achieved / (nsm * 128 * sm_mhz * 1e6 / 1e12),
@@ -454,7 +473,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
