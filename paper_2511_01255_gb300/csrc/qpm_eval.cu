@@ -1,15 +1,19 @@
 // qpm_eval.cu -- fitness of caller-supplied sign sequences (Sec. 2.1).
 //
-// Work split: a CTA takes 32 rows and one segment of the domains.  It walks the
-// segment in steps of 256 domains: the 32 x 256 genes (or their sign words) are
-// copied into shared memory with fully coalesced loads, the 256 phasors beside
-// them, then warp w scans domains [32w, 32w + 32) of the step for all 32 rows
-// (lane = row, so each phasor read is a broadcast) and the 8 warp partials are
-// combined in index order into the CTA's running monoid (A, B, C).  A second
-// kernel combines the S segment partials of every row in index order and closes
+// Work split: a warp takes 32 rows (lane = row) and one segment of L domains (L a
+// multiple of 128) and sweeps it in index order, so every row's running monoid
+// (A, B, C) is a plain sequential accumulation and every phasor read is a
+// broadcast from the segment's phasors, staged once per CTA in shared memory.
+// Float genes arrive 32 domains at a time with coalesced 16-byte loads issued one
+// step ahead and are transposed through a per-warp shared-memory tile; packed sign
+// words (32 domains each) are read four at a time straight into the lane of their
+// row.  The warps of a CTA take consecutive row groups of the same segment and
+// synchronise only to stage the phasors.  A second kernel (a warp per row) combines
+// the S segment partials of every row in index order and closes
 // d_eff = phi1 phi2 C + cdiag.
 #include <math.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -17,166 +21,94 @@
 
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
+#include "qpm_rows.cuh"
 
 namespace qpm {
 
-static constexpr int EV_WARPS = 8;
-static constexpr int EV_STEP = 256;  // domains staged per step (32 per warp)
-
-// genes of the step as float4 [column c4 = d/4][row], the row xor-swizzled by the
-// low 3 bits of the column: 8 consecutive columns of one row (a quarter-warp of
-// the coalesced staging stores) and 8 rows of one column (a quarter-warp of the
-// scan reads) both fall into 8 different 16-byte bank groups
-__device__ __forceinline__ int tile4_idx(int c4, int row) { return c4 * 32 + (row ^ (c4 & 7)); }
-
-// the genes (or sign word) of step `ms` that this thread stages, loaded into
-// registers ahead of time
-template <int KIND>
-struct StepRegs {
-  float4 v[8];
-  uint32_t w;
-  float4 p;
-};
-
-template <int KIND>
-__device__ __forceinline__ void load_step(const void *src, int64_t ld, const EvalShape &sh,
-                                          const float4 *table, int r0, int ms, StepRegs<KIND> &R) {
-  const int m = ms + threadIdx.x;
-  R.p = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-  if (KIND == 2) {
-    const int row = threadIdx.x >> 3, wd = threadIdx.x & 7;
-    const int gr = r0 + row;
-    R.w = 0u;
-    if (gr < sh.NP && ms + wd * 32 < sh.N)
-      R.w = __ldg((const uint32_t *)src + (int64_t)gr * ld + (ms >> 5) + wd);
-  } else {
+// partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
+// KIND 0: float genes (vector loads), 1: float genes (scalar loads), 2: packed sign
+// words (KIND 3: the same with 16-byte word loads).  grid (S, ceil(groups / ER_WPC)).
+template <int KIND, bool COMP>
+static __global__ void __launch_bounds__(ER_WPC * 32)
+    k_eval_rows(const void *__restrict__ src, int64_t ld, EvalShape sh,
+                const float4 *__restrict__ table, float2 *__restrict__ part) {
+  extern __shared__ float4 tb[];  // the segment's phasors
+  constexpr bool PACKED = KIND >= 2;
+  __shared__ float4 tile[PACKED ? 1 : ER_WPC][PACKED ? 1 : 256];  // float genes only
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
+  const bool live = r0 < sh.NP;
+  float4 R[8];
+  uint4 W = make_uint4(0u, 0u, 0u, 0u);
+  if (live) {  // the first step is in flight while the phasors are staged
+    if (PACKED) W = er_load_words<KIND == 3>((const uint32_t *)src, ld, sh, r0 + lane, m0);
+    else er_load_genes<KIND == 0>((const float *)src, ld, sh, r0, m0, R);
+  }
+  for (int i = threadIdx.x; i < sh.L; i += blockDim.x) {
+    const int m = m0 + i;
+    tb[i] = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  if (!live) return;
+  ErAcc<COMP> acc;
+  acc.zero();
+  if (PACKED) {
+    for (int ms = m0; ms < m1; ms += 128) {
+      const uint4 cur = W;
+      if (ms + 128 < m1) W = er_load_words<KIND == 3>((const uint32_t *)src, ld, sh, r0 + lane, ms + 128);
+      const float4 *tp = tb + (ms - m0);
+      const uint32_t ws[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int f = threadIdx.x + k * EV_WARPS * 32;  // float4 slot: 32 rows x 64 columns
-      const int row = f >> 6, c4 = f & 63;
-      const int gr = r0 + row, mm = ms + 4 * c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < sh.NP) {
-        const float *rp = (const float *)src + (int64_t)gr * ld;
-        if (KIND == 0 && mm + 4 <= sh.N) {
-          v = __ldg((const float4 *)(rp + mm));
-        } else {
-          if (mm < sh.N) v.x = __ldg(rp + mm);
-          if (mm + 1 < sh.N) v.y = __ldg(rp + mm + 1);
-          if (mm + 2 < sh.N) v.z = __ldg(rp + mm + 2);
-          if (mm + 3 < sh.N) v.w = __ldg(rp + mm + 3);
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll 8
+        for (int e = 0; e < 32; ++e) {
+          mono_push(acc.m, ((ws[q] >> e) & 1u) ? -1.0f : 1.0f, tp[32 * q + e]);
+          if ((e & 7) == 7) acc.fold();
         }
       }
-      R.v[k] = v;
+    }
+  } else {
+    float4 *T = tile[warp];
+    for (int ms = m0; ms < m1; ms += 32) {
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
+      __syncwarp();
+      if (ms + 32 < m1) er_load_genes<KIND == 0>((const float *)src, ld, sh, r0, ms + 32, R);
+      const float4 *tp = tb + (ms - m0);
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 x = T[er_tix(lane, c4)];
+        mono_push(acc.m, er_sgn(x.x), tp[4 * c4]);
+        mono_push(acc.m, er_sgn(x.y), tp[4 * c4 + 1]);
+        mono_push(acc.m, er_sgn(x.z), tp[4 * c4 + 2]);
+        mono_push(acc.m, er_sgn(x.w), tp[4 * c4 + 3]);
+        if (c4 & 1) acc.fold();
+      }
     }
   }
+  acc.fold();
+  const Mono run = acc.get();
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  const size_t o = (size_t)s * sh.NPpad + r0 + lane;
+  part[o] = run.A;
+  part[stride + o] = run.B;
+  part[2 * stride + o] = run.C;
 }
 
-// partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
-template <int KIND, bool COMP>  // KIND 0: float genes (vector loads), 1: float genes (scalar), 2: packed bits
-static __global__ void __launch_bounds__(EV_WARPS * 32)
-    k_eval_seg(const void *__restrict__ src, int64_t ld, EvalShape sh,
-               const float4 *__restrict__ table, float2 *__restrict__ part) {
-  __shared__ float4 tile4[EV_STEP / 4 * 32];         // genes, or sign words for KIND 2
-  __shared__ float4 tb[EV_STEP];                    // phasors of the step
-  __shared__ Mono wpart[EV_WARPS][32];              // per-warp partials of the step
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int s = blockIdx.x, grp = blockIdx.y;
-  const int r0 = grp * 32;
-  const int m0 = s * sh.L;
-  const int m1 = min(sh.N, m0 + sh.L);
-  Mono run = mono_zero();   // running monoid of the segment (warp 0, lane = row)
-  MonoK runk = monok_zero();
-  StepRegs<KIND> R;
-  if (m0 < m1) load_step<KIND>(src, ld, sh, table, r0, m0, R);
-  for (int ms = m0; ms < m1; ms += EV_STEP) {
-    __syncthreads();  // the previous step's tile and partials have been consumed
-    tb[threadIdx.x] = R.p;
-    if (KIND == 2) {
-      ((uint32_t *)tile4)[threadIdx.x] = R.w;  // [row][8 words]
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int f = threadIdx.x + k * EV_WARPS * 32;
-        tile4[tile4_idx(f & 63, f >> 6)] = R.v[k];
-      }
-    }
-    __syncthreads();
-    // the next step's loads are in flight while this step is scanned
-    if (ms + EV_STEP < m1) load_step<KIND>(src, ld, sh, table, r0, ms + EV_STEP, R);
-    // ---- warp w: domains [32w, 32w + 32) of the step for rows r0 + lane
-    Mono acc = mono_zero();
-    const int d0 = warp * 32;
-    if (KIND == 2) {
-      const uint32_t w = ((const uint32_t *)tile4)[lane * 8 + warp];
-#pragma unroll 8
-      for (int e = 0; e < 32; ++e) mono_push(acc, ((w >> e) & 1u) ? -1.0f : 1.0f, tb[d0 + e]);
-    } else {
-#pragma unroll 2
-      for (int e4 = 0; e4 < 8; ++e4) {
-        const int c4 = (d0 >> 2) + e4;
-        const float4 x = tile4[tile4_idx(c4, lane)];
-        const float4 *pp = tb + 4 * c4;
-        mono_push(acc, x.x < 0.f ? -1.f : 1.f, pp[0]);
-        mono_push(acc, x.y < 0.f ? -1.f : 1.f, pp[1]);
-        mono_push(acc, x.z < 0.f ? -1.f : 1.f, pp[2]);
-        mono_push(acc, x.w < 0.f ? -1.f : 1.f, pp[3]);
-      }
-    }
-    wpart[warp][lane] = acc;
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-      for (int w = 0; w < EV_WARPS; ++w) {
-        if (COMP) monok_fold_in(runk, wpart[w][lane]);
-        else run = mono_combine(run, wpart[w][lane]);
-      }
-    }
-  }
-  if (warp == 0) {
-    if (COMP) run = monok_fold(runk);
-    const size_t stride = (size_t)sh.S * sh.NPpad;
-    const size_t o = (size_t)s * sh.NPpad + r0 + lane;
-    part[o] = run.A;
-    part[stride + o] = run.B;
-    part[2 * stride + o] = run.C;
-  }
-}
-
-template <bool COMP>
+// one warp per row: d_eff = phi1 phi2 C + cdiag of the combined segments
 static __global__ void k_eval_combine(EvalShape sh, const float2 *__restrict__ part,
                                       const float2 *__restrict__ konst, float2 *__restrict__ deff,
                                       float *__restrict__ fit) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= sh.NP) return;
-  const size_t stride = (size_t)sh.S * sh.NPpad;
-  Mono acc = mono_zero();
-  float2 eB = make_float2(0.f, 0.f), eC = make_float2(0.f, 0.f);
-  for (int s = 0; s < sh.S; ++s) {
-    const size_t o = (size_t)s * sh.NPpad + i;
-    Mono r;
-    r.A = part[o];
-    r.B = part[stride + o];
-    r.C = part[2 * stride + o];
-    if (COMP) {
-      // C += C' + A' B and B += B' with Kahan compensation on C and B
-      const float br = __fsub_rn(acc.B.x, eB.x), bi = __fsub_rn(acc.B.y, eB.y);
-      const float xr = __fadd_rn(r.C.x, __fsub_rn(__fmul_rn(r.A.x, br), __fmul_rn(r.A.y, bi)));
-      const float xi = __fadd_rn(r.C.y, __fadd_rn(__fmul_rn(r.A.x, bi), __fmul_rn(r.A.y, br)));
-      kahan_add(acc.C.x, eC.x, xr);
-      kahan_add(acc.C.y, eC.y, xi);
-      kahan_add(acc.B.x, eB.x, r.B.x);
-      kahan_add(acc.B.y, eB.y, r.B.y);
-      acc.A.x += r.A.x;
-      acc.A.y += r.A.y;
-    } else {
-      acc = mono_combine(acc, r);
-    }
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= sh.NP) return;
+  const Mono acc = combine_segments(part, sh.S, sh.NPpad, row);
+  if ((threadIdx.x & 31) == 0) {
+    const float2 D = deff_from(acc, konst[0], konst[1]);
+    deff[row] = D;
+    if (fit) fit[row] = fit_of(D);
   }
-  if (COMP) acc.C = make_float2(__fsub_rn(acc.C.x, eC.x), __fsub_rn(acc.C.y, eC.y));
-  const float2 D = deff_from(acc, konst[0], konst[1]);
-  deff[i] = D;
-  if (fit) fit[i] = fit_of(D);
 }
 
 // ------------------------------------------------------------- caches (host)
@@ -270,22 +202,36 @@ qpm_status get_scratch(cudaStream_t stream, size_t bytes, void **ptr) {
 }
 }  // namespace
 
-EvalShape eval_shape(int NP, int N) {
+// split for the row sweep: about 20 resident warps per SM in total, segments a
+// multiple of ER_LQ domains and at most ER_LMAX
+EvalShape eval_rows_shape(int NP, int N) {
   EvalShape sh;
   sh.NP = NP;
   sh.N = N;
   sh.groups = (NP + 31) / 32;
   sh.NPpad = sh.groups * 32;
-  const int target_ctas = sm_count() * 6;
-  int S = (target_ctas + sh.groups - 1) / sh.groups;
-  const int maxS = (N + EV_STEP - 1) / EV_STEP;  // at least one step per segment
-  if (S > maxS) S = maxS;
-  if (S < 1) S = 1;
-  int L = (N + S - 1) / S;
-  L = (L + EV_STEP - 1) / EV_STEP * EV_STEP;
-  sh.S = (N + L - 1) / L;
+  const int target = sm_count() * 20;
+  const int S0 = std::max(1, (target + sh.groups - 1) / sh.groups);
+  int L = (N + S0 - 1) / S0;
+  L = (L + ER_LQ - 1) / ER_LQ * ER_LQ;
+  L = std::min(std::max(L, ER_LQ), ER_LMAX);
   sh.L = L;
+  sh.S = (N + L - 1) / L;
   return sh;
+}
+
+static void launch_eval_rows(int kind, bool comp, const void *src, int64_t ld, const EvalShape &sh,
+                             const float4 *table, float2 *part, cudaStream_t stream) {
+  const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
+  const size_t smem = sizeof(float4) * (size_t)sh.L;
+#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(src, ld, sh, table, part)
+  switch (kind) {
+    case 0: if (comp) QPM_ER(0, true); else QPM_ER(0, false); break;
+    case 1: if (comp) QPM_ER(1, true); else QPM_ER(1, false); break;
+    case 2: if (comp) QPM_ER(2, true); else QPM_ER(2, false); break;
+    default: if (comp) QPM_ER(3, true); else QPM_ER(3, false); break;
+  }
+#undef QPM_ER
 }
 
 static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t ld, int32_t NP,
@@ -301,25 +247,18 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   const float2 *konst;
   qpm_status st = get_table(prob, stream, &table, &konst);
   if (st != QPM_OK) return st;
-  const EvalShape sh = eval_shape(NP, prob->N);
+  if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
+  const EvalShape sh = eval_rows_shape(NP, prob->N);
   void *scratch;
   st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
   if (st != QPM_OK) return st;
   float2 *part = (float2 *)scratch;
-  dim3 grid(sh.S, sh.groups);
-  if (kind != 2 && (ld % 4 == 0) && (((uintptr_t)src & 15) == 0)) kind = 0;
-  else if (kind != 2) kind = 1;
-#define QPM_EV(K, C) k_eval_seg<K, C><<<grid, EV_WARPS * 32, 0, stream>>>(src, ld, sh, table, part)
-  if (kind == 0) { if (comp) QPM_EV(0, true); else QPM_EV(0, false); }
-  else if (kind == 1) { if (comp) QPM_EV(1, true); else QPM_EV(1, false); }
-  else { if (comp) QPM_EV(2, true); else QPM_EV(2, false); }
-#undef QPM_EV
+  const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
+  if (kind == 2) kind = aligned ? 3 : 2;
+  else kind = aligned ? 0 : 1;
+  launch_eval_rows(kind, comp != 0, src, ld, sh, table, part, stream);
   QPM_CUDA(cudaGetLastError());
-  const int cb = 128;
-  if (comp)
-    k_eval_combine<true><<<(NP + cb - 1) / cb, cb, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
-  else
-    k_eval_combine<false><<<(NP + cb - 1) / cb, cb, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
+  k_eval_combine<<<(NP + 7) / 8, 256, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }
@@ -374,7 +313,8 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (ld < prob->N) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: leading dimension smaller than the row");
   if (prob->N > (1 << 28) || NP > (1 << 26))
     return fail(QPM_ERR_ARG, "qpm_eval_noalloc: problem exceeds the fixed scratch (8 MiB)");
-  const EvalShape sh = eval_shape(NP, prob->N);
+  if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_noalloc: too many rows");
+  const EvalShape sh = eval_rows_shape(NP, prob->N);
   const int32_t Npad = (prob->N + 3) & ~3;
   const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
   const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));
@@ -398,21 +338,10 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   TableSpec ts{prob->N, Npad, 1, Npad, prob->kappa1, prob->kappa2};
   st = launch_table(ts, table, tpart, konst, nullptr, s);
   if (st != QPM_OK) return st;
-  dim3 grid(sh.S, sh.groups);
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
-  if (vec) {
-    if (compensated) k_eval_seg<0, true><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
-    else k_eval_seg<0, false><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
-  } else {
-    if (compensated) k_eval_seg<1, true><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
-    else k_eval_seg<1, false><<<grid, EV_WARPS * 32, 0, s>>>(genes, ld, sh, table, part);
-  }
+  launch_eval_rows(vec ? 0 : 1, compensated != 0, genes, ld, sh, table, part, s);
   QPM_CUDA(cudaGetLastError());
-  const int cb = 128;
-  if (compensated)
-    k_eval_combine<true><<<(NP + cb - 1) / cb, cb, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
-  else
-    k_eval_combine<false><<<(NP + cb - 1) / cb, cb, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
+  k_eval_combine<<<(NP + 7) / 8, 256, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }

@@ -38,14 +38,14 @@ qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2
 qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
                         const float2 **konst);
 
-// split of qpm_eval-style work: S segments of L domains (L a multiple of 256),
-// rows in groups of 32
+// split of qpm_eval-style work: S segments of L domains, rows in groups of 32
 struct EvalShape {
   int NP, N, S, L;
   int groups;  // ceil(NP / 32)
   int NPpad;   // groups * 32
 };
-EvalShape eval_shape(int NP, int N);
+// split of the row sweep (qpm_rows.cuh): segments a multiple of 128 domains
+EvalShape eval_rows_shape(int NP, int N);
 
 // current device's SM count (cached per device)
 int sm_count();

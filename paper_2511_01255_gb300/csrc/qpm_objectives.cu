@@ -8,9 +8,9 @@
 //
 // Multi-wavelength objective (Sec. 5): f = sum_k |G0 - G_k| + beta (G_max - G_min)
 // with G_k = |d_eff(kappa1_k, kappa2_k)|, to be minimised.  The K cascaded scans
-// share one staged copy of the genes: 32 rows x 256 domains per step are copied
-// into shared memory once, and every warp runs its 32 domains through the K
-// phasor tables of the step.
+// share one read of the genes: the row sweep of qpm_eval (qpm_rows.cuh) with the
+// K phasor tables of the segment staged side by side, every domain pushed into K
+// running monoids.  For K = 1 this is qpm_eval's arithmetic, operation for operation.
 #include <math.h>
 
 #include <algorithm>
@@ -18,6 +18,7 @@
 
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
+#include "qpm_rows.cuh"
 
 namespace qpm {
 
@@ -88,8 +89,6 @@ static __global__ void __launch_bounds__(SHG_THREADS)
 }
 
 // ------------------------------------------------- multi-wavelength objective
-static constexpr int MW_STEP = 256;
-static constexpr int MW_WARPS = 8;
 static constexpr int MW_KMAX = 4;
 
 struct MultiTables {
@@ -97,119 +96,82 @@ struct MultiTables {
   const float2 *konst[MW_KMAX];
 };
 
-__device__ __forceinline__ int mw_idx(int c4, int row) { return c4 * 32 + (row ^ (c4 & 7)); }
-
-// dynamic smem: tile [64 x 32] float4 | tables [K][256] float4 | partials [K][8][32] Mono
+// dynamic shared memory: the K phasor tables of the segment, [K][L] float4.
+// Partials as for qpm_eval, one set per problem: part[((3k + comp) * S + s) * NPpad + i].
+// grid (S, ceil(groups / ER_WPC)).
 template <bool VEC, int K>
-static __global__ void __launch_bounds__(MW_WARPS * 32)
-    k_multi_seg(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
-                float2 *__restrict__ part) {
-  extern __shared__ float4 mw[];
-  float4 *tile4 = mw;
-  float4 *tb = mw + MW_STEP / 4 * 32;
-  Mono *wpart = (Mono *)(tb + K * MW_STEP);
+static __global__ void __launch_bounds__(ER_WPC * 32)
+    k_multi_rows(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
+                 float2 *__restrict__ part) {
+  extern __shared__ float4 tb[];
+  __shared__ float4 tile[ER_WPC][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int s = blockIdx.x, r0 = blockIdx.y * 32;
-  const int m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
-  Mono run[K];
+  const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
+  const bool live = r0 < sh.NP;
+  float4 R[8];
+  if (live) er_load_genes<VEC>(genes, ld, sh, r0, m0, R);
 #pragma unroll
-  for (int k = 0; k < K; ++k) run[k] = mono_zero();
-  for (int ms = m0; ms < m1; ms += MW_STEP) {
-    __syncthreads();
-    {
-      const int m = ms + threadIdx.x;
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        tb[k * MW_STEP + threadIdx.x] = m < sh.N ? __ldg(mt.t[k] + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < K; ++k)
+    for (int i = threadIdx.x; i < sh.L; i += blockDim.x) {
+      const int m = m0 + i;
+      tb[k * sh.L + i] = m < sh.N ? __ldg(mt.t[k] + m) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+  __syncthreads();
+  if (!live) return;
+  Mono acc[K];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int f = threadIdx.x + i * MW_WARPS * 32;
-      const int row = f >> 6, c4 = f & 63;
-      const int gr = r0 + row, mm = ms + 4 * c4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gr < sh.NP) {
-        const float *rp = genes + (int64_t)gr * ld;
-        if (VEC && mm + 4 <= sh.N) {
-          v = __ldg((const float4 *)(rp + mm));
-        } else {
-          if (mm < sh.N) v.x = __ldg(rp + mm);
-          if (mm + 1 < sh.N) v.y = __ldg(rp + mm + 1);
-          if (mm + 2 < sh.N) v.z = __ldg(rp + mm + 2);
-          if (mm + 3 < sh.N) v.w = __ldg(rp + mm + 3);
-        }
-      }
-      tile4[mw_idx(c4, row)] = v;
-    }
-    __syncthreads();
-    Mono acc[K];
+  for (int k = 0; k < K; ++k) acc[k] = mono_zero();
+  float4 *T = tile[warp];
+  for (int ms = m0; ms < m1; ms += 32) {
+    __syncwarp();
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = mono_zero();
-    for (int e4 = 0; e4 < 8; ++e4) {
-      const int c4 = warp * 8 + e4;
-      const float4 x = tile4[mw_idx(c4, lane)];
-      const float d0 = x.x < 0.f ? -1.f : 1.f, d1 = x.y < 0.f ? -1.f : 1.f;
-      const float d2 = x.z < 0.f ? -1.f : 1.f, d3 = x.w < 0.f ? -1.f : 1.f;
+    for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
+    __syncwarp();
+    if (ms + 32 < m1) er_load_genes<VEC>(genes, ld, sh, r0, ms + 32, R);
+    const float4 *tp = tb + (ms - m0);
+#pragma unroll 2
+    for (int c4 = 0; c4 < 8; ++c4) {
+      const float4 x = T[er_tix(lane, c4)];
+      const float d[4] = {er_sgn(x.x), er_sgn(x.y), er_sgn(x.z), er_sgn(x.w)};
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const float4 *pp = tb + k * MW_STEP + 4 * c4;
-        mono_push(acc[k], d0, pp[0]);
-        mono_push(acc[k], d1, pp[1]);
-        mono_push(acc[k], d2, pp[2]);
-        mono_push(acc[k], d3, pp[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mono_push(acc[k], d[j], tp[k * sh.L + 4 * c4 + j]);
       }
     }
-#pragma unroll
-    for (int k = 0; k < K; ++k) wpart[(k * MW_WARPS + warp) * 32 + lane] = acc[k];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        for (int w = 0; w < MW_WARPS; ++w)
-          run[k] = mono_combine(run[k], wpart[(k * MW_WARPS + w) * 32 + lane]);
-    }
   }
-  if (warp == 0) {
-    const size_t stride = (size_t)sh.S * sh.NPpad;
+  const size_t stride = (size_t)sh.S * sh.NPpad;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + r0 + lane;
-      part[o] = run[k].A;
-      part[o + stride] = run[k].B;
-      part[o + 2 * stride] = run[k].C;
-    }
+  for (int k = 0; k < K; ++k) {
+    const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + r0 + lane;
+    part[o] = acc[k].A;
+    part[o + stride] = acc[k].B;
+    part[o + 2 * stride] = acc[k].C;
   }
 }
 
+// one warp per row: the K combined scans (as in qpm_eval), then the objective
 template <int K>
 static __global__ void k_multi_combine(EvalShape sh, const float2 *__restrict__ part, MultiTables mt,
                                        float G0, float beta, float2 *__restrict__ deff,
                                        float *__restrict__ obj) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= sh.NP) return;
-  const size_t stride = (size_t)sh.S * sh.NPpad;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= sh.NP) return;
+  const size_t set = (size_t)3 * sh.S * sh.NPpad;  // the partials of one problem
   float f = 0.f, gmax = -1.f, gmin = 3.0e38f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    Mono acc = mono_zero();
-    for (int s = 0; s < sh.S; ++s) {
-      const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + i;
-      Mono r;
-      r.A = part[o];
-      r.B = part[o + stride];
-      r.C = part[o + 2 * stride];
-      acc = mono_combine(acc, r);
-    }
+    const Mono acc = combine_segments(part + k * set, sh.S, sh.NPpad, row);
     const float2 D = deff_from(acc, mt.konst[k][0], mt.konst[k][1]);
-    if (deff) deff[(size_t)i * K + k] = D;
+    if (deff && (threadIdx.x & 31) == 0) deff[(size_t)row * K + k] = D;
     const float G = sqrtf(fit_of(D));
     f += fabsf(G0 - G);
     gmax = fmaxf(gmax, G);
     gmin = fminf(gmin, G);
   }
-  obj[i] = f + beta * (gmax - gmin);
+  if ((threadIdx.x & 31) == 0) obj[row] = f + beta * (gmax - gmin);
 }
-
 
 }  // namespace qpm
 
@@ -256,25 +218,25 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     qpm_status st = cached_table(&probs[k], s, &mt.t[k], &mt.konst[k]);
     if (st != QPM_OK) return st;
   }
-  const EvalShape sh = eval_shape(NP, N);
+  if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
+  const EvalShape sh = eval_rows_shape(NP, N);
   const size_t need = sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
   if (!scratch || scratch_bytes < need)
     return fail(QPM_ERR_ARG, "qpm_eval_multi: scratch smaller than qpm_eval_multi_scratch_bytes()");
   float2 *part = (float2 *)scratch;
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
-  const dim3 grid(sh.S, sh.groups);
-  const size_t smem = sizeof(float4) * (MW_STEP / 4 * 32 + (size_t)K * MW_STEP) +
-                      sizeof(Mono) * (size_t)K * MW_WARPS * 32;
+  const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
+  const size_t smem = sizeof(float4) * (size_t)K * sh.L;
 #define QPM_MW(KK)                                                                          \
   {                                                                                         \
-    const void *fn = vec ? (const void *)k_multi_seg<true, KK> : (const void *)k_multi_seg<false, KK>; \
+    const void *fn = vec ? (const void *)k_multi_rows<true, KK> : (const void *)k_multi_rows<false, KK>; \
     QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     EvalShape shv = sh;                                                                     \
     int64_t ldv = ld;                                                                       \
     void *args[] = {(void *)&genes, &ldv, &shv, &mt, &part};                                \
-    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(MW_WARPS * 32), args, smem, s));               \
-    k_multi_combine<KK><<<(NP + 127) / 128, 128, 0, s>>>(sh, part, mt, G0, beta,            \
-                                                         (float2 *)d_eff, objective);       \
+    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(ER_WPC * 32), args, smem, s));                 \
+    k_multi_combine<KK><<<(NP + 7) / 8, 256, 0, s>>>(sh, part, mt, G0, beta,               \
+                                                      (float2 *)d_eff, objective);          \
   }
   if (K == 1) QPM_MW(1) else if (K == 2) QPM_MW(2) else if (K == 3) QPM_MW(3) else QPM_MW(4)
 #undef QPM_MW
@@ -284,6 +246,6 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
 
 extern "C" size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP) {
   if (K < 1 || N < 1 || NP < 1) return 0;
-  const EvalShape sh = eval_shape(NP, N);
+  const EvalShape sh = eval_rows_shape(NP, N);
   return sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
 }

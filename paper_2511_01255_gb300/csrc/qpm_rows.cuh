@@ -1,0 +1,120 @@
+// qpm_rows.cuh -- the row sweep shared by the fitness kernels of qpm_eval and of
+// the multi-wavelength objective: a warp takes 32 rows (lane = row) and one
+// segment of L domains (a multiple of ER_LQ) and walks it in index order.
+#pragma once
+#include "qpm_common.cuh"
+#include "qpm_internal.h"
+
+namespace qpm {
+
+constexpr int ER_WPC = 4;      // warps (row groups of 32) per CTA
+constexpr int ER_LQ = 128;     // segment length quantum (domains)
+constexpr int ER_LMAX = 1920;  // longest segment: its phasors fit the default 48 KB
+
+// per-warp tile: 32 rows x 32 domains as float4 [row][c4], the column xor-swizzled by
+// the row so that both the staging stores (8 columns of a row per quarter-warp) and
+// the row walks (8 rows of a column) are free of bank conflicts
+__device__ __forceinline__ int er_tix(int row, int c4) { return row * 8 + (c4 ^ (row & 7)); }
+
+// float genes of one step (32 domains from ms) of rows r0..r0+31: lane l holds
+// float4 k * 32 + l, i.e. row 4k + l / 8, columns 4 (l % 8) .. +3
+template <bool VEC>
+__device__ __forceinline__ void er_load_genes(const float *__restrict__ g, int64_t ld,
+                                              const EvalShape &sh, int r0, int ms, float4 R[8]) {
+  const int lane = threadIdx.x & 31;
+  const int m = ms + 4 * (lane & 7);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int gr = r0 + 4 * k + (lane >> 3);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gr < sh.NP) {
+      const float *rp = g + (int64_t)gr * ld;
+      if (VEC && m + 4 <= sh.N) {
+        v = __ldg((const float4 *)(rp + m));
+      } else {
+        if (m < sh.N) v.x = __ldg(rp + m);
+        if (m + 1 < sh.N) v.y = __ldg(rp + m + 1);
+        if (m + 2 < sh.N) v.z = __ldg(rp + m + 2);
+        if (m + 3 < sh.N) v.w = __ldg(rp + m + 3);
+      }
+    }
+    R[k] = v;
+  }
+}
+
+// sign words of one packed step (128 domains from ms, a multiple of 128) of row
+// `row`; words beyond the row's last domain are zero
+template <bool VECW>
+__device__ __forceinline__ uint4 er_load_words(const uint32_t *__restrict__ w, int64_t ld,
+                                               const EvalShape &sh, int row, int ms) {
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (row < sh.NP) {
+    const uint32_t *rp = w + (int64_t)row * ld + (ms >> 5);
+    const int nw = (sh.N - ms + 31) >> 5;  // words of this row from ms on
+    if (VECW && nw >= 4) {
+      v = __ldg((const uint4 *)rp);
+    } else {
+      if (nw > 0) v.x = __ldg(rp);
+      if (nw > 1) v.y = __ldg(rp + 1);
+      if (nw > 2) v.z = __ldg(rp + 2);
+      if (nw > 3) v.w = __ldg(rp + 3);
+    }
+  }
+  return v;
+}
+
+__device__ __forceinline__ float er_sgn(float x) { return x < 0.f ? -1.f : 1.f; }
+
+// Running monoid of a lane's row: plain FP32 sums, or (COMP) plain sums over blocks
+// of 8 domains Kahan-folded into a compensated triple.
+template <bool COMP>
+struct ErAcc {
+  Mono m;
+  MonoK k;
+  __device__ __forceinline__ void zero() {
+    m = mono_zero();
+    if (COMP) k = monok_zero();
+  }
+  __device__ __forceinline__ void fold() {
+    if (COMP) {
+      monok_fold_in(k, m);
+      m = mono_zero();
+    }
+  }
+  __device__ __forceinline__ Mono get() { return COMP ? monok_fold(k) : m; }
+};
+
+// The S segment partials of row `row` combined in index order by one warp: lane l
+// folds its contiguous run of segments [l c, l c + c), c = ceil(S / 32), then the
+// 32 lane results are combined pairwise in lane order.  part is the structure of
+// arrays [comp][S][NPpad] (comp = A, B, C); the result is valid in lane 0.
+__device__ __forceinline__ Mono combine_segments(const float2 *__restrict__ part, int S, int NPpad,
+                                                 int row) {
+  const int lane = threadIdx.x & 31;
+  const size_t stride = (size_t)S * NPpad;
+  const int c = (S + 31) >> 5;
+  const int s0 = lane * c, s1 = min(S, s0 + c);
+  Mono acc = mono_zero();
+  for (int s = s0; s < s1; ++s) {
+    const size_t o = (size_t)s * NPpad + row;
+    Mono r;
+    r.A = part[o];
+    r.B = part[stride + o];
+    r.C = part[2 * stride + o];
+    acc = mono_combine(acc, r);
+  }
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    Mono r;
+    r.A.x = __shfl_down_sync(0xffffffffu, acc.A.x, off);
+    r.A.y = __shfl_down_sync(0xffffffffu, acc.A.y, off);
+    r.B.x = __shfl_down_sync(0xffffffffu, acc.B.x, off);
+    r.B.y = __shfl_down_sync(0xffffffffu, acc.B.y, off);
+    r.C.x = __shfl_down_sync(0xffffffffu, acc.C.x, off);
+    r.C.y = __shfl_down_sync(0xffffffffu, acc.C.y, off);
+    if ((lane & (2 * off - 1)) == 0) acc = mono_combine(acc, r);
+  }
+  return acc;
+}
+
+}  // namespace qpm
