@@ -18,20 +18,16 @@
 // same segment and share its staged phasors (p1, p2, q = p1 p2).
 //
 // Forward: every (row, segment) writes its partial sums (A_s, B_s, C_s, E_s) into
-// the row's saved block; the segments of a row are then combined in index order
-// (C = sum_s C_s + A_s Bpre_s with Bpre_s the b-sum of the segments before s),
-// D is closed and each segment's (A_s, B_s) is overwritten with the exclusive
-// prefixes (Apre_s, Bpre_s).  For up to RX_FUSE_S segments the combine is done by
-// the last warp to finish a row group (an arrival counter per row group, reset
-// by that warp); longer rows use a separate kernel with a warp per row.
+// the row's saved block; a second kernel (a warp per row, lanes over segments)
+// combines the segments in index order (C = sum_s C_s + A_s Bpre_s with Bpre_s
+// the b-sum of the segments before s), closes D and overwrites each segment's
+// (A_s, B_s) with the exclusive prefixes (Apre_s, Bpre_s).
 // Backward: each (row, segment) starts from those prefixes (P = Bpre_s,
 // R = A - Apre_s), updates P_k and R_k as it goes and writes the gradient back
 // through the same tile with coalesced stores.
 #include <math.h>
 
 #include <algorithm>
-#include <map>
-#include <mutex>
 
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
@@ -41,7 +37,6 @@ namespace qpm {
 static constexpr int RX_STEP = 32;   // domains per step (one per lane of a tile row)
 static constexpr int RX_LMAX = 256;  // longest segment
 static constexpr int RX_WPC = 4;     // warps (row groups of 32) per CTA
-static constexpr int RX_FUSE_S = 64; // longest row (in segments) combined inside the forward
 
 struct RelaxShape {
   int B, N, L, S;  // rows, domains, segment length, segments
@@ -157,54 +152,11 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// the segments of row `row` in index order (lane = row): D, f and A of the row,
-// and the exclusive prefixes (Apre_s, Bpre_s) in place of (A_s, B_s).  The
-// partials were written by other CTAs of the running grid: read past L1, four
-// segments' loads in flight before any of them is overwritten.
-__device__ __forceinline__ void combine_row(const RelaxShape &sh, const float2 *konst, float *sv,
-                                            float2 *Dout, float *fout, int row) {
-  float2 cA = make_float2(0.f, 0.f), cB = cA, C = cA, E = cA;
-  float4 *blk = (float4 *)(sv + 4);
-  for (int s0 = 0; s0 < sh.S; s0 += 4) {
-    float4 ab[4], ce[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      ab[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      ce[k] = ab[k];
-      if (s0 + k < sh.S) {
-        ab[k] = __ldcg(blk + 2 * (s0 + k));
-        ce[k] = __ldcg(blk + 2 * (s0 + k) + 1);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      C.x += ce[k].x + (ab[k].x * cB.x - ab[k].y * cB.y);
-      C.y += ce[k].y + (ab[k].x * cB.y + ab[k].y * cB.x);
-      E.x += ce[k].z;
-      E.y += ce[k].w;
-      if (s0 + k < sh.S) __stcg(blk + 2 * (s0 + k), make_float4(cA.x, cA.y, cB.x, cB.y));
-      cA.x += ab[k].x;
-      cA.y += ab[k].y;
-      cB.x += ab[k].z;
-      cB.y += ab[k].w;
-    }
-  }
-  const float2 phi12 = konst[0], psi = konst[2];
-  const float2 D = make_float2(phi12.x * C.x - phi12.y * C.y + (psi.x * E.x - psi.y * E.y),
-                               phi12.x * C.y + phi12.y * C.x + (psi.x * E.y + psi.y * E.x));
-  Dout[row] = D;
-  if (fout) fout[row] = fit_of(D);
-  sv[0] = cA.x;
-  sv[1] = cA.y;
-}
-
 // grid (ceil(row groups / RX_WPC), S), block RX_WPC warps
-template <bool VEC, bool FUSE>
+template <bool VEC>
 static __global__ void __launch_bounds__(RX_WPC * 32)
     k_relaxed_fwd(const float *__restrict__ theta, RelaxShape sh, const float4 *__restrict__ gtab,
-                  float *__restrict__ saved, const float2 *__restrict__ konst,
-                  unsigned *__restrict__ arrivals, float2 *__restrict__ Dout,
-                  float *__restrict__ fout) {
+                  float *__restrict__ saved) {
   __shared__ float4 sp[RX_LMAX];
   __shared__ float2 sq[RX_LMAX];
   __shared__ float4 tile[RX_WPC][RX_STEP * RX_STEP / 4];
@@ -244,23 +196,11 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
     }
   }
   const int row = r0 + lane;
-  float *sv = saved + (int64_t)row * sh.sf;
   if (row < sh.B) {
-    float4 *o = (float4 *)(sv + 4 + 8 * (int64_t)seg);
+    float4 *o = (float4 *)(saved + (int64_t)row * sh.sf + 4 + 8 * (int64_t)seg);
     o[0] = make_float4(acc.A.x, acc.A.y, acc.B.x, acc.B.y);
     o[1] = make_float4(acc.C.x, acc.C.y, E.x, E.y);
   }
-  if (!FUSE) return;
-  // the last of the S warps of this row group combines it
-  __threadfence();
-  __syncwarp();
-  unsigned last = 0;
-  const int group = r0 >> 5;
-  if (lane == 0) last = atomicAdd(arrivals + group, 1u) == (unsigned)(sh.S - 1);
-  if (!__shfl_sync(0xffffffffu, last, 0)) return;
-  __threadfence();
-  if (lane == 0) arrivals[group] = 0u;  // ready for the next call on this stream
-  if (row < sh.B) combine_row(sh, konst, sv, Dout, fout, row);
 }
 
 // one warp per row: segments in index order -> D, f, A; (A_s, B_s) -> prefixes
@@ -418,31 +358,6 @@ static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int
   return QPM_OK;
 }
 
-// zeroed arrival counters (one per row group) for the forward's fused combine,
-// per (device, stream); the kernel leaves them at zero
-static qpm_status rx_arrivals(cudaStream_t s, int groups, unsigned **out) {
-  static std::mutex mu;
-  static std::map<std::pair<int, cudaStream_t>, std::pair<unsigned *, int>> cache;
-  int dev = 0;
-  QPM_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> g(mu);
-  auto &e = cache[std::make_pair(dev, s)];
-  if (e.second < groups) {
-    if (e.first) {
-      QPM_CUDA(cudaStreamSynchronize(s));
-      QPM_CUDA(cudaFree(e.first));
-      e.first = nullptr;
-      e.second = 0;
-    }
-    const int n = std::max(groups, 256);
-    QPM_CUDA(cudaMalloc(&e.first, sizeof(unsigned) * n));
-    QPM_CUDA(cudaMemsetAsync(e.first, 0, sizeof(unsigned) * n, s));
-    e.second = n;
-  }
-  *out = e.first;
-  return QPM_OK;
-}
-
 static dim3 rx_grid(const RelaxShape &sh) {
   const int groups = (sh.B + 31) / 32;
   return dim3((groups + RX_WPC - 1) / RX_WPC, sh.S);
@@ -466,21 +381,10 @@ extern "C" qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float 
   if (st != QPM_OK) return st;
   float2 *D = (float2 *)d_eff;
   const dim3 grid = rx_grid(sh);
-  if (sh.S <= RX_FUSE_S) {
-    unsigned *arr;
-    st = rx_arrivals(s, (B + 31) / 32, &arr);
-    if (st != QPM_OK) return st;
-    if (sh.vec)
-      k_relaxed_fwd<true, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, arr, D, fit);
-    else
-      k_relaxed_fwd<false, true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, arr, D, fit);
-    QPM_CUDA(cudaGetLastError());
-    return QPM_OK;
-  }
   if (sh.vec)
-    k_relaxed_fwd<true, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, nullptr, D, fit);
+    k_relaxed_fwd<true><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved);
   else
-    k_relaxed_fwd<false, false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved, konst, nullptr, D, fit);
+    k_relaxed_fwd<false><<<grid, RX_WPC * 32, 0, s>>>(theta, sh, tab, saved);
   QPM_CUDA(cudaGetLastError());
   k_relaxed_combine<<<(B + 7) / 8, 256, 0, s>>>(sh, konst, saved, D, fit);
   QPM_CUDA(cudaGetLastError());
