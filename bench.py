@@ -61,7 +61,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "20"],
+                 "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -248,6 +248,8 @@ def run_gpu(args):
     ev_b = sum((2 * ci["NP"] - 3) * ci["N"] for ci in inst) * Gb + sum(ci["NP"] * ci["N"] for ci in inst)
     stb = q.State(probs_b, prms_b)
     stb.init()
+    from paper_2511_01255_gb300 import autotune
+    ctas = autotune.autotune_batch_cluster(stb, gens=10)  # CTAs per cluster, measured (cached)
     stb.run(3, q.RUN_BATCHED)  # warm-up (graph instantiation, caches)
     tb = []
     for _ in range(min(2, args.steps)):
@@ -263,6 +265,7 @@ def run_gpu(args):
     stb.close()
     batched = {
         "workload": "512 instances, N~U[500,8000], NP in {64,128,256,512}, G=1000, plain FP32 scan",
+        "cluster_ctas": ctas,
         "s_per_run": t_batched, "domain_evals_per_s": ev_b / t_batched,
         "gene_gens_per_s": gg_b / t_batched,
         "per_instance_persistent_s_per_gen": t_inst3 / 3,
@@ -473,7 +476,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)

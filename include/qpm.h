@@ -245,6 +245,18 @@ qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t steps, float 
 /* Threads per individual the state uses for instance `inst` (host int32 out). */
 qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out);
 
+/* Batched form (QPM_RUN_BATCHED): CTAs per thread-block cluster, 1 (default), 2, 4
+ * or 8.  An instance is run by all CTAs of one cluster (its individuals dealt to
+ * their warps, the generation's two dependencies as cluster barriers), so a large
+ * instance no longer holds one SM while the others have finished; the per-
+ * individual arithmetic, and hence every result, is the same for every size.  An
+ * execution choice with no counterpart in the paper; autotune.py picks it by
+ * measurement.  Host call; synchronises the device if a batched launch was already
+ * captured.  Errors: other values -> QPM_ERR_ARG; a size the device cannot
+ * co-schedule -> QPM_ERR_UNSUPPORTED; the current device is not the state's ->
+ * QPM_ERR_STATE. */
+qpm_status qpm_set_batch_cluster(qpm_state *st, int32_t ctas);
+
 /* Test hook: record FP32 fitness values of instance `inst` into trace (device,
  * float [NP * (1 + 2G)]): [0, NP) after init, then for generation g the trial
  * fitness at NP*(1+2g) and the GWO candidate fitness at NP*(2+2g) (NaN for the

@@ -18,6 +18,7 @@ __all__ = [
     "qpm_release_caches", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
+    "qpm_set_batch_cluster",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
 ]
@@ -79,6 +80,7 @@ def lib(build=True):
             "qpm_destroy": ([_P], ctypes.c_int),
             "qpm_generation": ([_P, _P], ctypes.c_int),
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
+            "qpm_set_batch_cluster": ([_P, i32], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
             "qpm_set_population": ([_P, i32, _P, i64, i32, _P], ctypes.c_int),
             "qpm_get_best": ([_P, i32, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -283,6 +285,11 @@ def qpm_team_of(st, inst=0):
     return t.value
 
 
+def qpm_set_batch_cluster(st, ctas):
+    """CTAs per thread-block cluster of the batched form (1, 2, 4 or 8)."""
+    _check(lib().qpm_set_batch_cluster(st, int(ctas)))
+
+
 def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):
     ld = _rows(genes_out, "genes_out")[1] if genes_out is not None else 0
     _check(lib().qpm_get_population(st, int(inst), _ptr(genes_out), ld, _ptr(fit_out),
@@ -355,6 +362,9 @@ class State:
 
     def run(self, generations, mode=RUN_GRAPH, stream=None):
         qpm_run(self.h, generations, mode, stream)
+
+    def set_batch_cluster(self, ctas):
+        qpm_set_batch_cluster(self.h, ctas)
 
     @property
     def generation(self):

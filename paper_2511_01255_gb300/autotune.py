@@ -1,11 +1,16 @@
-"""Autotuner for the threads-per-individual (team width) of a workload.
+"""Autotuner for the launch shapes of a workload.
 
-The library's automatic choice (qpm_params.team = 0) is a fixed rule: the
-smallest power of two in [32, 256] giving at most 4 domains per thread.  This
-module measures the candidates instead, through the C ABI, for a given problem
-size, population and execution form, and caches the fastest in a JSON file
-keyed by (device name, N bucket, NP, compensated, form).  Pass the result as
-qpm_params.team.
+Team width: the library's automatic choice (qpm_params.team = 0) is a fixed
+rule, the smallest power of two in [32, 256] giving at most 4 domains per
+thread.  autotune_team measures the candidates instead, through the C ABI, for a
+given problem size, population and execution form, and caches the fastest in a
+JSON file keyed by (device name, N bucket, NP, compensated, form).  Pass the
+result as qpm_params.team.
+
+Batched form: autotune_batch_cluster measures the CTAs per thread-block cluster
+(qpm_set_batch_cluster) on the state itself, a few generations per candidate from
+the initial population, and caches the fastest by (device, number of instances,
+work buckets of the largest and of the mean instance).
 """
 import json
 import os
@@ -97,3 +102,59 @@ def autotune_team(N, kappa1, kappa2, NP, compensated=0, form=None, gens=40,
     if use_cache:
         save_cache(cache, path)
     return best
+
+
+BATCH_CLUSTERS = (1, 2, 4)
+
+
+def _batch_key(device, sizes):
+    """sizes: N * NP of every instance; the makespan depends on the largest one."""
+    mean = sum(sizes) / len(sizes)
+    return f"{device}|batch|n{len(sizes)}|max{n_bucket(max(sizes))}|mean{n_bucket(int(mean))}"
+
+
+def measure_batch_cluster(state, ctas, gens=20):
+    """Seconds per generation of the batched form of `state` with clusters of `ctas`
+    CTAs, measured from the initial population (the state is re-initialised first)."""
+    import torch
+
+    import paper_2511_01255_gb300 as q
+    state.set_batch_cluster(ctas)
+    state.init()
+    state.run(1, q.RUN_BATCHED)  # capture and warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    state.run(gens, q.RUN_BATCHED)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / gens
+
+
+def autotune_batch_cluster(state, gens=20, candidates=BATCH_CLUSTERS, use_cache=True, path=CACHE,
+                           measure=None):
+    """Set and return the fastest cluster size of the batched form for `state` (cached).
+    Call it right after state.init(): the candidates run from the initial population
+    and the state is initialised again at the end (init is deterministic, so the
+    population is the same as before the call)."""
+    import torch
+    device = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    sizes = [state.problems[k][0] * state.params[k].NP for k in range(len(state.problems))]
+    key = _batch_key(device, sizes)
+    cache = load_cache(path) if use_cache else {}
+    if key in cache:
+        best = cache[key]["ctas"]
+    else:
+        measure = measure or measure_batch_cluster
+        timings = {c: measure(state, c, gens) for c in candidates}
+        best = choose(timings)
+        cache[key] = {"ctas": best, "s_per_generation": {str(k): v for k, v in timings.items()},
+                      "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+        if use_cache:
+            save_cache(cache, path)
+    state.set_batch_cluster(best)
+    if hasattr(state, "init"):
+        state.init()
+    return best
+

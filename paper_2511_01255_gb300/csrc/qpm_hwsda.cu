@@ -23,6 +23,8 @@
 
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -570,17 +572,44 @@ static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end,
 }
 
 // ------------------------------------------------------------ batched form
-// Many independent instances in one launch.  Each CTA takes whole instances from
-// a queue (largest first) and runs them for the requested generations by itself:
-// every warp is the team of one individual (instances use T = 32), and the two
-// dependencies of a generation are CTA barriers.  No CTA ever waits for another.
+// Many independent instances in one launch.  Each thread-block cluster (1, 2, 4
+// or 8 CTAs on as many SMs) takes whole instances from a queue (largest first)
+// and runs them for the requested generations: every warp is the team of one
+// individual (instances use T = 32), the individuals of an instance are dealt to
+// the warps of all CTAs of the cluster, and the two dependencies of a generation
+// are cluster barriers (release/acquire at cluster scope, which also orders the
+// population writes in global memory).  Each CTA's leader candidates are read by
+// the others through distributed shared memory.  No cluster waits for another,
+// so no co-residency beyond the cluster's own is needed.  Splitting an instance
+// over a cluster keeps the largest instance from setting the batch's makespan.
 static constexpr int BATCH_WARPS = 16;
 
+__device__ __forceinline__ unsigned cluster_rank() {
+  return cooperative_groups::this_cluster().block_rank();
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  return cooperative_groups::this_cluster().num_blocks();
+}
+// every thread of every CTA of the cluster (CL) or of the CTA; writes before it
+// (shared and global) are visible to every thread of the cluster after it
+template <bool CL>
+__device__ __forceinline__ void cluster_sync_all() {
+  if (CL) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
+}
+// the word at `p` in the shared memory of CTA `rank` of this cluster
+__device__ __forceinline__ unsigned long long ld_dsmem_u64(unsigned long long *p, unsigned rank) {
+  return *cooperative_groups::this_cluster().map_shared_rank(p, rank);
+}
+
 // one instance, generations [*gen, min(*gen + gens, G)), by the whole CTA
-template <bool COMP, bool TS>
+// CL: the instance is shared by the CTAs of a cluster (more than one)
+template <bool COMP, bool TS, bool CL>
 __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned long long *wk,
-                               int32_t *lead_sh) {
+                               unsigned long long *ck, int32_t *lead_sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned crank = CL ? cluster_rank() : 0u, csize = CL ? cluster_size() : 1u;
+  const int gw = (int)crank * nw + warp, gstride = (int)csize * nw;  // warp in the cluster
   if (TS) {
     for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
   }
@@ -592,66 +621,90 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
   for (; g < g_end; ++g) {
     const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
     int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
-    unsigned long long k0 = 0, k1 = 0, k2 = 0;
-    for (int i = warp; i < I.NP; i += nw) {
+    // each warp's running top three lives in shared memory (lane 0), which keeps
+    // six registers free across the DE loop
+    if (lane == 0) wk[3 * warp] = wk[3 * warp + 1] = wk[3 * warp + 2] = 0ull;
+    for (int i = gw; i < I.NP; i += gstride) {
       const unsigned long long key =
           de_individual<COMP, false, TS, false, true>(
               I, K, tbl, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out,
               nullptr);
-      if (lane == 0) top3_insert(k0, k1, k2, key);
-    }
-    if (lane == 0) {
-      wk[3 * warp] = k0;
-      wk[3 * warp + 1] = k1;
-      wk[3 * warp + 2] = k2;
+      if (lane == 0) {
+        unsigned long long a = wk[3 * warp], b = wk[3 * warp + 1], c = wk[3 * warp + 2];
+        top3_insert(a, b, c, key);
+        wk[3 * warp] = a;
+        wk[3 * warp + 1] = b;
+        wk[3 * warp + 2] = c;
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // Step 3: leaders of this instance
+    unsigned long long k0 = wk[0], k1 = wk[1], k2 = wk[2];
+    if (threadIdx.x == 0) {  // this CTA's candidates
       for (int w = 1; w < nw; ++w) {
         top3_insert(k0, k1, k2, wk[3 * w]);
         top3_insert(k0, k1, k2, wk[3 * w + 1]);
         top3_insert(k0, k1, k2, wk[3 * w + 2]);
       }
+      ck[0] = k0;
+      ck[1] = k1;
+      ck[2] = k2;
+    }
+    // every DE survivor of the instance and every CTA's candidates are now visible
+    cluster_sync_all<CL>();
+    if (threadIdx.x == 0) {  // Step 3: leaders of this instance (the same in every CTA)
+      for (unsigned r = 0; CL && r < csize; ++r) {
+        if (r == crank) continue;
+        top3_insert(k0, k1, k2, ld_dsmem_u64(ck, r));
+        top3_insert(k0, k1, k2, ld_dsmem_u64(ck + 1, r));
+        top3_insert(k0, k1, k2, ld_dsmem_u64(ck + 2, r));
+      }
       lead_sh[0] = key_index(k0);
       lead_sh[1] = key_index(k1);
       lead_sh[2] = key_index(k2);
-      I.lead[0] = lead_sh[0];
-      I.lead[1] = lead_sh[1];
-      I.lead[2] = lead_sh[2];
+      if (crank == 0) {
+        I.lead[0] = lead_sh[0];
+        I.lead[1] = lead_sh[1];
+        I.lead[2] = lead_sh[2];
+      }
     }
     __syncthreads();
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
-    for (int i = warp; i < I.NP; i += nw) {
+    for (int i = gw; i < I.NP; i += gstride) {
       if (i == la || i == lb || i == ld) continue;
       gwo_individual<COMP, false, TS, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld, nullptr);
     }
-    if (I.trace && threadIdx.x < 3) {
+    if (I.trace && crank == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
       I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
     }
-    __syncthreads();
+    // the next DE reads any individual, and ck is rewritten only after every CTA read it
+    cluster_sync_all<CL>();
   }
-  if (threadIdx.x == 0) *I.gen = g_end;
-  __syncthreads();
+  if (crank == 0 && threadIdx.x == 0) *I.gen = g_end;
 }
 
-template <bool TS>
+template <bool TS, bool CL>
 static __global__ void __launch_bounds__(BATCH_WARPS * 32, 1)
     k_batch(const InstDev *__restrict__ insts, const int32_t *__restrict__ order, int n_inst,
             unsigned *queue, int gens) {
   extern __shared__ float4 dyn[];
   __shared__ unsigned long long wk[3 * BATCH_WARPS];
+  __shared__ unsigned long long ck[3];  // this CTA's leader candidates, read by the cluster
   __shared__ int32_t lead_sh[3];
-  __shared__ int job_sh;
+  __shared__ unsigned long long job_sh;
   for (;;) {
-    if (threadIdx.x == 0) job_sh = (int)atomicAdd(queue, 1u);
-    __syncthreads();
-    const int job = job_sh;
-    __syncthreads();
+    int job;
+    {
+      const unsigned crank = CL ? cluster_rank() : 0u;
+      if (crank == 0 && threadIdx.x == 0) job_sh = (unsigned long long)atomicAdd(queue, 1u);
+      cluster_sync_all<CL>();
+      job = (int)(crank == 0 ? job_sh : ld_dsmem_u64(&job_sh, 0));
+      cluster_sync_all<CL>();  // every CTA has the job before rank 0 takes the next one
+    }
     if (job >= n_inst) break;
     const InstDev I = insts[order[job]];
-    if (I.compensated) batch_instance<true, TS>(I, gens, dyn, wk, lead_sh);
-    else batch_instance<false, TS>(I, gens, dyn, wk, lead_sh);
+    if (I.compensated) batch_instance<true, TS, CL>(I, gens, dyn, wk, ck, lead_sh);
+    else batch_instance<false, TS, CL>(I, gens, dyn, wk, ck, lead_sh);
   }
 }
 
@@ -894,6 +947,7 @@ struct qpm_state {
   int32_t *d_order = nullptr;  // instances by decreasing work
   size_t batch_smem = 0;       // 0: table read from global memory
   int grid_batch = 0;
+  int batch_cluster = 1;       // CTAs per thread-block cluster in the batched form
   cudaGraphExec_t gexec_b = nullptr;
   int graph_b_n = -1;
   void *polish = nullptr;  // leader-polish scratch (allocated on first use)
@@ -950,6 +1004,33 @@ static Variant variant_of(const InstDev &I) {
 // for one instance stay valid after another instance is set up
 static size_t persist_smem_cap(bool ts) {
   return smem_bytes(256) + (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
+}
+
+static const void *batch_kernel(bool ts, bool cl) {
+  if (ts) return cl ? (const void *)k_batch<true, true> : (const void *)k_batch<true, false>;
+  return cl ? (const void *)k_batch<false, true> : (const void *)k_batch<false, false>;
+}
+
+// co-resident CTAs of the batched kernel for clusters of `cs` CTAs (a multiple of cs)
+static qpm_status batch_grid(const qpm_state *st, int cs, int *grid) {
+  const void *kb = batch_kernel(st->batch_smem != 0, cs > 1);
+  QPM_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->batch_smem));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(cs * sm_count()));
+  cfg.blockDim = dim3(BATCH_WARPS * 32);
+  cfg.dynamicSmemBytes = st->batch_smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  QPM_CUDA(cudaOccupancyMaxActiveClusters(&clusters, kb, &cfg));
+  if (clusters < 1) return fail(QPM_ERR_UNSUPPORTED, "batched form: clusters of this size do not fit");
+  *grid = clusters * cs;
+  return QPM_OK;
 }
 
 static qpm_status occupancy(const InstDev &I, int *plain, int *persist) {
@@ -1131,13 +1212,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     for (int k = 0; k < n_inst; ++k) maxpad = std::max(maxpad, st->h[k].Npad);
     st->batch_smem = ((size_t)maxpad * sizeof(float4) <= BATCH_TS_MAX_BYTES)
                          ? (size_t)maxpad * sizeof(float4) : 0;
-    const void *kb = st->batch_smem ? (const void *)k_batch<true> : (const void *)k_batch<false>;
-    e = cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->batch_smem);
-    int occ = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb, BATCH_WARPS * 32, st->batch_smem);
-    if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "batch set-up"); }
-    st->grid_batch = std::max(1, occ) * nsm;
+    st->grid_batch = 0;  // set on the first batched run (or by qpm_set_batch_cluster)
   }
   e = cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaStreamCreate"); }
@@ -1243,6 +1318,10 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     for (int k = 0; k < st->n; ++k)
       if (st->h[k].T != 32)
         return fail(QPM_ERR_UNSUPPORTED, "batched form needs 32 threads per individual (team 32)");
+    if (st->grid_batch == 0) {
+      qpm_status r = batch_grid(st, st->batch_cluster, &st->grid_batch);
+      if (r != QPM_OK) return r;
+    }
     if (st->graph_b_n != generations || !st->gexec_b) {
       if (st->gexec_b) {
         cudaGraphExecDestroy(st->gexec_b);
@@ -1254,9 +1333,20 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
         int n = st->n, gens = generations;
         unsigned *queue = st->bar + 3;
         void *args[] = {&st->d_insts, &st->d_order, &n, &queue, &gens};
-        const void *kb = st->batch_smem ? (const void *)k_batch<true> : (const void *)k_batch<false>;
-        e = cudaLaunchKernel(kb, dim3(st->grid_batch), dim3(BATCH_WARPS * 32), args, st->batch_smem,
-                             st->cap_stream);
+        const void *kb = batch_kernel(st->batch_smem != 0, st->batch_cluster > 1);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)st->batch_cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)st->grid_batch);
+        cfg.blockDim = dim3(BATCH_WARPS * 32);
+        cfg.dynamicSmemBytes = st->batch_smem;
+        cfg.stream = st->cap_stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, kb, args);
       }
       cudaGraph_t graph = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(st->cap_stream, &graph);
@@ -1274,6 +1364,27 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     return fail(QPM_ERR_ARG, "qpm_run: unknown mode");
   }
   st->g += generations;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_set_batch_cluster(qpm_state *st, int32_t ctas) {
+  if (!st) return fail(QPM_ERR_ARG, "qpm_set_batch_cluster: NULL state");
+  if (ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8)
+    return fail(QPM_ERR_ARG, "qpm_set_batch_cluster: ctas must be 1, 2, 4 or 8");
+  int dev = -1;
+  QPM_CUDA(cudaGetDevice(&dev));
+  if (dev != st->dev) return fail(QPM_ERR_STATE, "state belongs to another device");
+  int grid = 0;
+  qpm_status r = batch_grid(st, ctas, &grid);
+  if (r != QPM_OK) return r;
+  if (st->gexec_b) {  // the captured launch has the old shape
+    QPM_CUDA(cudaDeviceSynchronize());
+    cudaGraphExecDestroy(st->gexec_b);
+    st->gexec_b = nullptr;
+    st->graph_b_n = -1;
+  }
+  st->batch_cluster = ctas;
+  st->grid_batch = grid;
   return QPM_OK;
 }
 

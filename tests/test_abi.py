@@ -57,6 +57,7 @@ def test_argument_errors_without_device(qlib):
     assert qlib.qpm_create(ctypes.byref(p), ctypes.byref(bad[0]), 1, ctypes.byref(st)) == 1
     assert b"NP < 4" in qlib.qpm_last_error()
     assert qlib.qpm_step(None, None) == 1
+    assert qlib.qpm_set_batch_cluster(None, 2) == 1
     assert qlib.qpm_destroy(None) == 0
 
 

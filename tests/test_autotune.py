@@ -38,3 +38,64 @@ def test_autotune_on_gpu(tmp_path):
     t = A.autotune_team(1000, 0.9, 4.0, 64, compensated=1, form=q.RUN_PERSISTENT, gens=10,
                         path=str(tmp_path / "c.json"))
     assert t in (32, 64, 128, 256)
+
+
+def test_batch_cluster_choice_and_cache(tmp_path, monkeypatch):
+    from paper_2511_01255_gb300 import autotune as A
+    import types
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        is_available=lambda: False, get_device_name=lambda: "cpu"))
+    monkeypatch.setitem(__import__("sys").modules, "torch", fake_torch)
+
+    class FakeState:
+        def __init__(self):
+            self.problems = [(1000, 1.0, 2.0), (8000, 1.0, 2.0)]
+            self.params = [types.SimpleNamespace(NP=64), types.SimpleNamespace(NP=512)]
+            self.ctas = None
+
+        def set_batch_cluster(self, c):
+            self.ctas = c
+
+    calls = []
+
+    def fake(state, ctas, gens):
+        calls.append(ctas)
+        return {1: 5.0, 2: 4.5, 4: 4.7}[ctas]
+
+    path = str(tmp_path / "cache.json")
+    st = FakeState()
+    assert A.autotune_batch_cluster(st, measure=fake, path=path) == 2 and st.ctas == 2
+    assert sorted(calls) == [1, 2, 4]
+    calls.clear()
+    st2 = FakeState()
+    assert A.autotune_batch_cluster(st2, measure=fake, path=path) == 2 and st2.ctas == 2
+    assert calls == []  # served from the cache
+    # another batch shape is another entry
+    st3 = FakeState()
+    st3.params[1].NP = 64
+    A.autotune_batch_cluster(st3, measure=fake, path=path)
+    assert sorted(calls) == [1, 2, 4]
+
+
+@pytest.mark.gpu
+def test_autotune_batch_cluster_on_gpu(tmp_path):
+    """A real measurement on a small batch picks a valid size and leaves the state
+    initialised with the same population as before."""
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01255_gb300 as q
+    from paper_2511_01255_gb300 import autotune as A
+    probs = [(300 + 100 * k, 0.9, 4.0) for k in range(6)]
+    prms = [q.Params(16 + 8 * k, 200, 0.5, 0.9, 3, 0, 0) for k in range(6)]
+    with q.State(probs, prms) as st:
+        st.init()
+        before = [st.population(k)[0].cpu().numpy() for k in range(6)]
+        c = A.autotune_batch_cluster(st, gens=5, path=str(tmp_path / "c.json"))
+        assert c in (1, 2, 4)
+        assert st.generation == 0
+        after = [st.population(k)[0].cpu().numpy() for k in range(6)]
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        st.run(2, q.RUN_BATCHED)  # carries on with the chosen size

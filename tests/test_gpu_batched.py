@@ -3,7 +3,8 @@
 Each instance k draws its random numbers with instance index k in the Philox
 counter, so the oracle replays instance k with inst = k.  Bit-exact populations
 in lockstep; fitness within tolerance; the batched launch equals the
-launch-by-launch form on the same state.
+launch-by-launch form on the same state, for every thread-block cluster size
+(an instance run by 1, 2 or 4 CTAs gives the same bits).
 """
 import math
 
@@ -49,10 +50,12 @@ def build(q, G, seed=7):
     return st, traces
 
 
-def test_batched_lockstep_every_instance(q, orc):
+@pytest.mark.parametrize("ctas", [1, 2, 4])
+def test_batched_lockstep_every_instance(q, orc, ctas):
     import torch
     G = 9
     st, traces = build(q, G)
+    st.set_batch_cluster(ctas)
     st.init()
     st.run(4, q.RUN_BATCHED)
     st.run(G - 4, q.RUN_BATCHED)
@@ -72,8 +75,10 @@ def test_batched_equals_launches(q):
     import torch
     G = 6
     pops = []
-    for mode in (q.RUN_BATCHED, q.RUN_LAUNCHES, q.RUN_PERSISTENT):
+    for mode, ctas in ((q.RUN_BATCHED, 1), (q.RUN_LAUNCHES, 1), (q.RUN_PERSISTENT, 1),
+                       (q.RUN_BATCHED, 2), (q.RUN_BATCHED, 8)):
         st, traces = build(q, G, seed=11)
+        st.set_batch_cluster(ctas)
         st.init()
         st.run(G, mode)
         torch.cuda.synchronize()
@@ -93,6 +98,7 @@ def test_batched_full_size_sampled(q, orc):
     probs = [(c["N"], c["kappa1"], c["kappa2"]) for c in inst]
     prms = [q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, c["compensated"]) for c in inst]
     st = q.State(probs, prms)
+    st.set_batch_cluster(2)
     sample = [0, 137, 511]
     traces = {}
     for k in sample:
