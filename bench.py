@@ -124,6 +124,21 @@ def algorithmic_lane_ops_per_gene_gen(compensated):
     return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
 
 
+def int_lane_ops_per_gene_gen():
+    """Integer part of the algorithmic count: the Philox rounds (1.75 calls x 80) and
+    the shift and conversion of each of the 7 uniforms (2 each)."""
+    return 1.75 * 80 + 7 * 2
+
+
+def mix_ceiling_gene_gens(compensated, issue):
+    """Gene-generations/s the op mix allows on this GPU: integer ops at the measured
+    three-input-xor rate, all ops at the measured FFMA issue rate (T lane-ops/s)."""
+    n_int = int_lane_ops_per_gene_gen()
+    n_all = algorithmic_lane_ops_per_gene_gen(compensated)
+    t = max(n_int / (issue["lop3"] * 1e12), n_all / (issue["ffma"] * 1e12))
+    return 1.0 / t
+
+
 def max_over_ranks(seconds, world, device=None):
     """Slowest rank's step time (the job's time); identity for one process."""
     if world <= 1:
@@ -174,6 +189,9 @@ def run_gpu(args):
     pk, pk_src = peaks()
     nsm = torch.cuda.get_device_properties(lrank).multi_processor_count
     peak_alu = nsm * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T lane-ops/s
+    # measured issue rates of this GPU (the library's microbenchmark), T lane-ops/s
+    issue = {name: q.qpm_measure_issue_peak(k) / 1e12
+             for k, name in enumerate(("ffma", "philox_mul_xor", "lop3"))}
     peak_hbm = pk.get("hbm_gbs", 6800.0)
     c = W.PAPER_SCALE
     N, NP, G = c["N"], c["NP"], c["G"]
@@ -272,7 +290,8 @@ def run_gpu(args):
         "speedup_vs_per_instance_persistent": (t_inst3 / 3 * Gb) / t_batched,
         "roofline": {"bound": "alu", "achieved": algorithmic_lane_ops_per_gene_gen(0) * gg_b / t_batched / 1e12,
                      "peak": peak_alu, "unit": "T lane-ops/s",
-                     "frac": algorithmic_lane_ops_per_gene_gen(0) * gg_b / t_batched / 1e12 / peak_alu},
+                     "frac": algorithmic_lane_ops_per_gene_gen(0) * gg_b / t_batched / 1e12 / peak_alu,
+                     "frac_of_mix_ceiling": gg_b / t_batched / mix_ceiling_gene_gens(0, issue)},
     }
 
     # --------------------------------------- precision: N = 1e5, NP = 1024, G = 500
@@ -290,7 +309,8 @@ def run_gpu(args):
         prec["compensated" if comp else "plain"] = {
             "s_per_run": tp, "gene_gens_per_s": ggp / tp,
             "domain_evals_per_s": (2 * cp["NP"] - 3) * cp["N"] * cp["G"] / tp,
-            "alu_frac": algorithmic_lane_ops_per_gene_gen(comp) * ggp / tp / 1e12 / peak_alu}
+            "alu_frac": algorithmic_lane_ops_per_gene_gen(comp) * ggp / tp / 1e12 / peak_alu,
+            "frac_of_mix_ceiling": ggp / tp / mix_ceiling_gene_gens(comp, issue)}
     prec["workload"] = cp["name"]
 
     # ---------------------------------- adjoint: B = 4096 rows of N = 4096, fwd + bwd
@@ -392,6 +412,9 @@ def run_gpu(args):
                      "peak_note": f"{nsm} SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
                                   f"(issue limit, derived; clocks {pk_src})",
                      "frac_at_median_clock": achieved / (nsm * 128 * sm_mhz * 1e6 / 1e12),
+                     "measured_issue_peaks": {k: v for k, v in issue.items()},
+                     "frac_of_measured_ffma": achieved / issue["ffma"],
+                     "frac_of_mix_ceiling": gene_gens / kdur / mix_ceiling_gene_gens(c["compensated"], issue),
                      "ops_per_gene_gen": ops_gene_gen, "launch_ms": kdur * 1e3,
                      "us_per_generation": kdur / G * 1e6},
         "batched": batched,

@@ -15,7 +15,7 @@ from . import build_lib
 
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc", "qpm_eval_shg", "qpm_eval_multi",
-    "qpm_release_caches", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
+    "qpm_release_caches", "qpm_measure_issue_peak", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_set_batch_cluster",
@@ -70,6 +70,7 @@ def lib(build=True):
                                 ctypes.c_size_t, _P], ctypes.c_int),
             "qpm_eval_multi_scratch_bytes": ([i32, i32, i32], ctypes.c_size_t),
             "qpm_release_caches": ([], ctypes.c_int),
+            "qpm_measure_issue_peak": ([i32, _P, _P], ctypes.c_int),
             "qpm_relaxed_saved_floats": ([i32], i64),
             "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
             "qpm_deff_relaxed_bwd": ([_P, _P, i64, i32, _P, _P, _P, _P, i64, _P], ctypes.c_int),
@@ -150,6 +151,13 @@ def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, s
     NP, ld = _rows(genes, "genes")
     _check(lib().qpm_eval_noalloc(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),
                                   int(compensated), _stream(stream)))
+
+
+def qpm_measure_issue_peak(kind, stream=None):
+    """Measured lane-ops/s of the current device: 0 FFMA, 1 Philox multiply+xor, 2 xor."""
+    v = ctypes.c_double()
+    _check(lib().qpm_measure_issue_peak(int(kind), ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def qpm_relaxed_saved_floats(N):

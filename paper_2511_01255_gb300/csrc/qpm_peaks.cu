@@ -1,0 +1,111 @@
+// qpm_peaks.cu -- issue-rate microbenchmarks for the ALU roofline.
+//
+// The generation step is bound by FP32 and integer issue (fitness monoid steps,
+// Philox rounds), for which no vendor figure is measured on this machine.  Each
+// kernel runs PK_CHAINS independent dependency chains of one instruction kind per
+// thread, long enough that launch and tail effects vanish, and writes its result
+// only under a condition the chains never meet, so nothing is optimised away.
+// Lane-ops/s = threads x iterations x chains x ops per chain step / elapsed time,
+// with the op counts of the roofline's own convention: a 32 x 32 -> 64 multiply
+// counts 2, a three-input logic op 1, an FFMA 1.
+#include <cuda_runtime.h>
+
+#include "qpm_internal.h"
+
+namespace qpm {
+
+static constexpr int PK_CHAINS = 8;
+static constexpr int PK_ITERS = 4096;
+static constexpr int PK_THREADS = 512;
+
+// x <- x * a + b in FP32 (one FFMA per chain and iteration)
+static __global__ void __launch_bounds__(PK_THREADS) k_peak_ffma(float a, float b, float *sink) {
+  float x[PK_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) x[c] = (float)(threadIdx.x + c);
+  for (int it = 0; it < PK_ITERS; ++it) {
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; ++c) x[c] = fmaf(x[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) s += x[c];
+  if (s == -1.2345f) sink[blockIdx.x] = s;
+}
+
+// x <- hi(x * m) ^ lo(x * m): the 32 x 32 -> 64 multiply of a Philox round
+// (one wide multiply and one xor per chain and iteration)
+static __global__ void __launch_bounds__(PK_THREADS) k_peak_imul(uint32_t m, uint32_t *sink) {
+  uint32_t x[PK_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) x[c] = threadIdx.x * 2654435761u + c;
+  for (int it = 0; it < PK_ITERS; ++it) {
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; ++c) {
+      const uint64_t p = (uint64_t)x[c] * m;
+      x[c] = (uint32_t)(p >> 32) ^ (uint32_t)p;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) s ^= x[c];
+  if (s == 0x9E3779B9u && m == 0u) sink[blockIdx.x] = s;
+}
+
+// x <- x ^ y ^ k: a three-input logic op (one LOP3 per chain and iteration)
+static __global__ void __launch_bounds__(PK_THREADS) k_peak_lop3(uint32_t k, uint32_t *sink) {
+  uint32_t x[PK_CHAINS], y[PK_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) {
+    x[c] = threadIdx.x + c;
+    y[c] = (threadIdx.x << 3) ^ (uint32_t)c * 0x85EBCA6Bu;
+  }
+  for (int it = 0; it < PK_ITERS; ++it) {
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; ++c) {
+      x[c] = x[c] ^ y[c] ^ (k + (uint32_t)it);
+      y[c] = y[c] ^ x[c] ^ k;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int c = 0; c < PK_CHAINS; ++c) s ^= x[c] ^ y[c];
+  if (s == 0x12345678u && k == 0u) sink[blockIdx.x] = s;
+}
+
+}  // namespace qpm
+
+using namespace qpm;
+
+extern "C" qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s,
+                                             qpm_stream_t stream) {
+  if (!lane_ops_per_s || kind < 0 || kind > 2)
+    return fail(QPM_ERR_ARG, "qpm_measure_issue_peak: kind must be 0, 1 or 2");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = sm_count() * 4;  // 2048 threads per SM: every scheduler full
+  void *sink = nullptr;
+  QPM_CUDA(cudaMalloc(&sink, sizeof(uint32_t) * blocks));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.f;
+  // ops per chain step: FFMA 1; wide multiply (2) + xor (1); two three-input xors
+  const double per_step = kind == 0 ? 1.0 : (kind == 1 ? 3.0 : 2.0);
+  const double per_thread = (double)PK_ITERS * PK_CHAINS * per_step;
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    e = cudaEventRecord(e0, s);
+    if (kind == 0) k_peak_ffma<<<blocks, PK_THREADS, 0, s>>>(1.000001f, 1e-7f, (float *)sink);
+    else if (kind == 1) k_peak_imul<<<blocks, PK_THREADS, 0, s>>>(0xD2511F53u, (uint32_t *)sink);
+    else k_peak_lop3<<<blocks, PK_THREADS, 0, s>>>(0xCD9E8D57u, (uint32_t *)sink);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "qpm_measure_issue_peak");
+  *lane_ops_per_s = (double)blocks * PK_THREADS * per_thread / (ms * 1e-3);
+  return QPM_OK;
+}

@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--team", type=int, default=0, help="threads per individual (0 = automatic)")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batch workload")
     ap.add_argument("--packed", type=int, default=0, help="eval workload: packed sign words")
+    ap.add_argument("--cluster", type=int, default=1, help="batched form: CTAs per cluster")
     a = ap.parse_args()
     q.lib()
     if a.workload == "relaxed":
@@ -91,7 +92,8 @@ def main():
         st = q.State([(c["N"], c["kappa1"], c["kappa2"]) for c in inst],
                       [q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
                        for c in inst])
-        c = {"name": "batch512_g1000"}
+        st.set_batch_cluster(a.cluster)
+        c = {"name": f"batch{a.instances}_g1000_cluster{a.cluster}"}
     else:
         c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
         comp = c["compensated"] if a.comp < 0 else a.comp

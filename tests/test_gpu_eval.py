@@ -149,3 +149,16 @@ def test_multi_wavelength_objective_against_oracle(q, orc, K):
         q.qpm_eval(N, kap[0][0], kap[0][1], torch.from_numpy(X).cuda(), D1)
         torch.cuda.synchronize()
         assert np.array_equal(D1.cpu().numpy(), Dg[:, 0])
+
+
+def test_issue_peak_microbenchmark(q):
+    """The measured issue rates are positive and the FFMA rate is within reach of
+    the derived peak (SMs x 128 lanes x clock; clocks may run below the maximum)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = nsm * 128 * 2.07e9
+    f = q.qpm_measure_issue_peak(0)
+    assert 0.3 * derived < f < 1.1 * derived
+    assert q.qpm_measure_issue_peak(1) > 0 and q.qpm_measure_issue_peak(2) > 0
+    with pytest.raises(q.QpmError):
+        q.qpm_measure_issue_peak(3)
