@@ -202,15 +202,16 @@ qpm_status get_scratch(cudaStream_t stream, size_t bytes, void **ptr) {
 }
 }  // namespace
 
-// split for the row sweep: about 20 resident warps per SM in total, segments a
-// multiple of ER_LQ domains and at most ER_LMAX
-EvalShape eval_rows_shape(int NP, int N) {
+// split for the row sweep: about `warps_per_sm` warps per SM in total (20 suit
+// float genes; the packed sweep holds fewer registers and runs best near 32),
+// segments a multiple of ER_LQ domains and at most ER_LMAX
+EvalShape eval_rows_shape(int NP, int N, int warps_per_sm) {
   EvalShape sh;
   sh.NP = NP;
   sh.N = N;
   sh.groups = (NP + 31) / 32;
   sh.NPpad = sh.groups * 32;
-  const int target = sm_count() * 20;
+  const int target = sm_count() * warps_per_sm;
   const int S0 = std::max(1, (target + sh.groups - 1) / sh.groups);
   int L = (N + S0 - 1) / S0;
   L = (L + ER_LQ - 1) / ER_LQ * ER_LQ;
@@ -248,7 +249,7 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   qpm_status st = get_table(prob, stream, &table, &konst);
   if (st != QPM_OK) return st;
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, prob->N);
+  const EvalShape sh = eval_rows_shape(NP, prob->N, kind == 2 ? 32 : 20);
   void *scratch;
   st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
   if (st != QPM_OK) return st;
@@ -314,7 +315,7 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (prob->N > (1 << 28) || NP > (1 << 26))
     return fail(QPM_ERR_ARG, "qpm_eval_noalloc: problem exceeds the fixed scratch (8 MiB)");
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_noalloc: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, prob->N);
+  const EvalShape sh = eval_rows_shape(NP, prob->N, 20);
   const int32_t Npad = (prob->N + 3) & ~3;
   const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
   const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));

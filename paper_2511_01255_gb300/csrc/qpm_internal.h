@@ -44,8 +44,9 @@ struct EvalShape {
   int groups;  // ceil(NP / 32)
   int NPpad;   // groups * 32
 };
-// split of the row sweep (qpm_rows.cuh): segments a multiple of 128 domains
-EvalShape eval_rows_shape(int NP, int N);
+// split of the row sweep (qpm_rows.cuh): segments a multiple of 128 domains,
+// about warps_per_sm warps of work per SM
+EvalShape eval_rows_shape(int NP, int N, int warps_per_sm);
 
 // current device's SM count (cached per device)
 int sm_count();

@@ -219,7 +219,7 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     if (st != QPM_OK) return st;
   }
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, N);
+  const EvalShape sh = eval_rows_shape(NP, N, 20);
   const size_t need = sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
   if (!scratch || scratch_bytes < need)
     return fail(QPM_ERR_ARG, "qpm_eval_multi: scratch smaller than qpm_eval_multi_scratch_bytes()");
@@ -246,6 +246,6 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
 
 extern "C" size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP) {
   if (K < 1 || N < 1 || NP < 1) return 0;
-  const EvalShape sh = eval_rows_shape(NP, N);
+  const EvalShape sh = eval_rows_shape(NP, N, 20);
   return sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
 }
