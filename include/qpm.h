@@ -67,7 +67,10 @@ typedef struct {
   uint64_t seed;       /* Philox4x32-10 key */
   int32_t gwo_combine; /* 0: (X1+X2+X3)/3; 1: |X_k|-weighted, per dimension */
   int32_t compensated; /* 0: plain FP32 scan; 1: Kahan-compensated FP32 scan */
-  int32_t team;        /* threads per individual: 0 = automatic, else 32, 64, 128 or 256 */
+  int32_t team;        /* threads per individual: 0 = automatic (the smallest power of two in
+                          [32, 256] with at most 4 domains per thread; 512 for a single
+                          long-row instance when one 512-thread CTA per SM leaves fewer CTA
+                          slots idle), else 32, 64, 128, 256 or 512 */
   int32_t f_schedule;  /* 0: F constant; 1: decaying F of Sec. 3.1.1,
                           F_g = F (cos(pi g / 2G) + 1) / 2 (1 - 0.2 (g / G)^2),
                           evaluated in FP64 and rounded to FP32 */

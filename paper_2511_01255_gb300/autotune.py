@@ -17,7 +17,7 @@ import os
 import time
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
-CANDIDATES = (32, 64, 128, 256)
+CANDIDATES = (32, 64, 128, 256, 512)
 
 
 def n_bucket(N):

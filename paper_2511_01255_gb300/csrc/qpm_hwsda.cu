@@ -506,8 +506,10 @@ __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_
 // (the leaders need every DE survivor) and after GWO (the next donors are any
 // individuals).  With one individual per CTA and 4 domains per thread, the GWO
 // random words are drawn between the arrival at the first barrier and the wait.
-template <bool COMP, bool TS, bool DUAL>
-static __global__ void __launch_bounds__(256, 2) k_persist(InstDev I, int g_end, Barrier bar) {
+// MAXT: the largest team the variant runs (256: two CTAs per SM; 512: one)
+template <bool COMP, bool TS, bool DUAL, int MAXT = 256>
+static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
+    k_persist(InstDev I, int g_end, Barrier bar) {
   extern __shared__ float4 dyn[];
   __shared__ int32_t lead_sh[3];
   Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
@@ -983,11 +985,14 @@ static Variant variant2(const InstDev &I) {
   v.de = (const void *)k_de<COMP, DUAL>;
   v.gwo = (const void *)k_gwo<COMP, DUAL>;
   v.smem = smem_bytes(I.T);
+  const bool wide = I.T > 256;
   if (I.Npad <= TS_MAX_NPAD) {
-    v.persist = (const void *)k_persist<COMP, true, DUAL>;
+    v.persist = wide ? (const void *)k_persist<COMP, true, DUAL, 512>
+                     : (const void *)k_persist<COMP, true, DUAL>;
     v.persist_smem = smem_bytes(I.T) + sizeof(float4) * (size_t)I.Npad;
   } else {
-    v.persist = (const void *)k_persist<COMP, false, DUAL>;
+    v.persist = wide ? (const void *)k_persist<COMP, false, DUAL, 512>
+                     : (const void *)k_persist<COMP, false, DUAL>;
     v.persist_smem = smem_bytes(I.T);
   }
   return v;
@@ -1003,7 +1008,7 @@ static Variant variant_of(const InstDev &I) {
 // instance (the largest any instance can need), so occupancy figures computed
 // for one instance stay valid after another instance is set up
 static size_t persist_smem_cap(bool ts) {
-  return smem_bytes(256) + (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
+  return smem_bytes(512) + (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
 }
 
 static const void *batch_kernel(bool ts, bool cl) {
@@ -1090,8 +1095,9 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (!(q.CR >= 0.f && q.CR <= 1.f)) return fail(QPM_ERR_ARG, "qpm_create: CR outside [0, 1]");
     if (q.gwo_combine != 0 && q.gwo_combine != 1)
       return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0 or 1");
-    if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256)
-      return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128 or 256");
+    if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256 &&
+        q.team != 512)
+      return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128, 256 or 512");
     if (q.f_schedule != 0 && q.f_schedule != 1)
       return fail(QPM_ERR_ARG, "qpm_create: f_schedule must be 0 or 1");
     if (!std::isfinite(p.kappa1) || !std::isfinite(p.kappa2))
@@ -1133,6 +1139,28 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     int occ_plain = 1, occ_persist = 1;
     qpm_status s2 = occupancy(I, &occ_plain, &occ_persist);
     if (s2 != QPM_OK) { delete st; return s2; }
+    if (q.team == 0 && n_inst == 1 && I.T == 256 && I.c >= 16) {
+      // long rows: 512 threads per individual (one CTA per SM) when that leaves fewer
+      // CTA slots idle in the last round of individuals of a phase
+      InstDev W = I;
+      W.T = 512;
+      W.Npad = (int32_t)align_up((size_t)p.N, 4 * (size_t)W.T);
+      W.c = W.Npad / W.T;
+      int wp = 1, wq = 1;
+      s2 = occupancy(W, &wp, &wq);
+      if (s2 != QPM_OK) { delete st; return s2; }
+      auto fill = [&](int slots) {
+        const int rounds = (I.NP + slots - 1) / slots;
+        return (double)I.NP / ((double)rounds * slots);
+      };
+      if (fill(wq * nsm) > fill(occ_persist * nsm) + 0.05) {
+        I.T = W.T;
+        I.Npad = W.Npad;
+        I.c = W.c;
+        occ_plain = wp;
+        occ_persist = wq;
+      }
+    }
     st->grid_plain[k] = std::min(I.NP, occ_plain * nsm);
     st->grid_persist[k] = std::min(I.NP, occ_persist * nsm);
     base[k] = total;

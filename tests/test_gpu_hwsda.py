@@ -130,7 +130,7 @@ def test_decaying_F_lockstep(q, orc, mode):
     assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
-@pytest.mark.parametrize("team", [32, 64, 256])
+@pytest.mark.parametrize("team", [32, 64, 256, 512])
 def test_team_widths_lockstep(q, orc, team):
     """Every team width (threads per individual) follows the oracle bit for bit."""
     N, NP, G = 1000, 16, 6
@@ -147,6 +147,21 @@ def test_team_widths_lockstep(q, orc, team):
         Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
         assert np.array_equal(X, Xo)
         assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
+
+
+def test_automatic_team_rule(q):
+    """team = 0: at most 4 domains per thread up to 256 threads; a single long-row
+    instance takes 512 threads when one CTA per SM fills the rounds of individuals
+    better (1024 individuals on 152 SMs: 304 two-CTA slots leave the fourth round a
+    third full, 152 one-CTA slots fill 6.7 of 7 rounds)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    cases = [(16, 32, 32), (1000, 256, 256), (100000, 256, 256)]
+    if nsm == 152:
+        cases.append((100000, 1024, 512))
+    for N, NP, want in cases:
+        with q.State([(N, 1.0, 2.0)], [q.Params(NP, 2, 0.5, 0.9, 1, 0, 1)]) as st:
+            assert q.qpm_team_of(st.h) == want, (N, NP)
 
 
 def test_paper_scale_step_sampled(q, orc):
