@@ -174,7 +174,7 @@ qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stre
  *              caller-owned: the forward fills it (it is also the forward's
  *              workspace) and the backward reads it.  Floats 0-1 of each row
  *              hold sum_a = sum_j d_j e^{-i kappa2 j}; the rest holds the
- *              row's prefix sums at segment starts (about N/32 floats).
+ *              row's prefix sums at segment starts (about N/16 floats).
  *   grad_fit   device float [B] upstream gradient dL/df (NULL = all ones)
  *   grad_theta device float [B][ld_grad] out: dL/dtheta = grad_fit * df/dtheta
  * Phasor table as for qpm_eval (cached per problem).  Errors: N < 1, B < 1,

@@ -11,8 +11,11 @@
 // Work split (both passes): a warp takes 32 rows (lane = row) and one segment of
 // L domains (L a multiple of 32 fixed by N alone, at most 256) and sweeps the
 // segment in index order in steps of 32 domains.  Each step's 32 x 32 theta
-// values are loaded with coalesced 16-byte loads one step ahead, transposed
-// through a per-warp shared-memory tile, and every lane then walks its own row:
+// values arrive one step ahead as coalesced 16-byte asynchronous copies
+// (cp.async, zero-filled past the row ends) straight into a double-buffered
+// per-warp shared-memory tile, transposed by its swizzle, so no registers hold
+// the prefetch (rows that are not 16-byte aligned use register loads instead);
+// every lane then walks its own row:
 // the running prefixes of a and b are plain sequential sums and every phasor
 // read is a broadcast.  The warps of a CTA take consecutive row groups of the
 // same segment and share its staged phasors (p1, p2, q = p1 p2).
@@ -45,8 +48,10 @@ struct RelaxShape {
   bool vec;        // theta rows 16-byte aligned with ld % 4 == 0
 };
 
-// segment length: S = ceil(N / L) is about 16 for short rows, L = 256 for long ones
-static int rx_seg_len(int N) { return std::min(RX_LMAX, RX_STEP * ((N + 511) / 512)); }
+// segment length: S = ceil(N / L) is about 32 for short rows, L = 256 for long ones
+// (4096 x 4096: 32 segments of 128 domains, 4096 warps of work)
+static constexpr int RX_SEGQ = 1024;  // about N / 32, rounded up to whole steps
+static int rx_seg_len(int N) { return std::min(RX_LMAX, RX_STEP * ((N + RX_SEGQ - 1) / RX_SEGQ)); }
 static int rx_nseg(int N) { return (N + rx_seg_len(N) - 1) / rx_seg_len(N); }
 // saved block of a row: [A (2 floats), 2 unused, then per segment 8 floats]
 static int64_t rx_saved_floats(int N) { return 4 + 8 * (int64_t)rx_nseg(N); }
@@ -116,6 +121,38 @@ __device__ __forceinline__ void put_step(float4 *T, const float4 R[8]) {
   for (int k = 0; k < 8; ++k) T[tix(4 * k + (lane >> 3), lane & 7)] = R[k];
 }
 
+// 16 bytes global -> shared without registers; bytes < 16 zero-fills the rest
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// one step (32 domains from ms) of rows r0..r0+31 copied asynchronously into the
+// tile T with the layout of put_step; 16-byte aligned rows (ld % 4 == 0) only
+__device__ __forceinline__ void copy_step(float4 *T, const float *__restrict__ theta,
+                                          const RelaxShape &sh, int r0, int ms) {
+  const int lane = threadIdx.x & 31;
+  const int m = ms + 4 * (lane & 7);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int tr = 4 * k + (lane >> 3), gr = r0 + tr;
+    const float *src = theta;
+    int bytes = 0;
+    if (gr < sh.B && m < sh.N) {
+      src = theta + (int64_t)gr * sh.ld + m;
+      bytes = 4 * min(4, sh.N - m);
+    }
+    cp_async16(&T[tix(tr, lane & 7)], src, bytes);
+  }
+  cp_async_commit();
+}
+
 // phasors of the CTA's segment [m0, m0 + L) (zero beyond N), then a CTA barrier
 __device__ __forceinline__ void stage_segment(float4 *sp, float2 *sq, const float4 *gtab, int m0,
                                               int L, int N) {
@@ -159,23 +196,36 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
                   float *__restrict__ saved) {
   __shared__ float4 sp[RX_LMAX];
   __shared__ float2 sq[RX_LMAX];
-  __shared__ float4 tile[RX_WPC][RX_STEP * RX_STEP / 4];
+  __shared__ float4 tile[RX_WPC][2][RX_STEP * RX_STEP / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = blockIdx.y, m0 = seg * sh.L;
   const int r0 = (blockIdx.x * RX_WPC + warp) * 32;
   const int nsteps = sh.L / RX_STEP;
-  float4 R[8];
-  if (r0 < sh.B) load_step<VEC>(theta, sh, r0, m0, R);  // in flight while the table is staged
+  float4 R[VEC ? 1 : 8];
+  if (r0 < sh.B) {  // the first step is in flight while the table is staged
+    if constexpr (VEC) copy_step(tile[warp][0], theta, sh, r0, m0);
+    else load_step<false>(theta, sh, r0, m0, R);
+  }
   stage_segment(sp, sq, gtab, m0, sh.L, sh.N);
   if (r0 >= sh.B) return;
-  float4 *T = tile[warp];
   Mono acc = mono_zero();
   float2 E = make_float2(0.f, 0.f);
   for (int t = 0; t < nsteps; ++t) {
-    __syncwarp();
-    put_step(T, R);
-    __syncwarp();
-    if (t + 1 < nsteps) load_step<VEC>(theta, sh, r0, m0 + (t + 1) * RX_STEP, R);
+    float4 *T = tile[warp][t & 1];
+    if constexpr (VEC) {
+      if (t + 1 < nsteps) {
+        copy_step(tile[warp][(t + 1) & 1], theta, sh, r0, m0 + (t + 1) * RX_STEP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+    } else {
+      __syncwarp();
+      put_step(T, R);
+      __syncwarp();
+      if (t + 1 < nsteps) load_step<false>(theta, sh, r0, m0 + (t + 1) * RX_STEP, R);
+    }
     const int e0 = t * RX_STEP;
 #pragma unroll
     for (int c4 = 0; c4 < 8; ++c4) {
@@ -194,6 +244,7 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
         E.y = fmaf(d2, q.y, E.y);
       }
     }
+    __syncwarp();  // every lane has read T before the copy two steps on refills it
   }
   const int row = r0 + lane;
   if (row < sh.B) {
@@ -257,16 +308,18 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
                   float *__restrict__ grad, int64_t ldg) {
   __shared__ float4 sp[RX_LMAX];
   __shared__ float2 sq[RX_LMAX];
-  __shared__ float4 tile[RX_WPC][RX_STEP * RX_STEP / 4];
+  __shared__ float4 tile[RX_WPC][2][RX_STEP * RX_STEP / 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int seg = blockIdx.y, m0 = seg * sh.L;
   const int r0 = (blockIdx.x * RX_WPC + warp) * 32;
   const int nsteps = sh.L / RX_STEP;
-  float4 R[8];
-  if (r0 < sh.B) load_step<VEC>(theta, sh, r0, m0, R);
+  float4 R[VEC ? 1 : 8];
+  if (r0 < sh.B) {
+    if constexpr (VEC) copy_step(tile[warp][0], theta, sh, r0, m0);
+    else load_step<false>(theta, sh, r0, m0, R);
+  }
   stage_segment(sp, sq, gtab, m0, sh.L, sh.N);
   if (r0 >= sh.B) return;
-  float4 *T = tile[warp];
   const int row = r0 + lane;
   // u = 8 g conj(D) phi1 phi2, v = 16 g conj(D) psi: df/dtheta_k =
   //   [Re(u (p2 P + p1 R)) + d Re(v q)] r (1 - r)   with (1 - d^2) = 4 r (1 - r)
@@ -287,10 +340,21 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
   const float vi = 16.f * g * (D.x * psi.y - D.y * psi.x);
   for (int t = 0; t < nsteps; ++t) {
     const int ms = m0 + t * RX_STEP;
-    __syncwarp();
-    put_step(T, R);
-    __syncwarp();
-    if (t + 1 < nsteps) load_step<VEC>(theta, sh, r0, ms + RX_STEP, R);
+    float4 *T = tile[warp][t & 1];
+    if constexpr (VEC) {
+      if (t + 1 < nsteps) {
+        copy_step(tile[warp][(t + 1) & 1], theta, sh, r0, ms + RX_STEP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+    } else {
+      __syncwarp();
+      put_step(T, R);
+      __syncwarp();
+      if (t + 1 < nsteps) load_step<false>(theta, sh, r0, ms + RX_STEP, R);
+    }
     const int e0 = t * RX_STEP;
 #pragma unroll
     for (int c4 = 0; c4 < 8; ++c4) {
@@ -335,6 +399,7 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
         }
       }
     }
+    __syncwarp();  // every lane has read T before the copy two steps on refills it
   }
 }
 

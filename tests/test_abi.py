@@ -63,8 +63,8 @@ def test_argument_errors_without_device(qlib):
 
 def test_relaxed_saved_block_size_and_errors(qlib):
     import paper_2511_01255_gb300 as q
-    # segments of L = min(256, 32 ceil(N / 512)) domains; 4 + 8 floats per segment
-    for N, L in ((1, 32), (5, 32), (512, 32), (513, 64), (1000, 64), (4096, 256), (100000, 256)):
+    # segments of L = min(256, 32 ceil(N / 1024)) domains; 4 + 8 floats per segment
+    for N, L in ((1, 32), (5, 32), (1024, 32), (1025, 64), (1000, 32), (4096, 128), (100000, 256)):
         assert qlib.qpm_relaxed_saved_floats(N) == 4 + 8 * ((N + L - 1) // L), N
     assert qlib.qpm_relaxed_saved_floats(0) == 0
     p = q.Problem(64, 1.0, 2.0)
