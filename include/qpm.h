@@ -82,8 +82,9 @@ enum {
   QPM_RUN_GRAPH = 1,      /* the same launches captured once into a CUDA graph */
   QPM_RUN_PERSISTENT = 2, /* one cooperative persistent kernel for all generations */
   QPM_RUN_BATCHED = 3     /* many instances in one launch (captured in a CUDA graph): each
-                             CTA runs whole instances from a largest-first queue; needs
-                             team = 32, the default when n_inst > 1 */
+                             thread-block cluster (qpm_set_batch_cluster) runs whole
+                             instances from a largest-first queue; needs team = 32, the
+                             default when n_inst > 1 */
 };
 
 const char *qpm_last_error(void);

@@ -18,7 +18,9 @@
 // Per generation: k_de (all NP trials + greedy selection + leader choice by the
 // last CTA) and k_gwo (omega wolves + greedy selection + generation counter by
 // the last CTA); or one cooperative persistent kernel that runs both phases for
-// many generations with bounded grid barriers in between.
+// many generations with bounded grid barriers in between; or, for many
+// instances, one launch of k_batch in which thread-block clusters take whole
+// instances from a queue.
 #include <math.h>
 
 #include <string.h>
