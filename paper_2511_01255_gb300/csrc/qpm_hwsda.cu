@@ -182,7 +182,8 @@ static __global__ void k_init(InstDev I) {
 template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
                                             const float4 *tbl, int g, int i, const int4 r,
-                                            const int32_t *sel_in, int32_t *sel_out, Mono *sh) {
+                                            const int32_t *sel_in, int32_t *sel_out, Mono *sh,
+                                            int *slot_out = nullptr) {
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
@@ -225,6 +226,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     }
     if (I.trace) I.trace[(size_t)I.NP * (1 + 2 * (size_t)g) + i] = f;
     key = lead_key(accept ? f : fx, i);
+    if (slot_out) *slot_out = accept ? (si ^ 1) : si;  // the survivor's slot
   }
   return key;
 }
@@ -237,10 +239,14 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
                                int i, int32_t *sel, int la, int lb, int ld, Mono *sh,
                                const uint4 *wpre = nullptr,
                                float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f),
-                               float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f)) {
+                               float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f),
+                               const int32_t *lslot = nullptr) {
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
-  const int si = sel[i], sa = sel[la], sb = sel[lb], sd = sel[ld];
+  // lslot: the leaders' current slots, when the leader search delivered them
+  const int si = sel[i];
+  const int sa = lslot ? lslot[0] : sel[la], sb = lslot ? lslot[1] : sel[lb];
+  const int sd = lslot ? lslot[2] : sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
   const float a = __fdiv_rn((float)(2 * (I.G - g)), (float)I.G);
   const float two_a = __fmul_rn(2.0f, a);
@@ -249,8 +255,10 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
     const float4 x = (PRE && k4 == 0) ? (si ? own1 : own0) : ld_cur<NC, DUAL>(I, i, si, off);
-    const float4 L0 = ld_cur<NC, DUAL>(I, la, sa, off), L1 = ld_cur<NC, DUAL>(I, lb, sb, off);
-    const float4 L2 = ld_cur<NC, DUAL>(I, ld, sd, off);
+    // a known slot needs one row read, not both
+    const float4 L0 = lslot ? ld_cur<NC, false>(I, la, sa, off) : ld_cur<NC, DUAL>(I, la, sa, off);
+    const float4 L1 = lslot ? ld_cur<NC, false>(I, lb, sb, off) : ld_cur<NC, DUAL>(I, lb, sb, off);
+    const float4 L2 = lslot ? ld_cur<NC, false>(I, ld, sd, off) : ld_cur<NC, DUAL>(I, ld, sd, off);
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
     uint4 w[6];
     if (PRE && k4 == 0) {
@@ -476,11 +484,22 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
 
 // Step 3 of the persistent form, after the grid barrier that follows DE: warp 0
 // reads the DE survivor keys of all individuals and takes the top three; every
-// thread returns after the CTA barrier with lead_sh set.  The keys are written in
+// thread returns after the CTA barrier with lead_sh and the leaders' current
+// slots (slot_sh) set.  The keys are written in
 // the DE phase only, so a CTA that is still choosing leaders never sees a fitness
 // already changed by another CTA's GWO selection.
+// The keys carry the survivor's slot: fitness bits << 32 | (0x7FFFFFFF - i) << 1 | slot,
+// which orders like lead_key (the slot bit never separates two individuals).
+__device__ __forceinline__ unsigned long long slot_key(unsigned long long key, int i, int slot) {
+  return (key & 0xFFFFFFFF00000000ull) |
+         (unsigned long long)(((0x7FFFFFFFu - (uint32_t)i) << 1) | (uint32_t)slot);
+}
+__device__ __forceinline__ int slot_key_index(unsigned long long k) {
+  return (int)(0x7FFFFFFFu - ((uint32_t)k >> 1));
+}
+
 __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_t *lead,
-                                  int32_t *lead_sh) {
+                                  int32_t *lead_sh, int32_t *slot_sh) {
   if (threadIdx.x < 32) {
     unsigned long long k0 = 0, k1 = 0, k2 = 0;
     for (int i = threadIdx.x; i < NP; i += 32) top3_insert(k0, k1, k2, keys[i]);
@@ -493,9 +512,12 @@ __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_
       top3_insert(k0, k1, k2, p2);
     }
     if (threadIdx.x == 0) {
-      lead_sh[0] = key_index(k0);
-      lead_sh[1] = key_index(k1);
-      lead_sh[2] = key_index(k2);
+      lead_sh[0] = slot_key_index(k0);
+      lead_sh[1] = slot_key_index(k1);
+      lead_sh[2] = slot_key_index(k2);
+      slot_sh[0] = (int32_t)(k0 & 1u);
+      slot_sh[1] = (int32_t)(k1 & 1u);
+      slot_sh[2] = (int32_t)(k2 & 1u);
       if (lead) { lead[0] = lead_sh[0]; lead[1] = lead_sh[1]; lead[2] = lead_sh[2]; }
     }
   }
@@ -513,7 +535,7 @@ template <bool COMP, bool TS, bool DUAL, int MAXT = 256>
 static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     k_persist(InstDev I, int g_end, Barrier bar) {
   extern __shared__ float4 dyn[];
-  __shared__ int32_t lead_sh[3];
+  __shared__ int32_t lead_sh[3], lslot_sh[3];
   Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
   if (TS) {
     for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
@@ -530,9 +552,11 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
+      int slot = 0;
       const unsigned long long key =
-          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh);
-      if (threadIdx.x == 0) I.dekey[i] = key;  // ordered before the barrier's release
+          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh, &slot);
+      // ordered before the barrier's release
+      if (threadIdx.x == 0) I.dekey[i] = slot_key(key, i, slot);
     }
     grid_arrive(bar, target);
     uint4 wpre[6];
@@ -552,16 +576,18 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       own1 = *(const float4 *)(r0 + I.Npad);
     }
     // every CTA finds the leaders itself (Sec. 3.2 Step 3) from the DE keys
-    leaders_from_keys(I.dekey, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh);
+    leaders_from_keys(I.dekey, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh, lslot_sh);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       if (pre)
         gwo_individual<COMP, false, TS, DUAL, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld,
-                                                           sh, wpre, own0, own1);
+                                                           sh, wpre, own0, own1, lslot_sh);
       else
-        gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh);
+        gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh, nullptr,
+                                              make_float4(0.f, 0.f, 0.f, 0.f),
+                                              make_float4(0.f, 0.f, 0.f, 0.f), lslot_sh);
     }
     if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
