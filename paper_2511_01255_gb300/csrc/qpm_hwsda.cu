@@ -535,7 +535,7 @@ template <bool COMP, bool TS, bool DUAL, int MAXT = 256>
 static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     k_persist(InstDev I, int g_end, Barrier bar) {
   extern __shared__ float4 dyn[];
-  __shared__ int32_t lead_sh[3], lslot_sh[3];
+  __shared__ int32_t lead_sh[3], lslot_sh[3], own_slot_sh;
   Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
   if (TS) {
     for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
@@ -556,7 +556,10 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       const unsigned long long key =
           de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh, &slot);
       // ordered before the barrier's release
-      if (threadIdx.x == 0) I.dekey[i] = slot_key(key, i, slot);
+      if (threadIdx.x == 0) {
+        I.dekey[i] = slot_key(key, i, slot);
+        own_slot_sh = slot;  // read after the barrier's CTA synchronisation
+      }
     }
     grid_arrive(bar, target);
     uint4 wpre[6];
@@ -567,13 +570,15 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
         wpre[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)blockIdx.x, jg);
     }
     if (!grid_wait(bar, target)) return;
-    // the own row (both slots) is requested before the leaders are known, so that
-    // its latency overlaps the leader search
+    // the own row (its current slot, known from this CTA's own selection) is
+    // requested before the leaders are known, so that its latency overlaps the
+    // leader search
     float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f), own1 = own0;
     if (pre) {
-      const float *r0 = I.pop + (size_t)2 * blockIdx.x * I.Npad + (size_t)threadIdx.x * 4;
+      const float *r0 = I.pop + ((size_t)2 * blockIdx.x + own_slot_sh) * I.Npad +
+                        (size_t)threadIdx.x * 4;
       own0 = *(const float4 *)r0;
-      own1 = *(const float4 *)(r0 + I.Npad);
+      own1 = own0;
     }
     // every CTA finds the leaders itself (Sec. 3.2 Step 3) from the DE keys
     leaders_from_keys(I.dekey, I.NP, blockIdx.x == 0 ? I.lead : nullptr, lead_sh, lslot_sh);
