@@ -124,18 +124,13 @@ def algorithmic_lane_ops_per_gene_gen(compensated):
     return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
 
 
-def int_lane_ops_per_gene_gen():
-    """Integer part of the algorithmic count: the Philox rounds (1.75 calls x 80) and
-    the shift and conversion of each of the 7 uniforms (2 each)."""
-    return 1.75 * 80 + 7 * 2
-
-
 def mix_ceiling_gene_gens(compensated, issue):
-    """Gene-generations/s the op mix allows on this GPU: integer ops at the measured
-    three-input-xor rate, all ops at the measured FFMA issue rate (T lane-ops/s)."""
-    n_int = int_lane_ops_per_gene_gen()
-    n_all = algorithmic_lane_ops_per_gene_gen(compensated)
-    t = max(n_int / (issue["lop3"] * 1e12), n_all / (issue["ffma"] * 1e12))
+    """Gene-generations/s the work of a gene-generation allows on this GPU when every
+    issue slot does useful work: 1.75 Philox4x32-10 calls at the measured rate of the
+    library's own generator, the rest of the algorithmic lane-ops at the measured
+    FFMA rate (they share the issue slots, so the times add)."""
+    n_rest = algorithmic_lane_ops_per_gene_gen(compensated) - 1.75 * 80
+    t = 1.75 / issue["philox_calls_per_s"] + n_rest / (issue["ffma"] * 1e12)
     return 1.0 / t
 
 
@@ -192,6 +187,7 @@ def run_gpu(args):
     # measured issue rates of this GPU (the library's microbenchmark), T lane-ops/s
     issue = {name: q.qpm_measure_issue_peak(k) / 1e12
              for k, name in enumerate(("ffma", "philox_mul_xor", "lop3"))}
+    issue["philox_calls_per_s"] = q.qpm_measure_issue_peak(3)
     peak_hbm = pk.get("hbm_gbs", 6800.0)
     c = W.PAPER_SCALE
     N, NP, G = c["N"], c["NP"], c["G"]

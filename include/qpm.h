@@ -157,9 +157,10 @@ qpm_status qpm_release_caches(void);
 
 /* Measured issue rate of the current device for the ALU roofline (no counterpart
  * in the paper): kind 0 FFMA, 1 the 32 x 32 -> 64 multiply and xor of a Philox
- * round, 2 three-input xor; lane-ops per second in *lane_ops_per_s (host double),
- * counting a wide multiply as 2 ops.  Synchronous (about 10 ms); allocates and
- * frees a small device buffer.  Errors: kind outside [0, 2] -> QPM_ERR_ARG. */
+ * round, 2 three-input xor (lane-ops per second, a wide multiply counting 2 ops),
+ * 3 whole Philox4x32-10 calls of the library's generator per second; the result in
+ * *lane_ops_per_s (host double).  Synchronous (about 10 ms); allocates and frees a
+ * small device buffer.  Errors: kind outside [0, 3] -> QPM_ERR_ARG. */
 qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stream_t stream);
 
 /* ---------------------------------------------------------------------------

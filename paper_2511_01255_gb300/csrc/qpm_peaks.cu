@@ -7,9 +7,11 @@
 // only under a condition the chains never meet, so nothing is optimised away.
 // Lane-ops/s = threads x iterations x chains x ops per chain step / elapsed time,
 // with the op counts of the roofline's own convention: a 32 x 32 -> 64 multiply
-// counts 2, a three-input logic op 1, an FFMA 1.
+// counts 2, a three-input logic op 1, an FFMA 1; kind 3 reports whole calls of the
+// generator's Philox4x32-10 per second.
 #include <cuda_runtime.h>
 
+#include "qpm_common.cuh"
 #include "qpm_internal.h"
 
 namespace qpm {
@@ -73,14 +75,32 @@ static __global__ void __launch_bounds__(PK_THREADS) k_peak_lop3(uint32_t k, uin
   if (s == 0x12345678u && k == 0u) sink[blockIdx.x] = s;
 }
 
+// whole Philox4x32-10 calls of the library's generator (the counter of each chain
+// is the previous output, so nothing is hoisted); one "op" per call here
+static constexpr int PK_PHILOX_ITERS = 256;
+static __global__ void __launch_bounds__(PK_THREADS) k_peak_philox(uint2 key, uint32_t *sink) {
+  const PhiloxKey K = philox_schedule(key);
+  uint4 c[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c[k] = make_uint4(threadIdx.x, blockIdx.x, k, 7u);
+  for (int it = 0; it < PK_PHILOX_ITERS; ++it) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = philox10(c[k], K);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s ^= c[k].x ^ c[k].y ^ c[k].z ^ c[k].w;
+  if (s == 0x2545F491u && key.x == 0u) sink[blockIdx.x] = s;
+}
+
 }  // namespace qpm
 
 using namespace qpm;
 
 extern "C" qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s,
                                              qpm_stream_t stream) {
-  if (!lane_ops_per_s || kind < 0 || kind > 2)
-    return fail(QPM_ERR_ARG, "qpm_measure_issue_peak: kind must be 0, 1 or 2");
+  if (!lane_ops_per_s || kind < 0 || kind > 3)
+    return fail(QPM_ERR_ARG, "qpm_measure_issue_peak: kind must be 0, 1, 2 or 3");
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = sm_count() * 4;  // 2048 threads per SM: every scheduler full
   void *sink = nullptr;
@@ -89,14 +109,17 @@ extern "C" qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float ms = 0.f;
-  // ops per chain step: FFMA 1; wide multiply (2) + xor (1); two three-input xors
+  // ops per chain step: FFMA 1; wide multiply (2) + xor (1); two three-input xors;
+  // kind 3 counts whole Philox calls (4 chains of PK_PHILOX_ITERS)
   const double per_step = kind == 0 ? 1.0 : (kind == 1 ? 3.0 : 2.0);
-  const double per_thread = (double)PK_ITERS * PK_CHAINS * per_step;
+  const double per_thread = kind == 3 ? (double)PK_PHILOX_ITERS * 4
+                                      : (double)PK_ITERS * PK_CHAINS * per_step;
   for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // the first launch warms up
     e = cudaEventRecord(e0, s);
     if (kind == 0) k_peak_ffma<<<blocks, PK_THREADS, 0, s>>>(1.000001f, 1e-7f, (float *)sink);
     else if (kind == 1) k_peak_imul<<<blocks, PK_THREADS, 0, s>>>(0xD2511F53u, (uint32_t *)sink);
-    else k_peak_lop3<<<blocks, PK_THREADS, 0, s>>>(0xCD9E8D57u, (uint32_t *)sink);
+    else if (kind == 2) k_peak_lop3<<<blocks, PK_THREADS, 0, s>>>(0xCD9E8D57u, (uint32_t *)sink);
+    else k_peak_philox<<<blocks, PK_THREADS, 0, s>>>(make_uint2(1u, 2u), (uint32_t *)sink);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);

@@ -160,5 +160,7 @@ def test_issue_peak_microbenchmark(q):
     f = q.qpm_measure_issue_peak(0)
     assert 0.3 * derived < f < 1.1 * derived
     assert q.qpm_measure_issue_peak(1) > 0 and q.qpm_measure_issue_peak(2) > 0
+    # whole Philox calls: at most one call per 40 issue slots of the FFMA rate
+    assert 0 < q.qpm_measure_issue_peak(3) < f / 40 * 1.1
     with pytest.raises(q.QpmError):
-        q.qpm_measure_issue_peak(3)
+        q.qpm_measure_issue_peak(4)
