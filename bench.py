@@ -116,21 +116,25 @@ class ClockSampler:
 K_PERSIST_DRAM_BYTES = 1145344 + 386816
 
 
+PHILOX_CALLS_PER_GENE_GEN = 0.25 + 0.75  # crossover word + three GWO words, 4 genes per call
+
+
 def algorithmic_lane_ops_per_gene_gen(compensated):
-    """Lane instructions the method needs per gene and generation (documented in
-    the design doc): Philox4x32-10 at 1.75 calls (80 ops each), 7 uniforms (3 ops),
+    """Lane instructions the method needs per gene and generation: Philox4x32-10 at
+    1.0 calls (80 ops each: a quarter for the crossover word, three quarters for
+    the three GWO words, each giving one leader's r1 and r2), 7 uniforms (3 ops),
     DE update (7), GWO update (30), two fitness domain-evals (10 plain; 14.25 with
     Kahan compensation folded in every 8 domains)."""
-    return 1.75 * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
+    return PHILOX_CALLS_PER_GENE_GEN * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
 
 
 def mix_ceiling_gene_gens(compensated, issue):
     """Gene-generations/s the work of a gene-generation allows on this GPU when every
-    issue slot does useful work: 1.75 Philox4x32-10 calls at the measured rate of the
+    issue slot does useful work: the Philox4x32-10 calls at the measured rate of the
     library's own generator, the rest of the algorithmic lane-ops at the measured
     FFMA rate (they share the issue slots, so the times add)."""
-    n_rest = algorithmic_lane_ops_per_gene_gen(compensated) - 1.75 * 80
-    t = 1.75 / issue["philox_calls_per_s"] + n_rest / (issue["ffma"] * 1e12)
+    n_rest = algorithmic_lane_ops_per_gene_gen(compensated) - PHILOX_CALLS_PER_GENE_GEN * 80
+    t = PHILOX_CALLS_PER_GENE_GEN / issue["philox_calls_per_s"] + n_rest / (issue["ffma"] * 1e12)
     return 1.0 / t
 
 

@@ -430,8 +430,9 @@ ORC_API void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
 /*   key = (seed low word, seed high word)                                    */
 /*   counter = (j/4, i, g, (instance << 8) | tag); word j%4 serves gene j     */
 /*   tags: 0 init, 1 DE indices (counter word 0 = 0), 2 crossover,            */
-/*         3..8 GWO r1/r2 for alpha, beta, gamma                              */
-/*   uniform U = (w >> 8) * 2^-24 in [0, 1)                                   */
+/*         3..5 GWO for alpha, beta, gamma                                    */
+/*   uniform U = (w >> 8) * 2^-24 in [0, 1) for init and crossover; the GWO   */
+/*   pair (r1, r2) of a leader and gene = (w >> 16, w & 0xFFFF) * 2^-16       */
 /*   index in [0, m): (w * m) >> 32  (Lemire multiply-shift)                  */
 /* ------------------------------------------------------------------------- */
 enum { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3 };
@@ -445,6 +446,9 @@ static inline uint32_t rng_word(uint64_t seed, uint32_t inst, uint32_t tag, uint
   return out[j & 3];
 }
 static inline float u24(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+/* the two 16-bit halves of one word as uniforms on [0, 1) (exact in FP32) */
+static inline float u16hi(uint32_t w) { return (float)(w >> 16) * 0x1p-16f; }
+static inline float u16lo(uint32_t w) { return (float)(w & 0xFFFFu) * 0x1p-16f; }
 static inline uint32_t lemire(uint32_t w, uint32_t m) {
   return (uint32_t)(((uint64_t)w * m) >> 32);
 }
@@ -570,8 +574,10 @@ static void gwo_cand_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
     float Xk[3];
     for (int k = 0; k < 3; ++k) {
       const float *Xp = X + (int64_t)lead[k] * c->ld; /* alpha, beta, gamma */
-      float r1 = u24(rng_word(c->seed, c->inst, TAG_GWO + 2 * k, g, (uint32_t)i, (uint32_t)j));
-      float r2 = u24(rng_word(c->seed, c->inst, TAG_GWO + 2 * k + 1, g, (uint32_t)i, (uint32_t)j));
+      /* r1 and r2 of leader k: the high and low 16 bits of one word (tag GWO + k) */
+      const uint32_t w = rng_word(c->seed, c->inst, TAG_GWO + k, g, (uint32_t)i, (uint32_t)j);
+      float r1 = u16hi(w);
+      float r2 = u16lo(w);
       float A = two_a * r1 - a;           /* A = 2 a r1 - a */
       float C = 2.0f * r2;                /* C = 2 r2 */
       float dist = fabsf(C * Xp[j] - x[j]); /* d = |C Xp - X| */

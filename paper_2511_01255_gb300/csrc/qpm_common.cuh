@@ -44,7 +44,8 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const PhiloxKey &K) {
 }
 
 // Random-number contract: key = seed, counter = (j/4, i, g, instance<<8 | tag);
-// word j%4 of the output serves gene j.
+// word j%4 of the output serves gene j.  Tags: 0 init, 1 DE indices, 2 crossover,
+// 3-5 GWO (one word per leader and gene: r1 its high, r2 its low 16 bits).
 enum : uint32_t { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3, TAG_THETA = 16 };
 
 __device__ __forceinline__ uint4 rng4(const PhiloxKey &K, uint32_t inst, uint32_t tag, uint32_t g,
@@ -55,6 +56,10 @@ __device__ __forceinline__ uint4 rng4(const PhiloxKey &K, uint32_t inst, uint32_
 __device__ __forceinline__ float u24(uint32_t w) {
   return __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
 }
+// the two 16-bit halves of one word as uniforms on [0, 1) (exact in FP32): the
+// GWO pair (r1, r2) of one leader and gene
+__device__ __forceinline__ float u16hi(uint32_t w) { return (float)(w >> 16) * 0x1p-16f; }
+__device__ __forceinline__ float u16lo(uint32_t w) { return (float)(w & 0xFFFFu) * 0x1p-16f; }
 // index in [0, m): Lemire's multiply-shift
 __device__ __forceinline__ uint32_t lemire(uint32_t w, uint32_t m) { return __umulhi(w, m); }
 

@@ -232,8 +232,9 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 }
 
 // ------------------------------------------------ Step 4-5: GWO + selection
-// PRE: the six GWO random words of the thread's first group of 4 domains were
-// drawn earlier (while waiting at the grid barrier) and are passed in wpre
+// PRE: the three GWO random words of the thread's first group of 4 domains were
+// drawn earlier (while waiting at the grid barrier) and are passed in wpre.
+// One word per leader and gene gives that leader's (r1, r2) as its 16-bit halves.
 template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool PRE = false>
 __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
                                int i, int32_t *sel, int la, int lb, int ld, Mono *sh,
@@ -260,28 +261,28 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
     const float4 L1 = lslot ? ld_cur<NC, false>(I, lb, sb, off) : ld_cur<NC, DUAL>(I, lb, sb, off);
     const float4 L2 = lslot ? ld_cur<NC, false>(I, ld, sd, off) : ld_cur<NC, DUAL>(I, ld, sd, off);
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
-    uint4 w[6];
+    uint4 w[3];
     if (PRE && k4 == 0) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) w[k] = wpre[k];
+      for (int k = 0; k < 3; ++k) w[k] = wpre[k];
     } else {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
+      for (int k = 0; k < 3; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
     }
     float4 y;
-#define QPM_PULL(Xp, xv, r1w, r2w, out_)                                               \
+#define QPM_PULL(Xp, xv, rw, out_)                                                     \
     {                                                                                  \
-      const float A = __fsub_rn(__fmul_rn(two_a, u24(r1w)), a);                         \
-      const float C = __fmul_rn(2.0f, u24(r2w));                                        \
+      const float A = __fsub_rn(__fmul_rn(two_a, u16hi(rw)), a);                        \
+      const float C = __fmul_rn(2.0f, u16lo(rw));                                       \
       const float dist = fabsf(__fsub_rn(__fmul_rn(C, Xp), xv));                        \
       out_ = __fsub_rn(Xp, __fmul_rn(A, dist));                                         \
     }
 #define QPM_GWO1(CMP)                                                                  \
     {                                                                                  \
       float Y0, Y1, Y2;                                                                \
-      QPM_PULL(L0.CMP, x.CMP, w[0].CMP, w[1].CMP, Y0)                                  \
-      QPM_PULL(L1.CMP, x.CMP, w[2].CMP, w[3].CMP, Y1)                                  \
-      QPM_PULL(L2.CMP, x.CMP, w[4].CMP, w[5].CMP, Y2)                                  \
+      QPM_PULL(L0.CMP, x.CMP, w[0].CMP, Y0)                                            \
+      QPM_PULL(L1.CMP, x.CMP, w[1].CMP, Y1)                                            \
+      QPM_PULL(L2.CMP, x.CMP, w[2].CMP, Y2)                                            \
       float v;                                                                         \
       if (I.combine == 0) {                                                            \
         v = __fdiv_rn(__fadd_rn(__fadd_rn(Y0, Y1), Y2), 3.0f);                          \
@@ -562,11 +563,11 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       }
     }
     grid_arrive(bar, target);
-    uint4 wpre[6];
+    uint4 wpre[3];
     if (pre) {
       const uint32_t jg = (uint32_t)((threadIdx.x * I.c) >> 2);
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
+      for (int k = 0; k < 3; ++k)
         wpre[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)blockIdx.x, jg);
     }
     if (!grid_wait(bar, target)) return;

@@ -145,6 +145,33 @@ def test_gwo_candidate_moments(orc):
     assert y.min() >= 0.5 - a and y.max() <= 0.5 + a
 
 
+def test_gwo_pair_from_one_word(orc):
+    """The GWO pair (r1, r2) of leader k and gene j are the high and low 16 bits of
+    one generator word (tag 3 + k): a candidate recomputed here from the words."""
+    NP, N, G, seed = 6, 9, 50, 12345
+    c = _cfg(orc, NP=NP, N=N, G=G, seed=seed)
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, (NP, N)).astype(np.float32)
+    lead = np.array([2, 0, 5])
+    g, i = 17, 3
+    Y = orc.gwo_candidates(c, g, X, lead)
+    a = np.float32(orc.a_of(g, G))
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
+    for j in range(N):
+        Xk = []
+        for k in range(3):
+            w = int(orc.philox(np.array([j // 4, i, g, 3 + k], dtype=np.uint32), key)[j % 4])
+            r1 = np.float32(w >> 16) * np.float32(2.0 ** -16)
+            r2 = np.float32(w & 0xFFFF) * np.float32(2.0 ** -16)
+            A = np.float32(np.float32(2 * a) * r1) - a
+            C = np.float32(2) * r2
+            Xp = X[lead[k], j]
+            d = np.float32(abs(np.float32(C * Xp) - X[i, j]))
+            Xk.append(np.float32(Xp - np.float32(A * d)))
+        y = np.float32(np.float32(np.float32(Xk[0] + Xk[1]) + Xk[2]) / np.float32(3))
+        assert Y[i, j] == np.clip(y, -1, 1), j
+
+
 def test_gwo_a_schedule(orc):
     G = 2000
     a = np.array([orc.a_of(g, G) for g in range(G)])
