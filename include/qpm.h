@@ -163,6 +163,17 @@ qpm_status qpm_release_caches(void);
  * small device buffer.  Errors: kind outside [0, 3] -> QPM_ERR_ARG. */
 qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stream_t stream);
 
+/* Exhaustive self-check of one of the library's arithmetic helpers against
+ * CUDA's own operation (no counterpart in the paper): kind 0 compares the
+ * GWO mean's division by 3 (Markstein's residual correction of x * RN(1/3))
+ * with the IEEE division x / 3 for every one of the 2^32 float bit patterns.
+ * *mismatches (host) receives the number of patterns whose results differ
+ * bitwise (two NaNs agree), *first_bad (host) the smallest such pattern, or
+ * 0xFFFFFFFF.  Synchronous (a few ms); allocates and frees 12 device bytes.
+ * Errors: kind other than 0 or a NULL output -> QPM_ERR_ARG. */
+qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t *first_bad,
+                         qpm_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Relaxed fitness and its adjoint (no counterpart in the paper's method, which
  * works on +-1 domains; used to polish the GWO leaders and exposed for

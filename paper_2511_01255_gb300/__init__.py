@@ -15,7 +15,7 @@ from . import build_lib
 
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc", "qpm_eval_shg", "qpm_eval_multi",
-    "qpm_release_caches", "qpm_measure_issue_peak", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
+    "qpm_release_caches", "qpm_measure_issue_peak", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_set_batch_cluster",
@@ -71,6 +71,7 @@ def lib(build=True):
             "qpm_eval_multi_scratch_bytes": ([i32, i32, i32], ctypes.c_size_t),
             "qpm_release_caches": ([], ctypes.c_int),
             "qpm_measure_issue_peak": ([i32, _P, _P], ctypes.c_int),
+            "qpm_selfcheck": ([i32, _P, _P, _P], ctypes.c_int),
             "qpm_relaxed_saved_floats": ([i32], i64),
             "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
             "qpm_deff_relaxed_bwd": ([_P, _P, i64, i32, _P, _P, _P, _P, i64, _P], ctypes.c_int),
@@ -158,6 +159,15 @@ def qpm_measure_issue_peak(kind, stream=None):
     v = ctypes.c_double()
     _check(lib().qpm_measure_issue_peak(int(kind), ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def qpm_selfcheck(kind, stream=None):
+    """Exhaustive check of a library arithmetic helper against CUDA's operation
+    (kind 0: the division by 3 of the GWO mean); returns (mismatches, first_bad)."""
+    n = ctypes.c_uint64()
+    first = ctypes.c_uint32()
+    _check(lib().qpm_selfcheck(int(kind), ctypes.byref(n), ctypes.byref(first), _stream(stream)))
+    return n.value, first.value
 
 
 def qpm_relaxed_saved_floats(N):

@@ -88,6 +88,18 @@ __device__ __forceinline__ int4 de_indices(const PhiloxKey &K, uint32_t inst, ui
 
 __device__ __forceinline__ float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
 
+// x / 3 rounded to nearest even, by Markstein's residual correction: q = RN(x r)
+// with r = RN(1/3) is within one ulp of the quotient, the residual x - 3q is exact
+// in one FMA, and RN(q + (x - 3q) r) is the correctly rounded quotient.  A zero
+// residual (x = +-0 keeps its sign) or a NaN one (x = +-inf) returns q itself.
+// qpm_selfcheck(0) compares it with the IEEE division over every float.
+__device__ __forceinline__ float div3_rn(float x) {
+  const float r = 0x1.555556p-2f;  // RN(1/3)
+  const float q = __fmul_rn(x, r);
+  const float rem = __fmaf_rn(-q, 3.0f, x);
+  return fabsf(rem) > 0.0f ? __fmaf_rn(rem, r, q) : q;
+}
+
 // ------------------------------------------------------------------ the monoid
 struct Mono {
   float2 A, B, C;

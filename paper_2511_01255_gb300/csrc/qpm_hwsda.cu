@@ -285,7 +285,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
       QPM_PULL(L2.CMP, x.CMP, w[2].CMP, Y2)                                            \
       float v;                                                                         \
       if (I.combine == 0) {                                                            \
-        v = __fdiv_rn(__fadd_rn(__fadd_rn(Y0, Y1), Y2), 3.0f);                          \
+        v = div3_rn(__fadd_rn(__fadd_rn(Y0, Y1), Y2));                                \
       } else {                                                                         \
         const float m0 = fabsf(Y0), m1 = fabsf(Y1), m2 = fabsf(Y2);                    \
         const float s = __fadd_rn(__fadd_rn(m0, m1), m2);                              \

@@ -1,4 +1,5 @@
-// qpm_peaks.cu -- issue-rate microbenchmarks for the ALU roofline.
+// qpm_peaks.cu -- issue-rate microbenchmarks for the ALU roofline, and exhaustive
+// self-checks of the library's own arithmetic helpers against CUDA's.
 //
 // The generation step is bound by FP32 and integer issue (fitness monoid steps,
 // Philox rounds), for which no vendor figure is measured on this machine.  Each
@@ -93,9 +94,56 @@ static __global__ void __launch_bounds__(PK_THREADS) k_peak_philox(uint2 key, ui
   if (s == 0x2545F491u && key.x == 0u) sink[blockIdx.x] = s;
 }
 
+// every float bit pattern x: div3_rn(x) against the IEEE division x / 3 (bitwise;
+// two NaNs agree); per-thread counts and first bad pattern, one atomic each
+static __global__ void k_check_div3(unsigned long long *bad, uint32_t *first) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long n = 0;
+  uint32_t f = 0xFFFFFFFFu;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < (1ull << 32); b += stride) {
+    const float x = __uint_as_float((uint32_t)b);
+    const float q = div3_rn(x), ref = __fdiv_rn(x, 3.0f);
+    const bool same = __float_as_uint(q) == __float_as_uint(ref) || (q != q && ref != ref);
+    if (!same) {
+      ++n;
+      f = min(f, (uint32_t)b);
+    }
+  }
+  if (n) {
+    atomicAdd(bad, n);
+    atomicMin(first, f);
+  }
+}
+
 }  // namespace qpm
 
 using namespace qpm;
+
+extern "C" qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t *first_bad,
+                                    qpm_stream_t stream) {
+  if (!mismatches || !first_bad || kind != 0)
+    return fail(QPM_ERR_ARG, "qpm_selfcheck: kind must be 0 and both outputs non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long *bad = nullptr;
+  QPM_CUDA(cudaMalloc(&bad, sizeof(unsigned long long) + sizeof(uint32_t)));
+  uint32_t *first = (uint32_t *)(bad + 1);
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    k_check_div3<<<sm_count() * 8, 256, 0, s>>>(bad, first);
+    e = cudaGetLastError();
+  }
+  unsigned long long h = 0;
+  uint32_t hf = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, first, sizeof hf, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(bad);
+  if (e != cudaSuccess) return cuda_fail(e, "qpm_selfcheck");
+  *mismatches = (uint64_t)h;
+  *first_bad = hf;
+  return QPM_OK;
+}
 
 extern "C" qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s,
                                              qpm_stream_t stream) {

@@ -164,3 +164,13 @@ def test_issue_peak_microbenchmark(q):
     assert 0 < q.qpm_measure_issue_peak(3) < f / 40 * 1.1
     with pytest.raises(q.QpmError):
         q.qpm_measure_issue_peak(4)
+
+
+def test_div3_matches_ieee_division_on_every_float(q):
+    """The GWO mean divides by 3 with Markstein's residual correction; it must give
+    the IEEE quotient for all 2^32 float bit patterns (the oracle divides in C)."""
+    bad, first = q.qpm_selfcheck(0)
+    assert bad == 0, f"{bad} mismatches, first pattern 0x{first:08x}"
+    assert first == 0xFFFFFFFF
+    with pytest.raises(q.QpmError):
+        q.qpm_selfcheck(1)
