@@ -122,10 +122,15 @@ PHILOX_CALLS_PER_GENE_GEN = 0.25 + 0.75  # crossover word + three GWO words, 4 g
 def algorithmic_lane_ops_per_gene_gen(compensated):
     """Lane instructions the method needs per gene and generation: Philox4x32-10 at
     1.0 calls (80 ops each: a quarter for the crossover word, three quarters for
-    the three GWO words, each giving one leader's r1 and r2), 7 uniforms (3 ops),
-    DE update (7), GWO update (30), two fitness domain-evals (10 plain; 14.25 with
-    Kahan compensation folded in every 8 domains)."""
-    return PHILOX_CALLS_PER_GENE_GEN * 80 + 7 * 3 + 7 + 30 + 2 * (14.25 if compensated else 10)
+    the three GWO words, each giving one leader's r1 and r2); the GWO's 2 r1 - 1
+    and 2 r2 of three leaders (3 ops each: shift, mask-or into a significand,
+    exact subtraction); the crossover test (1 integer compare); DE update (6:
+    difference, FMA, clamp 2, jrand compare, select); GWO update (19: per leader
+    A, the two FMAs and |.|, then two adds, the division by 3 in 3, clamp 2); two
+    fitness domain-evals (10 plain; 14.25 with Kahan compensation folded in every
+    8 domains)."""
+    return (PHILOX_CALLS_PER_GENE_GEN * 80 + 6 * 3 + 1 + 6 + 19
+            + 2 * (14.25 if compensated else 10))
 
 
 def mix_ceiling_gene_gens(compensated, issue):

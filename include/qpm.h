@@ -163,14 +163,21 @@ qpm_status qpm_release_caches(void);
  * small device buffer.  Errors: kind outside [0, 3] -> QPM_ERR_ARG. */
 qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stream_t stream);
 
-/* Exhaustive self-check of one of the library's arithmetic helpers against
- * CUDA's own operation (no counterpart in the paper): kind 0 compares the
- * GWO mean's division by 3 (Markstein's residual correction of x * RN(1/3))
- * with the IEEE division x / 3 for every one of the 2^32 float bit patterns.
- * *mismatches (host) receives the number of patterns whose results differ
- * bitwise (two NaNs agree), *first_bad (host) the smallest such pattern, or
- * 0xFFFFFFFF.  Synchronous (a few ms); allocates and frees 12 device bytes.
- * Errors: kind other than 0 or a NULL output -> QPM_ERR_ARG. */
+/* Exhaustive self-check of one of the library's arithmetic shortcuts against
+ * the plain operation it replaces (no counterpart in the paper), over all 2^32
+ * 32-bit patterns x:
+ *   kind 0: the GWO mean's division by 3 (Markstein's residual correction of
+ *           x * RN(1/3)) against the IEEE division x / 3 (two NaNs agree);
+ *   kind 1: the GWO's 2 r1 - 1 and 2 r2 built in the significand of a float in
+ *           [2, 4) against the same values through int-to-float conversions,
+ *           r1 = (x >> 16) 2^-16, r2 = (x & 0xFFFF) 2^-16;
+ *   kind 2: the crossover test as one integer compare (x <= 256 floor(2^24 CR)
+ *           + 255) against U <= CR in FP32, U = (x >> 8) 2^-24, for CR = 0,
+ *           2^-24, 1.5 2^-24, 0.5, 0.9f and its two neighbours, 1.
+ * *mismatches (host) receives the number of differing results (bitwise for
+ * values), *first_bad (host) the smallest pattern with one, or 0xFFFFFFFF.
+ * Synchronous (a few ms); allocates and frees 12 device bytes.
+ * Errors: kind outside [0, 2] or a NULL output -> QPM_ERR_ARG. */
 qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t *first_bad,
                          qpm_stream_t stream);
 

@@ -162,8 +162,9 @@ def qpm_measure_issue_peak(kind, stream=None):
 
 
 def qpm_selfcheck(kind, stream=None):
-    """Exhaustive check of a library arithmetic helper against CUDA's operation
-    (kind 0: the division by 3 of the GWO mean); returns (mismatches, first_bad)."""
+    """Exhaustive check of a library arithmetic shortcut against the operation it
+    replaces (0: division by 3 of the GWO mean, 1: GWO uniforms built in the
+    significand, 2: integer crossover test); returns (mismatches, first_bad)."""
     n = ctypes.c_uint64()
     first = ctypes.c_uint32()
     _check(lib().qpm_selfcheck(int(kind), ctypes.byref(n), ctypes.byref(first), _stream(stream)))

@@ -121,18 +121,6 @@ __device__ __forceinline__ void put_step(float4 *T, const float4 R[8]) {
   for (int k = 0; k < 8; ++k) T[tix(4 * k + (lane >> 3), lane & 7)] = R[k];
 }
 
-// 16 bytes global -> shared without registers; bytes < 16 zero-fills the rest
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a), "l"(gmem), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
-}
-
 // one step (32 domains from ms) of rows r0..r0+31 copied asynchronously into the
 // tile T with the layout of put_step; 16-byte aligned rows (ld % 4 == 0) only
 __device__ __forceinline__ void copy_step(float4 *T, const float *__restrict__ theta,

@@ -12,6 +12,7 @@
 // left operand on the lower domain indices.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace qpm {
@@ -56,10 +57,22 @@ __device__ __forceinline__ uint4 rng4(const PhiloxKey &K, uint32_t inst, uint32_
 __device__ __forceinline__ float u24(uint32_t w) {
   return __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
 }
-// the two 16-bit halves of one word as uniforms on [0, 1) (exact in FP32): the
-// GWO pair (r1, r2) of one leader and gene
-__device__ __forceinline__ float u16hi(uint32_t w) { return (float)(w >> 16) * 0x1p-16f; }
-__device__ __forceinline__ float u16lo(uint32_t w) { return (float)(w & 0xFFFFu) * 0x1p-16f; }
+// The GWO pair of one leader and gene: r1 = (w >> 16) 2^-16 and r2 = (w & 0xFFFF) 2^-16.
+// The update needs 2 r1 - 1 and 2 r2, built without a conversion: the 16 bits go to
+// the top of the significand of a float in [2, 4), which is then 2 + 2 r, and one
+// exact subtraction (both results lie on the 2^-15 grid in [-1, 2)) leaves the value.
+__device__ __forceinline__ float twice_u16hi_m1(uint32_t w) {  // 2 r1 - 1
+  return __fsub_rn(__uint_as_float(0x40000000u | ((w >> 9) & 0x007FFF80u)), 3.0f);
+}
+__device__ __forceinline__ float twice_u16lo(uint32_t w) {  // 2 r2
+  return __fsub_rn(__uint_as_float(0x40000000u | ((w << 7) & 0x007FFF80u)), 2.0f);
+}
+// crossover test U <= CR for U = (w >> 8) 2^-24 and CR in [0, 1], as one integer
+// compare: (w >> 8) <= floor(2^24 CR)  <=>  w <= 256 floor(2^24 CR) + 255
+static inline uint32_t cr_threshold(float CR) {
+  const double k = floor((double)CR * 16777216.0);
+  return k >= 16777216.0 ? 0xFFFFFFFFu : ((uint32_t)k << 8) | 0xFFu;
+}
 // index in [0, m): Lemire's multiply-shift
 __device__ __forceinline__ uint32_t lemire(uint32_t w, uint32_t m) { return __umulhi(w, m); }
 
@@ -98,6 +111,22 @@ __device__ __forceinline__ float div3_rn(float x) {
   const float q = __fmul_rn(x, r);
   const float rem = __fmaf_rn(-q, 3.0f, x);
   return fabsf(rem) > 0.0f ? __fmaf_rn(rem, r, q) : q;
+}
+
+// ------------------------------------------------------- asynchronous copies
+// 16 bytes global -> shared through L2 (cp.async.cg), no registers held while in
+// flight; bytes < 16 zero-fills the rest.  A thread sees its own copies after
+// cp_async_wait; other threads need a barrier as well.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int bytes = 16) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(a), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most PENDING of this thread's committed groups are still in flight
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
 // ------------------------------------------------------------------ the monoid

@@ -40,6 +40,7 @@ struct InstDev {
   int32_t N, Npad, NP, T, c, G;
   int32_t combine, compensated;
   float F, CR;
+  uint32_t crthr;  // cr_threshold(CR)
   uint32_t inst;
   uint2 key;
   double kappa1, kappa2;
@@ -177,32 +178,83 @@ static __global__ void k_init(InstDev I) {
 
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
+// Row staging (STG): the four rows an update reads (own + three donors or leaders)
+// are copied one group of 4 domains ahead into shared memory with cp.async, so
+// the next group's loads are in flight during this group's arithmetic without
+// holding registers.  Each thread owns 2 stages x 4 rows of 16 bytes at
+// stg[(stage * 4 + row) * blockDim.x + threadIdx.x] (8 blockDim.x float4 per CTA)
+// and reads back only what it copied itself, so no barrier is needed.
+static constexpr int STG_F4_PER_THREAD = 8;
+__device__ __forceinline__ void stage_rows(float4 *stg, int stage, size_t off, const float *r0,
+                                           const float *r1, const float *r2, const float *r3) {
+  const int nt = blockDim.x;
+  float4 *s = stg + (size_t)stage * 4 * nt + threadIdx.x;
+  cp_async16(s, r0 + off);
+  cp_async16(s + nt, r1 + off);
+  cp_async16(s + 2 * nt, r2 + off);
+  cp_async16(s + 3 * nt, r3 + off);
+}
+// the four rows of group k4 (whose copies were committed one iteration earlier);
+// commits the copies of group k4 + 1 first when there is one
+__device__ __forceinline__ void staged_rows(float4 *stg, int k4, int n4, size_t off_next,
+                                            const float *r0, const float *r1, const float *r2,
+                                            const float *r3, float4 &v0, float4 &v1, float4 &v2,
+                                            float4 &v3) {
+  if (k4 + 1 < n4) stage_rows(stg, (k4 + 1) & 1, off_next, r0, r1, r2, r3);
+  cp_async_commit();  // possibly empty: keeps one group per iteration
+  cp_async_wait<1>();
+  const int nt = blockDim.x;
+  const float4 *s = stg + (size_t)(k4 & 1) * 4 * nt + threadIdx.x;
+  v0 = s[0];
+  v1 = s[nt];
+  v2 = s[2 * nt];
+  v3 = s[3 * nt];
+}
+
 // WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
 // r = (r1, r2, r3, jrand) from de_indices
-template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false>
+// STG: rows staged through stg (known slots only, so not with DUAL)
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool STG = false>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
                                             const float4 *tbl, int g, int i, const int4 r,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh,
-                                            int *slot_out = nullptr) {
+                                            int *slot_out = nullptr, float4 *stg = nullptr) {
+  static_assert(!(STG && DUAL), "staged rows need known slots");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
-  const float F = I.Fsched ? I.Fsched[g] : I.F, CR = I.CR;
+  const float F = I.Fsched ? I.Fsched[g] : I.F;
+  const uint32_t crthr = I.crthr;
+  const int n4 = I.c / 4;
+  const float *ra = row_ptr(I, i, si), *rb = row_ptr(I, r.x, s1);
+  const float *rp = row_ptr(I, r.y, s2), *rq = row_ptr(I, r.z, s3);
+  if (STG) {
+    if (n4 > 0) stage_rows(stg, 0, (size_t)t * 4, ra, rb, rp, rq);
+    cp_async_commit();
+  }
   Acc<COMP> acc;
   acc.zero();
-  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+  for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
-    const float4 a = ld_cur<NC, DUAL>(I, i, si, off), b = ld_cur<NC, DUAL>(I, r.x, s1, off);
-    const float4 p = ld_cur<NC, DUAL>(I, r.y, s2, off), q = ld_cur<NC, DUAL>(I, r.z, s3, off);
+    float4 a, b, p, q;
+    if (STG) {
+      staged_rows(stg, k4, n4, off + (size_t)I.T * 4, ra, rb, rp, rq, a, b, p, q);
+    } else {
+      a = ld_cur<NC, DUAL>(I, i, si, off);
+      b = ld_cur<NC, DUAL>(I, r.x, s1, off);
+      p = ld_cur<NC, DUAL>(I, r.y, s2, off);
+      q = ld_cur<NC, DUAL>(I, r.z, s3, off);
+    }
     const int j0 = t * I.c + 4 * k4;
     const uint4 w = rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 u;
-    // v = x_r1 + F (x_r2 - x_r3), clamped; u = v if U <= CR or j == jrand, else x
+    // v = x_r1 + F (x_r2 - x_r3) (the difference rounded, then one FMA), clamped;
+    // u = v if U <= CR (integer form) or j == jrand, else x
 #define QPM_DE1(C, W, J)                                                              \
     {                                                                                 \
-      const float v = clamp1(__fadd_rn(b.C, __fmul_rn(F, __fsub_rn(p.C, q.C))));      \
-      u.C = (u24(w.W) <= CR || (J) == r.w) ? v : a.C;                                 \
+      const float v = clamp1(__fmaf_rn(F, __fsub_rn(p.C, q.C), b.C));                 \
+      u.C = (w.W <= crthr || (J) == r.w) ? v : a.C;                                   \
     }
     QPM_DE1(x, x, j0)
     QPM_DE1(y, y, j0 + 1)
@@ -235,13 +287,15 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 // PRE: the three GWO random words of the thread's first group of 4 domains were
 // drawn earlier (while waiting at the grid barrier) and are passed in wpre.
 // One word per leader and gene gives that leader's (r1, r2) as its 16-bit halves.
-template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool PRE = false>
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool PRE = false,
+          bool STG = false>
 __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
                                int i, int32_t *sel, int la, int lb, int ld, Mono *sh,
                                const uint4 *wpre = nullptr,
                                float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f),
                                float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f),
-                               const int32_t *lslot = nullptr) {
+                               const int32_t *lslot = nullptr, float4 *stg = nullptr) {
+  static_assert(!(STG && (DUAL || PRE)), "staged rows need known slots and no prefetched row");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
   // lslot: the leaders' current slots, when the leader search delivered them
@@ -250,16 +304,27 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   const int sd = lslot ? lslot[2] : sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
   const float a = __fdiv_rn((float)(2 * (I.G - g)), (float)I.G);
-  const float two_a = __fmul_rn(2.0f, a);
+  const int n4 = I.c / 4;
+  const float *rx = row_ptr(I, i, si), *r0 = row_ptr(I, la, sa), *r1 = row_ptr(I, lb, sb);
+  const float *r2 = row_ptr(I, ld, sd);
+  if (STG) {
+    if (n4 > 0) stage_rows(stg, 0, (size_t)t * 4, rx, r0, r1, r2);
+    cp_async_commit();
+  }
   Acc<COMP> acc;
   acc.zero();
-  for (int k4 = 0; k4 < I.c / 4; ++k4) {
+  for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
-    const float4 x = (PRE && k4 == 0) ? (si ? own1 : own0) : ld_cur<NC, DUAL>(I, i, si, off);
-    // a known slot needs one row read, not both
-    const float4 L0 = lslot ? ld_cur<NC, false>(I, la, sa, off) : ld_cur<NC, DUAL>(I, la, sa, off);
-    const float4 L1 = lslot ? ld_cur<NC, false>(I, lb, sb, off) : ld_cur<NC, DUAL>(I, lb, sb, off);
-    const float4 L2 = lslot ? ld_cur<NC, false>(I, ld, sd, off) : ld_cur<NC, DUAL>(I, ld, sd, off);
+    float4 x, L0, L1, L2;
+    if (STG) {
+      staged_rows(stg, k4, n4, off + (size_t)I.T * 4, rx, r0, r1, r2, x, L0, L1, L2);
+    } else {
+      x = (PRE && k4 == 0) ? (si ? own1 : own0) : ld_cur<NC, DUAL>(I, i, si, off);
+      // a known slot needs one row read, not both
+      L0 = lslot ? ld_cur<NC, false>(I, la, sa, off) : ld_cur<NC, DUAL>(I, la, sa, off);
+      L1 = lslot ? ld_cur<NC, false>(I, lb, sb, off) : ld_cur<NC, DUAL>(I, lb, sb, off);
+      L2 = lslot ? ld_cur<NC, false>(I, ld, sd, off) : ld_cur<NC, DUAL>(I, ld, sd, off);
+    }
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
     uint4 w[3];
     if (PRE && k4 == 0) {
@@ -270,12 +335,14 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
       for (int k = 0; k < 3; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
     }
     float4 y;
+    // A = 2 a r1 - a = a (2 r1 - 1), C = 2 r2, D = |C Xp - x|, Y = Xp - A D: each
+    // rounded once (the bracket is exact, the last two are FMAs)
 #define QPM_PULL(Xp, xv, rw, out_)                                                     \
     {                                                                                  \
-      const float A = __fsub_rn(__fmul_rn(two_a, u16hi(rw)), a);                        \
-      const float C = __fmul_rn(2.0f, u16lo(rw));                                       \
-      const float dist = fabsf(__fsub_rn(__fmul_rn(C, Xp), xv));                        \
-      out_ = __fsub_rn(Xp, __fmul_rn(A, dist));                                         \
+      const float A = __fmul_rn(a, twice_u16hi_m1(rw));                                 \
+      const float C = twice_u16lo(rw);                                                  \
+      const float dist = fabsf(__fmaf_rn(C, Xp, -(xv)));                                \
+      out_ = __fmaf_rn(-A, dist, Xp);                                                   \
     }
 #define QPM_GWO1(CMP)                                                                  \
     {                                                                                  \
@@ -535,14 +602,18 @@ __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_
 template <bool COMP, bool TS, bool DUAL, int MAXT = 256>
 static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     k_persist(InstDev I, int g_end, Barrier bar) {
+  // dynamic shared memory: [row staging (long rows)][phasor table (TS)][reduction]
+  constexpr bool STG = !DUAL;
   extern __shared__ float4 dyn[];
   __shared__ int32_t lead_sh[3], lslot_sh[3], own_slot_sh;
-  Mono *sh = (Mono *)(dyn + (TS ? I.Npad : 0));
+  float4 *stg = dyn;
+  float4 *tab = dyn + (STG ? STG_F4_PER_THREAD * blockDim.x : 0);
+  Mono *sh = (Mono *)(tab + (TS ? I.Npad : 0));
   if (TS) {
-    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
+    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) tab[e] = __ldg(I.table + e);
     __syncthreads();
   }
-  const float4 *tbl = TS ? (const float4 *)dyn : I.table;
+  const float4 *tbl = TS ? (const float4 *)tab : I.table;
   const PhiloxKey K = philox_schedule(I.key);
   const bool pre = DUAL && (I.c == 4) && (gridDim.x == (unsigned)I.NP);
   unsigned target = 0;
@@ -555,7 +626,8 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
       int slot = 0;
       const unsigned long long key =
-          de_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, r, sel_in, sel_out, sh, &slot);
+          de_individual<COMP, false, TS, DUAL, false, STG>(I, K, tbl, g, i, r, sel_in, sel_out,
+                                                            sh, &slot, stg);
       // ordered before the barrier's release
       if (threadIdx.x == 0) {
         I.dekey[i] = slot_key(key, i, slot);
@@ -591,9 +663,9 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
         gwo_individual<COMP, false, TS, DUAL, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld,
                                                            sh, wpre, own0, own1, lslot_sh);
       else
-        gwo_individual<COMP, false, TS, DUAL>(I, K, tbl, g, i, sel_out, la, lb, ld, sh, nullptr,
-                                              make_float4(0.f, 0.f, 0.f, 0.f),
-                                              make_float4(0.f, 0.f, 0.f, 0.f), lslot_sh);
+        gwo_individual<COMP, false, TS, DUAL, false, false, STG>(
+            I, K, tbl, g, i, sel_out, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
+            make_float4(0.f, 0.f, 0.f, 0.f), lslot_sh, stg);
     }
     if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -646,10 +718,12 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned crank = CL ? cluster_rank() : 0u, csize = CL ? cluster_size() : 1u;
   const int gw = (int)crank * nw + warp, gstride = (int)csize * nw;  // warp in the cluster
+  // dynamic shared memory: [row staging][phasor table (TS)]
+  float4 *stg = dyn, *tab = dyn + STG_F4_PER_THREAD * blockDim.x;
   if (TS) {
-    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) dyn[e] = __ldg(I.table + e);
+    for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) tab[e] = __ldg(I.table + e);
   }
-  const float4 *tbl = TS ? (const float4 *)dyn : I.table;
+  const float4 *tbl = TS ? (const float4 *)tab : I.table;
   const PhiloxKey K = philox_schedule(I.key);
   int g = *I.gen;
   const int g_end = min(g + gens, I.G);
@@ -662,9 +736,9 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
     if (lane == 0) wk[3 * warp] = wk[3 * warp + 1] = wk[3 * warp + 2] = 0ull;
     for (int i = gw; i < I.NP; i += gstride) {
       const unsigned long long key =
-          de_individual<COMP, false, TS, false, true>(
+          de_individual<COMP, false, TS, false, true, true>(
               I, K, tbl, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out,
-              nullptr);
+              nullptr, nullptr, stg);
       if (lane == 0) {
         unsigned long long a = wk[3 * warp], b = wk[3 * warp + 1], c = wk[3 * warp + 2];
         top3_insert(a, b, c, key);
@@ -707,7 +781,9 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = gw; i < I.NP; i += gstride) {
       if (i == la || i == lb || i == ld) continue;
-      gwo_individual<COMP, false, TS, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld, nullptr);
+      gwo_individual<COMP, false, TS, false, true, false, true>(
+          I, K, tbl, g, i, sel_out, la, lb, ld, nullptr, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
+          make_float4(0.f, 0.f, 0.f, 0.f), nullptr, stg);
     }
     if (I.trace && crank == 0 && threadIdx.x < 3) {
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -981,7 +1057,8 @@ struct qpm_state {
   unsigned long long timeout_ns = 5000000000ull;
   InstDev *d_insts = nullptr;  // device copy of the descriptors (batched form)
   int32_t *d_order = nullptr;  // instances by decreasing work
-  size_t batch_smem = 0;       // 0: table read from global memory
+  size_t batch_smem = 0;       // dynamic shared memory of the batched kernel
+  bool batch_ts = false;       // phasor tables in shared memory (else read from global)
   int grid_batch = 0;
   int batch_cluster = 1;       // CTAs per thread-block cluster in the batched form
   cudaGraphExec_t gexec_b = nullptr;
@@ -1020,14 +1097,16 @@ static Variant variant2(const InstDev &I) {
   v.gwo = (const void *)k_gwo<COMP, DUAL>;
   v.smem = smem_bytes(I.T);
   const bool wide = I.T > 256;
+  // row staging of the long-row variants (DUAL false)
+  const size_t stg = DUAL ? 0 : sizeof(float4) * STG_F4_PER_THREAD * (size_t)I.T;
   if (I.Npad <= TS_MAX_NPAD) {
     v.persist = wide ? (const void *)k_persist<COMP, true, DUAL, 512>
                      : (const void *)k_persist<COMP, true, DUAL>;
-    v.persist_smem = smem_bytes(I.T) + sizeof(float4) * (size_t)I.Npad;
+    v.persist_smem = stg + sizeof(float4) * (size_t)I.Npad + smem_bytes(I.T);
   } else {
     v.persist = wide ? (const void *)k_persist<COMP, false, DUAL, 512>
                      : (const void *)k_persist<COMP, false, DUAL>;
-    v.persist_smem = smem_bytes(I.T);
+    v.persist_smem = stg + smem_bytes(I.T);
   }
   return v;
 }
@@ -1042,7 +1121,8 @@ static Variant variant_of(const InstDev &I) {
 // instance (the largest any instance can need), so occupancy figures computed
 // for one instance stay valid after another instance is set up
 static size_t persist_smem_cap(bool ts) {
-  return smem_bytes(512) + (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
+  return sizeof(float4) * STG_F4_PER_THREAD * 512 + smem_bytes(512) +
+         (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
 }
 
 static const void *batch_kernel(bool ts, bool cl) {
@@ -1052,7 +1132,7 @@ static const void *batch_kernel(bool ts, bool cl) {
 
 // co-resident CTAs of the batched kernel for clusters of `cs` CTAs (a multiple of cs)
 static qpm_status batch_grid(const qpm_state *st, int cs, int *grid) {
-  const void *kb = batch_kernel(st->batch_smem != 0, cs > 1);
+  const void *kb = batch_kernel(st->batch_ts, cs > 1);
   QPM_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->batch_smem));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -1165,6 +1245,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.compensated = q.compensated ? 1 : 0;
     I.F = q.F;
     I.CR = q.CR;
+    I.crthr = cr_threshold(q.CR);
     I.inst = (uint32_t)k;
     I.key = make_uint2((uint32_t)q.seed, (uint32_t)(q.seed >> 32));
     I.kappa1 = p.kappa1;
@@ -1272,8 +1353,9 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (e != cudaSuccess) { cudaFree(st->arena); delete st; return cuda_fail(e, "cudaMemcpy"); }
     int maxpad = 0;
     for (int k = 0; k < n_inst; ++k) maxpad = std::max(maxpad, st->h[k].Npad);
-    st->batch_smem = ((size_t)maxpad * sizeof(float4) <= BATCH_TS_MAX_BYTES)
-                         ? (size_t)maxpad * sizeof(float4) : 0;
+    st->batch_ts = (size_t)maxpad * sizeof(float4) <= BATCH_TS_MAX_BYTES;
+    st->batch_smem = sizeof(float4) * STG_F4_PER_THREAD * BATCH_WARPS * 32 +
+                     (st->batch_ts ? (size_t)maxpad * sizeof(float4) : 0);
     st->grid_batch = 0;  // set on the first batched run (or by qpm_set_batch_cluster)
   }
   e = cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking);
@@ -1395,7 +1477,7 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
         int n = st->n, gens = generations;
         unsigned *queue = st->bar + 3;
         void *args[] = {&st->d_insts, &st->d_order, &n, &queue, &gens};
-        const void *kb = batch_kernel(st->batch_smem != 0, st->batch_cluster > 1);
+        const void *kb = batch_kernel(st->batch_ts, st->batch_cluster > 1);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;

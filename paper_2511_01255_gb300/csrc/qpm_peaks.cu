@@ -115,14 +115,64 @@ static __global__ void k_check_div3(unsigned long long *bad, uint32_t *first) {
   }
 }
 
+// every 32-bit word w: the GWO's 2 r1 - 1 and 2 r2 built in the significand against
+// the same values through conversions, r = (16-bit half) 2^-16 (bitwise)
+static __global__ void k_check_gwo_uniforms(unsigned long long *bad, uint32_t *first) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long n = 0;
+  uint32_t f = 0xFFFFFFFFu;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < (1ull << 32); b += stride) {
+    const uint32_t w = (uint32_t)b;
+    const float r1 = __fmul_rn(__uint2float_rn(w >> 16), 0x1p-16f);
+    const float r2 = __fmul_rn(__uint2float_rn(w & 0xFFFFu), 0x1p-16f);
+    const bool same = __float_as_uint(twice_u16hi_m1(w)) == __float_as_uint(__fsub_rn(__fmul_rn(2.0f, r1), 1.0f)) &&
+                      __float_as_uint(twice_u16lo(w)) == __float_as_uint(__fmul_rn(2.0f, r2));
+    if (!same) {
+      ++n;
+      f = min(f, w);
+    }
+  }
+  if (n) {
+    atomicAdd(bad, n);
+    atomicMin(first, f);
+  }
+}
+
+// every 32-bit word w and each of ncr crossover rates: the integer test against
+// cr_threshold(CR) against U <= CR with U = (w >> 8) 2^-24 in FP32
+struct CrCases {
+  float cr[8];
+  uint32_t thr[8];
+  int n;
+};
+static __global__ void k_check_cr(CrCases c, unsigned long long *bad, uint32_t *first) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long n = 0;
+  uint32_t f = 0xFFFFFFFFu;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < (1ull << 32); b += stride) {
+    const uint32_t w = (uint32_t)b;
+    const float u = u24(w);
+    for (int k = 0; k < c.n; ++k) {
+      if ((w <= c.thr[k]) != (u <= c.cr[k])) {
+        ++n;
+        f = min(f, w);
+      }
+    }
+  }
+  if (n) {
+    atomicAdd(bad, n);
+    atomicMin(first, f);
+  }
+}
+
 }  // namespace qpm
 
 using namespace qpm;
 
 extern "C" qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t *first_bad,
                                     qpm_stream_t stream) {
-  if (!mismatches || !first_bad || kind != 0)
-    return fail(QPM_ERR_ARG, "qpm_selfcheck: kind must be 0 and both outputs non-NULL");
+  if (!mismatches || !first_bad || kind < 0 || kind > 2)
+    return fail(QPM_ERR_ARG, "qpm_selfcheck: kind must be 0, 1 or 2 and both outputs non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long *bad = nullptr;
   QPM_CUDA(cudaMalloc(&bad, sizeof(unsigned long long) + sizeof(uint32_t)));
@@ -130,7 +180,23 @@ extern "C" qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t
   cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, sizeof(uint32_t), s);
   if (e == cudaSuccess) {
-    k_check_div3<<<sm_count() * 8, 256, 0, s>>>(bad, first);
+    const int blocks = sm_count() * 8;
+    if (kind == 0) {
+      k_check_div3<<<blocks, 256, 0, s>>>(bad, first);
+    } else if (kind == 1) {
+      k_check_gwo_uniforms<<<blocks, 256, 0, s>>>(bad, first);
+    } else {
+      // the edges of [0, 1], the rate of the workloads and its FP32 neighbours
+      const float cr[8] = {0.0f, 0x1p-24f, 0x1.8p-24f, 0.5f, nextafterf(0.9f, 0.0f), 0.9f,
+                           nextafterf(0.9f, 1.0f), 1.0f};
+      CrCases c;
+      c.n = 8;
+      for (int k = 0; k < 8; ++k) {
+        c.cr[k] = cr[k];
+        c.thr[k] = cr_threshold(cr[k]);
+      }
+      k_check_cr<<<blocks, 256, 0, s>>>(c, bad, first);
+    }
     e = cudaGetLastError();
   }
   unsigned long long h = 0;

@@ -166,11 +166,18 @@ def test_issue_peak_microbenchmark(q):
         q.qpm_measure_issue_peak(4)
 
 
-def test_div3_matches_ieee_division_on_every_float(q):
-    """The GWO mean divides by 3 with Markstein's residual correction; it must give
-    the IEEE quotient for all 2^32 float bit patterns (the oracle divides in C)."""
-    bad, first = q.qpm_selfcheck(0)
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_arithmetic_shortcuts_exact_on_every_pattern(q, kind):
+    """The kernels' shortcuts give the oracle's plain operation for all 2^32
+    inputs: 0 the GWO mean's division by 3 (Markstein's residual correction)
+    against the IEEE quotient; 1 the GWO's 2 r1 - 1 and 2 r2 built in the
+    significand against int-to-float conversions; 2 the integer crossover test
+    against U <= CR in FP32."""
+    bad, first = q.qpm_selfcheck(kind)
     assert bad == 0, f"{bad} mismatches, first pattern 0x{first:08x}"
     assert first == 0xFFFFFFFF
+
+
+def test_selfcheck_rejects_unknown_kind(q):
     with pytest.raises(q.QpmError):
-        q.qpm_selfcheck(1)
+        q.qpm_selfcheck(3)
