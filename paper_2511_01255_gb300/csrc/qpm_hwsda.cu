@@ -179,36 +179,54 @@ static __global__ void k_init(InstDev I) {
 // ------------------------------------------ Step 2: DE rand/1/bin + selection
 // returns (in thread 0) the key of the survivor for the leader choice
 // Row staging (STG): the four rows an update reads (own + three donors or leaders)
-// are copied one group of 4 domains ahead into shared memory with cp.async, so
-// the next group's loads are in flight during this group's arithmetic without
-// holding registers.  Each thread owns 2 stages x 4 rows of 16 bytes at
-// stg[(stage * 4 + row) * blockDim.x + threadIdx.x] (8 blockDim.x float4 per CTA)
-// and reads back only what it copied itself, so no barrier is needed.
-static constexpr int STG_F4_PER_THREAD = 8;
-__device__ __forceinline__ void stage_rows(float4 *stg, int stage, size_t off, const float *r0,
-                                           const float *r1, const float *r2, const float *r3) {
+// and, when the phasor table is not in shared memory (!TS), the group's four table
+// entries are copied one group of 4 domains ahead into shared memory with
+// cp.async, so the next group's loads are in flight during this group's
+// arithmetic without holding registers.  Each thread owns 2 stages x SPS float4
+// (SPS = 4 rows, + 4 table entries when !TS) at
+// stg[(stage * SPS + k) * blockDim.x + threadIdx.x] and reads back only what it
+// copied itself, so no barrier is needed.
+__host__ __device__ constexpr int stg_f4_per_thread(bool ts) { return ts ? 8 : 16; }
+template <bool TS>
+__device__ __forceinline__ void stage_group(float4 *stg, int stage, size_t off, const float *r0,
+                                            const float *r1, const float *r2, const float *r3,
+                                            const float4 *tb, int T) {
+  constexpr int SPS = stg_f4_per_thread(TS) / 2;
   const int nt = blockDim.x;
-  float4 *s = stg + (size_t)stage * 4 * nt + threadIdx.x;
+  float4 *s = stg + (size_t)stage * SPS * nt + threadIdx.x;
   cp_async16(s, r0 + off);
   cp_async16(s + nt, r1 + off);
   cp_async16(s + 2 * nt, r2 + off);
   cp_async16(s + 3 * nt, r3 + off);
+  if (!TS) {
+    cp_async16(s + 4 * nt, tb);
+    cp_async16(s + 5 * nt, tb + T);
+    cp_async16(s + 6 * nt, tb + 2 * T);
+    cp_async16(s + 7 * nt, tb + 3 * T);
+  }
 }
-// the four rows of group k4 (whose copies were committed one iteration earlier);
-// commits the copies of group k4 + 1 first when there is one
-__device__ __forceinline__ void staged_rows(float4 *stg, int k4, int n4, size_t off_next,
-                                            const float *r0, const float *r1, const float *r2,
-                                            const float *r3, float4 &v0, float4 &v1, float4 &v2,
-                                            float4 &v3) {
-  if (k4 + 1 < n4) stage_rows(stg, (k4 + 1) & 1, off_next, r0, r1, r2, r3);
+// group k4 (whose copies were committed one iteration earlier): commits the copies
+// of group k4 + 1 first when there is one, waits for group k4 and returns this
+// thread's stage base (rows at [0, 4 nt), table entries at [4 nt, 8 nt) if !TS)
+template <bool TS>
+__device__ __forceinline__ const float4 *staged_group(float4 *stg, int k4, int n4, size_t off_next,
+                                                      const float *r0, const float *r1,
+                                                      const float *r2, const float *r3,
+                                                      const float4 *tbl, int T, int t) {
+  constexpr int SPS = stg_f4_per_thread(TS) / 2;
+  if (k4 + 1 < n4)
+    stage_group<TS>(stg, (k4 + 1) & 1, off_next, r0, r1, r2, r3,
+                    tbl + (size_t)(k4 + 1) * 4 * T + t, T);
   cp_async_commit();  // possibly empty: keeps one group per iteration
   cp_async_wait<1>();
-  const int nt = blockDim.x;
-  const float4 *s = stg + (size_t)(k4 & 1) * 4 * nt + threadIdx.x;
-  v0 = s[0];
-  v1 = s[nt];
-  v2 = s[2 * nt];
-  v3 = s[3 * nt];
+  return stg + (size_t)(k4 & 1) * SPS * blockDim.x + threadIdx.x;
+}
+// the push of one staged group: table entries from the stage when !TS
+template <bool COMP, bool TS>
+__device__ __forceinline__ void push4_staged(Acc<COMP> &acc, const float4 *tbl, int T, int k4,
+                                             int t, const float4 *st, float4 u) {
+  if (TS) push4<COMP, true>(acc, tbl, T, k4, t, u);
+  else push4<COMP, true>(acc, st + 4 * blockDim.x, blockDim.x, 0, 0, u);
 }
 
 // WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
@@ -230,7 +248,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
   const float *ra = row_ptr(I, i, si), *rb = row_ptr(I, r.x, s1);
   const float *rp = row_ptr(I, r.y, s2), *rq = row_ptr(I, r.z, s3);
   if (STG) {
-    if (n4 > 0) stage_rows(stg, 0, (size_t)t * 4, ra, rb, rp, rq);
+    if (n4 > 0) stage_group<TS>(stg, 0, (size_t)t * 4, ra, rb, rp, rq, tbl + t, I.T);
     cp_async_commit();
   }
   Acc<COMP> acc;
@@ -238,8 +256,14 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
   for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
     float4 a, b, p, q;
+    const float4 *st = nullptr;
     if (STG) {
-      staged_rows(stg, k4, n4, off + (size_t)I.T * 4, ra, rb, rp, rq, a, b, p, q);
+      st = staged_group<TS>(stg, k4, n4, off + (size_t)I.T * 4, ra, rb, rp, rq, tbl, I.T, t);
+      const int nt = blockDim.x;
+      a = st[0];
+      b = st[nt];
+      p = st[2 * nt];
+      q = st[3 * nt];
     } else {
       a = ld_cur<NC, DUAL>(I, i, si, off);
       b = ld_cur<NC, DUAL>(I, r.x, s1, off);
@@ -262,7 +286,8 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     QPM_DE1(w, w, j0 + 3)
 #undef QPM_DE1
     *(float4 *)(out + off) = u;
-    push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
+    if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, u);
+    else push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
     if (k4 & 1) acc.fold();
   }
   const Mono m = WT ? warp_reduce(acc.get()) : block_reduce(acc.get(), sh);
@@ -308,7 +333,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   const float *rx = row_ptr(I, i, si), *r0 = row_ptr(I, la, sa), *r1 = row_ptr(I, lb, sb);
   const float *r2 = row_ptr(I, ld, sd);
   if (STG) {
-    if (n4 > 0) stage_rows(stg, 0, (size_t)t * 4, rx, r0, r1, r2);
+    if (n4 > 0) stage_group<TS>(stg, 0, (size_t)t * 4, rx, r0, r1, r2, tbl + t, I.T);
     cp_async_commit();
   }
   Acc<COMP> acc;
@@ -316,8 +341,14 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
     float4 x, L0, L1, L2;
+    const float4 *st = nullptr;
     if (STG) {
-      staged_rows(stg, k4, n4, off + (size_t)I.T * 4, rx, r0, r1, r2, x, L0, L1, L2);
+      st = staged_group<TS>(stg, k4, n4, off + (size_t)I.T * 4, rx, r0, r1, r2, tbl, I.T, t);
+      const int nt = blockDim.x;
+      x = st[0];
+      L0 = st[nt];
+      L1 = st[2 * nt];
+      L2 = st[3 * nt];
     } else {
       x = (PRE && k4 == 0) ? (si ? own1 : own0) : ld_cur<NC, DUAL>(I, i, si, off);
       // a known slot needs one row read, not both
@@ -369,7 +400,8 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
 #undef QPM_GWO1
 #undef QPM_PULL
     *(float4 *)(out + off) = y;
-    push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
+    if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, y);
+    else push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
     if (k4 & 1) acc.fold();
   }
   const Mono m = WT ? warp_reduce(acc.get()) : block_reduce(acc.get(), sh);
@@ -607,7 +639,7 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
   extern __shared__ float4 dyn[];
   __shared__ int32_t lead_sh[3], lslot_sh[3], own_slot_sh;
   float4 *stg = dyn;
-  float4 *tab = dyn + (STG ? STG_F4_PER_THREAD * blockDim.x : 0);
+  float4 *tab = dyn + (STG ? stg_f4_per_thread(TS) * blockDim.x : 0);
   Mono *sh = (Mono *)(tab + (TS ? I.Npad : 0));
   if (TS) {
     for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) tab[e] = __ldg(I.table + e);
@@ -719,7 +751,7 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
   const unsigned crank = CL ? cluster_rank() : 0u, csize = CL ? cluster_size() : 1u;
   const int gw = (int)crank * nw + warp, gstride = (int)csize * nw;  // warp in the cluster
   // dynamic shared memory: [row staging][phasor table (TS)]
-  float4 *stg = dyn, *tab = dyn + STG_F4_PER_THREAD * blockDim.x;
+  float4 *stg = dyn, *tab = dyn + stg_f4_per_thread(TS) * blockDim.x;
   if (TS) {
     for (int e = threadIdx.x; e < I.Npad; e += blockDim.x) tab[e] = __ldg(I.table + e);
   }
@@ -1098,8 +1130,9 @@ static Variant variant2(const InstDev &I) {
   v.smem = smem_bytes(I.T);
   const bool wide = I.T > 256;
   // row staging of the long-row variants (DUAL false)
-  const size_t stg = DUAL ? 0 : sizeof(float4) * STG_F4_PER_THREAD * (size_t)I.T;
-  if (I.Npad <= TS_MAX_NPAD) {
+  const bool ts = I.Npad <= TS_MAX_NPAD;
+  const size_t stg = DUAL ? 0 : sizeof(float4) * stg_f4_per_thread(ts) * (size_t)I.T;
+  if (ts) {
     v.persist = wide ? (const void *)k_persist<COMP, true, DUAL, 512>
                      : (const void *)k_persist<COMP, true, DUAL>;
     v.persist_smem = stg + sizeof(float4) * (size_t)I.Npad + smem_bytes(I.T);
@@ -1121,7 +1154,7 @@ static Variant variant_of(const InstDev &I) {
 // instance (the largest any instance can need), so occupancy figures computed
 // for one instance stay valid after another instance is set up
 static size_t persist_smem_cap(bool ts) {
-  return sizeof(float4) * STG_F4_PER_THREAD * 512 + smem_bytes(512) +
+  return sizeof(float4) * stg_f4_per_thread(ts) * 512 + smem_bytes(512) +
          (ts ? sizeof(float4) * (size_t)TS_MAX_NPAD : 0);
 }
 
@@ -1354,7 +1387,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     int maxpad = 0;
     for (int k = 0; k < n_inst; ++k) maxpad = std::max(maxpad, st->h[k].Npad);
     st->batch_ts = (size_t)maxpad * sizeof(float4) <= BATCH_TS_MAX_BYTES;
-    st->batch_smem = sizeof(float4) * STG_F4_PER_THREAD * BATCH_WARPS * 32 +
+    st->batch_smem = sizeof(float4) * stg_f4_per_thread(st->batch_ts) * BATCH_WARPS * 32 +
                      (st->batch_ts ? (size_t)maxpad * sizeof(float4) : 0);
     st->grid_batch = 0;  // set on the first batched run (or by qpm_set_batch_cluster)
   }
