@@ -143,6 +143,23 @@ def mix_ceiling_gene_gens(compensated, issue):
     return 1.0 / t
 
 
+def phase_bound_s_per_gen(N, NP, compensated, issue, hbm_gbs):
+    """Lower bound of one generation's time when each of the two phases runs at its
+    own roofline, for populations far larger than L2: DE reads the target and three
+    random donors and writes the trial (20 B of HBM per gene), GWO reads the target
+    and writes the candidate (8 B per gene; the three leaders' rows stay in L2).
+    Each phase takes the larger of its HBM time and its issue time (its Philox calls
+    at the measured call rate, its other lane-ops at the FFMA rate); the grid
+    barrier between the phases keeps them from overlapping."""
+    ev = 14.25 if compensated else 10
+    genes = N * NP
+    de_issue = genes * (0.25 / issue["philox_calls_per_s"] + (1 + 6 + ev) / (issue["ffma"] * 1e12))
+    gwo_issue = genes * (0.75 / issue["philox_calls_per_s"] + (6 * 3 + 19 + ev) / (issue["ffma"] * 1e12))
+    de_hbm = 20.0 * genes / (hbm_gbs * 1e9)
+    gwo_hbm = 8.0 * genes / (hbm_gbs * 1e9)
+    return max(de_issue, de_hbm) + max(gwo_issue, gwo_hbm)
+
+
 def max_over_ranks(seconds, world, device=None):
     """Slowest rank's step time (the job's time); identity for one process."""
     if world <= 1:
@@ -315,7 +332,11 @@ def run_gpu(args):
             "s_per_run": tp, "gene_gens_per_s": ggp / tp,
             "domain_evals_per_s": (2 * cp["NP"] - 3) * cp["N"] * cp["G"] / tp,
             "alu_frac": algorithmic_lane_ops_per_gene_gen(comp) * ggp / tp / 1e12 / peak_alu,
-            "frac_of_mix_ceiling": ggp / tp / mix_ceiling_gene_gens(comp, issue)}
+            "frac_of_mix_ceiling": ggp / tp / mix_ceiling_gene_gens(comp, issue),
+            "phase_bound_us_per_gen": 1e6 * phase_bound_s_per_gen(cp["N"], cp["NP"], comp, issue,
+                                                                  peak_hbm),
+            "frac_of_phase_bound": phase_bound_s_per_gen(cp["N"], cp["NP"], comp, issue, peak_hbm)
+                                   * cp["G"] / tp}
     prec["workload"] = cp["name"]
 
     # ---------------------------------- adjoint: B = 4096 rows of N = 4096, fwd + bwd

@@ -149,6 +149,27 @@ def test_team_widths_lockstep(q, orc, team):
         assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
+@pytest.mark.parametrize("N,team,mode", [(5000, 256, 2), (11000, 32, 3), (4500, 32, 3)])
+def test_staged_long_rows_lockstep(q, orc, N, team, mode):
+    """Long rows whose update stages rows one group ahead in shared memory: the
+    persistent form with the phasor table too large for shared memory (N = 5000,
+    so the table entries are staged with the rows), and the batched form with
+    the table in global memory (N = 11000) and in shared memory (N = 4500)."""
+    NP, G = 12, 4
+    k1, k2 = 2 * math.pi / 7.1, 2 * math.pi / 1.45
+    st, tr = make(q, N, k1, k2, NP, G, seed=11, comp=1, team=team)
+    assert q.qpm_team_of(st.h) == team
+    st.init()
+    st.run(G, mode)
+    X, f, D = snapshot(st)
+    trace = tr.cpu().numpy()
+    st.close()
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 11)
+    Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+    assert np.array_equal(X, Xo)
+    assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
+
+
 def test_automatic_team_rule(q):
     """team = 0: at most 4 domains per thread up to 256 threads; a single long-row
     instance takes 512 threads when one CTA per SM fills the rounds of individuals
