@@ -485,9 +485,13 @@ __device__ bool last_cta(unsigned *ctr) {
   return is_last;
 }
 
+// dynamic shared memory of k_de and k_gwo: [row + table staging (long rows)][reduction]
 template <bool COMP, bool DUAL>
 static __global__ void k_de(InstDev I) {
-  extern __shared__ Mono sh[];
+  constexpr bool STG = !DUAL;
+  extern __shared__ float4 dyn[];
+  float4 *stg = dyn;
+  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(false) * blockDim.x : 0));
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
@@ -496,8 +500,9 @@ static __global__ void k_de(InstDev I) {
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
     const unsigned long long key =
-        de_individual<COMP, true, false, DUAL>(
-            I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh);
+        de_individual<COMP, true, false, DUAL, false, STG>(
+            I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh,
+            nullptr, stg);
     if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
   }
   if (threadIdx.x == 0) {
@@ -513,7 +518,10 @@ static __global__ void k_de(InstDev I) {
 
 template <bool COMP, bool DUAL>
 static __global__ void k_gwo(InstDev I) {
-  extern __shared__ Mono sh[];
+  constexpr bool STG = !DUAL;
+  extern __shared__ float4 dyn[];
+  float4 *stg = dyn;
+  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(false) * blockDim.x : 0));
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
@@ -521,7 +529,9 @@ static __global__ void k_gwo(InstDev I) {
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
     __syncthreads();  // the reduction scratch is reused
-    gwo_individual<COMP, true, false, DUAL>(I, K, I.table, g, i, sel, la, lb, ld, sh);
+    gwo_individual<COMP, true, false, DUAL, false, false, STG>(
+        I, K, I.table, g, i, sel, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
+        make_float4(0.f, 0.f, 0.f, 0.f), nullptr, stg);
   }
   if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
     const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
@@ -1127,7 +1137,8 @@ static Variant variant2(const InstDev &I) {
   Variant v;
   v.de = (const void *)k_de<COMP, DUAL>;
   v.gwo = (const void *)k_gwo<COMP, DUAL>;
-  v.smem = smem_bytes(I.T);
+  // k_de / k_gwo read the table from global memory: long rows stage rows and table
+  v.smem = (DUAL ? 0 : sizeof(float4) * stg_f4_per_thread(false) * (size_t)I.T) + smem_bytes(I.T);
   const bool wide = I.T > 256;
   // row staging of the long-row variants (DUAL false)
   const bool ts = I.Npad <= TS_MAX_NPAD;
@@ -1190,6 +1201,10 @@ static qpm_status occupancy(const InstDev &I, int *plain, int *persist) {
   int a = 0, a2 = 0, b = 0;
   QPM_CUDA(cudaFuncSetAttribute(v.persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)persist_smem_cap(I.Npad <= TS_MAX_NPAD)));
+  // the largest dynamic shared memory any instance's k_de / k_gwo can need
+  const int plain_cap = (int)(sizeof(float4) * stg_f4_per_thread(false) * 512 + smem_bytes(512));
+  QPM_CUDA(cudaFuncSetAttribute(v.de, cudaFuncAttributeMaxDynamicSharedMemorySize, plain_cap));
+  QPM_CUDA(cudaFuncSetAttribute(v.gwo, cudaFuncAttributeMaxDynamicSharedMemorySize, plain_cap));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, I.T, v.smem));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, v.gwo, I.T, v.smem));
   QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.persist, I.T, v.persist_smem));
