@@ -5,10 +5,12 @@
 // (A, B, C) is a plain sequential accumulation and every phasor read is a
 // broadcast from the segment's phasors, staged once per CTA in shared memory.
 // Float genes arrive 32 domains at a time with coalesced 16-byte loads issued one
-// step ahead and are transposed through a per-warp shared-memory tile; packed sign
+// step ahead and are transposed through a per-warp shared-memory tile.  Packed sign
 // words (32 domains each) are read four at a time straight into the lane of their
-// row.  The warps of a CTA take consecutive row groups of the same segment and
-// synchronise only to stage the phasors.  A second kernel (a warp per row) combines
+// row, and their sweep appends a block of 4 domains per lookup in the sign-block
+// table (the block's monoid triple for its sign pattern, precomputed in FP64) instead
+// of one domain per phasor.  The warps of a CTA take consecutive row groups of the
+// same segment and synchronise only to stage the segment's table.  A second kernel (a warp per row) combines
 // the S segment partials of every row in index order and closes
 // d_eff = phi1 phi2 C + cdiag.
 #include <math.h>
@@ -26,25 +28,20 @@
 namespace qpm {
 
 // partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
-// KIND 0: float genes (vector loads), 1: float genes (scalar loads), 2: packed sign
-// words (KIND 3: the same with 16-byte word loads).  grid (S, ceil(groups / ER_WPC)).
+// KIND 0: float genes (vector loads), 1: float genes (scalar loads).
+// grid (S, ceil(groups / ER_WPC)).
 template <int KIND, bool COMP>
 static __global__ void __launch_bounds__(ER_WPC * 32)
-    k_eval_rows(const void *__restrict__ src, int64_t ld, EvalShape sh,
+    k_eval_rows(const float *__restrict__ src, int64_t ld, EvalShape sh,
                 const float4 *__restrict__ table, float2 *__restrict__ part) {
   extern __shared__ float4 tb[];  // the segment's phasors
-  constexpr bool PACKED = KIND >= 2;
-  __shared__ float4 tile[PACKED ? 1 : ER_WPC][PACKED ? 1 : 256];  // float genes only
+  __shared__ float4 tile[ER_WPC][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
   const bool live = r0 < sh.NP;
   float4 R[8];
-  uint4 W = make_uint4(0u, 0u, 0u, 0u);
-  if (live) {  // the first step is in flight while the phasors are staged
-    if (PACKED) W = er_load_words<KIND == 3>((const uint32_t *)src, ld, sh, r0 + lane, m0);
-    else er_load_genes<KIND == 0>((const float *)src, ld, sh, r0, m0, R);
-  }
+  if (live) er_load_genes<KIND == 0>(src, ld, sh, r0, m0, R);  // in flight while staging
   for (int i = threadIdx.x; i < sh.L; i += blockDim.x) {
     const int m = m0 + i;
     tb[i] = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -53,41 +50,89 @@ static __global__ void __launch_bounds__(ER_WPC * 32)
   if (!live) return;
   ErAcc<COMP> acc;
   acc.zero();
-  if (PACKED) {
-    for (int ms = m0; ms < m1; ms += 128) {
+  float4 *T = tile[warp];
+  for (int ms = m0; ms < m1; ms += 32) {
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
+    __syncwarp();
+    if (ms + 32 < m1) er_load_genes<KIND == 0>(src, ld, sh, r0, ms + 32, R);
+    const float4 *tp = tb + (ms - m0);
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+      const float4 x = T[er_tix(lane, c4)];
+      mono_push(acc.m, er_sgn(x.x), tp[4 * c4]);
+      mono_push(acc.m, er_sgn(x.y), tp[4 * c4 + 1]);
+      mono_push(acc.m, er_sgn(x.z), tp[4 * c4 + 2]);
+      mono_push(acc.m, er_sgn(x.w), tp[4 * c4 + 3]);
+      if (c4 & 1) acc.fold();
+    }
+  }
+  acc.fold();
+  const Mono run = acc.get();
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  const size_t o = (size_t)s * sh.NPpad + r0 + lane;
+  part[o] = run.A;
+  part[stride + o] = run.B;
+  part[2 * stride + o] = run.C;
+}
+
+// Packed sign words: the sign-block sweep.  A CTA of ER_WPC_P warps takes ER_WPC_P
+// row groups of one segment; per block of 4 domains the lane's 4 sign bits select the
+// block's triple among the staged sign-block entries (conflict-free: the 8 entries of
+// a block fall in distinct banks).  The entries are streamed per step of 128 domains
+// (32 blocks, 6 KB) into two buffers with cp.async, the next step's while this one
+// is swept, behind one CTA barrier per step; the sign words come one step ahead in
+// registers.  Compensation folds every 4 blocks.  VECW: 16-byte word loads.
+// grid (S, ceil(groups / ER_WPC_P)).
+template <bool VECW, bool COMP>
+static __global__ void __launch_bounds__(ER_WPC_P * 32)
+    k_eval_packed(const uint32_t *__restrict__ src, int64_t ld, EvalShape sh,
+                  const float4 *__restrict__ blk, float2 *__restrict__ part) {
+  extern __shared__ float4 tb[];  // two steps of sign-block entries
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  const int r0 = (blockIdx.y * ER_WPC_P + warp) * 32;
+  const bool live = r0 < sh.NP;
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
+  // the entries of step k (blocks m0 / 4 + 32 k ..) into buffer k & 1; blocks past
+  // the last one are zero
+  auto stage = [&](int k) {
+    const int b0 = (m0 >> 2) + 32 * k;
+    float4 *dst = tb + (k & 1) * ER_STEP_F4_P;
+    for (int i = threadIdx.x; i < ER_STEP_F4_P; i += blockDim.x) {
+      if (b0 + i / (BLK_F2 / 2) < nb) cp_async16(dst + i, blk + (size_t)b0 * (BLK_F2 / 2) + i);
+      else dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cp_async_commit();
+  };
+  uint4 W = make_uint4(0u, 0u, 0u, 0u);
+  if (live) W = er_load_words<VECW>(src, ld, sh, r0 + lane, m0);
+  stage(0);
+  const float2 *bt = (const float2 *)tb;
+  ErAcc<COMP> acc;
+  acc.zero();
+  for (int k = 0; k < nsteps; ++k) {
+    cp_async_wait<0>();  // this thread's copies of step k
+    __syncthreads();     // everyone's copies of step k; everyone done with step k - 1
+    if (k + 1 < nsteps) stage(k + 1);
+    if (live) {
+      const int ms = m0 + 128 * k;
       const uint4 cur = W;
-      if (ms + 128 < m1) W = er_load_words<KIND == 3>((const uint32_t *)src, ld, sh, r0 + lane, ms + 128);
-      const float4 *tp = tb + (ms - m0);
+      if (ms + 128 < m1) W = er_load_words<VECW>(src, ld, sh, r0 + lane, ms + 128);
+      const float2 *bp = bt + (size_t)(k & 1) * 2 * ER_STEP_F4_P;
       const uint32_t ws[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-#pragma unroll 8
-        for (int e = 0; e < 32; ++e) {
-          mono_push(acc.m, ((ws[q] >> e) & 1u) ? -1.0f : 1.0f, tp[32 * q + e]);
-          if ((e & 7) == 7) acc.fold();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {  // the word's 8 blocks of 4 domains
+          er_push_block(acc.m, (ws[q] >> (4 * j)) & 0xFu, bp + (8 * q + j) * BLK_F2);
+          if ((j & 3) == 3) acc.fold();
         }
       }
     }
-  } else {
-    float4 *T = tile[warp];
-    for (int ms = m0; ms < m1; ms += 32) {
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
-      __syncwarp();
-      if (ms + 32 < m1) er_load_genes<KIND == 0>((const float *)src, ld, sh, r0, ms + 32, R);
-      const float4 *tp = tb + (ms - m0);
-#pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 x = T[er_tix(lane, c4)];
-        mono_push(acc.m, er_sgn(x.x), tp[4 * c4]);
-        mono_push(acc.m, er_sgn(x.y), tp[4 * c4 + 1]);
-        mono_push(acc.m, er_sgn(x.z), tp[4 * c4 + 2]);
-        mono_push(acc.m, er_sgn(x.w), tp[4 * c4 + 3]);
-        if (c4 & 1) acc.fold();
-      }
-    }
   }
+  if (!live) return;
   acc.fold();
   const Mono run = acc.get();
   const size_t stride = (size_t)sh.S * sh.NPpad;
@@ -118,6 +163,8 @@ struct TableEntry {
   double2 *part = nullptr;
   float2 *konst = nullptr;
   cudaEvent_t ready = nullptr;
+  float2 *blk = nullptr;  // sign-block table, built on the first packed call
+  cudaEvent_t blk_ready = nullptr;
 };
 struct ScratchEntry {
   void *ptr = nullptr;
@@ -136,6 +183,8 @@ qpm_status release_device_caches(int dev) {
       cudaFree(it->second.part);
       cudaFree(it->second.konst);
       cudaEventDestroy(it->second.ready);
+      if (it->second.blk) cudaFree(it->second.blk);
+      if (it->second.blk_ready) cudaEventDestroy(it->second.blk_ready);
       it = g_tables.erase(it);
     } else {
       ++it;
@@ -152,9 +201,11 @@ qpm_status release_device_caches(int dev) {
   return QPM_OK;
 }
 
-// phasor table in natural order for (device, problem); built on `stream` on a miss
+// phasor table in natural order for (device, problem); built on `stream` on a miss.
+// blk (if non-NULL) receives the sign-block table, built on `stream` the first time
+// it is asked for.
 qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
-                     const float2 **konst) {
+                     const float2 **konst, const float2 **blk = nullptr) {
   int dev = 0;
   QPM_CUDA(cudaGetDevice(&dev));
   auto key = std::make_tuple(dev, p->N, p->kappa1, p->kappa2);
@@ -180,6 +231,20 @@ qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **t
   }
   *table = it->second.table;
   *konst = it->second.konst;
+  if (blk) {
+    TableEntry &e = it->second;
+    if (!e.blk) {
+      const size_t nb = (size_t)(p->N + 3) / 4;
+      QPM_CUDA(cudaMalloc(&e.blk, sizeof(float2) * BLK_F2 * nb));
+      QPM_CUDA(cudaEventCreateWithFlags(&e.blk_ready, cudaEventDisableTiming));
+      qpm_status st = launch_block_table(p->N, p->kappa1, p->kappa2, e.blk, stream);
+      if (st != QPM_OK) return st;
+      QPM_CUDA(cudaEventRecord(e.blk_ready, stream));
+    } else {
+      QPM_CUDA(cudaStreamWaitEvent(stream, e.blk_ready, 0));
+    }
+    *blk = e.blk;
+  }
   return QPM_OK;
 }
 
@@ -205,7 +270,7 @@ qpm_status get_scratch(cudaStream_t stream, size_t bytes, void **ptr) {
 // split for the row sweep: about `warps_per_sm` warps per SM in total (20 suit
 // float genes; the packed sweep holds fewer registers and runs best near 32),
 // segments a multiple of ER_LQ domains and at most ER_LMAX
-EvalShape eval_rows_shape(int NP, int N, int warps_per_sm) {
+EvalShape eval_rows_shape(int NP, int N, int warps_per_sm, int lmax) {
   EvalShape sh;
   sh.NP = NP;
   sh.N = N;
@@ -215,7 +280,7 @@ EvalShape eval_rows_shape(int NP, int N, int warps_per_sm) {
   const int S0 = std::max(1, (target + sh.groups - 1) / sh.groups);
   int L = (N + S0 - 1) / S0;
   L = (L + ER_LQ - 1) / ER_LQ * ER_LQ;
-  L = std::min(std::max(L, ER_LQ), ER_LMAX);
+  L = std::min(std::max(L, ER_LQ), lmax > 0 ? lmax : ER_LMAX);
   sh.L = L;
   sh.S = (N + L - 1) / L;
   return sh;
@@ -225,14 +290,29 @@ static void launch_eval_rows(int kind, bool comp, const void *src, int64_t ld, c
                              const float4 *table, float2 *part, cudaStream_t stream) {
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
   const size_t smem = sizeof(float4) * (size_t)sh.L;
-#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(src, ld, sh, table, part)
-  switch (kind) {
-    case 0: if (comp) QPM_ER(0, true); else QPM_ER(0, false); break;
-    case 1: if (comp) QPM_ER(1, true); else QPM_ER(1, false); break;
-    case 2: if (comp) QPM_ER(2, true); else QPM_ER(2, false); break;
-    default: if (comp) QPM_ER(3, true); else QPM_ER(3, false); break;
+  const float *g = (const float *)src;
+#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, table, part)
+  if (kind == 0) {
+    if (comp) QPM_ER(0, true); else QPM_ER(0, false);
+  } else {
+    if (comp) QPM_ER(1, true); else QPM_ER(1, false);
   }
 #undef QPM_ER
+}
+
+static void launch_eval_packed(bool vecw, bool comp, const uint32_t *src, int64_t ld,
+                               const EvalShape &sh, const float2 *blk, float2 *part,
+                               cudaStream_t stream) {
+  const dim3 grid(sh.S, (sh.groups + ER_WPC_P - 1) / ER_WPC_P);
+  const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
+  const float4 *b4 = (const float4 *)blk;
+#define QPM_EP(V, C) k_eval_packed<V, C><<<grid, ER_WPC_P * 32, smem, stream>>>(src, ld, sh, b4, part)
+  if (vecw) {
+    if (comp) QPM_EP(true, true); else QPM_EP(true, false);
+  } else {
+    if (comp) QPM_EP(false, true); else QPM_EP(false, false);
+  }
+#undef QPM_EP
 }
 
 static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t ld, int32_t NP,
@@ -245,19 +325,19 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
     return fail(QPM_ERR_ARG, "qpm_eval: leading dimension smaller than the row");
   std::lock_guard<std::mutex> lock(g_mu);
   const float4 *table;
-  const float2 *konst;
-  qpm_status st = get_table(prob, stream, &table, &konst);
+  const float2 *konst, *blk = nullptr;
+  qpm_status st = get_table(prob, stream, &table, &konst, kind == 2 ? &blk : nullptr);
   if (st != QPM_OK) return st;
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, prob->N, kind == 2 ? 32 : 20);
+  const EvalShape sh = kind == 2 ? eval_rows_shape(NP, prob->N, 32, ER_LMAX_P)
+                                 : eval_rows_shape(NP, prob->N, 20);
   void *scratch;
   st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
   if (st != QPM_OK) return st;
   float2 *part = (float2 *)scratch;
   const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
-  if (kind == 2) kind = aligned ? 3 : 2;
-  else kind = aligned ? 0 : 1;
-  launch_eval_rows(kind, comp != 0, src, ld, sh, table, part, stream);
+  if (kind == 2) launch_eval_packed(aligned, comp != 0, (const uint32_t *)src, ld, sh, blk, part, stream);
+  else launch_eval_rows(aligned ? 0 : 1, comp != 0, src, ld, sh, table, part, stream);
   QPM_CUDA(cudaGetLastError());
   k_eval_combine<<<(NP + 7) / 8, 256, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());

@@ -33,6 +33,13 @@ int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
                         double2 *konst64, cudaStream_t stream);
 
+// sign-block table of the packed row sweep: 8 patterns x (A, B, C) as float2 for every
+// block of 4 domains, float2 blk[(8 b + e) * 3 + k], ceil(N / 4) blocks (24 float2
+// = 192 bytes each); built in FP64, rounded to FP32
+qpm_status launch_block_table(int32_t N, double kappa1, double kappa2, float2 *blk,
+                              cudaStream_t stream);
+constexpr int BLK_F2 = 24;  // float2 per block of 4 domains
+
 // natural-order phasor table and FP32 constants of a problem, cached per
 // (device, N, kappa1, kappa2); built on `stream` on a miss (caller holds no lock)
 qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
@@ -46,7 +53,8 @@ struct EvalShape {
 };
 // split of the row sweep (qpm_rows.cuh): segments a multiple of 128 domains,
 // about warps_per_sm warps of work per SM
-EvalShape eval_rows_shape(int NP, int N, int warps_per_sm);
+// (lmax: longest segment, 0 for the phasor sweep's default)
+EvalShape eval_rows_shape(int NP, int N, int warps_per_sm, int lmax = 0);
 
 // current device's SM count (cached per device)
 int sm_count();

@@ -65,6 +65,29 @@ __device__ __forceinline__ uint4 er_load_words(const uint32_t *__restrict__ w, i
 
 __device__ __forceinline__ float er_sgn(float x) { return x < 0.f ? -1.f : 1.f; }
 
+// ---------------------------------------------- sign-block sweep (packed signs)
+// A block of 4 domains with +-1 signs takes one of 16 patterns, and its monoid
+// triple depends on the pattern only: the sign-block table (launch_block_table)
+// holds the 8 with d_0 = +1, and the packed sweep appends one block per lookup.
+constexpr int ER_WPC_P = 8;      // warps (row groups of 32) per CTA of the packed sweep
+constexpr int ER_LMAX_P = 4096;  // longest segment of the packed sweep
+constexpr int ER_STEP_F4_P = 32 * BLK_F2 / 2;  // float4 of entries per step of 128 domains
+
+// append the block with sign pattern e (bit j: d_j = -1) whose 8 stored entries
+// (d_0 = +1) start at E8: a pattern with d_0 = -1 is its complement's entry with A
+// and B negated (an exact sign flip) and C unchanged
+__device__ __forceinline__ void er_push_block(Mono &m, uint32_t e, const float2 *E8) {
+  const uint32_t neg = 0u - (e & 1u);  // all ones when d_0 = -1
+  const float2 *E = E8 + 3 * (((e ^ neg) & 0xFu) >> 1);
+  const float2 a = E[0], b = E[1];
+  const uint32_t sm = neg & 0x80000000u;
+  Mono R;
+  R.A = make_float2(__uint_as_float(__float_as_uint(a.x) ^ sm), __uint_as_float(__float_as_uint(a.y) ^ sm));
+  R.B = make_float2(__uint_as_float(__float_as_uint(b.x) ^ sm), __uint_as_float(__float_as_uint(b.y) ^ sm));
+  R.C = E[2];
+  m = mono_combine(m, R);
+}
+
 // Running monoid of a lane's row: plain FP32 sums, or (COMP) plain sums over blocks
 // of 8 domains Kahan-folded into a compensated triple.
 template <bool COMP>

@@ -10,6 +10,8 @@
 // reduction.
 #include <math.h>
 
+#include <algorithm>
+
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
 
@@ -99,6 +101,64 @@ static __global__ void k_table_finalize(int nparts, const double2 *__restrict__ 
     konst64[1] = cdiag;
     konst64[2] = ps;
   }
+}
+
+// Sign-block table of the packed-sign row sweep (qpm_eval_packed).
+// For +-1 domains a block of 4 consecutive domains 4b .. 4b+3 takes one of 16 sign
+// patterns, and its monoid triple (A, B, C) = (sum_j a_j, sum_j b_j,
+// sum_{j<k} a_k b_j), a = d p2, b = d p1, depends on the pattern only.  The 8
+// patterns with d_{4b} = +1 are stored: pattern e has d_{4b+j} = -1 iff bit j of
+// e << 1 is set (j = 1, 2, 3); the complement of a pattern has A and B negated and
+// C unchanged (C is a sum of products of two signs).  Phases are reduced and their
+// sines and cosines taken in FP64, the triples accumulated in FP64 in index order
+// and rounded once to FP32.  Domains past N have p = 0.
+// Layout: float2 blk[(8 b + e) * 3 + {0: A, 1: B, 2: C}], b < ceil(N / 4).
+static __global__ void __launch_bounds__(TBL_THREADS)
+    k_block_table(int N, int NB, double k1, double k2, float2 *__restrict__ blk) {
+  for (int b = blockIdx.x * TBL_THREADS + threadIdx.x; b < NB; b += gridDim.x * TBL_THREADS) {
+    double p1r[4], p1i[4], p2r[4], p2i[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = 4 * b + j;
+      p1r[j] = p1i[j] = p2r[j] = p2i[j] = 0.0;
+      if (m < N) {
+        double sn, cs;
+        sincos(reduce_2pi((double)m * k1), &sn, &cs);
+        p1r[j] = cs;
+        p1i[j] = -sn;
+        sincos(reduce_2pi((double)m * k2), &sn, &cs);
+        p2r[j] = cs;
+        p2i[j] = -sn;
+      }
+    }
+    for (int e = 0; e < 8; ++e) {
+      double Ar = 0.0, Ai = 0.0, Br = 0.0, Bi = 0.0, Cr = 0.0, Ci = 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double d = (j > 0 && ((e >> (j - 1)) & 1)) ? -1.0 : 1.0;
+        const double ar = d * p2r[j], ai = d * p2i[j];
+        Cr += ar * Br - ai * Bi;  // a_j times the strictly earlier b
+        Ci += ar * Bi + ai * Br;
+        Ar += ar;
+        Ai += ai;
+        Br += d * p1r[j];
+        Bi += d * p1i[j];
+      }
+      float2 *o = blk + ((size_t)8 * b + e) * 3;
+      o[0] = make_float2((float)Ar, (float)Ai);
+      o[1] = make_float2((float)Br, (float)Bi);
+      o[2] = make_float2((float)Cr, (float)Ci);
+    }
+  }
+}
+
+qpm_status launch_block_table(int32_t N, double kappa1, double kappa2, float2 *blk,
+                              cudaStream_t stream) {
+  const int NB = (N + 3) / 4;
+  const int nb = std::min(1024, (NB + TBL_THREADS - 1) / TBL_THREADS);
+  k_block_table<<<nb, TBL_THREADS, 0, stream>>>(N, NB, kappa1, kappa2, blk);
+  QPM_CUDA(cudaGetLastError());
+  return QPM_OK;
 }
 
 int table_part_count(int32_t Npad) {

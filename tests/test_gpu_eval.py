@@ -46,8 +46,30 @@ def test_eval_random_genes(q, orc, N, NP, comp):
     ref = orc.deff_genes(X, K1, K2)
     assert deff_err(D, ref, N).max() < TOL_D
     assert np.allclose(f, D[:, 0] ** 2 + D[:, 1] ** 2, rtol=1e-6, atol=0)
+    # packed signs: the sign-block sweep (4 domains per table lookup)
     Dp, fp = run_eval(q, X, N, K1, K2, comp, packed=True)
-    assert np.array_equal(D, Dp)  # same scan order from genes and from packed bits
+    assert deff_err(Dp, ref, N).max() < TOL_D
+    assert np.allclose(fp, Dp[:, 0] ** 2 + Dp[:, 1] ** 2, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("N", [1, 5, 30, 33, 1001])
+def test_packed_ignores_bits_past_the_row(q, N):
+    """Sign bits of the last word beyond domain N - 1 do not change d_eff: the
+    sign-block entries of a block that straddles N carry zero phasors there."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    X = W.random_genes(6, N, seed=N + 1)
+    words = W.pack_signs(X, N)
+    dirty = words.copy()
+    if N % 32:
+        dirty[:, -1] |= np.uint32((0xFFFFFFFF << (N % 32)) & 0xFFFFFFFF)
+    res = []
+    for w in (words, dirty):
+        D = torch.empty((6, 2), dtype=torch.float32, device="cuda")
+        q.qpm_eval_packed(N, K1, K2, torch.from_numpy(w.view(np.int32)).cuda(), D, None, 0)
+        torch.cuda.synchronize()
+        res.append(D.cpu().numpy())
+    assert np.array_equal(res[0], res[1])
 
 
 def test_eval_strided_rows_and_random_kappa(q, orc):
