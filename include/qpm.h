@@ -136,16 +136,17 @@ size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP);
  * owned by an external allocator, real-time paths that cannot afford the
  * implicit synchronisation of cudaMalloc).  Same arguments, layouts and result
  * as qpm_eval; it allocates nothing (no cudaMalloc/cudaFree, no allocating
- * library routine).  Its scratch -- the phasor table and the partial sums of the
- * scan -- lives in one fixed 8 MiB array in the library's device image, which
- * every GPU that loads the library holds until the process exits.
+ * library routine).  Its scratch -- the phasor table and the sign-block table
+ * (16 + 48 bytes per domain), the constants and the partial sums of the scan --
+ * lives in one fixed 16 MiB array in the library's device image, which every GPU
+ * that loads the library holds until the process exits.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make this first call
  *     before any stream capture on that device.
- *   - N and NP whose scratch needs exceed 8 MiB (about N = 250k domains with
- *     the default segment split) are rejected with QPM_ERR_ARG and a message
+ *   - N and NP whose scratch needs exceed 16 MiB (about N = 230k domains for a
+ *     few rows, N = 1.8e5 for 1024 rows) are rejected with QPM_ERR_ARG and a message
  *     stating the bytes needed; nothing is enqueued.
- *   - Every call rebuilds the phasor table in the shared array, so calls that
+ *   - Every call rebuilds the tables in the shared array, so calls that
  *     overlap on the GPU (different streams, or graphs replayed concurrently)
  *     race on it and must be serialised by the caller.  Nothing in the array
  *     needs to start at zero: each call writes every word it reads. */

@@ -147,7 +147,7 @@ def qpm_eval_packed(N, kappa1, kappa2, signs, d_eff, fit=None, compensated=0, st
 
 
 def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, stream=None):
-    """qpm_eval without any device allocation (fixed 8 MiB scratch inside the library)."""
+    """qpm_eval without any device allocation (fixed 16 MiB scratch inside the library)."""
     p = _problem(N, kappa1, kappa2)
     NP, ld = _rows(genes, "genes")
     _check(lib().qpm_eval_noalloc(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),

@@ -2,15 +2,15 @@
 //
 // Work split: a warp takes 32 rows (lane = row) and one segment of L domains (L a
 // multiple of 128) and sweeps it in index order, so every row's running monoid
-// (A, B, C) is a plain sequential accumulation and every phasor read is a
-// broadcast from the segment's phasors, staged once per CTA in shared memory.
+// (A, B, C) is a plain sequential accumulation.  The sweep appends a block of 4
+// domains per lookup in the sign-block table (the block's monoid triple for its sign
+// pattern, precomputed in FP64), whose entries are streamed into shared memory per
+// step of 128 domains, the next step's with cp.async while this one is swept.
 // Float genes arrive 32 domains at a time with coalesced 16-byte loads issued one
 // step ahead and are transposed through a per-warp shared-memory tile.  Packed sign
 // words (32 domains each) are read four at a time straight into the lane of their
-// row, and their sweep appends a block of 4 domains per lookup in the sign-block
-// table (the block's monoid triple for its sign pattern, precomputed in FP64) instead
-// of one domain per phasor.  The warps of a CTA take consecutive row groups of the
-// same segment and synchronise only to stage the segment's table.  A second kernel (a warp per row) combines
+// row.  The warps of a CTA take consecutive row groups of the same segment and
+// synchronise once per step of 128 domains.  A second kernel (a warp per row) combines
 // the S segment partials of every row in index order and closes
 // d_eff = phi1 phi2 C + cdiag.
 #include <math.h>
@@ -29,45 +29,48 @@ namespace qpm {
 
 // partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
 // KIND 0: float genes (vector loads), 1: float genes (scalar loads).
-// grid (S, ceil(groups / ER_WPC)).
+// blk: the problem's sign-block table, read as float4.  grid (S, ceil(groups / ER_WPC)).
 template <int KIND, bool COMP>
-static __global__ void __launch_bounds__(ER_WPC * 32)
+static __global__ void __launch_bounds__(ER_WPC * 32, 5)
     k_eval_rows(const float *__restrict__ src, int64_t ld, EvalShape sh,
-                const float4 *__restrict__ table, float2 *__restrict__ part) {
-  extern __shared__ float4 tb[];  // the segment's phasors
+                const float4 *__restrict__ blk, float2 *__restrict__ part) {
+  extern __shared__ float4 tb[];  // two steps of sign-block entries
   __shared__ float4 tile[ER_WPC][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
   const bool live = r0 < sh.NP;
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
   float4 R[8];
-  if (live) er_load_genes<KIND == 0>(src, ld, sh, r0, m0, R);  // in flight while staging
-  for (int i = threadIdx.x; i < sh.L; i += blockDim.x) {
-    const int m = m0 + i;
-    tb[i] = m < sh.N ? __ldg(table + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  __syncthreads();
-  if (!live) return;
+  if (live) er_load_genes<KIND == 0>(src, ld, sh, r0, m0, R);
+  er_stage_step(tb, blk, m0, 0, nb);
+  const float2 *bt = (const float2 *)tb;
   ErAcc<COMP> acc;
   acc.zero();
   float4 *T = tile[warp];
-  for (int ms = m0; ms < m1; ms += 32) {
-    __syncwarp();
+  for (int k = 0; k < nsteps; ++k) {
+    cp_async_wait<0>();  // this thread's copies of step k
+    __syncthreads();     // everyone's copies of step k; everyone done with step k - 1
+    if (k + 1 < nsteps) er_stage_step(tb + ((k + 1) & 1) * ER_STEP_F4_P, blk, m0, k + 1, nb);
+    if (!live) continue;
+    const float2 *bp = bt + (size_t)(k & 1) * 2 * ER_STEP_F4_P;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {  // 4 sub-steps of 32 domains
+      const int ms = m0 + 128 * k + 32 * q;
+      if (ms >= m1) break;
+      __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
-    __syncwarp();
-    if (ms + 32 < m1) er_load_genes<KIND == 0>(src, ld, sh, r0, ms + 32, R);
-    const float4 *tp = tb + (ms - m0);
+      for (int j = 0; j < 8; ++j) T[er_tix(4 * j + (lane >> 3), lane & 7)] = R[j];
+      __syncwarp();
+      if (ms + 32 < m1) er_load_genes<KIND == 0>(src, ld, sh, r0, ms + 32, R);
 #pragma unroll
-    for (int c4 = 0; c4 < 8; ++c4) {
-      const float4 x = T[er_tix(lane, c4)];
-      mono_push(acc.m, er_sgn(x.x), tp[4 * c4]);
-      mono_push(acc.m, er_sgn(x.y), tp[4 * c4 + 1]);
-      mono_push(acc.m, er_sgn(x.z), tp[4 * c4 + 2]);
-      mono_push(acc.m, er_sgn(x.w), tp[4 * c4 + 3]);
-      if (c4 & 1) acc.fold();
+      for (int c4 = 0; c4 < 8; ++c4) {  // the sub-step's 8 blocks of 4 domains
+        er_push_block(acc.m, er_pattern(T[er_tix(lane, c4)]), bp + (8 * q + c4) * BLK_F2);
+        if ((c4 & 3) == 3) acc.fold();
+      }
     }
   }
+  if (!live) return;
   acc.fold();
   const Mono run = acc.get();
   const size_t stride = (size_t)sh.S * sh.NPpad;
@@ -95,27 +98,16 @@ static __global__ void __launch_bounds__(ER_WPC_P * 32)
   const int r0 = (blockIdx.y * ER_WPC_P + warp) * 32;
   const bool live = r0 < sh.NP;
   const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
-  // the entries of step k (blocks m0 / 4 + 32 k ..) into buffer k & 1; blocks past
-  // the last one are zero
-  auto stage = [&](int k) {
-    const int b0 = (m0 >> 2) + 32 * k;
-    float4 *dst = tb + (k & 1) * ER_STEP_F4_P;
-    for (int i = threadIdx.x; i < ER_STEP_F4_P; i += blockDim.x) {
-      if (b0 + i / (BLK_F2 / 2) < nb) cp_async16(dst + i, blk + (size_t)b0 * (BLK_F2 / 2) + i);
-      else dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    cp_async_commit();
-  };
   uint4 W = make_uint4(0u, 0u, 0u, 0u);
   if (live) W = er_load_words<VECW>(src, ld, sh, r0 + lane, m0);
-  stage(0);
+  er_stage_step(tb, blk, m0, 0, nb);
   const float2 *bt = (const float2 *)tb;
   ErAcc<COMP> acc;
   acc.zero();
   for (int k = 0; k < nsteps; ++k) {
     cp_async_wait<0>();  // this thread's copies of step k
     __syncthreads();     // everyone's copies of step k; everyone done with step k - 1
-    if (k + 1 < nsteps) stage(k + 1);
+    if (k + 1 < nsteps) er_stage_step(tb + ((k + 1) & 1) * ER_STEP_F4_P, blk, m0, k + 1, nb);
     if (live) {
       const int ms = m0 + 128 * k;
       const uint4 cur = W;
@@ -287,11 +279,12 @@ EvalShape eval_rows_shape(int NP, int N, int warps_per_sm, int lmax) {
 }
 
 static void launch_eval_rows(int kind, bool comp, const void *src, int64_t ld, const EvalShape &sh,
-                             const float4 *table, float2 *part, cudaStream_t stream) {
+                             const float2 *blk, float2 *part, cudaStream_t stream) {
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
-  const size_t smem = sizeof(float4) * (size_t)sh.L;
+  const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
   const float *g = (const float *)src;
-#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, table, part)
+  const float4 *b4 = (const float4 *)blk;
+#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part)
   if (kind == 0) {
     if (comp) QPM_ER(0, true); else QPM_ER(0, false);
   } else {
@@ -326,7 +319,7 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   std::lock_guard<std::mutex> lock(g_mu);
   const float4 *table;
   const float2 *konst, *blk = nullptr;
-  qpm_status st = get_table(prob, stream, &table, &konst, kind == 2 ? &blk : nullptr);
+  qpm_status st = get_table(prob, stream, &table, &konst, &blk);
   if (st != QPM_OK) return st;
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
   const EvalShape sh = kind == 2 ? eval_rows_shape(NP, prob->N, 32, ER_LMAX_P)
@@ -337,7 +330,7 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   float2 *part = (float2 *)scratch;
   const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
   if (kind == 2) launch_eval_packed(aligned, comp != 0, (const uint32_t *)src, ld, sh, blk, part, stream);
-  else launch_eval_rows(aligned ? 0 : 1, comp != 0, src, ld, sh, table, part, stream);
+  else launch_eval_rows(aligned ? 0 : 1, comp != 0, src, ld, sh, blk, part, stream);
   QPM_CUDA(cudaGetLastError());
   k_eval_combine<<<(NP + 7) / 8, 256, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
@@ -355,7 +348,7 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
 // lives in one file-scope device array of fixed size that every GPU loading
 // this library holds until the process exits.
 // ---------------------------------------------------------------------------
-static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;  // 8 MiB
+static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -398,29 +391,33 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   const EvalShape sh = eval_rows_shape(NP, prob->N, 20);
   const int32_t Npad = (prob->N + 3) & ~3;
   const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
+  const size_t b_blk = up256(sizeof(float2) * BLK_F2 * (size_t)(Npad / 4));
   const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));
   const size_t b_konst = 256;
   const size_t b_part = up256(sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad);
-  const size_t need = b_table + b_tpart + b_konst + b_part;
+  const size_t need = b_table + b_blk + b_tpart + b_konst + b_part;
   if (need > NOALLOC_SCRATCH_BYTES)
     return fail(QPM_ERR_ARG, "qpm_eval_noalloc: N and NP need " + std::to_string(need) +
-                                 " bytes of scratch, more than the fixed 8 MiB (8388608)");
+                                 " bytes of scratch, more than the fixed 16 MiB (16777216)");
   void *base = nullptr;
   qpm_status st = noalloc_base(&base);
   if (st != QPM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   char *p = (char *)base;
   float4 *table = (float4 *)p;
-  double2 *tpart = (double2 *)(p + b_table);
-  float2 *konst = (float2 *)(p + b_table + b_tpart);
-  float2 *part = (float2 *)(p + b_table + b_tpart + b_konst);
-  // every word read below is written first in this call (table, its partial
-  // sums, every segment partial of every padded row), so nothing needs zeroing
+  float2 *blk = (float2 *)(p + b_table);
+  double2 *tpart = (double2 *)(p + b_table + b_blk);
+  float2 *konst = (float2 *)(p + b_table + b_blk + b_tpart);
+  float2 *part = (float2 *)(p + b_table + b_blk + b_tpart + b_konst);
+  // every word read below is written first in this call (tables, the constants'
+  // partial sums, every segment partial of every padded row), so nothing needs zeroing
   TableSpec ts{prob->N, Npad, 1, Npad, prob->kappa1, prob->kappa2};
   st = launch_table(ts, table, tpart, konst, nullptr, s);
   if (st != QPM_OK) return st;
+  st = launch_block_table(prob->N, prob->kappa1, prob->kappa2, blk, s);
+  if (st != QPM_OK) return st;
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
-  launch_eval_rows(vec ? 0 : 1, compensated != 0, genes, ld, sh, table, part, s);
+  launch_eval_rows(vec ? 0 : 1, compensated != 0, genes, ld, sh, blk, part, s);
   QPM_CUDA(cudaGetLastError());
   k_eval_combine<<<(NP + 7) / 8, 256, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
@@ -431,6 +428,13 @@ qpm_status qpm::cached_table(const qpm_problem *p, cudaStream_t stream, const fl
                              const float2 **konst) {
   std::lock_guard<std::mutex> lock(g_mu);
   return get_table(p, stream, table, konst);
+}
+
+qpm_status qpm::cached_block_table(const qpm_problem *p, cudaStream_t stream, const float2 **blk,
+                                   const float2 **konst) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const float4 *table;
+  return get_table(p, stream, &table, konst, blk);
 }
 
 extern "C" qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld,

@@ -33,7 +33,7 @@ int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
                         double2 *konst64, cudaStream_t stream);
 
-// sign-block table of the packed row sweep: 8 patterns x (A, B, C) as float2 for every
+// sign-block table of the row sweeps: 8 patterns x (A, B, C) as float2 for every
 // block of 4 domains, float2 blk[(8 b + e) * 3 + k], ceil(N / 4) blocks (24 float2
 // = 192 bytes each); built in FP64, rounded to FP32
 qpm_status launch_block_table(int32_t N, double kappa1, double kappa2, float2 *blk,
@@ -44,6 +44,9 @@ constexpr int BLK_F2 = 24;  // float2 per block of 4 domains
 // (device, N, kappa1, kappa2); built on `stream` on a miss (caller holds no lock)
 qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
                         const float2 **konst);
+// the same cache entry's sign-block table (built on `stream` the first time)
+qpm_status cached_block_table(const qpm_problem *p, cudaStream_t stream, const float2 **blk,
+                              const float2 **konst);
 
 // split of qpm_eval-style work: S segments of L domains, rows in groups of 32
 struct EvalShape {

@@ -92,11 +92,13 @@ static __global__ void __launch_bounds__(SHG_THREADS)
 static constexpr int MW_KMAX = 4;
 
 struct MultiTables {
-  const float4 *t[MW_KMAX];
+  const float4 *t[MW_KMAX];  // sign-block tables (launch_block_table), read as float4
   const float2 *konst[MW_KMAX];
 };
 
-// dynamic shared memory: the K phasor tables of the segment, [K][L] float4.
+// The qpm_eval sweep with K sign-block tables (the same segments and order, so K = 1
+// reproduces qpm_eval's plain scan bit for bit).  Dynamic shared memory: two steps of
+// the K tables' entries, [2][K][ER_STEP_F4_P] float4.
 // Partials as for qpm_eval, one set per problem: part[((3k + comp) * S + s) * NPpad + i].
 // grid (S, ceil(groups / ER_WPC)).
 template <bool VEC, int K>
@@ -109,38 +111,46 @@ static __global__ void __launch_bounds__(ER_WPC * 32)
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
   const bool live = r0 < sh.NP;
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
   float4 R[8];
   if (live) er_load_genes<VEC>(genes, ld, sh, r0, m0, R);
+  // step k of problem p in buffer ((k & 1) * K + p); one commit group per step
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-    for (int i = threadIdx.x; i < sh.L; i += blockDim.x) {
-      const int m = m0 + i;
-      tb[k * sh.L + i] = m < sh.N ? __ldg(mt.t[k] + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  __syncthreads();
-  if (!live) return;
+  for (int p = 0; p < K; ++p) er_stage_step(tb + p * ER_STEP_F4_P, mt.t[p], m0, 0, nb);
+  const float2 *bt = (const float2 *)tb;
   Mono acc[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = mono_zero();
+  for (int p = 0; p < K; ++p) acc[p] = mono_zero();
   float4 *T = tile[warp];
-  for (int ms = m0; ms < m1; ms += 32) {
-    __syncwarp();
+  for (int k = 0; k < nsteps; ++k) {
+    cp_async_wait<0>();
+    __syncthreads();
+    if (k + 1 < nsteps) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) T[er_tix(4 * k + (lane >> 3), lane & 7)] = R[k];
-    __syncwarp();
-    if (ms + 32 < m1) er_load_genes<VEC>(genes, ld, sh, r0, ms + 32, R);
-    const float4 *tp = tb + (ms - m0);
+      for (int p = 0; p < K; ++p)
+        er_stage_step(tb + (((k + 1) & 1) * K + p) * ER_STEP_F4_P, mt.t[p], m0, k + 1, nb);
+    }
+    if (!live) continue;
+    const float2 *bp = bt + (size_t)(k & 1) * K * 2 * ER_STEP_F4_P;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int ms = m0 + 128 * k + 32 * q;
+      if (ms >= m1) break;
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) T[er_tix(4 * j + (lane >> 3), lane & 7)] = R[j];
+      __syncwarp();
+      if (ms + 32 < m1) er_load_genes<VEC>(genes, ld, sh, r0, ms + 32, R);
 #pragma unroll 2
-    for (int c4 = 0; c4 < 8; ++c4) {
-      const float4 x = T[er_tix(lane, c4)];
-      const float d[4] = {er_sgn(x.x), er_sgn(x.y), er_sgn(x.z), er_sgn(x.w)};
+      for (int c4 = 0; c4 < 8; ++c4) {
+        const uint32_t e = er_pattern(T[er_tix(lane, c4)]);
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mono_push(acc[k], d[j], tp[k * sh.L + 4 * c4 + j]);
+        for (int p = 0; p < K; ++p)
+          er_push_block(acc[p], e, bp + (size_t)p * 2 * ER_STEP_F4_P + (8 * q + c4) * BLK_F2);
       }
     }
   }
+  if (!live) return;
   const size_t stride = (size_t)sh.S * sh.NPpad;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -215,8 +225,10 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     mt.konst[k] = nullptr;
   }
   for (int k = 0; k < K; ++k) {
-    qpm_status st = cached_table(&probs[k], s, &mt.t[k], &mt.konst[k]);
+    const float2 *blk;
+    qpm_status st = cached_block_table(&probs[k], s, &blk, &mt.konst[k]);
     if (st != QPM_OK) return st;
+    mt.t[k] = (const float4 *)blk;
   }
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
   const EvalShape sh = eval_rows_shape(NP, N, 20);
@@ -226,7 +238,7 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
   float2 *part = (float2 *)scratch;
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
-  const size_t smem = sizeof(float4) * (size_t)K * sh.L;
+  const size_t smem = sizeof(float4) * 2 * (size_t)K * ER_STEP_F4_P;
 #define QPM_MW(KK)                                                                          \
   {                                                                                         \
     const void *fn = vec ? (const void *)k_multi_rows<true, KK> : (const void *)k_multi_rows<false, KK>; \

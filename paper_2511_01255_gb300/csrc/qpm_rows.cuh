@@ -1,15 +1,19 @@
 // qpm_rows.cuh -- the row sweep shared by the fitness kernels of qpm_eval and of
 // the multi-wavelength objective: a warp takes 32 rows (lane = row) and one
-// segment of L domains (a multiple of ER_LQ) and walks it in index order.
+// segment of L domains (a multiple of ER_LQ) and walks it in index order, one block
+// of 4 domains at a time: a block of +-1 domains takes one of 16 sign patterns and
+// its monoid triple depends on the pattern only, so the sign-block table
+// (launch_block_table) holds the triples and the sweep appends one per lookup.  The
+// table entries are streamed into shared memory per step of 128 domains.
 #pragma once
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
 
 namespace qpm {
 
-constexpr int ER_WPC = 4;      // warps (row groups of 32) per CTA
+constexpr int ER_WPC = 4;      // warps (row groups of 32) per CTA of the float sweeps
 constexpr int ER_LQ = 128;     // segment length quantum (domains)
-constexpr int ER_LMAX = 1920;  // longest segment: its phasors fit the default 48 KB
+constexpr int ER_LMAX = 1920;  // longest segment of the float sweeps
 
 // per-warp tile: 32 rows x 32 domains as float4 [row][c4], the column xor-swizzled by
 // the row so that both the staging stores (8 columns of a row per quarter-warp) and
@@ -63,15 +67,28 @@ __device__ __forceinline__ uint4 er_load_words(const uint32_t *__restrict__ w, i
   return v;
 }
 
-__device__ __forceinline__ float er_sgn(float x) { return x < 0.f ? -1.f : 1.f; }
+// sign pattern of 4 genes: bit j set iff gene j < 0 (d_j = -1; -0.0 counts as +1)
+__device__ __forceinline__ uint32_t er_pattern(const float4 &x) {
+  return (x.x < 0.f ? 1u : 0u) | (x.y < 0.f ? 2u : 0u) | (x.z < 0.f ? 4u : 0u) |
+         (x.w < 0.f ? 8u : 0u);
+}
 
-// ---------------------------------------------- sign-block sweep (packed signs)
-// A block of 4 domains with +-1 signs takes one of 16 patterns, and its monoid
-// triple depends on the pattern only: the sign-block table (launch_block_table)
-// holds the 8 with d_0 = +1, and the packed sweep appends one block per lookup.
 constexpr int ER_WPC_P = 8;      // warps (row groups of 32) per CTA of the packed sweep
 constexpr int ER_LMAX_P = 4096;  // longest segment of the packed sweep
 constexpr int ER_STEP_F4_P = 32 * BLK_F2 / 2;  // float4 of entries per step of 128 domains
+
+// the sign-block entries of step k of a segment starting at m0 (blocks
+// m0 / 4 + 32 k .. + 31) into buf, copied with cp.async by the whole CTA and
+// committed as one group; blocks past the last of the problem are zero
+__device__ __forceinline__ void er_stage_step(float4 *buf, const float4 *__restrict__ blk, int m0,
+                                              int k, int nb) {
+  const int b0 = (m0 >> 2) + 32 * k;
+  for (int i = threadIdx.x; i < ER_STEP_F4_P; i += blockDim.x) {
+    if (b0 + i / (BLK_F2 / 2) < nb) cp_async16(buf + i, blk + (size_t)b0 * (BLK_F2 / 2) + i);
+    else buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  cp_async_commit();
+}
 
 // append the block with sign pattern e (bit j: d_j = -1) whose 8 stored entries
 // (d_0 = +1) start at E8: a pattern with d_0 = -1 is its complement's entry with A
@@ -88,8 +105,8 @@ __device__ __forceinline__ void er_push_block(Mono &m, uint32_t e, const float2 
   m = mono_combine(m, R);
 }
 
-// Running monoid of a lane's row: plain FP32 sums, or (COMP) plain sums over blocks
-// of 8 domains Kahan-folded into a compensated triple.
+// Running monoid of a lane's row: plain FP32 sums, or (COMP) plain sums over 16
+// domains (4 sign blocks) Kahan-folded into a compensated triple.
 template <bool COMP>
 struct ErAcc {
   Mono m;

@@ -103,7 +103,7 @@ static __global__ void k_table_finalize(int nparts, const double2 *__restrict__ 
   }
 }
 
-// Sign-block table of the packed-sign row sweep (qpm_eval_packed).
+// Sign-block table of the row sweeps (qpm_eval, qpm_eval_packed, qpm_eval_multi).
 // For +-1 domains a block of 4 consecutive domains 4b .. 4b+3 takes one of 16 sign
 // patterns, and its monoid triple (A, B, C) = (sum_j a_j, sum_j b_j,
 // sum_{j<k} a_k b_j), a = d p2, b = d p1, depends on the pattern only.  The 8

@@ -72,4 +72,4 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(q):
     D = torch.empty((NP, 2), dtype=torch.float32, device="cuda")
     with pytest.raises(q.QpmError) as e:
         q.qpm_eval_noalloc(N, 1.0, 2.0, X, D)
-    assert e.value.status == 1 and "8 MiB" in str(e.value)
+    assert e.value.status == 1 and "16 MiB" in str(e.value)
