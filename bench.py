@@ -128,14 +128,14 @@ PACKED_OPS_PER_DOMAIN = 22 / 4
 def algorithmic_lane_ops_per_gene_gen(compensated):
     """Lane instructions the method needs per gene and generation: Philox4x32-10 at
     1.0 calls (80 ops each: a quarter for the crossover word, three quarters for
-    the three GWO words, each giving one leader's r1 and r2); the GWO's 2 r1 - 1
-    and 2 r2 of three leaders (3 ops each: shift, mask-or into a significand,
-    exact subtraction); the crossover test (1 integer compare); DE update (6:
-    difference, FMA, clamp 2, jrand compare, select); GWO update (19: per leader
-    A, the two FMAs and |.|, then two adds, the division by 3 in 3, clamp 2); two
-    fitness domain-evals (10 plain; 14.25 with Kahan compensation folded in every
-    8 domains)."""
-    return (PHILOX_CALLS_PER_GENE_GEN * 80 + 6 * 3 + 1 + 6 + 19
+    the three GWO words, each giving one leader's r1 and r2); the GWO's r1 and 2 r2
+    of three leaders (3 ops each: shift, mask-or into a significand, exact
+    subtraction); the crossover test (1 integer compare); DE update (7: difference,
+    product, sum, clamp 2, jrand compare, select); GWO update (28: per leader A in
+    2, |C Xp - x| in 3, Xp - A D in 2; then two adds, the division by 3 in 3, clamp
+    2); two fitness domain-evals (10 plain; 14.25 with Kahan compensation folded in
+    every 8 domains)."""
+    return (PHILOX_CALLS_PER_GENE_GEN * 80 + 6 * 3 + 1 + 7 + 28
             + 2 * (14.25 if compensated else 10))
 
 
@@ -159,8 +159,8 @@ def phase_bound_s_per_gen(N, NP, compensated, issue, hbm_gbs):
     barrier between the phases keeps them from overlapping."""
     ev = 14.25 if compensated else 10
     genes = N * NP
-    de_issue = genes * (0.25 / issue["philox_calls_per_s"] + (1 + 6 + ev) / (issue["ffma"] * 1e12))
-    gwo_issue = genes * (0.75 / issue["philox_calls_per_s"] + (6 * 3 + 19 + ev) / (issue["ffma"] * 1e12))
+    de_issue = genes * (0.25 / issue["philox_calls_per_s"] + (1 + 7 + ev) / (issue["ffma"] * 1e12))
+    gwo_issue = genes * (0.75 / issue["philox_calls_per_s"] + (6 * 3 + 28 + ev) / (issue["ffma"] * 1e12))
     de_hbm = 20.0 * genes / (hbm_gbs * 1e9)
     gwo_hbm = 8.0 * genes / (hbm_gbs * 1e9)
     return max(de_issue, de_hbm) + max(gwo_issue, gwo_hbm)

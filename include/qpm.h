@@ -169,8 +169,8 @@ qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stre
  * 32-bit patterns x:
  *   kind 0: the GWO mean's division by 3 (Markstein's residual correction of
  *           x * RN(1/3)) against the IEEE division x / 3 (two NaNs agree);
- *   kind 1: the GWO's 2 r1 - 1 and 2 r2 built in the significand of a float in
- *           [2, 4) against the same values through int-to-float conversions,
+ *   kind 1: the GWO's r1 and 2 r2 built in the significand of a float in [1, 2)
+ *           or [2, 4) against the same values through int-to-float conversions,
  *           r1 = (x >> 16) 2^-16, r2 = (x & 0xFFFF) 2^-16;
  *   kind 2: the crossover test as one integer compare (x <= 256 floor(2^24 CR)
  *           + 255) against U <= CR in FP32, U = (x >> 8) 2^-24, for CR = 0,

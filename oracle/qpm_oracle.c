@@ -19,9 +19,8 @@
  *   - the relaxed gradient d|d_eff|^2/d(theta_k), d_k = tanh(theta_k), by exact
  *     differentiation of the same quadrature sum, and by central differences.
  *   - the HWSDA loop (Sec. 2.2.1 DE, Sec. 2.2.2 GWO, Sec. 3.2 Steps 1-7) with
- *     FP32 genes and FP32 update arithmetic in a fixed operation order (C99 fmaf,
- *     one rounding, exactly where written; no other contraction: build with
- *     -ffp-contract=off), random numbers from Philox4x32-10
+ *     FP32 genes and FP32 update arithmetic in a fixed operation order (no FMA:
+ *     build with -ffp-contract=off), random numbers from Philox4x32-10
  *     (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
  *     SC'11), written here from that published definition.
  *
@@ -38,11 +37,10 @@
  *     towards the lower index;
  *   - real gene -> domain sign: d = (x < 0) ? -1 : +1;
  *   - genes are clamped to [-1, 1] after mutation and after the GWO move;
- *   - each update formula is rounded once per product-sum: the DE mutant is
- *     x_r1 + F (x_r2 - x_r3) with the difference rounded and then one fused
- *     multiply-add; in the GWO move A = 2 a r1 - a is taken as a (2 r1 - 1) (the
- *     bracket is exact on the 2^-15 grid, so one rounding of the exact value),
- *     C = 2 r2 is exact, and |C X_p - X| and X_p - A D are one FMA each;
+ *   - the update formulas are evaluated in FP32 in the order they are written,
+ *     every operation rounded: v = fl(x_r1 + fl(F fl(x_r2 - x_r3))),
+ *     A = fl(fl(2a r1) - a), C = fl(2 r2), D = |fl(fl(C X_p) - X)|,
+ *     X_k = fl(X_p - fl(A D)), y = fl(fl(fl(X_1 + X_2) + X_3) / 3);
  *   - a decays linearly from 2 to 0: a_g = 2(G-g)/G, one rounded FP32 division.
  * Parity status: every function here is pinned by the CPU test-suite
  * (closed forms, invariants, an independent analytic closed form, brute force,
@@ -539,7 +537,8 @@ static void de_trial_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
   const float F = orc_F_of(c, (int32_t)g);
   for (int32_t j = 0; j < c->N; ++j) {
     float diff = x2[j] - x3[j];
-    float v = clamp1(fmaf(F, diff, x1[j])); /* x_r1 + F diff, one rounding */
+    float step = F * diff;
+    float v = clamp1(x1[j] + step);
     float randb = u24(rng_word(c->seed, c->inst, TAG_CR, g, (uint32_t)i, (uint32_t)j));
     u[j] = (randb <= c->CR || j == r[3]) ? v : x[j];
   }
@@ -573,6 +572,7 @@ ORC_API float orc_a_of(int32_t g, int32_t G) {
 static void gwo_cand_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X,
                          const int32_t lead[3], float *y) {
   float a = orc_a_of((int32_t)g, c->G);
+  float two_a = 2.0f * a;
   const float *x = X + (int64_t)i * c->ld;
   for (int32_t j = 0; j < c->N; ++j) {
     float Xk[3];
@@ -582,10 +582,10 @@ static void gwo_cand_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
       const uint32_t w = rng_word(c->seed, c->inst, TAG_GWO + k, g, (uint32_t)i, (uint32_t)j);
       float r1 = u16hi(w);
       float r2 = u16lo(w);
-      float A = a * (2.0f * r1 - 1.0f);        /* A = 2 a r1 - a, one rounding */
-      float C = 2.0f * r2;                     /* C = 2 r2 (exact) */
-      float dist = fabsf(fmaf(C, Xp[j], -x[j])); /* d = |C Xp - X| */
-      Xk[k] = fmaf(-A, dist, Xp[j]);           /* X_k = Xp - A d */
+      float A = two_a * r1 - a;             /* A = 2 a r1 - a */
+      float C = 2.0f * r2;                  /* C = 2 r2 */
+      float dist = fabsf(C * Xp[j] - x[j]); /* d = |C Xp - X| */
+      Xk[k] = Xp[j] - A * dist;             /* X_k = Xp - A d */
     }
     float yj;
     if (c->combine == 0) {

@@ -58,11 +58,11 @@ __device__ __forceinline__ float u24(uint32_t w) {
   return __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
 }
 // The GWO pair of one leader and gene: r1 = (w >> 16) 2^-16 and r2 = (w & 0xFFFF) 2^-16.
-// The update needs 2 r1 - 1 and 2 r2, built without a conversion: the 16 bits go to
-// the top of the significand of a float in [2, 4), which is then 2 + 2 r, and one
-// exact subtraction (both results lie on the 2^-15 grid in [-1, 2)) leaves the value.
-__device__ __forceinline__ float twice_u16hi_m1(uint32_t w) {  // 2 r1 - 1
-  return __fsub_rn(__uint_as_float(0x40000000u | ((w >> 9) & 0x007FFF80u)), 3.0f);
+// The update needs r1 and C = 2 r2, built without a conversion: the 16 bits go to the
+// top of the significand of a float in [1, 2) (for r1) or [2, 4) (for 2 r2), which is
+// then 1 + r1 or 2 + 2 r2, and one exact subtraction leaves the value.
+__device__ __forceinline__ float u16hi(uint32_t w) {  // r1
+  return __fsub_rn(__uint_as_float(0x3F800000u | ((w >> 9) & 0x007FFF80u)), 1.0f);
 }
 __device__ __forceinline__ float twice_u16lo(uint32_t w) {  // 2 r2
   return __fsub_rn(__uint_as_float(0x40000000u | ((w << 7) & 0x007FFF80u)), 2.0f);

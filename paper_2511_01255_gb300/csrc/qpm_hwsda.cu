@@ -289,11 +289,11 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     const int j0 = t * I.c + 4 * k4;
     const uint4 w = rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 u;
-    // v = x_r1 + F (x_r2 - x_r3) (the difference rounded, then one FMA), clamped;
+    // v = fl(x_r1 + fl(F fl(x_r2 - x_r3))) (no FMA), clamped;
     // u = v if U <= CR (integer form) or j == jrand, else x
 #define QPM_DE1(C, W, J)                                                              \
     {                                                                                 \
-      const float v = clamp1(__fmaf_rn(F, __fsub_rn(p.C, q.C), b.C));                 \
+      const float v = clamp1(__fadd_rn(b.C, __fmul_rn(F, __fsub_rn(p.C, q.C))));      \
       u.C = (w.W <= crthr || (J) == r.w) ? v : a.C;                                   \
     }
     QPM_DE1(x, x, j0)
@@ -345,6 +345,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   const int sd = lslot ? lslot[2] : sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
   const float a = __fdiv_rn((float)(2 * (I.G - g)), (float)I.G);
+  const float two_a = __fmul_rn(2.0f, a);
   const int n4 = I.c / 4;
   const float *rx = row_ptr(I, i, si), *r0 = row_ptr(I, la, sa), *r1 = row_ptr(I, lb, sb);
   const float *r2 = row_ptr(I, ld, sd);
@@ -379,14 +380,14 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
       for (int k = 0; k < 3; ++k) w[k] = rng4(K, I.inst, TAG_GWO + k, (uint32_t)g, (uint32_t)i, jg);
     }
     float4 y;
-    // A = 2 a r1 - a = a (2 r1 - 1), C = 2 r2, D = |C Xp - x|, Y = Xp - A D: each
-    // rounded once (the bracket is exact, the last two are FMAs)
+    // A = fl(fl(2a r1) - a), C = 2 r2, D = |fl(fl(C Xp) - x)|, Y = fl(Xp - fl(A D)),
+    // in this order, no FMA
 #define QPM_PULL(Xp, xv, rw, out_)                                                     \
     {                                                                                  \
-      const float A = __fmul_rn(a, twice_u16hi_m1(rw));                                 \
+      const float A = __fsub_rn(__fmul_rn(two_a, u16hi(rw)), a);                        \
       const float C = twice_u16lo(rw);                                                  \
-      const float dist = fabsf(__fmaf_rn(C, Xp, -(xv)));                                \
-      out_ = __fmaf_rn(-A, dist, Xp);                                                   \
+      const float dist = fabsf(__fsub_rn(__fmul_rn(C, Xp), xv));                        \
+      out_ = __fsub_rn(Xp, __fmul_rn(A, dist));                                         \
     }
 #define QPM_GWO1(CMP)                                                                  \
     {                                                                                  \

@@ -115,8 +115,8 @@ static __global__ void k_check_div3(unsigned long long *bad, uint32_t *first) {
   }
 }
 
-// every 32-bit word w: the GWO's 2 r1 - 1 and 2 r2 built in the significand against
-// the same values through conversions, r = (16-bit half) 2^-16 (bitwise)
+// every 32-bit word w: the GWO's r1 and 2 r2 built in the significand against the
+// same values through conversions, r = (16-bit half) 2^-16 (bitwise)
 static __global__ void k_check_gwo_uniforms(unsigned long long *bad, uint32_t *first) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   unsigned long long n = 0;
@@ -125,7 +125,7 @@ static __global__ void k_check_gwo_uniforms(unsigned long long *bad, uint32_t *f
     const uint32_t w = (uint32_t)b;
     const float r1 = __fmul_rn(__uint2float_rn(w >> 16), 0x1p-16f);
     const float r2 = __fmul_rn(__uint2float_rn(w & 0xFFFFu), 0x1p-16f);
-    const bool same = __float_as_uint(twice_u16hi_m1(w)) == __float_as_uint(__fsub_rn(__fmul_rn(2.0f, r1), 1.0f)) &&
+    const bool same = __float_as_uint(u16hi(w)) == __float_as_uint(r1) &&
                       __float_as_uint(twice_u16lo(w)) == __float_as_uint(__fmul_rn(2.0f, r2));
     if (!same) {
       ++n;

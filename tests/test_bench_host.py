@@ -14,13 +14,13 @@ ISSUE = {"ffma": 38.0, "philox_calls_per_s": 4.0e11}
 
 
 def test_op_count_per_gene_generation():
-    # 80 Philox + 18 GWO uniforms + 1 crossover + 6 DE + 19 GWO + two domain-evals
-    assert bench.algorithmic_lane_ops_per_gene_gen(0) == 144.0
-    assert bench.algorithmic_lane_ops_per_gene_gen(1) == 152.5
+    # 80 Philox + 18 GWO uniforms + 1 crossover + 7 DE + 28 GWO + two domain-evals
+    assert bench.algorithmic_lane_ops_per_gene_gen(0) == 154.0
+    assert bench.algorithmic_lane_ops_per_gene_gen(1) == 162.5
 
 
 def test_mix_ceiling_adds_generator_and_other_times():
-    n_rest = 144.0 - 80.0
+    n_rest = 154.0 - 80.0
     t = 1.0 / ISSUE["philox_calls_per_s"] + n_rest / (ISSUE["ffma"] * 1e12)
     assert bench.mix_ceiling_gene_gens(0, ISSUE) == pytest.approx(1.0 / t)
     assert bench.mix_ceiling_gene_gens(1, ISSUE) < bench.mix_ceiling_gene_gens(0, ISSUE)

@@ -21,25 +21,10 @@ import ctypes.util
 import json
 import os
 
-from fractions import Fraction
-
 import numpy as np
 import pytest
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-
-
-def _rn32(x):
-    """The Fraction x rounded to the nearest float32, ties to even (the FP32
-    result of an operation that rounds the exact value once)."""
-    f = np.float32(float(x))  # within one float32 step of the answer
-    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
-    return min(cands, key=lambda c: (abs(Fraction(float(c)) - x),
-                                     int(np.array(c, dtype=np.float32).view(np.uint32)) & 1))
-
-
-def _fr(v):
-    return Fraction(float(v))
 
 
 def _curand():
@@ -112,20 +97,17 @@ def test_init_population_uniform(orc):
 
 
 def test_de_trial_structure(orc):
-    # F = 0.7 (not a power of 2, so F (x_r2 - x_r3) is not exact and the single
-    # rounding of the product-sum shows)
+    # F = 0.7 (not a power of 2, so F (x_r2 - x_r3) is not exact and a fused
+    # multiply-add would show)
     c = _cfg(orc, NP=16, N=64, F=0.7, CR=0.9)
     X = orc.init_population(c)
     U = orc.de_trials(c, 4, X)
     taken = 0
-    F = _fr(np.float32(c.F))
+    F = np.float32(c.F)
     for i in range(c.NP):
         r1, r2, r3, jr = orc.de_indices(c.seed, c.inst, 4, i, c.NP, c.N)
-        # mutant x_r1 + F (x_r2 - x_r3): the difference rounded, then the
-        # product-sum rounded once (exact rationals here)
-        d = (X[r2] - X[r3]).astype(np.float32)
-        v = np.array([_rn32(_fr(X[r1][j]) + F * _fr(d[j])) for j in range(c.N)], np.float32)
-        v = np.clip(v, -1, 1)
+        # mutant fl(x_r1 + fl(F fl(x_r2 - x_r3))), every operation rounded to FP32
+        v = np.clip(X[r1] + F * (X[r2] - X[r3]), -1, 1).astype(np.float32)
         from_v = U[i] == v
         from_x = U[i] == X[i]
         assert np.all(from_v | from_x)
@@ -169,8 +151,8 @@ def test_gwo_candidate_moments(orc):
 
 def test_gwo_pair_from_one_word(orc):
     """The GWO pair (r1, r2) of leader k and gene j are the high and low 16 bits of
-    one generator word (tag 3 + k), and each formula of the move is one rounding of
-    its exact value: a candidate recomputed here from the words in exact rationals."""
+    one generator word (tag 3 + k), and the move is evaluated in FP32 in its written
+    order: a candidate recomputed here from the words."""
     NP, N, G, seed = 6, 9, 50, 12345
     c = _cfg(orc, NP=NP, N=N, G=G, seed=seed)
     rng = np.random.default_rng(2)
@@ -178,21 +160,20 @@ def test_gwo_pair_from_one_word(orc):
     lead = np.array([2, 0, 5])
     g, i = 17, 3
     Y = orc.gwo_candidates(c, g, X, lead)
-    a = _fr(np.float32(orc.a_of(g, G)))
+    a = np.float32(orc.a_of(g, G))
     key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
     for j in range(N):
         Xk = []
         for k in range(3):
             w = int(orc.philox(np.array([j // 4, i, g, 3 + k], dtype=np.uint32), key)[j % 4])
-            r1 = Fraction(w >> 16, 2 ** 16)
-            r2 = Fraction(w & 0xFFFF, 2 ** 16)
-            A = _fr(_rn32(2 * a * r1 - a))          # A = 2 a r1 - a
-            C = 2 * r2                              # C = 2 r2, exact in FP32
-            Xp = _fr(X[lead[k], j])
-            d = abs(_fr(_rn32(C * Xp - _fr(X[i, j]))))  # d = |C Xp - X|
-            Xk.append(_fr(_rn32(Xp - A * d)))      # X_k = Xp - A d
-        s01 = _fr(_rn32(Xk[0] + Xk[1]))
-        y = _rn32(_fr(_rn32(s01 + Xk[2])) / 3)
+            r1 = np.float32(w >> 16) * np.float32(2.0 ** -16)
+            r2 = np.float32(w & 0xFFFF) * np.float32(2.0 ** -16)
+            A = np.float32(np.float32(2 * a) * r1) - a
+            C = np.float32(2) * r2
+            Xp = X[lead[k], j]
+            d = np.float32(abs(np.float32(C * Xp) - X[i, j]))
+            Xk.append(np.float32(Xp - np.float32(A * d)))
+        y = np.float32(np.float32(np.float32(Xk[0] + Xk[1]) + Xk[2]) / np.float32(3))
         assert Y[i, j] == np.clip(y, -1, 1), j
 
 
