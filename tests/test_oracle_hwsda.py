@@ -183,6 +183,15 @@ def test_gwo_a_schedule(orc):
     assert a[0] == 2.0 and np.all(np.diff(a) < 0) and abs(a[-1] - 2.0 / G) < 1e-7
 
 
+@pytest.mark.parametrize("G", [1, 7, 500, 1000, 2000, 4999, 20000])
+def test_gwo_a_equals_fp64_form(orc, G):
+    """a_g as one rounded FP32 division 2(G - g)/G equals 2(1 - g/G) evaluated in
+    FP64 and rounded to FP32, for every generation."""
+    g = np.arange(G)
+    a = np.array([orc.a_of(int(k), G) for k in g], dtype=np.float32)
+    assert np.array_equal(a, (2.0 * (1.0 - g / G)).astype(np.float32))
+
+
 def test_gwo_weighted_combination_reduces_to_mean(orc):
     # with identical leaders and the wolf on them, A d = A |C-1| |x| for every k, and the
     # |X_k|-weighted combination of equal-sign X_k is (sum X_k^2 / sum |X_k|) / 3
