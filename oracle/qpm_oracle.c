@@ -433,6 +433,7 @@ ORC_API void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
 /* Random-number contract of this implementation (the paper fixes none):     */
 /*   key = (seed low word, seed high word)                                    */
 /*   counter = (j/4, i, g, (instance << 8) | tag); word j%4 serves gene j     */
+/*   (g = 0xFFFFFFFF for the initial draw)                                    */
 /*   tags: 0 init, 1 DE indices (counter word 0 = 0), 2 crossover,            */
 /*         3..5 GWO for alpha, beta, gamma                                    */
 /*   uniform U = (w >> 8) * 2^-24 in [0, 1) for init and crossover; the GWO   */
@@ -440,6 +441,7 @@ ORC_API void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t o
 /*   index in [0, m): (w * m) >> 32  (Lemire multiply-shift)                  */
 /* ------------------------------------------------------------------------- */
 enum { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3 };
+#define GEN_INIT 0xFFFFFFFFu /* the generation word of the initial draw */
 
 static inline uint32_t rng_word(uint64_t seed, uint32_t inst, uint32_t tag, uint32_t g,
                                 uint32_t i, uint32_t j) {
@@ -520,7 +522,7 @@ static inline float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
 ORC_API void orc_init_population(const orc_cfg *c, float *X) {
   for (int32_t i = 0; i < c->NP; ++i)
     for (int32_t j = 0; j < c->N; ++j) {
-      float U = u24(rng_word(c->seed, c->inst, TAG_INIT, 0, (uint32_t)i, (uint32_t)j));
+      float U = u24(rng_word(c->seed, c->inst, TAG_INIT, GEN_INIT, (uint32_t)i, (uint32_t)j));
       X[(int64_t)i * c->ld + j] = 2.0f * U - 1.0f;
     }
 }

@@ -45,9 +45,11 @@ __device__ __forceinline__ uint4 philox10(uint4 c, const PhiloxKey &K) {
 }
 
 // Random-number contract: key = seed, counter = (j/4, i, g, instance<<8 | tag);
-// word j%4 of the output serves gene j.  Tags: 0 init, 1 DE indices, 2 crossover,
-// 3-5 GWO (one word per leader and gene: r1 its high, r2 its low 16 bits).
+// word j%4 of the output serves gene j.  Tags: 0 init (with g = 0xFFFFFFFF), 1 DE
+// indices, 2 crossover, 3-5 GWO (one word per leader and gene: r1 its high, r2 its
+// low 16 bits).
 enum : uint32_t { TAG_INIT = 0, TAG_DEIDX = 1, TAG_CR = 2, TAG_GWO = 3, TAG_THETA = 16 };
+constexpr uint32_t GEN_INIT = 0xFFFFFFFFu;  // the generation word of the initial draw
 
 __device__ __forceinline__ uint4 rng4(const PhiloxKey &K, uint32_t inst, uint32_t tag, uint32_t g,
                                       uint32_t i, uint32_t jgroup) {

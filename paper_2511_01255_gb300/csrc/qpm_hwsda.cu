@@ -141,7 +141,7 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
   acc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const int j0 = t * I.c + 4 * k4;
-    const uint4 w = rng4(K, I.inst, TAG_INIT, 0u, (uint32_t)i, (uint32_t)(j0 >> 2));
+    const uint4 w = rng4(K, I.inst, TAG_INIT, GEN_INIT, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 x;
     x.x = __fsub_rn(__fmul_rn(2.0f, u24(w.x)), 1.0f);
     x.y = __fsub_rn(__fmul_rn(2.0f, u24(w.y)), 1.0f);

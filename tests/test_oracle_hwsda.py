@@ -94,6 +94,13 @@ def test_init_population_uniform(orc):
     assert abs(X.mean()) < 0.02 and abs(X.var() - 1.0 / 3.0) < 0.02
     # x = 2U - 1 with U on the 24-bit grid
     assert np.all((X + 1) * 2 ** 23 == np.floor((X + 1) * 2 ** 23))
+    # the draw of gene j of individual i: word j % 4 of Philox at counter
+    # (j / 4, i, 0xFFFFFFFF, tag 0), U = (w >> 8) 2^-24, x = 2U - 1
+    key = np.array([c.seed & 0xFFFFFFFF, c.seed >> 32], dtype=np.uint32)
+    for i, j in ((0, 0), (3, 7), (63, 255), (17, 130)):
+        w = int(orc.philox(np.array([j // 4, i, 0xFFFFFFFF, 0], dtype=np.uint32), key)[j % 4])
+        U = np.float32(w >> 8) * np.float32(2.0 ** -24)
+        assert X[i, j] == np.float32(2) * U - np.float32(1), (i, j)
 
 
 def test_de_trial_structure(orc):
