@@ -446,6 +446,9 @@ def run_gpu(args):
                      "peak_note": f"{nsm} SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0)} MHz "
                                   f"(issue limit, derived; clocks {pk_src})",
                      "frac_at_median_clock": achieved / (nsm * 128 * sm_mhz * 1e6 / 1e12),
+                     "frac_at_loaded_median_clock_of_peaks_file":
+                         achieved / (nsm * 128 * pk.get("clocks_under_load", {}).get(
+                             "sm_mhz_median", pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12),
                      "measured_issue_peaks": {k: v for k, v in issue.items()},
                      "frac_of_measured_ffma": achieved / issue["ffma"],
                      "frac_of_mix_ceiling": gene_gens / kdur / mix_ceiling_gene_gens(c["compensated"], issue),
@@ -463,6 +466,7 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget)
+        line["cpu_baseline"]["closed_form_scan"] = cpu_closed_form()
     print(json.dumps(line), flush=True)
 
 
@@ -496,6 +500,30 @@ def cpu_baseline(budget_s=15.0, steps_cap=None):
             "kind": "oracle",
             "sample": f"init + {g} generations of {c['name']} ({el:.1f} s, FP64 quadrature, "
                       f"Q=16 Gauss-Legendre nodes per domain and level)"}
+
+
+def cpu_closed_form(budget_s=2.0):
+    """A fairer CPU throughput figure than the quadrature oracle: the oracle's FP64
+    closed-form scan of the same fitness (all host cores), on the workload's row
+    shape (NP rows of N domains), repeated for about budget_s."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.PAPER_SCALE
+    X = W.random_genes(c["NP"], c["N"], seed=1)
+    oracle.deff_closed_genes(X, c["kappa1"], c["kappa2"])  # warm the rule and threads
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.deff_closed_genes(X, c["kappa1"], c["kappa2"])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    return {"value": reps * c["NP"] * c["N"] / el, "unit": "domain-evals/s",
+            "cores": oracle.num_threads(), "kind": "oracle closed-form FP64 scan",
+            "sample": f"{reps} evaluations of {c['NP']} rows x {c['N']} domains ({el:.1f} s)"}
 
 
 def run_reference(args):

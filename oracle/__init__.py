@@ -39,6 +39,7 @@ def lib():
         L.orc_gauss_legendre.argtypes = [ctypes.c_int, P, P]
         L.orc_deff_quad.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, dbl, P, ctypes.c_int, P]
         L.orc_deff_genes.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, dbl, P, ctypes.c_int, P]
+        L.orc_deff_closed.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, dbl, P, ctypes.c_int, P]
         L.orc_bruteforce.argtypes = [ctypes.c_int, dbl, dbl, ctypes.c_int, P, P]
         L.orc_bruteforce.restype = dbl
         L.orc_shg_genes.argtypes = [ctypes.c_int, ctypes.c_int, i64, dbl, P, ctypes.c_int, P]
@@ -103,6 +104,16 @@ def deff_genes(X, kappa1, kappa2, Q=Q_DEFAULT):
     NP, N = X.shape
     out = np.zeros((NP, 2))
     lib().orc_deff_genes(NP, N, N, kappa1, kappa2, _p(X), Q, _p(out))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def deff_closed_genes(X, kappa1, kappa2, Q=Q_DEFAULT):
+    """d_eff of FP32 gene rows by the closed form for unit domains (FP64 scan in
+    index order; phi and psi by the Q-node rule) -- the CPU throughput reference."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    NP, N = X.shape
+    out = np.zeros((NP, 2))
+    lib().orc_deff_closed(NP, N, N, kappa1, kappa2, _p(X), Q, _p(out))
     return out[:, 0] + 1j * out[:, 1]
 
 

@@ -193,6 +193,71 @@ ORC_API void orc_deff_genes(int NP, int N, int64_t ld, double kappa1, double kap
   }
 }
 
+/* ------------------------------------------------------------------------- */
+/* d_eff by the closed form of the same integral for unit domains (Sec. 2.1): */
+/*   int_j^{j+1} e^{-ik2 z} dz = e^{-ik2 j} phi2 and                         */
+/*   int_m^{m+1} e^{-ik1 x} dx = e^{-ik1 m} phi1 turn the off-diagonal part   */
+/*   into phi1 phi2 sum_j d_j e^{-ik2 j} sum_{m<j} d_m e^{-ik1 m}, and the     */
+/*   diagonal part (x and z in the same domain j) into                        */
+/*   psi sum_j d_j^2 e^{-i(k1+k2) j}, with phi(k) = int_0^1 e^{-iks} ds and      */
+/*   psi = int_0^1 e^{-ik2 s} int_0^s e^{-ik1 t} dt ds, both taken here by the */
+/*   same Gauss-Legendre rule (exact to rounding for these smooth integrands). */
+/* FP64, rows in index order: a CPU throughput reference, pinned against the  */
+/* quadrature.                                                                */
+/* ------------------------------------------------------------------------- */
+static void unit_integrals(double k1, double k2, int Q, double phi1[2], double phi2[2],
+                           double psi[2]) {
+  ensure_rule(Q);
+  phi1[0] = phi1[1] = phi2[0] = phi2[1] = psi[0] = psi[1] = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const double s = 0.5 * (1.0 + g_t[q]), w = 0.5 * g_w[q];
+    double er, ei;
+    cis_neg(k1, s, &er, &ei);
+    phi1[0] += w * er;
+    phi1[1] += w * ei;
+    cis_neg(k2, s, &er, &ei);
+    phi2[0] += w * er;
+    phi2[1] += w * ei;
+    double inr = 0.0, ini = 0.0; /* int_0^s e^{-ik1 t} dt */
+    for (int r = 0; r < Q; ++r) {
+      const double t = 0.5 * s * (1.0 + g_t[r]);
+      double fr, fi;
+      cis_neg(k1, t, &fr, &fi);
+      inr += 0.5 * s * g_w[r] * fr;
+      ini += 0.5 * s * g_w[r] * fi;
+    }
+    psi[0] += w * (er * inr - ei * ini);
+    psi[1] += w * (er * ini + ei * inr);
+  }
+}
+
+ORC_API void orc_deff_closed(int NP, int N, int64_t ld, double kappa1, double kappa2,
+                             const float *X, int Q, double *D) {
+  double p1[2], p2[2], ps[2];
+  unit_integrals(kappa1, kappa2, Q, p1, p2, ps);
+  const double p12r = p1[0] * p2[0] - p1[1] * p2[1], p12i = p1[0] * p2[1] + p1[1] * p2[0];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < NP; ++i) {
+    acc_t S = {0, 0, 0, 0};   /* sum_{m<j} d_m e^{-ik1 m} */
+    acc_t off = {0, 0, 0, 0}; /* sum_j d_j e^{-ik2 j} S_j */
+    acc_t dg = {0, 0, 0, 0};  /* sum_j d_j^2 e^{-i(k1+k2) j} */
+    for (int j = 0; j < N; ++j) {
+      const double d = (X[(int64_t)i * ld + j] < 0.0f) ? -1.0 : 1.0;
+      double ar, ai, br, bi, cr, ci;
+      cis_neg(kappa2, (double)j, &ar, &ai);
+      const double sr = acc_re(&S), si = acc_im(&S);
+      acc_add(&off, d * (ar * sr - ai * si), d * (ar * si + ai * sr));
+      cis_neg(kappa1, (double)j, &br, &bi);
+      acc_add(&S, d * br, d * bi);
+      cis_neg(kappa1 + kappa2, (double)j, &cr, &ci);
+      acc_add(&dg, d * d * cr, d * d * ci);
+    }
+    const double orr = acc_re(&off), oi = acc_im(&off), gr = acc_re(&dg), gi = acc_im(&dg);
+    D[2 * i] = (p12r * orr - p12i * oi) + (ps[0] * gr - ps[1] * gi);
+    D[2 * i + 1] = (p12r * oi + p12i * orr) + (ps[0] * gi + ps[1] * gr);
+  }
+}
+
 /* exhaustive search over all 2^N sign patterns (bit m set -> d_m = -1).
  * Writes f = |d_eff|^2 of every pattern to fit[2^N] (may be NULL) and returns
  * the best value; best_mask gets the lowest pattern index attaining it. */

@@ -110,6 +110,18 @@ def test_matches_exact_antiderivatives(orc, N):
         assert abs(D - ref) <= 1e-12 * max(abs(ref), N), (N, trial, D, ref)
 
 
+@pytest.mark.parametrize("N", [1, 2, 17, 1000])
+def test_closed_form_scan_matches_quadrature(orc, N):
+    """The FP64 closed-form scan (the CPU throughput reference) against the nested
+    quadrature of the same integral, including k1 = 0 and k1 = k2 = 0."""
+    rng = np.random.default_rng(7 + N)
+    X = rng.uniform(-1, 1, (5, N)).astype(np.float32)
+    for k1, k2 in ((0.0, 0.0), (0.0, 2.1), (0.9106, 4.0537), (-3.3, 1.2), (1e-6, 3.0)):
+        Dq = orc.deff_genes(X, k1, k2)
+        Dc = orc.deff_closed_genes(X, k1, k2)
+        assert np.all(np.abs(Dc - Dq) <= 1e-11 * np.maximum(np.abs(Dq), N)), (N, k1, k2)
+
+
 def test_physical_scaling_with_domain_width(orc):
     # d_eff in physical units is w^2 * D(kappa = dk * w): halving w at fixed L doubles N
     # and, at zero mismatch, leaves the physical L^2/2 unchanged
