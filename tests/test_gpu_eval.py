@@ -119,6 +119,10 @@ def test_eval_full_size_sampled(q, orc, comp):
     ref = orc.deff_genes(X[rows], K1, K2)
     err = deff_err(D[rows], ref, N)
     assert err.max() < TOL_D, err
+    # the same rows as packed sign words (the packed sweep's own segmenting)
+    Dp, _ = run_eval(q, X, N, K1, K2, comp, packed=True)
+    errp = deff_err(Dp[rows], ref, N)
+    assert errp.max() < TOL_D, errp
 
 
 @pytest.mark.parametrize("N", [1, 7, 1000, 4097, 100000])
