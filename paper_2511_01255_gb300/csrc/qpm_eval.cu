@@ -344,7 +344,8 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
 // e.g. while a CUDA stream is being captured into a graph, inside a host
 // callback, under an external allocator that owns all device memory, or on a
 // real-time path where an allocation's implicit device synchronisation is not
-// acceptable.  Its scratch (phasor table, table reduction, segment partials)
+// acceptable.  Its scratch (phasor and sign-block tables, table reduction,
+// segment partials)
 // lives in one file-scope device array of fixed size that every GPU loading
 // this library holds until the process exits.
 // ---------------------------------------------------------------------------

@@ -9,7 +9,7 @@
 // Multi-wavelength objective (Sec. 5): f = sum_k |G0 - G_k| + beta (G_max - G_min)
 // with G_k = |d_eff(kappa1_k, kappa2_k)|, to be minimised.  The K cascaded scans
 // share one read of the genes: the row sweep of qpm_eval (qpm_rows.cuh) with the
-// K phasor tables of the segment staged side by side, every domain pushed into K
+// K sign-block tables streamed side by side, every block of 4 domains appended to K
 // running monoids.  For K = 1 this is qpm_eval's arithmetic, operation for operation.
 #include <math.h>
 
