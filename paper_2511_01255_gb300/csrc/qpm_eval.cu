@@ -227,11 +227,21 @@ qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **t
     TableEntry &e = it->second;
     if (!e.blk) {
       const size_t nb = (size_t)(p->N + 3) / 4;
-      QPM_CUDA(cudaMalloc(&e.blk, sizeof(float2) * BLK_F2 * nb));
-      QPM_CUDA(cudaEventCreateWithFlags(&e.blk_ready, cudaEventDisableTiming));
-      qpm_status st = launch_block_table(p->N, p->kappa1, p->kappa2, e.blk, stream);
-      if (st != QPM_OK) return st;
-      QPM_CUDA(cudaEventRecord(e.blk_ready, stream));
+      float2 *b = nullptr;
+      cudaEvent_t ev = nullptr;
+      QPM_CUDA(cudaMalloc(&b, sizeof(float2) * BLK_F2 * nb));
+      cudaError_t ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      qpm_status st = ce == cudaSuccess ? launch_block_table(p->N, p->kappa1, p->kappa2, b, stream)
+                                        : cuda_fail(ce, "cudaEventCreateWithFlags");
+      if (st == QPM_OK && (ce = cudaEventRecord(ev, stream)) != cudaSuccess)
+        st = cuda_fail(ce, "cudaEventRecord");
+      if (st != QPM_OK) {  // the entry keeps no half-built table
+        cudaFree(b);
+        if (ev) cudaEventDestroy(ev);
+        return st;
+      }
+      e.blk = b;
+      e.blk_ready = ev;
     } else {
       QPM_CUDA(cudaStreamWaitEvent(stream, e.blk_ready, 0));
     }
