@@ -570,17 +570,23 @@ __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// bounded wait (thread 0) until *p >= need; false when it ran out or another CTA failed
+// bounded wait (thread 0) until *p >= need; false when it ran out or another CTA failed.
+// The error flag and the clock are looked at on the first failed poll and then on
+// every 16th: each poll is an L2 round trip already, and a flag load after every poll
+// (ordered behind the acquire) or after the success would add one more in series.
+// A CTA that passes this wait just after another CTA gave up stops at the next one.
 __device__ bool wait_geq(const Barrier &b, const unsigned *p, unsigned need) {
   const unsigned long long t0 = globaltimer_ns();
-  while ((int)(ld_acquire(p) - need) < 0) {
-    if (*(volatile int32_t *)b.err != 0) return false;
-    if (globaltimer_ns() - t0 > b.timeout_ns) {
-      atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
-      return false;
+  for (unsigned spin = 0; (int)(ld_acquire(p) - need) < 0; ++spin) {
+    if ((spin & 15u) == 0u) {
+      if (*(volatile int32_t *)b.err != 0) return false;
+      if (globaltimer_ns() - t0 > b.timeout_ns) {
+        atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+        return false;
+      }
     }
   }
-  return *(volatile int32_t *)b.err == 0;
+  return true;
 }
 
 // grid-wide barrier split into arrival and wait, so that independent work can
