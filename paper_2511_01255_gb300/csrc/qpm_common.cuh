@@ -264,6 +264,29 @@ __device__ __forceinline__ void top3_insert(unsigned long long &k0, unsigned lon
   else if (x > k1) { k2 = k1; k1 = x; }
   else if (x > k2) { k2 = x; }
 }
+// The warp's three largest keys (keys distinct, 0 = none) from each lane's sorted
+// triple k0 >= k1 >= k2, returned in every lane: three rounds of a two-word maximum
+// (redux.sync on the high word, then on the low word among the lanes holding that
+// high word), after each of which the lane holding the winner moves its triple up.
+__device__ __forceinline__ void warp_top3(unsigned long long &k0, unsigned long long &k1,
+                                          unsigned long long &k2) {
+  unsigned long long out[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t hi = (uint32_t)(k0 >> 32), lo = (uint32_t)k0;
+    const uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+    const uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    out[r] = ((unsigned long long)mhi << 32) | mlo;
+    if (k0 != 0ull && hi == mhi && lo == mlo) {
+      k0 = k1;
+      k1 = k2;
+      k2 = 0ull;
+    }
+  }
+  k0 = out[0];
+  k1 = out[1];
+  k2 = out[2];
+}
 
 // ----------------------------------------------- FP64 phase argument reduction
 // r = x - 2 pi n with n = rint(x / 2pi), 2pi split into a double-double

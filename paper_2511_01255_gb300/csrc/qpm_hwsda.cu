@@ -251,11 +251,15 @@ __device__ __forceinline__ void push4_staged(Acc<COMP> &acc, const float4 *tbl, 
 // WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
 // r = (r1, r2, r3, jrand) from de_indices
 // STG: rows staged through stg (known slots only, so not with DUAL)
+// has_wcr: wcr is the crossover word of the thread's first group of 4 domains, drawn
+// earlier (while waiting at the grid barrier)
 template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool STG = false>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
                                             const float4 *tbl, int g, int i, const int4 r,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh,
-                                            int *slot_out = nullptr, float4 *stg = nullptr) {
+                                            int *slot_out = nullptr, float4 *stg = nullptr,
+                                            bool has_wcr = false,
+                                            uint4 wcr = make_uint4(0u, 0u, 0u, 0u)) {
   static_assert(!(STG && DUAL), "staged rows need known slots");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
@@ -287,7 +291,9 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
       q = ld_cur<NC, DUAL>(I, r.z, s3, off);
     }
     const int j0 = t * I.c + 4 * k4;
-    const uint4 w = rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
+    const uint4 w = (has_wcr && k4 == 0)
+                        ? wcr
+                        : rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)i, (uint32_t)(j0 >> 2));
     float4 u;
     // v = fl(x_r1 + fl(F fl(x_r2 - x_r3))) (no FMA), clamped;
     // u = v if U <= CR (integer form) or j == jrand, else x
@@ -612,10 +618,11 @@ __device__ bool grid_sync(const Barrier &b, unsigned &target) {
   return grid_wait(b, target);
 }
 
-// Step 3 of the persistent form, after the grid barrier that follows DE: warp 0
-// reads the DE survivor keys of all individuals and takes the top three; every
-// thread returns after the CTA barrier with lead_sh and the leaders' current
-// slots (slot_sh) set.  The keys are written in
+// Step 3 of the persistent form, after the grid barrier that follows DE: the CTA
+// reads the DE survivor keys of all individuals (each thread its share), every warp
+// takes the top three of its keys and warp 0 those of the warps; every thread
+// returns after the CTA barrier with lead_sh and the leaders' current slots
+// (slot_sh) set.  The keys are written in
 // the DE phase only, so a CTA that is still choosing leaders never sees a fitness
 // already changed by another CTA's GWO selection.
 // The keys carry the survivor's slot: fitness bits << 32 | (0x7FFFFFFF - i) << 1 | slot,
@@ -630,18 +637,28 @@ __device__ __forceinline__ int slot_key_index(unsigned long long k) {
 
 __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_t *lead,
                                   int32_t *lead_sh, int32_t *slot_sh) {
-  if (threadIdx.x < 32) {
-    unsigned long long k0 = 0, k1 = 0, k2 = 0;
-    for (int i = threadIdx.x; i < NP; i += 32) top3_insert(k0, k1, k2, keys[i]);
-    for (int s = 16; s > 0; s >>= 1) {
-      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
-      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
-      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
-      top3_insert(k0, k1, k2, p0);
-      top3_insert(k0, k1, k2, p1);
-      top3_insert(k0, k1, k2, p2);
+  // every thread takes its keys, every warp its top three (redux), warp 0 those of
+  // the warps
+  __shared__ unsigned long long wtop[3 * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) top3_insert(k0, k1, k2, keys[i]);
+  warp_top3(k0, k1, k2);
+  if (lane == 0) {
+    wtop[3 * warp] = k0;
+    wtop[3 * warp + 1] = k1;
+    wtop[3 * warp + 2] = k2;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    k0 = k1 = k2 = 0ull;
+    if (lane < nw) {
+      k0 = wtop[3 * lane];
+      k1 = wtop[3 * lane + 1];
+      k2 = wtop[3 * lane + 2];
     }
-    if (threadIdx.x == 0) {
+    warp_top3(k0, k1, k2);
+    if (lane == 0) {
       lead_sh[0] = slot_key_index(k0);
       lead_sh[1] = slot_key_index(k1);
       lead_sh[2] = slot_key_index(k2);
@@ -680,16 +697,26 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
   const bool pre = DUAL && (I.c == 4) && (gridDim.x == (unsigned)I.NP);
   unsigned target = 0;
   int g = *I.gen;
+  // pre (one individual per CTA, one group of 4 domains per thread): the DE donors
+  // and the crossover word of a generation depend on (g, i) only and are drawn
+  // while the previous generation's last barrier completes
+  const uint32_t jg0 = (uint32_t)((threadIdx.x * I.c) >> 2);
+  int4 r_pre = make_int4(0, 0, 0, 0);
+  uint4 wcr_pre = make_uint4(0u, 0u, 0u, 0u);
+  if (pre && g < g_end) {
+    r_pre = de_indices(K, I.inst, (uint32_t)g, blockIdx.x, I.NP, I.N);
+    wcr_pre = rng4(K, I.inst, TAG_CR, (uint32_t)g, (uint32_t)blockIdx.x, jg0);
+  }
   for (; g < g_end; ++g) {
     const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
     int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
-      const int4 r = de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
+      const int4 r = pre ? r_pre : de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
       int slot = 0;
       const unsigned long long key =
           de_individual<COMP, false, TS, DUAL, false, STG>(I, K, tbl, g, i, r, sel_in, sel_out,
-                                                            sh, &slot, stg);
+                                                            sh, &slot, stg, pre, wcr_pre);
       // ordered before the barrier's release
       if (threadIdx.x == 0) {
         I.dekey[i] = slot_key(key, i, slot);
@@ -734,7 +761,12 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
     }
     // the next DE phase reads any individual: every CTA must have finished GWO
-    if (!grid_sync(bar, target)) return;
+    grid_arrive(bar, target);
+    if (pre && g + 1 < g_end) {
+      r_pre = de_indices(K, I.inst, (uint32_t)(g + 1), blockIdx.x, I.NP, I.N);
+      wcr_pre = rng4(K, I.inst, TAG_CR, (uint32_t)(g + 1), (uint32_t)blockIdx.x, jg0);
+    }
+    if (!grid_wait(bar, target)) return;
   }
   // every CTA read the start generation before its first barrier; later kernels
   // see the new value after this launch completes
