@@ -170,6 +170,27 @@ def test_staged_long_rows_lockstep(q, orc, N, team, mode):
     assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
+@pytest.mark.parametrize("N,team", [(3000, 512), (5000, 256)])
+def test_persistent_several_individuals_per_cta_lockstep(q, orc, N, team):
+    """NP = 400 individuals, more than the persistent grid holds CTAs (152 one-CTA
+    slots of 512-thread teams, 304 of 256-thread teams), so CTAs loop over several
+    individuals per phase: short rows (N = 3000, both slots read, redux leader
+    search) and long rows (N = 5000, rows and table staged, warp-0 leader search)."""
+    NP, G = 400, 3
+    k1, k2 = 2 * math.pi / 6.7, 2 * math.pi / 1.5
+    st, tr = make(q, N, k1, k2, NP, G, seed=13, comp=1, team=team)
+    assert q.qpm_team_of(st.h) == team
+    st.init()
+    st.run(G, q.RUN_PERSISTENT)
+    X, f, D = snapshot(st)
+    trace = tr.cpu().numpy()
+    st.close()
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 13)
+    Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+    assert np.array_equal(X, Xo)
+    assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
+
+
 def test_automatic_team_rule(q):
     """team = 0: at most 4 domains per thread up to 256 threads; a single long-row
     instance takes 512 threads when one CTA per SM fills the rounds of individuals
