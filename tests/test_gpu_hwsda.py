@@ -191,6 +191,31 @@ def test_persistent_several_individuals_per_cta_lockstep(q, orc, N, team):
     assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_solve_end_to_end_host_buffers(q, orc, mode):
+    """qpm_solve (create, init, run, read back, destroy, with host buffers) returns
+    what the state API returns for the same run, and its FP64 d_eff of the best
+    genes matches the oracle's quadrature."""
+    import torch
+    N, NP, G = 333, 24, 12
+    k1, k2 = 2 * math.pi / 7.3, 2 * math.pi / 1.4
+    prm = q.Params(NP, G, 0.5, 0.9, 21, 0, 1)
+    x_h = torch.empty(N, dtype=torch.float32)
+    d_h = torch.empty(2, dtype=torch.float64)
+    f_h = torch.empty(1, dtype=torch.float32)
+    q.qpm_solve(N, k1, k2, prm, mode, x_h, d_h, f_h)
+    with q.State([(N, k1, k2)], [prm]) as st:
+        st.init()
+        st.run(G, mode)
+        x, d64, f, idx = st.best()
+        torch.cuda.synchronize()
+        assert np.array_equal(x_h.numpy(), x.cpu().numpy())
+        assert np.array_equal(d_h.numpy(), d64.cpu().numpy())
+        assert f_h.item() == f.item()
+    ref = orc.deff_genes(x_h.numpy()[None], k1, k2)[0]
+    assert abs(complex(d_h[0].item(), d_h[1].item()) - ref) <= 1e-9 * abs(ref)
+
+
 def test_automatic_team_rule(q):
     """team = 0: at most 4 domains per thread up to 256 threads; a single long-row
     instance takes 512 threads when one CTA per SM fills the rounds of individuals
