@@ -259,11 +259,14 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh,
                                             int *slot_out = nullptr, float4 *stg = nullptr,
                                             bool has_wcr = false,
-                                            uint4 wcr = make_uint4(0u, 0u, 0u, 0u)) {
+                                            uint4 wcr = make_uint4(0u, 0u, 0u, 0u),
+                                            int own_slot = -1) {
   static_assert(!(STG && DUAL), "staged rows need known slots");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
-  const int si = sel_in[i], s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
+  // own_slot >= 0: the individual's current slot, known to the caller
+  const int si = own_slot >= 0 ? own_slot : sel_in[i];
+  const int s1 = sel_in[r.x], s2 = sel_in[r.y], s3 = sel_in[r.z];
   float *out = row_ptr(I, i, si ^ 1);
   const float F = I.Fsched ? I.Fsched[g] : I.F;
   const uint32_t crthr = I.crthr;
@@ -345,12 +348,14 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
                                const uint4 *wpre = nullptr,
                                float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f),
                                float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f),
-                               const int32_t *lslot = nullptr, float4 *stg = nullptr) {
+                               const int32_t *lslot = nullptr, float4 *stg = nullptr,
+                               int own_slot = -1, int *slot_out = nullptr) {
   static_assert(!(STG && (DUAL || PRE)), "staged rows need known slots and no prefetched row");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;
-  // lslot: the leaders' current slots, when the leader search delivered them
-  const int si = sel[i];
+  // lslot: the leaders' current slots, when the leader search delivered them;
+  // own_slot >= 0: the individual's current slot, known to the caller
+  const int si = own_slot >= 0 ? own_slot : sel[i];
   const int sa = lslot ? lslot[0] : sel[la], sb = lslot ? lslot[1] : sel[lb];
   const int sd = lslot ? lslot[2] : sel[ld];
   float *out = row_ptr(I, i, si ^ 1);
@@ -443,6 +448,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
       I.dval[i] = D;
     }
     if (I.trace) I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + i] = f;
+    if (slot_out) *slot_out = accept ? (si ^ 1) : si;  // the survivor's slot
   }
 }
 
@@ -737,6 +743,10 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
   // and the crossover word of a generation depend on (g, i) only and are drawn
   // while the previous generation's last barrier completes
   const uint32_t jg0 = (uint32_t)((threadIdx.x * I.c) >> 2);
+  // pre: own_slot_sh carries the individual's current slot from one phase to the next
+  // (set by thread 0 after its selection), so its selector is not read back; the first
+  // DE phase of a launch reads it
+  bool own_known = false;
   int4 r_pre = make_int4(0, 0, 0, 0);
   uint4 wcr_pre = make_uint4(0u, 0u, 0u, 0u);
   if (pre && g < g_end) {
@@ -752,7 +762,8 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       int slot = 0;
       const unsigned long long key =
           de_individual<COMP, false, TS, DUAL, false, STG>(I, K, tbl, g, i, r, sel_in, sel_out,
-                                                            sh, &slot, stg, pre, wcr_pre);
+                                                            sh, &slot, stg, pre, wcr_pre,
+                                                            own_known ? own_slot_sh : -1);
       // ordered before the barrier's release
       if (threadIdx.x == 0) {
         I.dekey[i] = slot_key(key, i, slot);
@@ -784,9 +795,14 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i == la || i == lb || i == ld) continue;
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
-      if (pre)
+      if (pre) {
+        int gslot = 0;
         gwo_individual<COMP, false, TS, DUAL, false, true>(I, K, tbl, g, i, sel_out, la, lb, ld,
-                                                           sh, wpre, own0, own1, lslot_sh);
+                                                           sh, wpre, own0, own1, lslot_sh,
+                                                           nullptr, own_slot_sh, &gslot);
+        // read by every thread after the next barrier's CTA synchronisation
+        if (threadIdx.x == 0) own_slot_sh = gslot;
+      }
       else
         gwo_individual<COMP, false, TS, DUAL, false, false, STG>(
             I, K, tbl, g, i, sel_out, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
@@ -798,6 +814,7 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     }
     // the next DE phase reads any individual: every CTA must have finished GWO
     grid_arrive(bar, target);
+    own_known = pre;
     if (pre && g + 1 < g_end) {
       r_pre = de_indices(K, I.inst, (uint32_t)(g + 1), blockIdx.x, I.NP, I.N);
       wcr_pre = rng4(K, I.inst, TAG_CR, (uint32_t)(g + 1), (uint32_t)blockIdx.x, jg0);
