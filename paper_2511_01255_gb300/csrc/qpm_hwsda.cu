@@ -176,8 +176,7 @@ static __global__ void k_init(InstDev I) {
   }
 }
 
-// ------------------------------------------ Step 2: DE rand/1/bin + selection
-// returns (in thread 0) the key of the survivor for the leader choice
+// ------------------------------------------------------------- row staging
 // Row staging (STG): the four rows an update reads (own + three donors or leaders)
 // and, when the phasor table is not in shared memory (!TS), the group's four table
 // entries are copied ahead into shared memory with cp.async, so the next group's
@@ -248,6 +247,8 @@ __device__ __forceinline__ void push4_staged(Acc<COMP> &acc, const float4 *tbl, 
   else push4<COMP, true>(acc, st + 4 * blockDim.x, blockDim.x, 0, 0, u);
 }
 
+// ------------------------------------------ Step 2: DE rand/1/bin + selection
+// returns (in thread 0) the key of the survivor for the leader choice
 // WT: the team is one warp (t = lane, warp reduction) instead of the whole CTA
 // r = (r1, r2, r3, jrand) from de_indices
 // STG: rows staged through stg (known slots only, so not with DUAL)
