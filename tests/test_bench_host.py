@@ -41,3 +41,24 @@ def test_phase_bound_takes_each_phase_limit():
     for hbm in (100.0, 1000.0, 7000.0):
         tb = bench.phase_bound_s_per_gen(N, NP, 1, ISSUE, hbm)
         assert tb >= t1 * (1 - 1e-12) and tb >= 28.0 * genes / (hbm * 1e9) * (1 - 1e-12)
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one JSON line
+    with the contract's keys, marked as the reference, with no GPU work."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--cpu-budget", "0.2"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["gpu_launches"] == 0 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["config"]["workload"] == "n1000_np256_g2000"
