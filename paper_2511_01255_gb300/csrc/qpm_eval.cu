@@ -397,7 +397,7 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (prob->N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: need N >= 1 and NP >= 1");
   if (ld < prob->N) return fail(QPM_ERR_ARG, "qpm_eval_noalloc: leading dimension smaller than the row");
   if (prob->N > (1 << 28) || NP > (1 << 26))
-    return fail(QPM_ERR_ARG, "qpm_eval_noalloc: problem exceeds the fixed scratch (8 MiB)");
+    return fail(QPM_ERR_ARG, "qpm_eval_noalloc: N above 2^28 or NP above 2^26");
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_noalloc: too many rows");
   const EvalShape sh = eval_rows_shape(NP, prob->N, 20);
   const int32_t Npad = (prob->N + 3) & ~3;
