@@ -6,8 +6,10 @@
 // domains per lookup in the sign-block table (the block's monoid triple for its sign
 // pattern, precomputed in FP64), whose entries are streamed into shared memory per
 // step of 128 domains, the next step's with cp.async while this one is swept.
-// Float genes arrive 32 domains at a time with coalesced 16-byte loads issued one
-// step ahead and are transposed through a per-warp shared-memory tile.  Packed sign
+// Float genes arrive 32 domains at a time and are transposed through per-warp
+// shared-memory tiles: rows that are 16-byte aligned through a ring of ER_RING tiles
+// filled by cp.async ER_RING - 1 sub-steps ahead, other rows with register loads one
+// sub-step ahead.  Packed sign
 // words (32 domains each) are read four at a time straight into the lane of their
 // row.  The warps of a CTA take consecutive row groups of the same segment and
 // synchronise once per step of 128 domains.  A second kernel (a warp per row) combines
@@ -28,9 +30,10 @@
 namespace qpm {
 
 // partial monoids, structure of arrays: part[(comp * S + s) * NPpad + i], comp in A,B,C
-// KIND 0: float genes (vector loads), 1: float genes (scalar loads).
-// blk: the problem's sign-block table, read as float4.  grid (S, ceil(groups / ER_WPC)).
-template <int KIND, bool COMP>
+// Float genes of rows that are not 16-byte aligned (scalar loads, one sub-step ahead
+// in registers).  blk: the problem's sign-block table, read as float4.
+// grid (S, ceil(groups / ER_WPC)).
+template <bool COMP>
 static __global__ void __launch_bounds__(ER_WPC * 32, 5)
     k_eval_rows(const float *__restrict__ src, int64_t ld, EvalShape sh,
                 const float4 *__restrict__ blk, float2 *__restrict__ part) {
@@ -42,7 +45,7 @@ static __global__ void __launch_bounds__(ER_WPC * 32, 5)
   const bool live = r0 < sh.NP;
   const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
   float4 R[8];
-  if (live) er_load_genes<KIND == 0>(src, ld, sh, r0, m0, R);
+  if (live) er_load_genes<false>(src, ld, sh, r0, m0, R);
   er_stage_step(tb, blk, m0, 0, nb);
   const float2 *bt = (const float2 *)tb;
   ErAcc<COMP> acc;
@@ -62,7 +65,7 @@ static __global__ void __launch_bounds__(ER_WPC * 32, 5)
 #pragma unroll
       for (int j = 0; j < 8; ++j) T[er_tix(4 * j + (lane >> 3), lane & 7)] = R[j];
       __syncwarp();
-      if (ms + 32 < m1) er_load_genes<KIND == 0>(src, ld, sh, r0, ms + 32, R);
+      if (ms + 32 < m1) er_load_genes<false>(src, ld, sh, r0, ms + 32, R);
 #pragma unroll
       for (int c4 = 0; c4 < 8; ++c4) {  // the sub-step's 8 blocks of 4 domains
         er_push_block(acc.m, er_pattern(T[er_tix(lane, c4)]), bp + (8 * q + c4) * BLK_F2);
@@ -70,6 +73,78 @@ static __global__ void __launch_bounds__(ER_WPC * 32, 5)
       }
     }
   }
+  if (!live) return;
+  acc.fold();
+  const Mono run = acc.get();
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+  const size_t o = (size_t)s * sh.NPpad + r0 + lane;
+  part[o] = run.A;
+  part[stride + o] = run.B;
+  part[2 * stride + o] = run.C;
+}
+
+// Float genes of 16-byte aligned rows.  Sub-step u (32 domains) of the warp's 32
+// rows lands by cp.async in slot u % ER_RING of the warp's ring of 4 KB tiles, issued
+// ER_RING - 1 sub-steps before it is swept: 8 KB of each warp's loads stay in flight
+// without holding registers (60 KB of shared memory per CTA, 3 CTAs per SM).  Every
+// sub-step commits one cp.async group (empty past the segment's end), holding the
+// genes of sub-step u + ER_RING - 1 and, at the start of a 128-domain step, the next
+// step's sign-block entries; waiting until at most ER_RING - 2 groups are pending
+// therefore completes sub-step u's genes and, for ER_RING <= 5, its step's entries.
+// The accumulation order equals k_eval_rows'.  grid (S, ceil(groups / ER_WPC)).
+constexpr int ER_RING = 3;
+constexpr int ER_RING_CTAS = 3;  // resident CTAs per SM (shared memory)
+static_assert(ER_RING >= 2 && ER_RING <= 5, "entries of a step must complete with its first sub-step");
+constexpr size_t ER_RING_SMEM = sizeof(float4) * (2 * ER_STEP_F4_P + ER_WPC * ER_RING * 256);
+template <bool COMP>
+static __global__ void __launch_bounds__(ER_WPC * 32, ER_RING_CTAS)
+    k_eval_rows_ring(const float *__restrict__ src, int64_t ld, EvalShape sh,
+                     const float4 *__restrict__ blk, float2 *__restrict__ part) {
+  extern __shared__ float4 dyn[];  // [two steps of sign-block entries][ER_WPC rings]
+  float4 *tb = dyn;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *ring = dyn + 2 * ER_STEP_F4_P + warp * (ER_RING * 256);
+  const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
+  const bool live = r0 < sh.NP;
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7, nsub = (m1 - m0 + 31) >> 5;
+  er_stage_entries(tb, blk, m0, 0, nb);
+  cp_async_commit();
+#pragma unroll
+  for (int u = 0; u < ER_RING - 1; ++u) {
+    if (live && u < nsub) er_copy_genes(ring + u * 256, src, ld, sh, r0, m0 + 32 * u);
+    cp_async_commit();
+  }
+  const float2 *bt = (const float2 *)tb;
+  ErAcc<COMP> acc;
+  acc.zero();
+  int slot = 0;  // u % ER_RING
+  for (int k = 0; k < nsteps; ++k) {
+    const float2 *bp = bt + (size_t)(k & 1) * 2 * ER_STEP_F4_P;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {  // 4 sub-steps of 32 domains
+      const int u = 4 * k + q;
+      if (u >= nsub) break;
+      cp_async_wait<ER_RING - 2>();  // this thread's copies of sub-step u (and of step k)
+      if (q == 0) __syncthreads();   // everyone's; everyone done with step k - 1
+      else __syncwarp();             // the warp's lanes' copies; done with sub-step u - 1
+      const int ua = u + ER_RING - 1;
+      const int sa = slot == 0 ? ER_RING - 1 : slot - 1;  // the slot swept at u - 1
+      if (live && ua < nsub) er_copy_genes(ring + sa * 256, src, ld, sh, r0, m0 + 32 * ua);
+      if (q == 0 && k + 1 < nsteps)
+        er_stage_entries(tb + ((k + 1) & 1) * ER_STEP_F4_P, blk, m0, k + 1, nb);
+      cp_async_commit();
+      const float4 *T = ring + slot * 256;
+      slot = slot + 1 == ER_RING ? 0 : slot + 1;
+      if (!live) continue;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {  // the sub-step's 8 blocks of 4 domains
+        er_push_block(acc.m, er_pattern(T[er_tix(lane, c4)]), bp + (8 * q + c4) * BLK_F2);
+        if ((c4 & 3) == 3) acc.fold();
+      }
+    }
+  }
+  cp_async_wait<0>();
   if (!live) return;
   acc.fold();
   const Mono run = acc.get();
@@ -288,19 +363,28 @@ EvalShape eval_rows_shape(int NP, int N, int warps_per_sm, int lmax) {
   return sh;
 }
 
-static void launch_eval_rows(int kind, bool comp, const void *src, int64_t ld, const EvalShape &sh,
-                             const float2 *blk, float2 *part, cudaStream_t stream) {
+// shape of the float-gene sweep: the ring kernel for aligned rows keeps ER_WPC x
+// ER_RING_CTAS warps per SM, the register-prefetch kernel 20
+static EvalShape eval_genes_shape(int NP, int N, bool aligned) {
+  return eval_rows_shape(NP, N, aligned ? ER_WPC * ER_RING_CTAS : 20);
+}
+
+static qpm_status launch_eval_rows(bool aligned, bool comp, const float *g, int64_t ld,
+                                   const EvalShape &sh, const float2 *blk, float2 *part,
+                                   cudaStream_t stream) {
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
-  const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
-  const float *g = (const float *)src;
   const float4 *b4 = (const float4 *)blk;
-#define QPM_ER(K, C) k_eval_rows<K, C><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part)
-  if (kind == 0) {
-    if (comp) QPM_ER(0, true); else QPM_ER(0, false);
+  if (aligned) {
+    const void *fn = comp ? (const void *)k_eval_rows_ring<true> : (const void *)k_eval_rows_ring<false>;
+    QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ER_RING_SMEM));
+    if (comp) k_eval_rows_ring<true><<<grid, ER_WPC * 32, ER_RING_SMEM, stream>>>(g, ld, sh, b4, part);
+    else k_eval_rows_ring<false><<<grid, ER_WPC * 32, ER_RING_SMEM, stream>>>(g, ld, sh, b4, part);
   } else {
-    if (comp) QPM_ER(1, true); else QPM_ER(1, false);
+    const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
+    if (comp) k_eval_rows<true><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
+    else k_eval_rows<false><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
   }
-#undef QPM_ER
+  return QPM_OK;
 }
 
 static void launch_eval_packed(bool vecw, bool comp, const uint32_t *src, int64_t ld,
@@ -332,15 +416,19 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   qpm_status st = get_table(prob, stream, &table, &konst, &blk);
   if (st != QPM_OK) return st;
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
+  const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
   const EvalShape sh = kind == 2 ? eval_rows_shape(NP, prob->N, 32, ER_LMAX_P)
-                                 : eval_rows_shape(NP, prob->N, 20);
+                                 : eval_genes_shape(NP, prob->N, aligned);
   void *scratch;
   st = get_scratch(stream, sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad, &scratch);
   if (st != QPM_OK) return st;
   float2 *part = (float2 *)scratch;
-  const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
-  if (kind == 2) launch_eval_packed(aligned, comp != 0, (const uint32_t *)src, ld, sh, blk, part, stream);
-  else launch_eval_rows(aligned ? 0 : 1, comp != 0, src, ld, sh, blk, part, stream);
+  if (kind == 2) {
+    launch_eval_packed(aligned, comp != 0, (const uint32_t *)src, ld, sh, blk, part, stream);
+  } else {
+    st = launch_eval_rows(aligned, comp != 0, (const float *)src, ld, sh, blk, part, stream);
+    if (st != QPM_OK) return st;
+  }
   QPM_CUDA(cudaGetLastError());
   k_eval_combine<<<(NP + 7) / 8, 256, 0, stream>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());
@@ -399,7 +487,8 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (prob->N > (1 << 28) || NP > (1 << 26))
     return fail(QPM_ERR_ARG, "qpm_eval_noalloc: N above 2^28 or NP above 2^26");
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_noalloc: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, prob->N, 20);
+  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
+  const EvalShape sh = eval_genes_shape(NP, prob->N, vec);
   const int32_t Npad = (prob->N + 3) & ~3;
   const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
   const size_t b_blk = up256(sizeof(float2) * BLK_F2 * (size_t)(Npad / 4));
@@ -427,8 +516,8 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (st != QPM_OK) return st;
   st = launch_block_table(prob->N, prob->kappa1, prob->kappa2, blk, s);
   if (st != QPM_OK) return st;
-  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
-  launch_eval_rows(vec ? 0 : 1, compensated != 0, genes, ld, sh, blk, part, s);
+  st = launch_eval_rows(vec, compensated != 0, genes, ld, sh, blk, part, s);
+  if (st != QPM_OK) return st;
   QPM_CUDA(cudaGetLastError());
   k_eval_combine<<<(NP + 7) / 8, 256, 0, s>>>(sh, part, konst, (float2 *)d_eff, fit);
   QPM_CUDA(cudaGetLastError());

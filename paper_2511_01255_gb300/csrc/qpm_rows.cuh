@@ -46,6 +46,27 @@ __device__ __forceinline__ void er_load_genes(const float *__restrict__ g, int64
   }
 }
 
+// the same step copied asynchronously (cp.async, not committed) into the per-warp
+// tile T in the layout of er_tix: lane l's copy k lands at row 4k + l / 8, columns
+// 4 (l % 8) .. +3.  16-byte aligned rows (ld % 4 == 0) only; genes past the row
+// end and rows past NP are zero-filled.
+__device__ __forceinline__ void er_copy_genes(float4 *T, const float *__restrict__ g, int64_t ld,
+                                              const EvalShape &sh, int r0, int ms) {
+  const int lane = threadIdx.x & 31;
+  const int m = ms + 4 * (lane & 7);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int tr = 4 * k + (lane >> 3), gr = r0 + tr;
+    const float *src = g;
+    int bytes = 0;
+    if (gr < sh.NP && m < sh.N) {
+      src = g + (int64_t)gr * ld + m;
+      bytes = 4 * min(4, sh.N - m);
+    }
+    cp_async16(&T[er_tix(tr, lane & 7)], src, bytes);
+  }
+}
+
 // sign words of one packed step (128 domains from ms, a multiple of 128) of row
 // `row`; words beyond the row's last domain are zero
 template <bool VECW>
@@ -78,15 +99,21 @@ constexpr int ER_LMAX_P = 4096;  // longest segment of the packed sweep
 constexpr int ER_STEP_F4_P = 32 * BLK_F2 / 2;  // float4 of entries per step of 128 domains
 
 // the sign-block entries of step k of a segment starting at m0 (blocks
-// m0 / 4 + 32 k .. + 31) into buf, copied with cp.async by the whole CTA and
-// committed as one group; blocks past the last of the problem are zero
-__device__ __forceinline__ void er_stage_step(float4 *buf, const float4 *__restrict__ blk, int m0,
-                                              int k, int nb) {
+// m0 / 4 + 32 k .. + 31) into buf, copied with cp.async by the whole CTA (not
+// committed); blocks past the last of the problem are zero
+__device__ __forceinline__ void er_stage_entries(float4 *buf, const float4 *__restrict__ blk,
+                                                 int m0, int k, int nb) {
   const int b0 = (m0 >> 2) + 32 * k;
   for (int i = threadIdx.x; i < ER_STEP_F4_P; i += blockDim.x) {
     if (b0 + i / (BLK_F2 / 2) < nb) cp_async16(buf + i, blk + (size_t)b0 * (BLK_F2 / 2) + i);
     else buf[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+}
+
+// er_stage_entries committed as one group
+__device__ __forceinline__ void er_stage_step(float4 *buf, const float4 *__restrict__ blk, int m0,
+                                              int k, int nb) {
+  er_stage_entries(buf, blk, m0, k, nb);
   cp_async_commit();
 }
 
