@@ -169,7 +169,8 @@ def test_multi_wavelength_objective_against_oracle(q, orc, K):
     # each |G0 - G_k| term carries the d_eff error; FP32 rounding of G0-sized sums
     scale = K * G0 + beta * np.abs(Dr).max()
     assert np.max(np.abs(obj.cpu().numpy() - objr)) <= TOL_D * scale
-    # one problem through the fused path equals qpm_eval
+    # one problem through the fused path equals qpm_eval: at this size both sweeps
+    # split the rows into the same 128-domain segments
     if K == 1:
         D1 = torch.empty((NP, 2), device="cuda")
         q.qpm_eval(N, kap[0][0], kap[0][1], torch.from_numpy(X).cuda(), D1)
