@@ -52,6 +52,35 @@ def test_eval_random_genes(q, orc, N, NP, comp):
     assert np.allclose(fp, Dp[:, 0] ** 2 + Dp[:, 1] ** 2, rtol=1e-6, atol=0)
 
 
+@pytest.mark.parametrize("N", [1, 3, 33, 130, 1001, 4097])
+@pytest.mark.parametrize("comp", [0, 1])
+def test_eval_aligned_rows_with_ragged_tail(q, orc, N, comp):
+    """16-byte aligned rows (leading dimension a multiple of 4) whose length is not:
+    the last asynchronous copy of every row is partial and zero-fills the rest; the
+    padding columns hold NaN and must never be read."""
+    from paper_2511_01255_gb300 import workloads as W
+    ld = (N + 3) // 4 * 4 + 4
+    X = W.random_genes(37, N, seed=N + 5, ld=ld)
+    X[:, N:] = np.nan
+    D, f = run_eval(q, X, N, K1, K2, comp)
+    ref = orc.deff_genes(np.ascontiguousarray(X[:, :N]), K1, K2)
+    assert deff_err(D, ref, N).max() < TOL_D
+    assert np.all(np.isfinite(f))
+
+
+def test_eval_aligned_long_ragged_rows_sampled(q, orc):
+    """N = 99997 in 16-byte aligned rows of 100000 floats (NaN padding), 64 rows: many
+    segments and 128-domain steps, a ragged last sub-step; 3 rows re-done by the oracle."""
+    from paper_2511_01255_gb300 import workloads as W
+    N, ld = 99997, 100000
+    X = W.random_genes(64, N, seed=17, ld=ld)
+    X[:, N:] = np.nan
+    D, _ = run_eval(q, X, N, K1, K2, 1)
+    rows = [0, 31, 63]
+    ref = orc.deff_genes(np.ascontiguousarray(X[rows, :N]), K1, K2)
+    assert deff_err(D[rows], ref, N).max() < TOL_D
+
+
 @pytest.mark.parametrize("N", [1, 5, 30, 33, 1001])
 def test_packed_ignores_bits_past_the_row(q, N):
     """Sign bits of the last word beyond domain N - 1 do not change d_eff: the

@@ -54,12 +54,14 @@ def _close(Da, Db, N):
 
 def test_noalloc_matches_qpm_eval_on_two_calls_in_a_row(q):
     from paper_2511_01255_gb300 import workloads as W
-    # two different problems back to back: the second call must not depend on
-    # what the first left in the shared scratch
-    cases = [(4097, 2 * math.pi / 6.9, 2 * math.pi / 1.55, 37, 1),
-             (1000, 2 * math.pi / 7.0, 2 * math.pi / 1.6, 256, 0)]
-    for N, k1, k2, NP, comp in cases:
-        X = W.random_genes(NP, N, seed=N + NP)
+    # different problems back to back: a call must not depend on
+    # what the one before left in the shared scratch
+    # (rows of 4097 floats take the scalar-load sweep, rows of 4100 the cp.async ring)
+    cases = [(4097, 2 * math.pi / 6.9, 2 * math.pi / 1.55, 37, 1, 4097),
+             (1000, 2 * math.pi / 7.0, 2 * math.pi / 1.6, 256, 0, 1000),
+             (4097, 2 * math.pi / 6.9, 2 * math.pi / 1.55, 37, 1, 4100)]
+    for N, k1, k2, NP, comp, ld in cases:
+        X = W.random_genes(NP, N, seed=N + NP, ld=ld)
         D0, f0, D1, f1 = _both(q, N, k1, k2, X, comp)
         assert _close(D1, D0, N) < TOL_D
         assert np.all(np.abs(f1 - f0) <= 2 * TOL_D * np.maximum(f0, (1e-3 * N * N / 2) ** 2))
