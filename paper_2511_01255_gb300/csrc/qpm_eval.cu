@@ -83,68 +83,27 @@ static __global__ void __launch_bounds__(ER_WPC * 32, 5)
   part[2 * stride + o] = run.C;
 }
 
-// Float genes of 16-byte aligned rows.  Sub-step u (32 domains) of the warp's 32
-// rows lands by cp.async in slot u % ER_RING of the warp's ring of 4 KB tiles, issued
-// ER_RING - 1 sub-steps before it is swept: 8 KB of each warp's loads stay in flight
-// without holding registers (60 KB of shared memory per CTA, 3 CTAs per SM).  Every
-// sub-step commits one cp.async group (empty past the segment's end), holding the
-// genes of sub-step u + ER_RING - 1 and, at the start of a 128-domain step, the next
-// step's sign-block entries; waiting until at most ER_RING - 2 groups are pending
-// therefore completes sub-step u's genes and, for ER_RING <= 5, its step's entries.
-// The accumulation order equals k_eval_rows'.  grid (S, ceil(groups / ER_WPC)).
-constexpr int ER_RING = 3;
+// Float genes of 16-byte aligned rows through the per-warp ring of er_ring_sweep (60 KB
+// of shared memory per CTA, 3 CTAs per SM); the accumulation order equals k_eval_rows'.
+// grid (S, ceil(groups / ER_WPC)).
 constexpr int ER_RING_CTAS = 3;  // resident CTAs per SM (shared memory)
-static_assert(ER_RING >= 2 && ER_RING <= 5, "entries of a step must complete with its first sub-step");
-constexpr size_t ER_RING_SMEM = sizeof(float4) * (2 * ER_STEP_F4_P + ER_WPC * ER_RING * 256);
 template <bool COMP>
 static __global__ void __launch_bounds__(ER_WPC * 32, ER_RING_CTAS)
     k_eval_rows_ring(const float *__restrict__ src, int64_t ld, EvalShape sh,
                      const float4 *__restrict__ blk, float2 *__restrict__ part) {
-  extern __shared__ float4 dyn[];  // [two steps of sign-block entries][ER_WPC rings]
-  float4 *tb = dyn;
+  extern __shared__ float4 dyn[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 *ring = dyn + 2 * ER_STEP_F4_P + warp * (ER_RING * 256);
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
   const bool live = r0 < sh.NP;
-  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7, nsub = (m1 - m0 + 31) >> 5;
-  er_stage_entries(tb, blk, m0, 0, nb);
-  cp_async_commit();
-#pragma unroll
-  for (int u = 0; u < ER_RING - 1; ++u) {
-    if (live && u < nsub) er_copy_genes(ring + u * 256, src, ld, sh, r0, m0 + 32 * u);
-    cp_async_commit();
-  }
-  const float2 *bt = (const float2 *)tb;
+  const float4 *const tabs[1] = {blk};
   ErAcc<COMP> acc;
   acc.zero();
-  int slot = 0;  // u % ER_RING
-  for (int k = 0; k < nsteps; ++k) {
-    const float2 *bp = bt + (size_t)(k & 1) * 2 * ER_STEP_F4_P;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {  // 4 sub-steps of 32 domains
-      const int u = 4 * k + q;
-      if (u >= nsub) break;
-      cp_async_wait<ER_RING - 2>();  // this thread's copies of sub-step u (and of step k)
-      if (q == 0) __syncthreads();   // everyone's; everyone done with step k - 1
-      else __syncwarp();             // the warp's lanes' copies; done with sub-step u - 1
-      const int ua = u + ER_RING - 1;
-      const int sa = slot == 0 ? ER_RING - 1 : slot - 1;  // the slot swept at u - 1
-      if (live && ua < nsub) er_copy_genes(ring + sa * 256, src, ld, sh, r0, m0 + 32 * ua);
-      if (q == 0 && k + 1 < nsteps)
-        er_stage_entries(tb + ((k + 1) & 1) * ER_STEP_F4_P, blk, m0, k + 1, nb);
-      cp_async_commit();
-      const float4 *T = ring + slot * 256;
-      slot = slot + 1 == ER_RING ? 0 : slot + 1;
-      if (!live) continue;
-#pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {  // the sub-step's 8 blocks of 4 domains
-        er_push_block(acc.m, er_pattern(T[er_tix(lane, c4)]), bp + (8 * q + c4) * BLK_F2);
-        if ((c4 & 3) == 3) acc.fold();
-      }
-    }
-  }
-  cp_async_wait<0>();
+  er_ring_sweep<1>(dyn, src, ld, sh, tabs, m0, m1, r0, live,
+                   [&](uint32_t e, const float2 *E, int b) {
+                     er_push_block(acc.m, e, E + b * BLK_F2);
+                     if ((b & 3) == 3) acc.fold();
+                   });
   if (!live) return;
   acc.fold();
   const Mono run = acc.get();
@@ -376,9 +335,10 @@ static qpm_status launch_eval_rows(bool aligned, bool comp, const float *g, int6
   const float4 *b4 = (const float4 *)blk;
   if (aligned) {
     const void *fn = comp ? (const void *)k_eval_rows_ring<true> : (const void *)k_eval_rows_ring<false>;
-    QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ER_RING_SMEM));
-    if (comp) k_eval_rows_ring<true><<<grid, ER_WPC * 32, ER_RING_SMEM, stream>>>(g, ld, sh, b4, part);
-    else k_eval_rows_ring<false><<<grid, ER_WPC * 32, ER_RING_SMEM, stream>>>(g, ld, sh, b4, part);
+    const size_t smem = er_ring_smem(1);
+    QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (comp) k_eval_rows_ring<true><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
+    else k_eval_rows_ring<false><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
   } else {
     const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
     if (comp) k_eval_rows<true><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);

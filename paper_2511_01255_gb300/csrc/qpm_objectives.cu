@@ -96,12 +96,46 @@ struct MultiTables {
   const float2 *konst[MW_KMAX];
 };
 
-// The qpm_eval sweep with K sign-block tables (the same segments and order, so K = 1
-// reproduces qpm_eval's plain scan bit for bit).  Dynamic shared memory: two steps of
-// the K tables' entries, [2][K][ER_STEP_F4_P] float4.
-// Partials as for qpm_eval, one set per problem: part[((3k + comp) * S + s) * NPpad + i].
+// The qpm_eval sweeps with K sign-block tables: the same segments and order for the
+// same rows, so K = 1 reproduces qpm_eval's plain scan bit for bit.  Partials as for
+// qpm_eval, one set per problem: part[((3k + comp) * S + s) * NPpad + i].
 // grid (S, ceil(groups / ER_WPC)).
-template <bool VEC, int K>
+
+// 16-byte aligned rows: er_ring_sweep with K tables; K x 12 KB + 48 KB of shared memory
+// per CTA, so 3 CTAs per SM for K <= 2 and 2 for K = 3, 4
+__host__ __device__ constexpr int mw_ring_ctas(int K) { return K <= 2 ? 3 : 2; }
+template <int K>
+static __global__ void __launch_bounds__(ER_WPC * 32, mw_ring_ctas(K))
+    k_multi_rows_ring(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
+                      float2 *__restrict__ part) {
+  extern __shared__ float4 dyn[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
+  const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
+  const bool live = r0 < sh.NP;
+  Mono acc[K];
+#pragma unroll
+  for (int p = 0; p < K; ++p) acc[p] = mono_zero();
+  er_ring_sweep<K>(dyn, genes, ld, sh, mt.t, m0, m1, r0, live,
+                   [&](uint32_t e, const float2 *E, int b) {
+#pragma unroll
+                     for (int p = 0; p < K; ++p)
+                       er_push_block(acc[p], e, E + (size_t)p * 2 * ER_STEP_F4_P + b * BLK_F2);
+                   });
+  if (!live) return;
+  const size_t stride = (size_t)sh.S * sh.NPpad;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const size_t o = (size_t)(3 * k) * stride + (size_t)s * sh.NPpad + r0 + lane;
+    part[o] = acc[k].A;
+    part[o + stride] = acc[k].B;
+    part[o + 2 * stride] = acc[k].C;
+  }
+}
+
+// other rows: scalar gene loads one sub-step ahead in registers.  Dynamic shared
+// memory: two steps of the K tables' entries, [2][K][ER_STEP_F4_P] float4.
+template <int K>
 static __global__ void __launch_bounds__(ER_WPC * 32)
     k_multi_rows(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
                  float2 *__restrict__ part) {
@@ -113,7 +147,7 @@ static __global__ void __launch_bounds__(ER_WPC * 32)
   const bool live = r0 < sh.NP;
   const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7;
   float4 R[8];
-  if (live) er_load_genes<VEC>(genes, ld, sh, r0, m0, R);
+  if (live) er_load_genes<false>(genes, ld, sh, r0, m0, R);
   // step k of problem p in buffer ((k & 1) * K + p); one commit group per step
 #pragma unroll
   for (int p = 0; p < K; ++p) er_stage_step(tb + p * ER_STEP_F4_P, mt.t[p], m0, 0, nb);
@@ -140,7 +174,7 @@ static __global__ void __launch_bounds__(ER_WPC * 32)
 #pragma unroll
       for (int j = 0; j < 8; ++j) T[er_tix(4 * j + (lane >> 3), lane & 7)] = R[j];
       __syncwarp();
-      if (ms + 32 < m1) er_load_genes<VEC>(genes, ld, sh, r0, ms + 32, R);
+      if (ms + 32 < m1) er_load_genes<false>(genes, ld, sh, r0, ms + 32, R);
 #pragma unroll 2
       for (int c4 = 0; c4 < 8; ++c4) {
         const uint32_t e = er_pattern(T[er_tix(lane, c4)]);
@@ -231,17 +265,17 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     mt.t[k] = (const float4 *)blk;
   }
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
-  const EvalShape sh = eval_rows_shape(NP, N, 20);
+  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
+  const EvalShape sh = eval_rows_shape(NP, N, vec ? ER_WPC * mw_ring_ctas(K) : 20);
   const size_t need = sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;
   if (!scratch || scratch_bytes < need)
     return fail(QPM_ERR_ARG, "qpm_eval_multi: scratch smaller than qpm_eval_multi_scratch_bytes()");
   float2 *part = (float2 *)scratch;
-  const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
-  const size_t smem = sizeof(float4) * 2 * (size_t)K * ER_STEP_F4_P;
 #define QPM_MW(KK)                                                                          \
   {                                                                                         \
-    const void *fn = vec ? (const void *)k_multi_rows<true, KK> : (const void *)k_multi_rows<false, KK>; \
+    const void *fn = vec ? (const void *)k_multi_rows_ring<KK> : (const void *)k_multi_rows<KK>; \
+    const size_t smem = vec ? er_ring_smem(KK) : sizeof(float4) * 2 * (size_t)KK * ER_STEP_F4_P; \
     QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     EvalShape shv = sh;                                                                     \
     int64_t ldv = ld;                                                                       \
@@ -256,6 +290,8 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
   return QPM_OK;
 }
 
+// sized for the split of unaligned rows: fewer resident warps (the ring form of aligned
+// rows) only lengthen the segments, so no split the call takes has more of them
 extern "C" size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP) {
   if (K < 1 || N < 1 || NP < 1) return 0;
   const EvalShape sh = eval_rows_shape(NP, N, 20);

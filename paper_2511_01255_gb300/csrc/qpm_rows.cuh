@@ -117,6 +117,69 @@ __device__ __forceinline__ void er_stage_step(float4 *buf, const float4 *__restr
   cp_async_commit();
 }
 
+// Ring sweep of one warp over its segment [m0, m1) for float genes in 16-byte aligned
+// rows, with NT sign-block tables.  Sub-step u (32 domains) of the warp's 32 rows lands
+// by cp.async in slot u % ER_RING of the warp's ring of 4 KB tiles, issued ER_RING - 1
+// sub-steps before it is swept, so 8 KB of each warp's loads stay in flight without
+// holding registers.  Every sub-step commits one cp.async group (empty past the
+// segment's end) holding the genes of sub-step u + ER_RING - 1 and, at the start of a
+// 128-domain step, the next step's entries of every table; waiting until at most
+// ER_RING - 2 groups are pending therefore completes sub-step u's genes and, for
+// ER_RING <= 5, its step's entries.  Shared memory `dyn`: [2 steps][NT][ER_STEP_F4_P]
+// entries, then ER_WPC rings of ER_RING tiles.  push(e, E, b) appends block b (0..31)
+// of the current step with sign pattern e; table t's entries of the step start at
+// E + t * 2 * ER_STEP_F4_P (float2).  Every thread of the CTA must call this (it holds
+// CTA barriers); warps without rows (live false) only stage entries.
+constexpr int ER_RING = 3;
+static_assert(ER_RING >= 2 && ER_RING <= 5, "a step's entries must complete with its first sub-step");
+__host__ __device__ constexpr size_t er_ring_smem(int NT) {
+  return sizeof(float4) * (2 * (size_t)NT * ER_STEP_F4_P + (size_t)ER_WPC * ER_RING * 256);
+}
+
+template <int NT, class Push>
+__device__ __forceinline__ void er_ring_sweep(float4 *dyn, const float *__restrict__ g, int64_t ld,
+                                              const EvalShape &sh, const float4 *const *tabs,
+                                              int m0, int m1, int r0, bool live, Push &&push) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *ring = dyn + 2 * NT * ER_STEP_F4_P + warp * (ER_RING * 256);
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7, nsub = (m1 - m0 + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) er_stage_entries(dyn + t * ER_STEP_F4_P, tabs[t], m0, 0, nb);
+  cp_async_commit();
+#pragma unroll
+  for (int u = 0; u < ER_RING - 1; ++u) {
+    if (live && u < nsub) er_copy_genes(ring + u * 256, g, ld, sh, r0, m0 + 32 * u);
+    cp_async_commit();
+  }
+  int slot = 0;  // u % ER_RING
+  for (int k = 0; k < nsteps; ++k) {
+    const float2 *bp = (const float2 *)dyn + (size_t)(k & 1) * NT * 2 * ER_STEP_F4_P;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {  // 4 sub-steps of 32 domains
+      const int u = 4 * k + q;
+      if (u >= nsub) break;
+      cp_async_wait<ER_RING - 2>();  // this thread's copies of sub-step u (and of step k)
+      if (q == 0) __syncthreads();   // everyone's; everyone done with step k - 1
+      else __syncwarp();             // the warp's lanes' copies; done with sub-step u - 1
+      const int ua = u + ER_RING - 1;
+      const int sa = slot == 0 ? ER_RING - 1 : slot - 1;  // the slot swept at u - 1
+      if (live && ua < nsub) er_copy_genes(ring + sa * 256, g, ld, sh, r0, m0 + 32 * ua);
+      if (q == 0 && k + 1 < nsteps) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          er_stage_entries(dyn + (((k + 1) & 1) * NT + t) * ER_STEP_F4_P, tabs[t], m0, k + 1, nb);
+      }
+      cp_async_commit();
+      const float4 *T = ring + slot * 256;
+      slot = slot + 1 == ER_RING ? 0 : slot + 1;
+      if (!live) continue;
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) push(er_pattern(T[er_tix(lane, c4)]), bp, 8 * q + c4);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 // append the block with sign pattern e (bit j: d_j = -1) whose 8 stored entries
 // (d_0 = +1) start at E8: a pattern with d_0 = -1 is its complement's entry with A
 // and B negated (an exact sign flip) and C unchanged

@@ -198,13 +198,30 @@ def test_multi_wavelength_objective_against_oracle(q, orc, K):
     # each |G0 - G_k| term carries the d_eff error; FP32 rounding of G0-sized sums
     scale = K * G0 + beta * np.abs(Dr).max()
     assert np.max(np.abs(obj.cpu().numpy() - objr)) <= TOL_D * scale
-    # one problem through the fused path equals qpm_eval: at this size both sweeps
-    # split the rows into the same 128-domain segments
+    # one problem through the fused path equals qpm_eval
     if K == 1:
         D1 = torch.empty((NP, 2), device="cuda")
         q.qpm_eval(N, kap[0][0], kap[0][1], torch.from_numpy(X).cuda(), D1)
         torch.cuda.synchronize()
         assert np.array_equal(D1.cpu().numpy(), Dg[:, 0])
+
+
+@pytest.mark.parametrize("ld_extra", [0, 1])
+def test_multi_wavelength_k1_equals_qpm_eval_on_long_rows(q, ld_extra):
+    """K = 1 takes qpm_eval's segments and order for long rows too: aligned rows (the
+    cp.async ring form, fewer and longer segments) and unaligned rows (ld = N + 1)."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    N, NP = 99996, 70
+    X = torch.from_numpy(W.random_genes(NP, N, seed=23, ld=N + ld_extra)).cuda()
+    kap = [(2 * math.pi / 6.9, 2 * math.pi / 1.55)]
+    obj = torch.empty(NP, device="cuda")
+    D = torch.empty((NP, 1, 2), device="cuda")
+    q.qpm_eval_multi(N, kap, X, 2.0e4, 0.7, obj, D)
+    D1 = torch.empty((NP, 2), device="cuda")
+    q.qpm_eval(N, kap[0][0], kap[0][1], X, D1)
+    torch.cuda.synchronize()
+    assert np.array_equal(D1.cpu().numpy(), D.cpu().numpy()[:, 0])
 
 
 def test_issue_peak_microbenchmark(q):
