@@ -150,9 +150,11 @@ static __global__ void __launch_bounds__(ER_WPC_P * 32)
       const uint32_t ws[4] = {cur.x, cur.y, cur.z, cur.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        const ErWord f = er_fold_word(ws[q]);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {  // the word's 8 blocks of 4 domains
-          er_push_block(acc.m, (ws[q] >> (4 * j)) & 0xFu, bp + (8 * q + j) * BLK_F2);
+          er_push_entry(acc.m, (f.folded >> (4 * j + 1)) & 7u, (f.lo << (31 - 4 * j)) & 0x80000000u,
+                        bp + (8 * q + j) * BLK_F2);
           if ((j & 3) == 3) acc.fold();
         }
       }

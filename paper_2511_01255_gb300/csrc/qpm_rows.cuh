@@ -180,19 +180,34 @@ __device__ __forceinline__ void er_ring_sweep(float4 *dyn, const float *__restri
   cp_async_wait<0>();
 }
 
-// append the block with sign pattern e (bit j: d_j = -1) whose 8 stored entries
-// (d_0 = +1) start at E8: a pattern with d_0 = -1 is its complement's entry with A
-// and B negated (an exact sign flip) and C unchanged
-__device__ __forceinline__ void er_push_block(Mono &m, uint32_t e, const float2 *E8) {
-  const uint32_t neg = 0u - (e & 1u);  // all ones when d_0 = -1
-  const float2 *E = E8 + 3 * (((e ^ neg) & 0xFu) >> 1);
+// append stored entry idx (0..7, the pattern with d_0 = +1) of a block whose 8
+// entries start at E8, with A and B negated when sm = 0x80000000 (the block's pattern
+// has d_0 = -1 and is the complement of entry idx: an exact sign flip, C unchanged)
+__device__ __forceinline__ void er_push_entry(Mono &m, uint32_t idx, uint32_t sm, const float2 *E8) {
+  const float2 *E = E8 + 3 * idx;
   const float2 a = E[0], b = E[1];
-  const uint32_t sm = neg & 0x80000000u;
   Mono R;
   R.A = make_float2(__uint_as_float(__float_as_uint(a.x) ^ sm), __uint_as_float(__float_as_uint(a.y) ^ sm));
   R.B = make_float2(__uint_as_float(__float_as_uint(b.x) ^ sm), __uint_as_float(__float_as_uint(b.y) ^ sm));
   R.C = E[2];
   m = mono_combine(m, R);
+}
+
+// append the block with sign pattern e (bit j: d_j = -1)
+__device__ __forceinline__ void er_push_block(Mono &m, uint32_t e, const float2 *E8) {
+  const uint32_t neg = 0u - (e & 1u);  // all ones when d_0 = -1
+  er_push_entry(m, ((e ^ neg) & 0xFu) >> 1, neg & 0x80000000u, E8);
+}
+
+// the 8 sign patterns of a packed word folded onto the stored entries at once: every
+// nibble whose d_0 bit is set is complemented, so stored entry j of the word's block j
+// is bits 4j+1 .. 4j+3 of the result and its sign flip is bit 4j of `lo`
+struct ErWord {
+  uint32_t folded, lo;
+};
+__device__ __forceinline__ ErWord er_fold_word(uint32_t w) {
+  const uint32_t lo = w & 0x11111111u;
+  return {w ^ (lo * 0xFu), lo};
 }
 
 // Running monoid of a lane's row: plain FP32 sums, or (COMP) plain sums over 16
