@@ -101,7 +101,11 @@ int32_t qpm_abi_version(void);
  * The per-problem phasor table is built on first use of (device, N, kappa1,
  * kappa2) and cached by the library (library-owned device memory, released by
  * qpm_release_caches); the scan's partial results use a library-owned scratch
- * buffer grown on demand.  Errors: N < 1, NP < 1, ld < N -> QPM_ERR_ARG.
+ * buffer grown on demand.  Rows that start on 16-byte boundaries (genes or
+ * signs 16-byte aligned, ld or ld_words a multiple of 4) are read with 16-byte
+ * accesses; other rows are read 4 bytes at a time, which is slower but gives
+ * results within the same tolerance.  Errors: N < 1, NP < 1, ld < N ->
+ * QPM_ERR_ARG.
  * ------------------------------------------------------------------------- */
 qpm_status qpm_eval(const qpm_problem *prob, const float *genes, int64_t ld, int32_t NP,
                     float *d_eff, float *fit, int32_t compensated, qpm_stream_t stream);
