@@ -101,7 +101,10 @@ int32_t qpm_abi_version(void);
  * The per-problem phasor table is built on first use of (device, N, kappa1,
  * kappa2) and cached by the library (library-owned device memory, released by
  * qpm_release_caches); the scan's partial results use a library-owned scratch
- * buffer grown on demand.  Rows that start on 16-byte boundaries (genes or
+ * buffer grown on demand.  The cache holds at most 64 problems per device: a call
+ * that needs room for new problems first synchronises the device and frees all of
+ * that device's tables and scratch (never while another host thread's call is
+ * between its table lookup and its launches).  Rows that start on 16-byte boundaries (genes or
  * signs 16-byte aligned, ld or ld_words a multiple of 4) are read with 16-byte
  * accesses; other rows are read 4 bytes at a time, which is slower but gives
  * results within the same tolerance.  Errors: N < 1, NP < 1, ld < N ->
@@ -134,26 +137,29 @@ qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const float *gene
                           void *scratch, size_t scratch_bytes, qpm_stream_t stream);
 size_t qpm_eval_multi_scratch_bytes(int32_t K, int32_t N, int32_t NP);
 
-/* Allocation-free qpm_eval (no counterpart in the paper; it exists for callers
- * that cannot allocate device memory: code running while a stream is being
- * captured into a CUDA graph, host callbacks, processes whose device memory is
- * owned by an external allocator, real-time paths that cannot afford the
- * implicit synchronisation of cudaMalloc).  Same arguments, layouts and result
- * as qpm_eval; it allocates nothing (no cudaMalloc/cudaFree, no allocating
- * library routine).  Its scratch -- the phasor table and the sign-block table
- * (16 + 48 bytes per domain), the constants and the partial sums of the scan --
- * lives in one fixed 16 MiB array in the library's device image, which every GPU
- * that loads the library holds until the process exits.
+/* Allocation-free qpm_eval (no counterpart in the paper).  It exists for callers
+ * that cannot allocate device memory: host callbacks and other code that must not
+ * call into the allocator, processes whose device memory is all owned by an
+ * external allocator, and real-time paths that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  Same arguments, layouts and result as
+ * qpm_eval; it allocates nothing (no cudaMalloc/cudaFree, no allocating library
+ * routine).  Its scratch lives in one fixed 16 MiB array in the library's device
+ * image, which every GPU that loads the library holds until the process exits:
+ *   bytes = 192 ceil(N / 4) (sign-block table, rounded up to 256)
+ *         + 16 min(1024, ceil(N / 256)) + 256 (the constants and their partial sums)
+ *         + 24 S NPpad (segment partials; NPpad = 32 ceil(NP / 32), S the number of
+ *           segments the row sweep splits N into, which grows with the SM count)
+ *   must not exceed 16777216.  On a 152-SM GB300 that admits N up to about 3.1e5
+ *   domains for up to 256 rows, 2.75e5 for 1024 rows and 1.7e5 for 4096 rows.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make this first call
  *     before any stream capture on that device.
- *   - N and NP whose scratch needs exceed 16 MiB (about N = 230k domains for a
- *     few rows, N = 1.8e5 for 1024 rows) are rejected with QPM_ERR_ARG and a message
- *     stating the bytes needed; nothing is enqueued.
- *   - Every call rebuilds the tables in the shared array, so calls that
- *     overlap on the GPU (different streams, or graphs replayed concurrently)
- *     race on it and must be serialised by the caller.  Nothing in the array
- *     needs to start at zero: each call writes every word it reads. */
+ *   - Sizes whose scratch exceeds 16 MiB are rejected with QPM_ERR_ARG and a
+ *     message stating the bytes needed; nothing is enqueued.
+ *   - Every call rebuilds its tables in the shared array, so calls that overlap on
+ *     the GPU (for example on different streams) race on it and must be serialised
+ *     by the caller.  Nothing in the array needs to start at zero: each call
+ *     writes every word it reads. */
 qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *genes, int64_t ld, int32_t NP,
                             float *d_eff, float *fit, int32_t compensated, qpm_stream_t stream);
 
@@ -238,6 +244,12 @@ qpm_status qpm_init(qpm_state *st, qpm_stream_t stream);
 qpm_status qpm_step(qpm_state *st, qpm_stream_t stream);
 qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode, qpm_stream_t stream);
 qpm_status qpm_destroy(qpm_state *st);
+
+/* Size of instance `inst` (host int32 outs, each may be NULL): domains N, population
+ * NP and generations G, as given to qpm_create.  Lets a caller size the buffers of
+ * the calls below.  Errors: bad state or instance -> QPM_ERR_ARG. */
+qpm_status qpm_instance_shape(const qpm_state *st, int32_t inst, int32_t *N_out, int32_t *NP_out,
+                              int32_t *G_out);
 
 /* generation counter of the state as seen by the host (host int32 out) */
 qpm_status qpm_generation(const qpm_state *st, int32_t *g_out);

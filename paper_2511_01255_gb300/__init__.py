@@ -18,6 +18,7 @@ __all__ = [
     "qpm_release_caches", "qpm_measure_issue_peak", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
+    "qpm_instance_shape",
     "qpm_set_batch_cluster",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
@@ -82,6 +83,7 @@ def lib(build=True):
             "qpm_destroy": ([_P], ctypes.c_int),
             "qpm_generation": ([_P, _P], ctypes.c_int),
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
+            "qpm_instance_shape": ([_P, i32, _P, _P, _P], ctypes.c_int),
             "qpm_set_batch_cluster": ([_P, i32], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
             "qpm_set_population": ([_P, i32, _P, i64, i32, _P], ctypes.c_int),
@@ -118,12 +120,69 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _rows(t, what):
-    """(rows, leading dimension) of a row-major 2-D tensor with unit column stride."""
+def _cuda(t, what, dtypes, min_numel=0, contiguous=True):
+    """Check that t is a CUDA tensor on the current device with one of `dtypes`,
+    at least `min_numel` elements and (if asked) contiguous, before its address
+    goes to the library: a wrong pointer would otherwise become an out-of-bounds
+    access on the device instead of a Python error."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: need a torch tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: need a CUDA tensor, got one on {t.device}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what}: tensor is on {t.device}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{what}: need dtype {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+    if contiguous and not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous tensor")
+    if t.numel() < min_numel:
+        raise ValueError(f"{what}: need at least {min_numel} elements, got {t.numel()}")
+    return t
+
+
+def _host(t, what, dtype, min_numel):
+    """Same for the host (CPU) buffers of qpm_solve."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{what}: need a contiguous CPU tensor of dtype {dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{what}: need at least {min_numel} elements, got {t.numel()}")
+    return t
+
+
+def _f32():
+    import torch
+    return (torch.float32,)
+
+
+def _i32():
+    import torch
+    return (torch.int32,)
+
+
+def _rows(t, what, min_cols=0, dtypes=None):
+    """(rows, leading dimension) of a row-major 2-D CUDA tensor with unit column
+    stride and at least min_cols columns (float32 unless `dtypes` says otherwise)."""
+    _cuda(t, what, dtypes or _f32(), contiguous=False)
     if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
         raise ValueError(f"{what}: need a 2-D tensor with contiguous rows")
+    if t.shape[1] < min_cols:
+        raise ValueError(f"{what}: need at least {min_cols} columns, got {t.shape[1]}")
+    if t.shape[0] < 1:
+        raise ValueError(f"{what}: need at least one row")
     ld = t.stride(0) if t.shape[0] > 1 else max(t.stride(0), t.shape[1])
     return t.shape[0], ld
+
+
+def _out(t, what, min_numel, dtypes=None, optional=True):
+    """An output buffer: None (where allowed) or a contiguous CUDA tensor."""
+    if t is None:
+        if not optional:
+            raise ValueError(f"{what}: required")
+        return None
+    return _cuda(t, what, dtypes or _f32(), min_numel)
 
 
 def _problem(N, kappa1, kappa2):
@@ -133,15 +192,21 @@ def _problem(N, kappa1, kappa2):
 def qpm_eval(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, stream=None):
     """d_eff (float32 [NP, 2]) and fit of the rows of genes (float32 CUDA [NP, ld])."""
     p = _problem(N, kappa1, kappa2)
-    NP, ld = _rows(genes, "genes")
+    NP, ld = _rows(genes, "genes", N)
+    _out(d_eff, "d_eff", 2 * NP, optional=False)
+    _out(fit, "fit", NP)
     _check(lib().qpm_eval(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),
                           int(compensated), _stream(stream)))
 
 
 def qpm_eval_packed(N, kappa1, kappa2, signs, d_eff, fit=None, compensated=0, stream=None):
     """Same from packed signs (int32/uint32 CUDA [NP, ld_words], bit set -> d = -1)."""
+    import torch
     p = _problem(N, kappa1, kappa2)
-    NP, ld = _rows(signs, "signs")
+    NP, ld = _rows(signs, "signs", (int(N) + 31) // 32,
+                   (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ()))
+    _out(d_eff, "d_eff", 2 * NP, optional=False)
+    _out(fit, "fit", NP)
     _check(lib().qpm_eval_packed(ctypes.byref(p), _ptr(signs), ld, NP, _ptr(d_eff), _ptr(fit),
                                  int(compensated), _stream(stream)))
 
@@ -149,7 +214,9 @@ def qpm_eval_packed(N, kappa1, kappa2, signs, d_eff, fit=None, compensated=0, st
 def qpm_eval_noalloc(N, kappa1, kappa2, genes, d_eff, fit=None, compensated=0, stream=None):
     """qpm_eval without any device allocation (fixed 16 MiB scratch inside the library)."""
     p = _problem(N, kappa1, kappa2)
-    NP, ld = _rows(genes, "genes")
+    NP, ld = _rows(genes, "genes", N)
+    _out(d_eff, "d_eff", 2 * NP, optional=False)
+    _out(fit, "fit", NP)
     _check(lib().qpm_eval_noalloc(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(d_eff), _ptr(fit),
                                   int(compensated), _stream(stream)))
 
@@ -182,9 +249,18 @@ def relaxed_saved(B, N, device="cuda"):
     return torch.empty((B, qpm_relaxed_saved_floats(N)), dtype=torch.float32, device=device)
 
 
+def _check_saved(saved, B, N):
+    _cuda(saved, "saved", _f32(), B * qpm_relaxed_saved_floats(N))
+    if saved.data_ptr() % 16:
+        raise ValueError("saved: need a 16-byte aligned block")
+
+
 def qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, d_eff, fit, saved, stream=None):
     p = _problem(N, kappa1, kappa2)
-    B, ld = _rows(theta, "theta")
+    B, ld = _rows(theta, "theta", N)
+    _out(d_eff, "d_eff", 2 * B, optional=False)
+    _out(fit, "fit", B)
+    _check_saved(saved, B, N)
     _check(lib().qpm_deff_relaxed_fwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff), _ptr(fit),
                                       _ptr(saved), _stream(stream)))
 
@@ -192,8 +268,13 @@ def qpm_deff_relaxed_fwd(N, kappa1, kappa2, theta, d_eff, fit, saved, stream=Non
 def qpm_deff_relaxed_bwd(N, kappa1, kappa2, theta, d_eff, saved, grad_fit, grad_theta,
                          stream=None):
     p = _problem(N, kappa1, kappa2)
-    B, ld = _rows(theta, "theta")
-    _, ldg = _rows(grad_theta, "grad_theta")
+    B, ld = _rows(theta, "theta", N)
+    Bg, ldg = _rows(grad_theta, "grad_theta", N)
+    if Bg < B:
+        raise ValueError(f"grad_theta: need at least {B} rows, got {Bg}")
+    _out(d_eff, "d_eff", 2 * B, optional=False)
+    _out(grad_fit, "grad_fit", B)
+    _check_saved(saved, B, N)
     _check(lib().qpm_deff_relaxed_bwd(ctypes.byref(p), _ptr(theta), ld, B, _ptr(d_eff),
                                       _ptr(saved), _ptr(grad_fit), _ptr(grad_theta), ldg,
                                       _stream(stream)))
@@ -244,7 +325,9 @@ def deff_relaxed(theta, kappa1, kappa2):
 def qpm_eval_shg(N, kappa, genes, e_shg, fit=None, stream=None):
     """SHG field integral of each gene row (dk w = kappa)."""
     p = _problem(N, kappa, 0.0)
-    NP, ld = _rows(genes, "genes")
+    NP, ld = _rows(genes, "genes", N)
+    _out(e_shg, "e_shg", 2 * NP, optional=False)
+    _out(fit, "fit", NP)
     _check(lib().qpm_eval_shg(ctypes.byref(p), _ptr(genes), ld, NP, _ptr(e_shg), _ptr(fit),
                               _stream(stream)))
 
@@ -254,7 +337,9 @@ def qpm_eval_multi(N, kappas, genes, G0, beta, objective, d_eff=None, stream=Non
     import torch
     K = len(kappas)
     probs = (Problem * K)(*[_problem(N, k1, k2) for k1, k2 in kappas])
-    NP, ld = _rows(genes, "genes")
+    NP, ld = _rows(genes, "genes", N)
+    _out(objective, "objective", NP, optional=False)
+    _out(d_eff, "d_eff", 2 * K * NP)
     nbytes = lib().qpm_eval_multi_scratch_bytes(K, N, NP)
     scratch = torch.empty(max(1, nbytes), dtype=torch.uint8, device=genes.device)
     _check(lib().qpm_eval_multi(probs, K, _ptr(genes), ld, NP, float(G0), float(beta),
@@ -309,30 +394,57 @@ def qpm_set_batch_cluster(st, ctas):
     _check(lib().qpm_set_batch_cluster(st, int(ctas)))
 
 
+def qpm_instance_shape(st, inst=0):
+    """(N, NP, G) of instance `inst`."""
+    n, p, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().qpm_instance_shape(st, int(inst), ctypes.byref(n), ctypes.byref(p), ctypes.byref(g)))
+    return n.value, p.value, g.value
+
+
 def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):
-    ld = _rows(genes_out, "genes_out")[1] if genes_out is not None else 0
+    N, NP, _ = qpm_instance_shape(st, inst)
+    ld = 0
+    if genes_out is not None:
+        rows, ld = _rows(genes_out, "genes_out", N)
+        if rows < NP:
+            raise ValueError(f"genes_out: need {NP} rows, got {rows}")
+    _out(fit_out, "fit_out", NP)
+    _out(d_eff_out, "d_eff_out", 2 * NP)
     _check(lib().qpm_get_population(st, int(inst), _ptr(genes_out), ld, _ptr(fit_out),
                                     _ptr(d_eff_out), _stream(stream)))
 
 
 def qpm_set_population(st, inst, genes, generation, stream=None):
-    _, ld = _rows(genes, "genes")
+    N, NP, _ = qpm_instance_shape(st, inst)
+    rows, ld = _rows(genes, "genes", N)
+    if rows < NP:
+        raise ValueError(f"genes: need {NP} rows, got {rows}")
     _check(lib().qpm_set_population(st, int(inst), _ptr(genes), ld, int(generation),
                                     _stream(stream)))
 
 
 def qpm_get_best(st, inst, genes_out=None, d_eff64_out=None, fit_out=None, index_out=None,
                  stream=None):
+    import torch
+    N, _, _ = qpm_instance_shape(st, inst)
+    _out(genes_out, "genes_out", N)
+    _out(d_eff64_out, "d_eff64_out", 2, (torch.float64,))
+    _out(fit_out, "fit_out", 1)
+    _out(index_out, "index_out", 1, _i32())
     _check(lib().qpm_get_best(st, int(inst), _ptr(genes_out), _ptr(d_eff64_out), _ptr(fit_out),
                               _ptr(index_out), _stream(stream)))
 
 
 def qpm_polish_leaders(st, inst=0, steps=8, lr=0.5, tau=3.0, accepted_out=None, stream=None):
+    _out(accepted_out, "accepted_out", 3, _i32())
     _check(lib().qpm_polish_leaders(st, int(inst), int(steps), float(lr), float(tau),
                                     _ptr(accepted_out), _stream(stream)))
 
 
 def qpm_set_trace(st, inst, trace):
+    if trace is not None:
+        _, NP, G = qpm_instance_shape(st, inst)
+        _out(trace, "trace", NP * (1 + 2 * G))
     _check(lib().qpm_set_trace(st, int(inst), _ptr(trace)))
 
 
@@ -343,7 +455,12 @@ def qpm_set_wait_timeout_ns(st, ns):
 def qpm_solve(N, kappa1, kappa2, params, mode, best_genes_host, best_deff64_host,
               best_fit_host=None):
     """End to end with host (CPU) tensors; synchronous."""
+    import torch
     p = _problem(N, kappa1, kappa2)
+    _host(best_genes_host, "best_genes_host", torch.float32, N)
+    _host(best_deff64_host, "best_deff64_host", torch.float64, 2)
+    if best_fit_host is not None:
+        _host(best_fit_host, "best_fit_host", torch.float32, 1)
     _check(lib().qpm_solve(ctypes.byref(p), ctypes.byref(params), int(mode),
                            _ptr(best_genes_host), _ptr(best_deff64_host), _ptr(best_fit_host)))
 

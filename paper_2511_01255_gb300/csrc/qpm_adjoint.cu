@@ -391,15 +391,16 @@ static __global__ void __launch_bounds__(RX_WPC * 32)
   }
 }
 
+// the caller's lease stays alive until its launches are enqueued
 static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int64_t ld,
-                                int32_t B, const void *saved, cudaStream_t s, RelaxShape *sh,
-                                const float4 **tab, const float2 **konst) {
+                                int32_t B, const void *saved, cudaStream_t s, TableLease &lease,
+                                RelaxShape *sh, const float4 **tab, const float2 **konst) {
   if (!prob || !theta || !saved) return fail(QPM_ERR_ARG, "relaxed: NULL theta or saved block");
   if (prob->N < 1 || B < 1) return fail(QPM_ERR_ARG, "relaxed: need N >= 1 and B >= 1");
   if (ld < prob->N) return fail(QPM_ERR_ARG, "relaxed: leading dimension smaller than the row");
   if (((uintptr_t)saved & 15) != 0) return fail(QPM_ERR_ARG, "relaxed: saved block not 16-byte aligned");
   if (rx_nseg(prob->N) > 65535) return fail(QPM_ERR_ARG, "relaxed: N too large");
-  qpm_status st = cached_table(prob, s, tab, konst);
+  qpm_status st = lease.table(prob, s, tab, konst);
   if (st != QPM_OK) return st;
   sh->B = B;
   sh->N = prob->N;
@@ -427,10 +428,12 @@ extern "C" qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float 
                                            qpm_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (!d_eff) return fail(QPM_ERR_ARG, "qpm_deff_relaxed_fwd: NULL d_eff");
+  if (!prob) return fail(QPM_ERR_ARG, "relaxed: NULL problem");
+  TableLease lease(prob, 1);
   RelaxShape sh;
   const float4 *tab;
   const float2 *konst;
-  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, &sh, &tab, &konst);
+  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, lease, &sh, &tab, &konst);
   if (st != QPM_OK) return st;
   float2 *D = (float2 *)d_eff;
   const dim3 grid = rx_grid(sh);
@@ -453,10 +456,12 @@ extern "C" qpm_status qpm_deff_relaxed_bwd(const qpm_problem *prob, const float 
     return fail(QPM_ERR_ARG, "qpm_deff_relaxed_bwd: NULL d_eff or grad_theta");
   if (!prob || ld_grad < prob->N)
     return fail(QPM_ERR_ARG, "qpm_deff_relaxed_bwd: gradient leading dimension smaller than the row");
+  if (!prob) return fail(QPM_ERR_ARG, "relaxed: NULL problem");
+  TableLease lease(prob, 1);
   RelaxShape sh;
   const float4 *tab;
   const float2 *konst;
-  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, &sh, &tab, &konst);
+  qpm_status st = relaxed_setup(prob, theta, ld, B, saved, s, lease, &sh, &tab, &konst);
   if (st != QPM_OK) return st;
   const bool vg = (ld_grad % 4 == 0) && (((uintptr_t)grad_theta & 15) == 0);
   const float2 *D = (const float2 *)d_eff;

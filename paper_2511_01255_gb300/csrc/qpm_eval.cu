@@ -229,9 +229,16 @@ qpm_status release_device_caches(int dev) {
   return QPM_OK;
 }
 
+size_t device_table_count(int dev) {
+  size_t n = 0;
+  for (const auto &kv : g_tables) n += (std::get<0>(kv.first) == dev);
+  return n;
+}
+
 // phasor table in natural order for (device, problem); built on `stream` on a miss.
 // blk (if non-NULL) receives the sign-block table, built on `stream` the first time
-// it is asked for.
+// it is asked for.  Never evicts: TableLease makes room before its first lookup.
+// Caller holds g_mu.
 qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
                      const float2 **konst, const float2 **blk = nullptr) {
   int dev = 0;
@@ -239,20 +246,26 @@ qpm_status get_table(const qpm_problem *p, cudaStream_t stream, const float4 **t
   auto key = std::make_tuple(dev, p->N, p->kappa1, p->kappa2);
   auto it = g_tables.find(key);
   if (it == g_tables.end()) {
-    if (g_tables.size() >= MAX_TABLES) {
-      qpm_status st = release_device_caches(dev);
-      if (st != QPM_OK) return st;
-    }
     TableEntry e;
     const int32_t Npad = (p->N + 3) & ~3;
-    QPM_CUDA(cudaMalloc(&e.table, sizeof(float4) * (size_t)Npad));
-    QPM_CUDA(cudaMalloc(&e.part, sizeof(double2) * (size_t)table_part_count(Npad)));
-    QPM_CUDA(cudaMalloc(&e.konst, sizeof(float2) * 4));
-    QPM_CUDA(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
-    TableSpec s{p->N, Npad, 1, Npad, p->kappa1, p->kappa2};
-    qpm_status st = launch_table(s, e.table, e.part, e.konst, nullptr, stream);
-    if (st != QPM_OK) return st;
-    QPM_CUDA(cudaEventRecord(e.ready, stream));
+    cudaError_t ce = cudaMalloc(&e.table, sizeof(float4) * (size_t)Npad);
+    if (ce == cudaSuccess) ce = cudaMalloc(&e.part, sizeof(double2) * (size_t)table_part_count(Npad));
+    if (ce == cudaSuccess) ce = cudaMalloc(&e.konst, sizeof(float2) * 4);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming);
+    qpm_status st = ce == cudaSuccess ? QPM_OK : cuda_fail(ce, "allocating a phasor table");
+    if (st == QPM_OK) {
+      TableSpec s{p->N, Npad, 1, Npad, p->kappa1, p->kappa2};
+      st = launch_table(s, e.table, e.part, e.konst, nullptr, stream);
+    }
+    if (st == QPM_OK && (ce = cudaEventRecord(e.ready, stream)) != cudaSuccess)
+      st = cuda_fail(ce, "cudaEventRecord");
+    if (st != QPM_OK) {  // the cache keeps no half-built entry
+      cudaFree(e.table);
+      cudaFree(e.part);
+      cudaFree(e.konst);
+      if (e.ready) cudaEventDestroy(e.ready);
+      return st;
+    }
     it = g_tables.emplace(key, e).first;
   } else {
     QPM_CUDA(cudaStreamWaitEvent(stream, it->second.ready, 0));
@@ -372,10 +385,9 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
   if (prob->N > (1 << 28)) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: N too large");
   if (kind == 2 ? (ld < (prob->N + 31) / 32) : (ld < prob->N))
     return fail(QPM_ERR_ARG, "qpm_eval: leading dimension smaller than the row");
-  std::lock_guard<std::mutex> lock(g_mu);
-  const float4 *table;
+  TableLease lease(prob, 1);  // held until the launches below are enqueued
   const float2 *konst, *blk = nullptr;
-  qpm_status st = get_table(prob, stream, &table, &konst, &blk);
+  qpm_status st = lease.block_table(prob, stream, &blk, &konst);
   if (st != QPM_OK) return st;
   if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval: too many rows");
   const bool aligned = (ld % 4 == 0) && (((uintptr_t)src & 15) == 0);
@@ -399,15 +411,13 @@ static qpm_status eval_common(const qpm_problem *prob, const void *src, int64_t 
 
 
 // ---------------------------------------------------------------------------
-// Allocation-free variant of qpm_eval.  For callers that must not allocate
-// device memory: code running where cudaMalloc is not allowed or not wanted,
-// e.g. while a CUDA stream is being captured into a graph, inside a host
-// callback, under an external allocator that owns all device memory, or on a
-// real-time path where an allocation's implicit device synchronisation is not
-// acceptable.  Its scratch (phasor and sign-block tables, table reduction,
-// segment partials)
-// lives in one file-scope device array of fixed size that every GPU loading
-// this library holds until the process exits.
+// Allocation-free variant of qpm_eval.  For callers that must not allocate device
+// memory: host callbacks and other code that may not call into the allocator,
+// processes whose device memory is all owned by an external allocator, and real-time
+// paths where the implicit device synchronisation of cudaMalloc/cudaFree is not
+// acceptable.  Its scratch (sign-block table, the constants' reduction, segment
+// partials) lives in one file-scope device array of fixed size that every GPU
+// loading this library holds until the process exits.
 // ---------------------------------------------------------------------------
 static constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -435,6 +445,16 @@ qpm_status noalloc_base(void **out) {
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// bytes of the fixed array one call uses: the sign-block table (192 bytes per block of
+// 4 domains), the reduction partials of the constants, the constants, and the segment
+// partials of the scan (3 float2 per segment and padded row)
+size_t noalloc_bytes(int32_t N, const EvalShape &sh) {
+  const int32_t Npad = (N + 3) & ~3;
+  return up256(sizeof(float2) * BLK_F2 * (size_t)(Npad / 4)) +
+         up256(sizeof(double2) * (size_t)table_part_count(Npad)) + 256 +
+         up256(sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad);
+}
 }  // namespace
 
 }  // namespace qpm
@@ -452,12 +472,7 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   const EvalShape sh = eval_genes_shape(NP, prob->N, vec);
   const int32_t Npad = (prob->N + 3) & ~3;
-  const size_t b_table = up256(sizeof(float4) * (size_t)Npad);
-  const size_t b_blk = up256(sizeof(float2) * BLK_F2 * (size_t)(Npad / 4));
-  const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));
-  const size_t b_konst = 256;
-  const size_t b_part = up256(sizeof(float2) * 3 * (size_t)sh.S * sh.NPpad);
-  const size_t need = b_table + b_blk + b_tpart + b_konst + b_part;
+  const size_t need = noalloc_bytes(prob->N, sh);
   if (need > NOALLOC_SCRATCH_BYTES)
     return fail(QPM_ERR_ARG, "qpm_eval_noalloc: N and NP need " + std::to_string(need) +
                                  " bytes of scratch, more than the fixed 16 MiB (16777216)");
@@ -466,15 +481,17 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   if (st != QPM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   char *p = (char *)base;
-  float4 *table = (float4 *)p;
-  float2 *blk = (float2 *)(p + b_table);
-  double2 *tpart = (double2 *)(p + b_table + b_blk);
-  float2 *konst = (float2 *)(p + b_table + b_blk + b_tpart);
-  float2 *part = (float2 *)(p + b_table + b_blk + b_tpart + b_konst);
-  // every word read below is written first in this call (tables, the constants'
-  // partial sums, every segment partial of every padded row), so nothing needs zeroing
+  const size_t b_blk = up256(sizeof(float2) * BLK_F2 * (size_t)(Npad / 4));
+  const size_t b_tpart = up256(sizeof(double2) * (size_t)table_part_count(Npad));
+  float2 *blk = (float2 *)p;
+  double2 *tpart = (double2 *)(p + b_blk);
+  float2 *konst = (float2 *)(p + b_blk + b_tpart);
+  float2 *part = (float2 *)(p + b_blk + b_tpart + 256);
+  // every word read below is written first in this call (the sign-block table, the
+  // constants and their partial sums, every segment partial of every padded row), so
+  // nothing needs zeroing; the constants come from k_table without a phasor table
   TableSpec ts{prob->N, Npad, 1, Npad, prob->kappa1, prob->kappa2};
-  st = launch_table(ts, table, tpart, konst, nullptr, s);
+  st = launch_table(ts, nullptr, tpart, konst, nullptr, s);
   if (st != QPM_OK) return st;
   st = launch_block_table(prob->N, prob->kappa1, prob->kappa2, blk, s);
   if (st != QPM_OK) return st;
@@ -486,15 +503,38 @@ extern "C" qpm_status qpm_eval_noalloc(const qpm_problem *prob, const float *gen
   return QPM_OK;
 }
 
-qpm_status qpm::cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
-                             const float2 **konst) {
-  std::lock_guard<std::mutex> lock(g_mu);
+qpm::TableLease::TableLease(const qpm_problem *problems, int count) {
+  g_mu.lock();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    st_ = cuda_fail(e, "cudaGetDevice");
+    return;
+  }
+  size_t misses = 0;
+  for (int k = 0; k < count; ++k) {
+    const qpm_problem &p = problems[k];
+    bool seen = g_tables.count(std::make_tuple(dev, p.N, p.kappa1, p.kappa2)) != 0;
+    for (int m = 0; m < k && !seen; ++m)
+      seen = problems[m].N == p.N && problems[m].kappa1 == p.kappa1 &&
+             problems[m].kappa2 == p.kappa2;
+    misses += !seen;
+  }
+  if (misses > 0 && device_table_count(dev) + misses > MAX_TABLES)
+    st_ = release_device_caches(dev);
+}
+
+qpm::TableLease::~TableLease() { g_mu.unlock(); }
+
+qpm_status qpm::TableLease::table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
+                                  const float2 **konst) {
+  if (st_ != QPM_OK) return st_;
   return get_table(p, stream, table, konst);
 }
 
-qpm_status qpm::cached_block_table(const qpm_problem *p, cudaStream_t stream, const float2 **blk,
-                                   const float2 **konst) {
-  std::lock_guard<std::mutex> lock(g_mu);
+qpm_status qpm::TableLease::block_table(const qpm_problem *p, cudaStream_t stream,
+                                        const float2 **blk, const float2 **konst) {
+  if (st_ != QPM_OK) return st_;
   const float4 *table;
   return get_table(p, stream, &table, konst, blk);
 }

@@ -1358,6 +1358,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (p.N < 1) return fail(QPM_ERR_ARG, "qpm_create: N < 1");
     if (p.N > (1 << 26)) return fail(QPM_ERR_UNSUPPORTED, "qpm_create: N too large");
     if (q.NP < 4) return fail(QPM_ERR_ARG, "qpm_create: NP < 4 (rand/1 needs three donors)");
+    if (q.NP > (1 << 28)) return fail(QPM_ERR_UNSUPPORTED, "qpm_create: NP above 2^28");
     if (q.G < 1) return fail(QPM_ERR_ARG, "qpm_create: G < 1");
     if (!(q.F >= 0.f && q.F <= 2.f)) return fail(QPM_ERR_ARG, "qpm_create: F outside [0, 2]");
     if (!(q.CR >= 0.f && q.CR <= 1.f)) return fail(QPM_ERR_ARG, "qpm_create: CR outside [0, 1]");
@@ -1689,6 +1690,15 @@ extern "C" qpm_status qpm_set_batch_cluster(qpm_state *st, int32_t ctas) {
 extern "C" qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out) {
   if (!st || !team_out || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad arguments");
   *team_out = st->h[inst].T;
+  return QPM_OK;
+}
+
+extern "C" qpm_status qpm_instance_shape(const qpm_state *st, int32_t inst, int32_t *N_out,
+                                         int32_t *NP_out, int32_t *G_out) {
+  if (!st || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad state or instance");
+  if (N_out) *N_out = st->h[inst].N;
+  if (NP_out) *NP_out = st->h[inst].NP;
+  if (G_out) *G_out = st->h[inst].G;
   return QPM_OK;
 }
 

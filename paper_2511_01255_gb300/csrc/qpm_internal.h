@@ -28,7 +28,7 @@ struct TableSpec {
 };
 
 // float2 konst[4] = {phi1*phi2, cdiag, psi, phi1}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
-// part: scratch of table_part_count(Npad) double2
+// part: scratch of table_part_count(Npad) double2; table may be NULL (constants only)
 int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,
                         double2 *konst64, cudaStream_t stream);
@@ -40,13 +40,32 @@ qpm_status launch_block_table(int32_t N, double kappa1, double kappa2, float2 *b
                               cudaStream_t stream);
 constexpr int BLK_F2 = 24;  // float2 per block of 4 domains
 
-// natural-order phasor table and FP32 constants of a problem, cached per
-// (device, N, kappa1, kappa2); built on `stream` on a miss (caller holds no lock)
-qpm_status cached_table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
-                        const float2 **konst);
-// the same cache entry's sign-block table (built on `stream` the first time)
-qpm_status cached_block_table(const qpm_problem *p, cudaStream_t stream, const float2 **blk,
-                              const float2 **konst);
+// Access to the per-(device, N, kappa1, kappa2) cache of phasor tables, FP32
+// constants and sign-block tables.  A lease holds the cache's lock from its
+// construction to its destruction: the caller keeps it alive from the first lookup
+// until the last launch that uses the returned pointers has been enqueued, so no
+// other host thread can evict those tables in between.  The cache holds at most
+// MAX_TABLES problems per device; a lease that will look up `problems` distinct
+// problems makes room for all of them when it is created (freeing every table of
+// the device once, after a device synchronisation), never between two lookups.
+class TableLease {
+ public:
+  TableLease(const qpm_problem *problems, int count);
+  ~TableLease();
+  TableLease(const TableLease &) = delete;
+  TableLease &operator=(const TableLease &) = delete;
+  // status of the set-up (a failed eviction is reported by the first lookup)
+  qpm_status status() const { return st_; }
+  // natural-order phasor table and FP32 constants; built on `stream` on a miss
+  qpm_status table(const qpm_problem *p, cudaStream_t stream, const float4 **table,
+                   const float2 **konst);
+  // the same entry's sign-block table (built on `stream` the first time) and constants
+  qpm_status block_table(const qpm_problem *p, cudaStream_t stream, const float2 **blk,
+                         const float2 **konst);
+
+ private:
+  qpm_status st_ = QPM_OK;
+};
 
 // split of qpm_eval-style work: S segments of L domains, rows in groups of 32
 struct EvalShape {

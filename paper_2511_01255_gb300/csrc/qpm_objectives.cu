@@ -227,9 +227,10 @@ extern "C" qpm_status qpm_eval_shg(const qpm_problem *prob, const float *genes, 
   if (prob->N < 1 || NP < 1) return fail(QPM_ERR_ARG, "qpm_eval_shg: need N >= 1 and NP >= 1");
   if (ld < prob->N) return fail(QPM_ERR_ARG, "qpm_eval_shg: leading dimension smaller than the row");
   cudaStream_t s = (cudaStream_t)stream;
+  TableLease lease(prob, 1);  // held until the launch below is enqueued
   const float4 *table;
   const float2 *konst;
-  qpm_status st = cached_table(prob, s, &table, &konst);
+  qpm_status st = lease.table(prob, s, &table, &konst);
   if (st != QPM_OK) return st;
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   const int grid = (NP + SHG_ROWS - 1) / SHG_ROWS;
@@ -258,13 +259,16 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     mt.t[k] = nullptr;
     mt.konst[k] = nullptr;
   }
+  if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
+  // one lease for all K lookups and the launches: room for the K tables is made
+  // before the first lookup, so no lookup can evict a table returned before it
+  TableLease lease(probs, K);
   for (int k = 0; k < K; ++k) {
     const float2 *blk;
-    qpm_status st = cached_block_table(&probs[k], s, &blk, &mt.konst[k]);
+    qpm_status st = lease.block_table(&probs[k], s, &blk, &mt.konst[k]);
     if (st != QPM_OK) return st;
     mt.t[k] = (const float4 *)blk;
   }
-  if (NP > ER_WPC * 32 * 65535) return fail(QPM_ERR_UNSUPPORTED, "qpm_eval_multi: too many rows");
   const bool vec = (ld % 4 == 0) && (((uintptr_t)genes & 15) == 0);
   const EvalShape sh = eval_rows_shape(NP, N, vec ? ER_WPC * mw_ring_ctas(K) : 20);
   const size_t need = sizeof(float2) * 3 * (size_t)K * sh.S * sh.NPpad;

@@ -65,3 +65,14 @@ def relaxed_theta(B, N, seed=1):
     """theta ~ N(0, 1), float32 [B, N]."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((B, N)).astype(np.float32)
+
+
+def two_tone_signs(N, kappa1, kappa2):
+    """A +-1 row (float32 [N]) whose sign follows cos(kappa1 j) + cos(kappa2 j)
+    (+1 where the sum is zero): a sequence carrying both phase-mismatch
+    frequencies, so that both integrals of the cascade grow with the length and
+    |d_eff| is a sizeable fraction of L^2/2 (about 0.07 at the paper-scale
+    mismatches) instead of the ~N of a random row."""
+    j = np.arange(N, dtype=np.float64)
+    s = np.cos(kappa1 * j) + np.cos(kappa2 * j)
+    return np.where(s < 0.0, -1.0, 1.0).astype(np.float32)

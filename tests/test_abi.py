@@ -95,3 +95,29 @@ def test_workload_generators_are_seeded():
             assert ((int(words[i, j // 32]) >> (j % 32)) & 1) == int(a[i, j] < 0)
     inst = W.batched_instances(512)
     assert len(inst) == 512 and min(x["N"] for x in inst) >= 500 and max(x["N"] for x in inst) <= 8000
+
+
+def test_binding_rejects_bad_tensors_before_the_library():
+    """The binding checks device, dtype, layout and size of every tensor it hands to
+    the library; a CPU tensor, a float64 gene array or a short output is a Python
+    error, never a device pointer.  (No device is needed: the checks come first.)"""
+    import torch
+
+    import paper_2511_01255_gb300 as q
+    X = torch.zeros((4, 16), dtype=torch.float32)
+    D = torch.zeros((4, 2), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        q.qpm_eval(16, 1.0, 2.0, X, D)
+    with pytest.raises(ValueError, match="CUDA"):
+        q.qpm_eval_noalloc(16, 1.0, 2.0, X.double(), D)
+    with pytest.raises(ValueError, match="CUDA"):
+        q.qpm_eval_packed(16, 1.0, 2.0, torch.zeros((4, 1), dtype=torch.int32), D)
+    with pytest.raises(ValueError, match="CUDA"):
+        q.qpm_deff_relaxed_fwd(16, 1.0, 2.0, X, D, None, torch.zeros((4, 8)))
+    # host buffers of qpm_solve: dtype and size are checked before the call
+    prm = q.Params(8, 10, 0.5, 0.9, 1, 0, 0)
+    with pytest.raises(ValueError, match="best_genes_host"):
+        q.qpm_solve(16, 1.0, 2.0, prm, q.RUN_PERSISTENT, torch.zeros(15), torch.zeros(2, dtype=torch.float64))
+    with pytest.raises(ValueError, match="best_deff64_host"):
+        q.qpm_solve(16, 1.0, 2.0, prm, q.RUN_PERSISTENT, torch.zeros(16), torch.zeros(2))
+

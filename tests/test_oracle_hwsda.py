@@ -304,3 +304,18 @@ def test_decaying_F_schedule(orc):
     U = orc.de_trials(c0, 3, X)
     r1 = orc.de_indices(c0.seed, 0, 3, 2, 10, 30)[0]
     assert np.array_equal(U[2], X[r1])
+
+
+def test_philox_known_answers_of_the_random123_distribution(orc):
+    """Philox4x32-10 against the known-answer vectors published with Random123
+    (Salmon, Moraes, Dror, Shaw, SC'11), read from tests/golden: they include the
+    all-ones counter and a counter whose fourth word is set, the word that carries
+    (instance << 8) | tag in this implementation's random-number contract."""
+    import numpy as np
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        ctr, key, want = v[0:4], v[4:6], v[6:10]
+        assert list(orc.philox(ctr, key)) == want, r
