@@ -174,6 +174,20 @@ qpm_status qpm_release_caches(void);
  * small device buffer.  Errors: kind outside [0, 3] -> QPM_ERR_ARG. */
 qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stream_t stream);
 
+/* Measured latency on the current device for the latency floor of a generation of
+ * the persistent form (no counterpart in the paper), in nanoseconds (*ns_out, host):
+ *   kind 0: one grid barrier of the persistent kernel (the same code: release
+ *           reduction on a counter, bounded acquire polling), `ctas` co-resident CTAs of
+ *           256 threads, averaged over 2000 barriers in one cooperative launch;
+ *   kind 1: one dependent load served by L2 (a single thread chasing a scrambled
+ *           cyclic permutation of 16 MB that is L2-resident), averaged over 8192 loads;
+ *           `ctas` is ignored.
+ * Synchronous (a few ms); allocates and frees its device buffers (256 bytes, or
+ * 16 MB).  Errors: NULL output, kind outside [0, 1], ctas outside [1, the co-resident
+ * CTA count] for kind 0 -> QPM_ERR_ARG; a barrier wait that ran out (1 s) ->
+ * QPM_ERR_TIMEOUT. */
+qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns_out, qpm_stream_t stream);
+
 /* Exhaustive self-check of one of the library's arithmetic shortcuts against
  * the plain operation it replaces (no counterpart in the paper), over all 2^32
  * 32-bit patterns x:

@@ -15,7 +15,7 @@ from . import build_lib
 
 __all__ = [
     "QpmError", "Problem", "Params", "lib", "qpm_eval", "qpm_eval_packed", "qpm_eval_noalloc", "qpm_eval_shg", "qpm_eval_multi",
-    "qpm_release_caches", "qpm_measure_issue_peak", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
+    "qpm_release_caches", "qpm_measure_issue_peak", "qpm_measure_latency", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
     "qpm_instance_shape",
@@ -72,6 +72,7 @@ def lib(build=True):
             "qpm_eval_multi_scratch_bytes": ([i32, i32, i32], ctypes.c_size_t),
             "qpm_release_caches": ([], ctypes.c_int),
             "qpm_measure_issue_peak": ([i32, _P, _P], ctypes.c_int),
+            "qpm_measure_latency": ([i32, i32, _P, _P], ctypes.c_int),
             "qpm_selfcheck": ([i32, _P, _P, _P], ctypes.c_int),
             "qpm_relaxed_saved_floats": ([i32], i64),
             "qpm_deff_relaxed_fwd": ([_P, _P, i64, i32, _P, _P, _P, _P], ctypes.c_int),
@@ -225,6 +226,14 @@ def qpm_measure_issue_peak(kind, stream=None):
     """Measured lane-ops/s of the current device: 0 FFMA, 1 Philox multiply+xor, 2 xor."""
     v = ctypes.c_double()
     _check(lib().qpm_measure_issue_peak(int(kind), ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def qpm_measure_latency(kind, ctas=256, stream=None):
+    """Measured nanoseconds of 0: one grid barrier of the persistent kernel over `ctas`
+    co-resident CTAs; 1: one dependent load served by L2."""
+    v = ctypes.c_double()
+    _check(lib().qpm_measure_latency(int(kind), int(ctas), ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -12,8 +12,11 @@
 // generator's Philox4x32-10 per second.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
+#include "qpm_sync.cuh"
 
 namespace qpm {
 
@@ -245,4 +248,124 @@ extern "C" qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_
   if (e != cudaSuccess) return cuda_fail(e, "qpm_measure_issue_peak");
   *lane_ops_per_s = (double)blocks * PK_THREADS * per_thread / (ms * 1e-3);
   return QPM_OK;
+}
+
+// ------------------------------------------------------- latency probes
+// The latency floor of a generation of the persistent kernel: its two grid barriers
+// and its dependent L2 round trips (donor rows, survivor keys, leader rows).
+namespace qpm {
+
+static constexpr int LP_THREADS = 256;  // the team width of the 1000-domain workload
+
+// `reps` grid barriers of the persistent kernel's own form, back to back
+static __global__ void __launch_bounds__(LP_THREADS) k_probe_barrier(Barrier b, int reps) {
+  unsigned target = 0;
+  for (int r = 0; r < reps; ++r)
+    if (!grid_sync(b, target)) return;
+}
+
+// one thread follows a cyclic permutation with L2-cached loads: every load depends
+// on the one before, so the time per step is the latency of a load served by L2
+static __global__ void k_probe_chase(const uint32_t *__restrict__ next, int steps,
+                                     uint32_t *sink) {
+  uint32_t i = 0;
+  for (int s = 0; s < steps; ++s) i = __ldcg(next + i);
+  if (i == 0xFFFFFFFFu) *sink = i;
+}
+
+}  // namespace qpm
+
+extern "C" qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns_out,
+                                          qpm_stream_t stream) {
+  using namespace qpm;
+  if (!ns_out) return fail(QPM_ERR_ARG, "qpm_measure_latency: NULL output");
+  if (kind != 0 && kind != 1) return fail(QPM_ERR_ARG, "qpm_measure_latency: kind must be 0 or 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  QPM_CUDA(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "cudaEventCreate");
+  }
+  qpm_status st = QPM_OK;
+  void *buf = nullptr;
+  // elapsed ms of one launch made by `launch`
+  auto timed = [&](auto launch, float *ms) -> qpm_status {
+    cudaError_t e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    return e == cudaSuccess ? QPM_OK : cuda_fail(e, "latency probe launch");
+  };
+  if (kind == 0) {
+    int occ = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probe_barrier, LP_THREADS, 0);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    else if (ctas < 1 || ctas > occ * sm_count())
+      st = fail(QPM_ERR_ARG, "qpm_measure_latency: ctas outside [1, co-resident CTAs]");
+    if (st == QPM_OK) {
+      ce = cudaMalloc(&buf, 256);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(buf, 0, 256, s);
+      if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMalloc(barrier words)");
+    }
+    float t[2] = {0.f, 0.f};
+    const int reps[2] = {100, 2100};  // the difference removes the launch cost
+    for (int k = 0; k < 2 && st == QPM_OK; ++k) {
+      for (int w = 0; w < 2 && st == QPM_OK; ++w) {  // the second launch is the timed one
+        Barrier b{(unsigned *)buf, (int32_t *)buf + 32, 1000000000ull};  // 1 s per wait
+        int r = reps[k];
+        void *args[] = {&b, &r};
+        st = timed([&] {
+          cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(unsigned), s);
+          return e == cudaSuccess ? cudaLaunchCooperativeKernel((const void *)k_probe_barrier,
+                                                                ctas, LP_THREADS, args, 0, s)
+                                  : e;
+        }, &t[k]);
+      }
+    }
+    int32_t err = 0;
+    if (st == QPM_OK) {
+      ce = cudaMemcpy(&err, (int32_t *)buf + 32, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMemcpy");
+      else if (err != 0) st = fail(QPM_ERR_TIMEOUT, "qpm_measure_latency: a barrier wait gave up");
+    }
+    if (st == QPM_OK) *ns_out = 1e6 * (double)(t[1] - t[0]) / (double)(reps[1] - reps[0]);
+  } else {
+    const size_t n = (size_t)4 << 20;  // 16 MB of uint32: in L2 after the first pass
+    std::vector<uint32_t> h(n);
+    // one cycle through all n words in a scrambled order (an affine map modulo n,
+    // odd multiplier: a permutation of the ring; consecutive steps land far apart)
+    for (size_t i = 0; i < n; ++i) h[i] = (uint32_t)((i * 2654435761ull + 40503ull) % n);
+    std::vector<uint32_t> nx(n);
+    {
+      // follow the permutation's order to make next[] a single cycle
+      std::vector<uint32_t> order(n);
+      for (size_t i = 0; i < n; ++i) order[i] = h[i];
+      for (size_t i = 0; i < n; ++i) nx[order[i]] = order[(i + 1) % n];
+    }
+    ce = cudaMalloc(&buf, n * sizeof(uint32_t) + 256);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(buf, nx.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "latency probe buffer");
+    const uint32_t *next = (const uint32_t *)buf;
+    uint32_t *sink = (uint32_t *)((char *)buf + n * sizeof(uint32_t));
+    float t[2] = {0.f, 0.f};
+    const int steps[2] = {1024, 9216};
+    for (int k = 0; k < 2 && st == QPM_OK; ++k) {
+      for (int w = 0; w < 2 && st == QPM_OK; ++w) {
+        const int stp = w == 0 ? (int)n / 8 : steps[k];  // warm pass brings lines into L2
+        st = timed([&] {
+          k_probe_chase<<<1, 1, 0, s>>>(next, stp, sink);
+          return cudaGetLastError();
+        }, &t[k]);
+      }
+    }
+    if (st == QPM_OK) *ns_out = 1e6 * (double)(t[1] - t[0]) / (double)(steps[1] - steps[0]);
+  }
+  if (buf) cudaFree(buf);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }

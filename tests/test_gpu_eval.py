@@ -239,6 +239,20 @@ def test_issue_peak_microbenchmark(q):
         q.qpm_measure_issue_peak(4)
 
 
+def test_latency_microbenchmark(q):
+    """The barrier and L2 latencies behind the latency floor of the persistent form:
+    positive, of the expected order, and the barrier costs more than a load."""
+    bar = q.qpm_measure_latency(0, 256)
+    l2 = q.qpm_measure_latency(1)
+    assert 50.0 < l2 < 5000.0
+    assert l2 < bar < 50000.0
+    assert q.qpm_measure_latency(0, 1) > 0.0
+    with pytest.raises(q.QpmError):
+        q.qpm_measure_latency(2)
+    with pytest.raises(q.QpmError):
+        q.qpm_measure_latency(0, 10 ** 6)
+
+
 @pytest.mark.parametrize("kind", [0, 1, 2])
 def test_arithmetic_shortcuts_exact_on_every_pattern(q, kind):
     """The kernels' shortcuts give the oracle's plain operation for all 2^32
@@ -254,3 +268,30 @@ def test_arithmetic_shortcuts_exact_on_every_pattern(q, kind):
 def test_selfcheck_rejects_unknown_kind(q):
     with pytest.raises(q.QpmError):
         q.qpm_selfcheck(3)
+
+
+def test_multi_wavelength_with_a_full_table_cache(q):
+    """63 problems fill the table cache (64 per device); qpm_eval_multi with two new
+    problems must make room before its first lookup, never between them, so neither
+    of its tables is freed under it (a freed table is reallocated for the next problem
+    and the first problem would be scanned with the wrong phasors).  Its d_eff agree
+    with qpm_eval's."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    q.qpm_release_caches()
+    N, NP = 1001, 40
+    X = torch.from_numpy(W.random_genes(NP, N, seed=77)).cuda()
+    D = torch.empty((NP, 2), device="cuda")
+    for k in range(63):
+        q.qpm_eval(N, 0.5 + 0.01 * k, 2.0, X, D)
+    kap = [(0.123, 3.21), (0.456, 2.34)]
+    obj = torch.empty(NP, device="cuda")
+    Dm = torch.empty((NP, 2, 2), device="cuda")
+    q.qpm_eval_multi(N, kap, X, 1.0e4, 0.5, obj, Dm)
+    torch.cuda.synchronize()
+    for k, (k1, k2) in enumerate(kap):
+        q.qpm_eval(N, k1, k2, X, D)
+        torch.cuda.synchronize()
+        a, b = D.cpu().numpy(), Dm.cpu().numpy()[:, k]
+        assert deff_err(b, a[:, 0] + 1j * a[:, 1], N).max() < TOL_D
+    q.qpm_release_caches()
