@@ -73,7 +73,20 @@ typedef struct {
                           slots idle), else 32, 64, 128, 256 or 512 */
   int32_t f_schedule;  /* 0: F constant; 1: decaying F of Sec. 3.1.1,
                           F_g = F (cos(pi g / 2G) + 1) / 2 (1 - 0.2 (g / G)^2),
-                          evaluated in FP64 and rounded to FP32 */
+                          evaluated in FP64 and rounded to FP32;
+                          2: the adaptive F of Sec. 3.1.1 (the field F is unused):
+                          F in [0.01, 0.1], F_0 = 0.1; after the DE phase of generation
+                          g, over the DE survivors, with cv their fitness' standard
+                          deviation over its mean and rho the fraction of trials that
+                          strictly improved on their target: cv < 0.05 or rho < 0.1
+                          -> F = min(0.1, 1.25 F); else cv > 0.5 or max f - min f < 1e3
+                          -> F = max(0.01, 0.8 F); else F = 0.1 (cos(pi (g+1) / 2G)
+                          + 1) / 2 (1 - 0.2 ((g+1) / G)^2).  cv is decided from exact
+                          integer statistics (fitness quantised to 20 bits against the
+                          population maximum), so the decision is independent of any
+                          summation order.  NP <= 2^23.  A run resumed with
+                          qpm_set_population continues from the F history the state
+                          holds (qpm_get_F) */
 } qpm_params;
 
 /* Execution modes of qpm_run. */
@@ -264,6 +277,13 @@ qpm_status qpm_destroy(qpm_state *st);
  * the calls below.  Errors: bad state or instance -> QPM_ERR_ARG. */
 qpm_status qpm_instance_shape(const qpm_state *st, int32_t inst, int32_t *N_out, int32_t *NP_out,
                               int32_t *G_out);
+
+/* The F of every generation of instance `inst`: F_out device float [G + 1], entry g
+ * the F the DE phase of generation g uses (constant F: F everywhere; decaying F: the
+ * schedule; adaptive F: the values computed so far, entry g + 1 written during
+ * generation g).  Enqueued on `stream`.  Errors: bad state, instance or NULL output ->
+ * QPM_ERR_ARG; before qpm_init -> QPM_ERR_STATE. */
+qpm_status qpm_get_F(qpm_state *st, int32_t inst, float *F_out, qpm_stream_t stream);
 
 /* generation counter of the state as seen by the host (host int32 out) */
 qpm_status qpm_generation(const qpm_state *st, int32_t *g_out);

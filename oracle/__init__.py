@@ -61,9 +61,12 @@ def lib():
         L.orc_a_of.argtypes = [i32, i32]
         L.orc_a_of.restype = ctypes.c_float
         L.orc_gwo_candidates.argtypes = [P, u32, P, P, P]
-        L.orc_hwsda_generation.argtypes = [P, dbl, dbl, ctypes.c_int, i32, P, P, P, P, P, P, P, P, P]
+        L.orc_hwsda_generation.argtypes = [P, dbl, dbl, ctypes.c_int, i32, P, P, P, P, P, P, P, P, P,
+                                           P, P]
         L.orc_hwsda_generation.restype = ctypes.c_int
-        L.orc_hwsda_run.argtypes = [P, dbl, dbl, ctypes.c_int, P, P, P, P]
+        L.orc_adaptive_F.argtypes = [P, i32, P, P, ctypes.c_float, P, P]
+        L.orc_adaptive_F.restype = ctypes.c_int
+        L.orc_hwsda_run.argtypes = [P, dbl, dbl, ctypes.c_int, P, P, P, P, P]
         L.orc_hwsda_run.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -237,13 +240,26 @@ def gwo_candidates(cfg, g, X, lead):
     return Y
 
 
+def adaptive_F(cfg, g, f, improved, F_g):
+    """The adaptive F of Sec. 3.1.1 (see orc_adaptive_F): (branch, F of generation
+    g + 1, (cv^2, improved fraction, fitness range)); branch 0 schedule, 1 raised,
+    2 lowered."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    imp = np.ascontiguousarray(improved, dtype=np.uint8)
+    out = ctypes.c_float()
+    st = np.zeros(3)
+    br = lib().orc_adaptive_F(ctypes.byref(cfg), g, _p(f), _p(imp), F_g, ctypes.byref(out), _p(st))
+    return br, out.value, tuple(st)
+
+
 def hwsda_generation(cfg, kappa1, kappa2, g, X, fdec, f64=None, lock_trial=None,
-                     lock_cand=None, eval_mask=None, Q=Q_DEFAULT):
+                     lock_cand=None, eval_mask=None, Q=Q_DEFAULT, F=None):
     """One generation (Sec. 3.2 Steps 2-6) from population X.
 
-    Returns (X_next, fdec_next, f64_next, trial_f64, cand_f64, leaders).  In lockstep
-    mode (lock_trial/lock_cand given) the FP32 values decide; eval_mask limits
-    which rows get an FP64 fitness (NaN elsewhere)."""
+    Returns (X_next, fdec_next, f64_next, trial_f64, cand_f64, leaders), plus
+    (F_next, branch) at the end when F (the adaptive F of generation g) is given
+    (cfg.f_schedule == 2).  In lockstep mode (lock_trial/lock_cand given) the FP32
+    values decide; eval_mask limits which rows get an FP64 fitness (NaN elsewhere)."""
     X = np.array(X, dtype=np.float32, order="C", copy=True)
     fdec = np.array(fdec, dtype=np.float32, copy=True)
     f64 = np.zeros(cfg.NP) if f64 is None else np.array(f64, dtype=np.float64, copy=True)
@@ -253,15 +269,23 @@ def hwsda_generation(cfg, kappa1, kappa2, g, X, fdec, f64=None, lock_trial=None,
     tt = np.zeros(cfg.NP)
     tc = np.zeros(cfg.NP)
     lead = np.zeros(3, dtype=np.int32)
+    Fio = None if F is None else ctypes.c_float(F)
+    br = ctypes.c_int32(-1)
     rc = lib().orc_hwsda_generation(ctypes.byref(cfg), kappa1, kappa2, Q, g, _p(X), _p(fdec),
-                                    _p(f64), _p(lt), _p(lc), _p(em), _p(tt), _p(tc), _p(lead))
-    if rc != 0:
+                                    _p(f64), _p(lt), _p(lc), _p(em), _p(tt), _p(tc), _p(lead),
+                                    None if Fio is None else ctypes.byref(Fio), ctypes.byref(br))
+    if rc == -1:
         raise ValueError("orc_hwsda_generation: eval_mask needs lockstep mode")
+    if rc == -2:
+        raise ValueError("orc_hwsda_generation: F is given exactly for the adaptive F")
+    if Fio is not None:
+        return X, fdec, f64, tt, tc, lead, Fio.value, br.value
     return X, fdec, f64, tt, tc, lead
 
 
-def hwsda_run(cfg, kappa1, kappa2, lockstep=None, want_trace=False, Q=Q_DEFAULT):
-    """Run the HWSDA loop of Sec. 3.2.  Returns (X_final, f64_final[, trace64])."""
+def hwsda_run(cfg, kappa1, kappa2, lockstep=None, want_trace=False, Q=Q_DEFAULT, want_F=False):
+    """Run the HWSDA loop of Sec. 3.2.  Returns (X_final, f64_final[, trace64][, F history
+    of G + 1 values])."""
     X = np.zeros((cfg.NP, cfg.ld), dtype=np.float32)
     f = np.zeros(cfg.NP)
     n_tr = cfg.NP * (1 + 2 * cfg.G)
@@ -270,5 +294,11 @@ def hwsda_run(cfg, kappa1, kappa2, lockstep=None, want_trace=False, Q=Q_DEFAULT)
         ls = np.ascontiguousarray(lockstep, dtype=np.float32).ravel()
         assert ls.size == n_tr
     tr = np.zeros(n_tr) if want_trace else None
-    lib().orc_hwsda_run(ctypes.byref(cfg), kappa1, kappa2, Q, _p(X), _p(f), _p(ls), _p(tr))
-    return (X, f, tr) if want_trace else (X, f)
+    Fh = np.zeros(cfg.G + 1, dtype=np.float32) if want_F else None
+    lib().orc_hwsda_run(ctypes.byref(cfg), kappa1, kappa2, Q, _p(X), _p(f), _p(ls), _p(tr), _p(Fh))
+    out = (X, f)
+    if want_trace:
+        out += (tr,)
+    if want_F:
+        out += (Fh,)
+    return out

@@ -565,7 +565,8 @@ typedef struct {
   uint64_t seed;
   uint32_t inst;
   int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension */
-  int32_t f_schedule; /* 0 = constant F; 1 = decaying F of Sec. 3.1.1 */
+  int32_t f_schedule; /* 0 = constant F; 1 = decaying F of Sec. 3.1.1;
+                         2 = the adaptive F of Sec. 3.1.1 (orc_adaptive_F) */
 } orc_cfg;
 
 /* F of generation g.  Sec. 3.1.1 lets F follow (cos(pi g / 2G) + 1) / 2 times a
@@ -578,7 +579,101 @@ ORC_API float orc_F_of(const orc_cfg *c, int32_t g) {
   const double x = (double)g / (double)c->G;
   const double cs = 0.5 * (cos(M_PI * (double)g / (2.0 * (double)c->G)) + 1.0);
   const double qd = 1.0 - 0.2 * x * x;
-  return (float)((double)c->F * cs * qd);
+  /* adaptive form: the decay is the schedule of its intermediate state, scaled to the
+   * interval [0.01, 0.1] that Sec. 3.1.1 keeps F in (its top) */
+  const double top = c->f_schedule == 2 ? 0.1 : (double)c->F;
+  return (float)(top * cs * qd);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive F (Sec. 3.1.1, "dual mechanism").  The paper keeps F in [0.01, 0.1]  */
+/* and moves it by the population's state: when diversity is low (the standard  */
+/* deviation below a threshold, or the convergence rate below 0.1) F is raised; */
+/* when diversity is too high or the fitness range is small (the deviation above */
+/* a threshold, or the range below 10^3) F is lowered; otherwise F follows the   */
+/* cosine decay (cos(pi g / 2G) + 1) / 2 times a factor falling from 1.0 to 0.8. */
+/* It states neither the thresholds, the step sizes, which deviation, nor what   */
+/* the convergence rate is.  Readings taken (all after the DE phase of g, on the */
+/* DE survivors, deciding the F of generation g + 1):                            */
+/*   deviation: of the survivors' fitness, relative to its mean (coefficient of  */
+/*     variation cv); thresholds cv < 0.05 (low) and cv > 0.5 (high);             */
+/*   convergence rate: the fraction of the NP trials that strictly improved on    */
+/*     their target;                                                              */
+/*   range: max f - min f of the survivors, in the library's fitness units        */
+/*     (|d_eff / w^2|^2), against 10^3;                                           */
+/*   raise: F <- min(0.1, 1.25 F); lower: F <- max(0.01, 0.8 F); otherwise        */
+/*     F <- 0.1 (cos(pi (g+1) / 2G) + 1) / 2 (1 - 0.2 ((g+1)/G)^2) (orc_F_of);    */
+/*     the low test is taken first; F of generation 0 is the schedule's 0.1.      */
+/* So that both implementations take every decision identically whatever their  */
+/* summation order, the deviation is computed from exact integers: with E such   */
+/* that 2^(E-1) <= max f < 2^E, every fitness is quantised to                    */
+/* n = floor(f 2^(20 - E)) in [0, 2^20) by shifting its significand (exact), the */
+/* sums S1 = sum n and S2 = sum n^2 are exact 64-bit integers (NP <= 2^23), and  */
+/* cv^2 = (NP S2 - S1^2) / S1^2 is compared as NP S2 - S1^2 against t^2 S1^2 in  */
+/* FP64, each operation rounded once (no contraction).  All f = 0 counts as low  */
+/* diversity.                                                                     */
+/* ------------------------------------------------------------------------- */
+#define AF_FMIN 0.01f
+#define AF_FMAX 0.1f
+#define AF_UP 1.25f
+#define AF_DOWN 0.8f
+
+/* n = floor(f 2^(20 - E)) for f >= 0 given the biased exponent field emax of max f
+ * (emax >= 1), from the bits: f = m 2^(e - 150) with m its 24-bit significand */
+static inline uint32_t af_quantise(float f, uint32_t emax) {
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0) e = 1; else m |= 0x800000u; /* subnormal: no hidden bit */
+  const uint32_t sh = 4u + emax - e;     /* >= 4 since e <= emax */
+  return sh >= 24u ? 0u : m >> sh;
+}
+
+/* F of generation g + 1 from the survivors' fitness f[NP] (the decision precision)
+ * and the strict-improvement flags of the generation's trials; returns the branch
+ * taken (0 schedule, 1 raised, 2 lowered), *F_next the new F.  stats (may be NULL)
+ * receives {cv^2 (as the FP64 ratio, for reports), improved fraction, range}. */
+ORC_API int orc_adaptive_F(const orc_cfg *c, int32_t g, const float *f, const uint8_t *improved,
+                           float F_g, float *F_next, double *stats) {
+  const int32_t NP = c->NP;
+  float fmax = 0.0f, fmin = f[0];
+  int64_t nimp = 0;
+  for (int32_t i = 0; i < NP; ++i) {
+    if (f[i] > fmax) fmax = f[i];
+    if (f[i] < fmin) fmin = f[i];
+    nimp += improved[i] ? 1 : 0;
+  }
+  uint32_t ub;
+  memcpy(&ub, &fmax, sizeof ub);
+  uint32_t emax = (ub >> 23) & 0xFFu;
+  if (emax == 0) emax = 1;
+  uint64_t S1 = 0, S2 = 0;
+  for (int32_t i = 0; i < NP; ++i) {
+    const uint64_t n = af_quantise(f[i], emax);
+    S1 += n;
+    S2 += n * n;
+  }
+  const double a = (double)NP * (double)S2;
+  const double b = (double)S1 * (double)S1;
+  const double num = a - b;
+  const float range = fmax - fmin;
+  const int low = (S1 == 0) || (num < 0.0025 * b) || (10 * nimp < (int64_t)NP);
+  const int high = !low && ((num > 0.25 * b) || (range < 1000.0f));
+  if (stats) {
+    stats[0] = b > 0.0 ? num / b : 0.0;
+    stats[1] = (double)nimp / (double)NP;
+    stats[2] = (double)range;
+  }
+  if (low) {
+    *F_next = fminf(AF_FMAX, F_g * AF_UP);
+    return 1;
+  }
+  if (high) {
+    *F_next = fmaxf(AF_FMIN, F_g * AF_DOWN);
+    return 2;
+  }
+  *F_next = orc_F_of(c, g + 1);
+  return 0;
 }
 
 static inline float clamp1(float v) { return fminf(fmaxf(v, -1.0f), 1.0f); }
@@ -594,14 +689,14 @@ ORC_API void orc_init_population(const orc_cfg *c, float *X) {
 
 /* Sec. 2.2.1 steps 2-3 for target i: mutant v = x_r1 + F (x_r2 - x_r3), clamped,
  * then binomial crossover with the target -> trial u */
-static void de_trial_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X, float *u) {
+static void de_trial_one(const orc_cfg *c, uint32_t g, float F, int32_t i, const float *X,
+                         float *u) {
   int32_t r[4];
   orc_de_indices(c->seed, c->inst, g, i, c->NP, c->N, r);
   const float *x = X + (int64_t)i * c->ld;
   const float *x1 = X + (int64_t)r[0] * c->ld;
   const float *x2 = X + (int64_t)r[1] * c->ld;
   const float *x3 = X + (int64_t)r[2] * c->ld;
-  const float F = orc_F_of(c, (int32_t)g);
   for (int32_t j = 0; j < c->N; ++j) {
     float diff = x2[j] - x3[j];
     float step = F * diff;
@@ -611,9 +706,14 @@ static void de_trial_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
   }
 }
 
-ORC_API void orc_de_trials(const orc_cfg *c, uint32_t g, const float *X, float *U) {
+/* trials of every target with the scale factor F of generation g */
+static void de_trials_F(const orc_cfg *c, uint32_t g, float F, const float *X, float *U) {
 #pragma omp parallel for schedule(static)
-  for (int32_t i = 0; i < c->NP; ++i) de_trial_one(c, g, i, X, U + (int64_t)i * c->ld);
+  for (int32_t i = 0; i < c->NP; ++i) de_trial_one(c, g, F, i, X, U + (int64_t)i * c->ld);
+}
+
+ORC_API void orc_de_trials(const orc_cfg *c, uint32_t g, const float *X, float *U) {
+  de_trials_F(c, g, orc_F_of(c, (int32_t)g), X, U);
 }
 
 /* Sec. 3.2 Step 3: the three best wolves (descending f, ties to the lower index) */
@@ -706,30 +806,45 @@ static void eval_rows(const orc_cfg *c, double kappa1, double kappa2, int Q, con
  *                 fitness computed (lockstep only; decisions do not need them)
  *   tr_trial, tr_cand: if non-NULL, receive the FP64 fitness of trials and
  *                 candidates (NaN where not evaluated)
- *   lead_out[3]:  if non-NULL, receives the leaders of this generation */
+ *   lead_out[3]:  if non-NULL, receives the leaders of this generation
+ *   F_io:         adaptive F (f_schedule = 2) only: in, the F of generation g; out,
+ *                 the F of generation g + 1 (orc_adaptive_F on the DE survivors);
+ *                 NULL otherwise (F then follows orc_F_of)
+ *   branch_out:   if non-NULL (adaptive F), receives orc_adaptive_F's branch */
 ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2, int Q, int32_t g,
                                  float *X, float *fdec, double *f64, const float *lock_trial,
                                  const float *lock_cand, const uint8_t *eval_mask,
-                                 double *tr_trial, double *tr_cand, int32_t *lead_out) {
+                                 double *tr_trial, double *tr_cand, int32_t *lead_out,
+                                 float *F_io, int32_t *branch_out) {
   ensure_rule(Q);
   const int lock = (lock_trial != NULL);
   if (!lock && eval_mask) return -1;
+  if ((c->f_schedule == 2) != (F_io != NULL)) return -2;
   int32_t NP = c->NP;
   int64_t sz = (int64_t)NP * c->ld;
   float *U = (float *)calloc((size_t)sz, sizeof(float));
   double *ft = (double *)malloc(sizeof(double) * NP);
   uint8_t *mask = (uint8_t *)malloc((size_t)NP);
   /* Step 2: mutation, crossover and selection over all NP individuals */
-  orc_de_trials(c, (uint32_t)g, X, U);
+  de_trials_F(c, (uint32_t)g, F_io ? *F_io : orc_F_of(c, g), X, U);
   eval_rows(c, kappa1, kappa2, Q, U, eval_mask, ft);
   if (tr_trial) memcpy(tr_trial, ft, sizeof(double) * NP);
   for (int32_t i = 0; i < NP; ++i) {
+    /* strict improvement of the trial over its target, in the decision precision */
+    mask[i] = lock ? (lock_trial[i] > fdec[i]) : ((float)ft[i] > fdec[i]);
     int accept = lock ? (lock_trial[i] >= fdec[i]) : (ft[i] >= f64[i]);
     if (accept) {
       memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
       f64[i] = ft[i];
       fdec[i] = lock ? lock_trial[i] : (float)ft[i];
     }
+  }
+  /* Sec. 3.2 Step 6 for the adaptive F, from the DE survivors (Sec. 3.1.1) */
+  if (F_io) {
+    float Fn;
+    const int br = orc_adaptive_F(c, g, fdec, mask, *F_io, &Fn, NULL);
+    *F_io = Fn;
+    if (branch_out) *branch_out = br;
   }
   /* Step 3: the three leaders */
   int32_t lead[3];
@@ -776,9 +891,11 @@ ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2,
  *              lockstep[NP*(1+2g) .. NP*(2+2g))        trial fitness of generation g
  *              lockstep[NP*(2+2g) .. NP*(3+2g))        GWO candidate fitness of gen g
  *   trace64:   if non-NULL, same layout, filled with the oracle's FP64 fitness
+ *   Fhist:     if non-NULL, [G + 1]: the F of every generation (the last entry: the
+ *              F the run would use next)
  *   Returns 0. */
 ORC_API int orc_hwsda_run(const orc_cfg *c, double kappa1, double kappa2, int Q, float *X,
-                          double *fcur, const float *lockstep, double *trace64) {
+                          double *fcur, const float *lockstep, double *trace64, float *Fhist) {
   ensure_rule(Q);
   int32_t NP = c->NP;
   float *fdec = (float *)malloc(sizeof(float) * NP);
@@ -786,13 +903,17 @@ ORC_API int orc_hwsda_run(const orc_cfg *c, double kappa1, double kappa2, int Q,
   eval_rows(c, kappa1, kappa2, Q, X, NULL, fcur);
   if (trace64) memcpy(trace64, fcur, sizeof(double) * NP);
   for (int32_t i = 0; i < NP; ++i) fdec[i] = lockstep ? lockstep[i] : (float)fcur[i];
+  float F = orc_F_of(c, 0); /* the adaptive F starts from the schedule */
   for (int32_t g = 0; g < c->G; ++g) {
     const float *lt = lockstep ? lockstep + (int64_t)NP * (1 + 2 * g) : NULL;
     const float *lc = lockstep ? lockstep + (int64_t)NP * (2 + 2 * g) : NULL;
     double *tt = trace64 ? trace64 + (int64_t)NP * (1 + 2 * g) : NULL;
     double *tc = trace64 ? trace64 + (int64_t)NP * (2 + 2 * g) : NULL;
-    orc_hwsda_generation(c, kappa1, kappa2, Q, g, X, fdec, fcur, lt, lc, NULL, tt, tc, NULL);
+    if (Fhist) Fhist[g] = c->f_schedule == 2 ? F : orc_F_of(c, g);
+    orc_hwsda_generation(c, kappa1, kappa2, Q, g, X, fdec, fcur, lt, lc, NULL, tt, tc, NULL,
+                         c->f_schedule == 2 ? &F : NULL, NULL);
   }
+  if (Fhist) Fhist[c->G] = c->f_schedule == 2 ? F : orc_F_of(c, c->G);
   free(fdec);
   return 0;
 }

@@ -18,7 +18,7 @@ __all__ = [
     "qpm_release_caches", "qpm_measure_issue_peak", "qpm_measure_latency", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
-    "qpm_instance_shape",
+    "qpm_instance_shape", "qpm_get_F",
     "qpm_set_batch_cluster",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
@@ -85,6 +85,7 @@ def lib(build=True):
             "qpm_generation": ([_P, _P], ctypes.c_int),
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
             "qpm_instance_shape": ([_P, i32, _P, _P, _P], ctypes.c_int),
+            "qpm_get_F": ([_P, i32, _P, _P], ctypes.c_int),
             "qpm_set_batch_cluster": ([_P, i32], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
             "qpm_set_population": ([_P, i32, _P, i64, i32, _P], ctypes.c_int),
@@ -408,6 +409,18 @@ def qpm_instance_shape(st, inst=0):
     n, p, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().qpm_instance_shape(st, int(inst), ctypes.byref(n), ctypes.byref(p), ctypes.byref(g)))
     return n.value, p.value, g.value
+
+
+def qpm_get_F(st, inst=0, F_out=None, stream=None):
+    """F of every generation of instance `inst` (float32 CUDA [G + 1]; allocated when
+    F_out is None)."""
+    import torch
+    _, _, G = qpm_instance_shape(st, inst)
+    if F_out is None:
+        F_out = torch.empty(G + 1, dtype=torch.float32, device="cuda")
+    _out(F_out, "F_out", G + 1, optional=False)
+    _check(lib().qpm_get_F(st, int(inst), _ptr(F_out), _stream(stream)))
+    return F_out
 
 
 def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):

@@ -115,44 +115,6 @@ __device__ __forceinline__ float div3_rn(float x) {
   return fabsf(rem) > 0.0f ? __fmaf_rn(rem, r, q) : q;
 }
 
-// ------------------------------------------------------- packed FP32 pairs
-// sm_100 and later issue two single-precision operations on a register pair as one
-// instruction (add/sub/mul/fma .rn.f32x2): each half is the IEEE operation rounded to
-// nearest, exactly as the scalar instruction would give it, at half the issue slots.
-// The pair's halves are the .x and .y of a float2.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {  // a * b + c
-  float2 r;
-  asm("{.reg .b64 A, B, C, D;\n\tmov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\t"
-      "mov.b64 C, {%6, %7};\n\tfma.rn.f32x2 D, A, B, C;\n\tmov.b64 {%0, %1}, D;}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return r;
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  float2 r;
-  asm("{.reg .b64 A, B, D;\n\tmov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\t"
-      "mul.rn.f32x2 D, A, B;\n\tmov.b64 {%0, %1}, D;}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-  float2 r;
-  asm("{.reg .b64 A, B, D;\n\tmov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\t"
-      "add.rn.f32x2 D, A, B;\n\tmov.b64 {%0, %1}, D;}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // a - b
-  float2 r;
-  asm("{.reg .b64 A, B, D;\n\tmov.b64 A, {%2, %3};\n\tmov.b64 B, {%4, %5};\n\t"
-      "sub.rn.f32x2 D, A, B;\n\tmov.b64 {%0, %1}, D;}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-
 // ------------------------------------------------------- asynchronous copies
 // 16 bytes global -> shared through L2 (cp.async.cg), no registers held while in
 // flight; bytes < 16 zero-fills the rest.  A thread sees its own copies after

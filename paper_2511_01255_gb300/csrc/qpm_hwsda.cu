@@ -59,7 +59,10 @@ struct InstDev {
   int32_t *gen;          // [1] completed generations
   int32_t *best;         // [1] best index (get_best)
   float *trace;          // optional fitness trace
-  const float *Fsched;   // [G] F of every generation, or NULL for constant F
+  float *Fsched;         // [G + 1] F of every generation, or NULL for constant F; the
+                         // adaptive F (f_schedule 2) writes entry g + 1 during generation g
+  const float *Fbase;    // [G + 1] adaptive F only: the schedule of its intermediate state
+  int32_t adaptive;      // f_schedule == 2
   unsigned long long *dekey;  // [NP] persistent form: DE survivor keys (lead_key) for Step 3
 };
 
@@ -262,7 +265,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
                                             int *slot_out = nullptr, float4 *stg = nullptr,
                                             bool has_wcr = false,
                                             uint4 wcr = make_uint4(0u, 0u, 0u, 0u),
-                                            int own_slot = -1) {
+                                            int own_slot = -1, int *impr_out = nullptr) {
   static_assert(!(STG && DUAL), "staged rows need known slots");
   const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
@@ -335,6 +338,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     if (I.trace) I.trace[(size_t)I.NP * (1 + 2 * (size_t)g) + i] = f;
     key = lead_key(accept ? f : fx, i);
     if (slot_out) *slot_out = accept ? (si ^ 1) : si;  // the survivor's slot
+    if (impr_out) *impr_out = f > fx;                   // a strict improvement (adaptive F)
   }
   return key;
 }
@@ -454,6 +458,117 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   }
 }
 
+// The keys carry the survivor's slot and whether its trial strictly improved on the
+// target: fitness bits << 32 | (0x3FFFFFFF - i) << 2 | improved << 1 | slot, which
+// orders like lead_key (the two low bits never separate two individuals).
+__device__ __forceinline__ unsigned long long slot_key(unsigned long long key, int i, int slot,
+                                                       int improved = 0) {
+  return (key & 0xFFFFFFFF00000000ull) |
+         (unsigned long long)(((0x3FFFFFFFu - (uint32_t)i) << 2) | ((uint32_t)improved << 1) |
+                              (uint32_t)slot);
+}
+__device__ __forceinline__ int slot_key_index(unsigned long long k) {
+  return (int)(0x3FFFFFFFu - ((uint32_t)k >> 2));
+}
+
+// ------------------------------------------------------------- adaptive F
+// Sec. 3.1.1's adaptive F (f_schedule 2).  The paper keeps F in [0.01, 0.1], raises it
+// when the population's diversity is low (standard deviation below a threshold, or a
+// convergence rate below 0.1), lowers it when diversity is too high or the fitness
+// range small (deviation above a threshold, or range below 10^3), and otherwise lets
+// it follow the cosine-times-quadratic decay.  Readings (the paper gives neither the
+// thresholds nor the steps): after the DE phase of generation g, over the DE survivors,
+// cv = the fitness' standard deviation over its mean, the convergence rate = the
+// fraction of trials that strictly improved on their target; cv < 0.05 or a rate below
+// 0.1 raises F to min(0.1, 1.25 F); cv > 0.5 or max f - min f < 10^3 lowers it to
+// max(0.01, 0.8 F); otherwise F = Fbase[g + 1] = 0.1 (cos(pi (g+1) / 2G) + 1) / 2
+// (1 - 0.2 ((g+1)/G)^2).  The decision uses exact integer statistics, so that it does
+// not depend on a summation order: with E such that 2^(E-1) <= max f < 2^E, every
+// fitness is quantised to n = floor(f 2^(20 - E)) by shifting its significand, and
+// S1 = sum n, S2 = sum n^2 are 64-bit integers (NP <= 2^23); cv^2 < t^2 is tested as
+// NP S2 - S1^2 < t^2 S1^2 with every FP64 operation rounded once.
+constexpr float AF_FMIN = 0.01f, AF_FMAX = 0.1f, AF_UP = 1.25f, AF_DOWN = 0.8f;
+
+// n = floor(f 2^(20 - E)) for the fitness bits fb (f >= 0) and the exponent field emax
+// (>= 1) of the largest fitness: f = m 2^(e - 150), m the 24-bit significand
+__device__ __forceinline__ uint32_t af_quantise(uint32_t fb, uint32_t emax) {
+  uint32_t e = (fb >> 23) & 0xFFu, m = fb & 0x7FFFFFu;
+  if (e == 0) e = 1;
+  else m |= 0x800000u;
+  const uint32_t sh = 4u + emax - e;
+  return sh >= 24u ? 0u : m >> sh;
+}
+
+// F of generation g + 1 from the survivor keys of generation g (slot_key layout), by
+// every thread of one CTA; thread 0 writes it to I.Fsched[g + 1].  Every thread returns
+// after a CTA barrier.
+__device__ void adaptive_F_block(const InstDev &I, const unsigned long long *keys, int g) {
+  __shared__ uint32_t red_u[3][32];
+  __shared__ unsigned long long red_s[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t mx = 0u, mn = 0xFFFFFFFFu, cnt = 0u;
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) {
+    const unsigned long long k = keys[i];
+    const uint32_t fb = (uint32_t)(k >> 32);
+    mx = max(mx, fb);
+    mn = min(mn, fb);
+    cnt += ((uint32_t)k >> 1) & 1u;
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0) {
+    red_u[0][warp] = mx;
+    red_u[1][warp] = mn;
+    red_u[2][warp] = cnt;
+  }
+  __syncthreads();
+  mx = 0u;
+  mn = 0xFFFFFFFFu;
+  cnt = 0u;
+  for (int w = 0; w < nw; ++w) {
+    mx = max(mx, red_u[0][w]);
+    mn = min(mn, red_u[1][w]);
+    cnt += red_u[2][w];
+  }
+  uint32_t emax = (mx >> 23) & 0xFFu;
+  if (emax == 0) emax = 1;
+  unsigned long long s1 = 0ull, s2 = 0ull;
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) {
+    const uint32_t n = af_quantise((uint32_t)(keys[i] >> 32), emax);
+    s1 += n;
+    s2 += (unsigned long long)n * n;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red_s[0][warp] = s1;
+    red_s[1][warp] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s1 = s2 = 0ull;
+    for (int w = 0; w < nw; ++w) {
+      s1 += red_s[0][w];
+      s2 += red_s[1][w];
+    }
+    const double a = __dmul_rn((double)I.NP, (double)s2);
+    const double b = __dmul_rn((double)s1, (double)s1);
+    const double num = __dsub_rn(a, b);
+    const float range = __fsub_rn(__uint_as_float(mx), __uint_as_float(mn));
+    const bool low = (s1 == 0ull) || (num < __dmul_rn(0.0025, b)) ||
+                     (10ull * cnt < (unsigned long long)I.NP);
+    const bool high = !low && ((num > __dmul_rn(0.25, b)) || (range < 1000.0f));
+    const float Fg = I.Fsched[g];
+    I.Fsched[g + 1] = low ? fminf(AF_FMAX, __fmul_rn(Fg, AF_UP))
+                          : (high ? fmaxf(AF_FMIN, __fmul_rn(Fg, AF_DOWN)) : I.Fbase[g + 1]);
+  }
+  __syncthreads();
+}
+
 // top-3 merge over the CTA: every thread passes its sorted triple, thread 0 gets the result
 __device__ void block_top3(unsigned long long &k0, unsigned long long &k1, unsigned long long &k2,
                            unsigned long long *sh) {
@@ -535,11 +650,15 @@ static __global__ void k_de(InstDev I) {
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
+    int slot = 0, impr = 0;
     const unsigned long long key =
         de_individual<COMP, true, false, DUAL, false, STG>(
             I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh,
-            nullptr, stg);
-    if (threadIdx.x == 0) top3_insert(k0, k1, k2, key);
+            &slot, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr);
+    if (threadIdx.x == 0) {
+      top3_insert(k0, k1, k2, key);
+      if (I.adaptive) I.dekey[i] = slot_key(key, i, slot, impr);
+    }
   }
   if (threadIdx.x == 0) {
     I.topk[3 * blockIdx.x] = k0;
@@ -548,6 +667,7 @@ static __global__ void k_de(InstDev I) {
   }
   if (last_cta(&I.ctr[0])) {
     merge_leaders(I.topk, gridDim.x, I.lead, nullptr);  // Step 3
+    if (I.adaptive) adaptive_F_block(I, I.dekey, g);     // Step 6: the next F
     if (threadIdx.x == 0) I.ctr[0] = 0u;
   }
 }
@@ -593,16 +713,6 @@ static __global__ void k_gwo(InstDev I) {
 // search is a negligible part of a generation.  The keys are written in
 // the DE phase only, so a CTA that is still choosing leaders never sees a fitness
 // already changed by another CTA's GWO selection.
-// The keys carry the survivor's slot: fitness bits << 32 | (0x7FFFFFFF - i) << 1 | slot,
-// which orders like lead_key (the slot bit never separates two individuals).
-__device__ __forceinline__ unsigned long long slot_key(unsigned long long key, int i, int slot) {
-  return (key & 0xFFFFFFFF00000000ull) |
-         (unsigned long long)(((0x7FFFFFFFu - (uint32_t)i) << 1) | (uint32_t)slot);
-}
-__device__ __forceinline__ int slot_key_index(unsigned long long k) {
-  return (int)(0x7FFFFFFFu - ((uint32_t)k >> 1));
-}
-
 template <bool REDUX>
 __device__ void leaders_from_keys(const unsigned long long *keys, int NP, int32_t *lead,
                                   int32_t *lead_sh, int32_t *slot_sh) {
@@ -709,14 +819,14 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
     for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
       if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
       const int4 r = pre ? r_pre : de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N);
-      int slot = 0;
+      int slot = 0, impr = 0;
       const unsigned long long key =
           de_individual<COMP, false, TS, DUAL, false, STG>(I, K, tbl, g, i, r, sel_in, sel_out,
                                                             sh, &slot, stg, pre, wcr_pre,
-                                                            own_known ? own_slot_sh : -1);
+                                                            own_known ? own_slot_sh : -1, &impr);
       // ordered before the barrier's release
       if (threadIdx.x == 0) {
-        I.dekey[i] = slot_key(key, i, slot);
+        I.dekey[i] = slot_key(key, i, slot, impr);
         own_slot_sh = slot;  // read after the barrier's CTA synchronisation
       }
     }
@@ -762,6 +872,10 @@ static __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : 2)
       const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
       I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
     }
+    // Step 6, the adaptive F of the next generation, by the CTA of the alpha leader
+    // (which moves no wolf when it holds one individual): the survivor keys stay
+    // unchanged until the next DE phase, which the barrier below keeps after this
+    if (I.adaptive && (int)blockIdx.x == la % (int)gridDim.x) adaptive_F_block(I, I.dekey, g);
     // the next DE phase reads any individual: every CTA must have finished GWO
     grid_arrive(bar, target);
     own_known = pre;
@@ -832,10 +946,12 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
     // six registers free across the DE loop
     if (lane == 0) wk[3 * warp] = wk[3 * warp + 1] = wk[3 * warp + 2] = 0ull;
     for (int i = gw; i < I.NP; i += gstride) {
+      int impr = 0;
       const unsigned long long key =
           de_individual<COMP, false, TS, false, true, true>(
               I, K, tbl, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out,
-              nullptr, nullptr, stg);
+              nullptr, nullptr, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr);
+      if (lane == 0 && I.adaptive) I.dekey[i] = slot_key(key, i, 0, impr);
       if (lane == 0) {
         unsigned long long a = wk[3 * warp], b = wk[3 * warp + 1], c = wk[3 * warp + 2];
         top3_insert(a, b, c, key);
@@ -875,6 +991,9 @@ __device__ void batch_instance(const InstDev &I, int gens, float4 *dyn, unsigned
       }
     }
     __syncthreads();
+    // Step 6: the adaptive F of the next generation, by the cluster's first CTA; the
+    // cluster barrier after the GWO phase orders it before the next DE phase
+    if (I.adaptive && crank == 0) adaptive_F_block(I, I.dekey, g);
     const int la = lead_sh[0], lb = lead_sh[1], ld = lead_sh[2];
     for (int i = gw; i < I.NP; i += gstride) {
       if (i == la || i == lb || i == ld) continue;
@@ -1316,8 +1435,10 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256 &&
         q.team != 512)
       return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128, 256 or 512");
-    if (q.f_schedule != 0 && q.f_schedule != 1)
-      return fail(QPM_ERR_ARG, "qpm_create: f_schedule must be 0 or 1");
+    if (q.f_schedule < 0 || q.f_schedule > 2)
+      return fail(QPM_ERR_ARG, "qpm_create: f_schedule must be 0, 1 or 2");
+    if (q.f_schedule == 2 && q.NP > (1 << 23))
+      return fail(QPM_ERR_UNSUPPORTED, "qpm_create: the adaptive F needs NP <= 2^23");
     if (!std::isfinite(p.kappa1) || !std::isfinite(p.kappa2))
       return fail(QPM_ERR_ARG, "qpm_create: kappa must be finite");
   }
@@ -1392,7 +1513,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += 256 + 256 + 256;  // konst, konst64, lead
     total += align_up(6 * NP * sizeof(unsigned long long), 256);
     total += align_up(NP * sizeof(unsigned long long), 256);  // DE survivor keys
-    total += align_up((size_t)q.G * sizeof(float), 256);  // F schedule
+    total += 2 * align_up((size_t)(q.G + 1) * sizeof(float), 256);  // F history, F base
     total += 256 + 256 + 256;  // ctr, gen, best
   }
   const size_t desc_off = total;
@@ -1421,8 +1542,13 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
     I.dekey = (unsigned long long *)take(NP * sizeof(unsigned long long));
-    I.Fsched = st->params[k].f_schedule ? (const float *)take((size_t)I.G * sizeof(float))
-                                        : (take((size_t)I.G * sizeof(float)), nullptr);
+    {
+      float *fs = (float *)take((size_t)(I.G + 1) * sizeof(float));
+      float *fb = (float *)take((size_t)(I.G + 1) * sizeof(float));
+      I.Fsched = st->params[k].f_schedule ? fs : nullptr;
+      I.Fbase = st->params[k].f_schedule == 2 ? fb : nullptr;
+      I.adaptive = st->params[k].f_schedule == 2 ? 1 : 0;
+    }
     I.ctr = (unsigned *)take(4 * sizeof(unsigned));
     I.gen = (int32_t *)take(sizeof(int32_t));
     I.best = (int32_t *)take(sizeof(int32_t));
@@ -1437,18 +1563,26 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
       return (long long)st->h[a].NP * st->h[a].Npad > (long long)st->h[b].NP * st->h[b].Npad;
     });
-    // F schedules (Sec. 3.1.1): cosine decay times a quadratic factor 1.0 -> 0.8
+    // F schedules (Sec. 3.1.1): cosine decay times a quadratic factor 1.0 -> 0.8, for
+    // generations 0 .. G; from F (f_schedule 1), or from the top 0.1 of the adaptive
+    // F's interval (f_schedule 2: its intermediate state's values in Fbase, and its
+    // first generation's F in the history)
     for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
       if (!st->h[k].Fsched) continue;
       const int G = st->h[k].G;
-      std::vector<float> F(G);
-      for (int g = 0; g < G; ++g) {
+      const bool adaptive = st->h[k].adaptive != 0;
+      const double top = adaptive ? 0.1 : (double)st->params[k].F;
+      std::vector<float> F(G + 1);
+      for (int g = 0; g <= G; ++g) {
         const double x = (double)g / (double)G;
         const double c = 0.5 * (std::cos(M_PI * (double)g / (2.0 * (double)G)) + 1.0);
         const double qd = 1.0 - 0.2 * x * x;
-        F[g] = (float)((double)st->params[k].F * c * qd);
+        F[g] = (float)(top * c * qd);
       }
-      e = cudaMemcpy((void *)st->h[k].Fsched, F.data(), sizeof(float) * G, cudaMemcpyHostToDevice);
+      e = cudaMemcpy(st->h[k].Fsched, F.data(), sizeof(float) * (G + 1), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess && adaptive)
+        e = cudaMemcpy((void *)st->h[k].Fbase, F.data(), sizeof(float) * (G + 1),
+                       cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess)
       e = cudaMemcpy(st->d_order, order.data(), sizeof(int32_t) * n_inst, cudaMemcpyHostToDevice);
@@ -1648,6 +1782,20 @@ extern "C" qpm_status qpm_instance_shape(const qpm_state *st, int32_t inst, int3
   if (N_out) *N_out = st->h[inst].N;
   if (NP_out) *NP_out = st->h[inst].NP;
   if (G_out) *G_out = st->h[inst].G;
+  return QPM_OK;
+}
+
+static __global__ void k_copy_F(InstDev I, float *out) {
+  for (int g = threadIdx.x + blockIdx.x * blockDim.x; g <= I.G; g += blockDim.x * gridDim.x)
+    out[g] = I.Fsched ? I.Fsched[g] : I.F;
+}
+
+extern "C" qpm_status qpm_get_F(qpm_state *st, int32_t inst, float *F_out, qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n || !F_out) return fail(QPM_ERR_ARG, "bad arguments");
+  if (!st->inited) return fail(QPM_ERR_STATE, "qpm_init has not been called");
+  const InstDev &I = st->h[inst];
+  k_copy_F<<<(I.G + 256) / 256, 256, 0, (cudaStream_t)stream>>>(I, F_out);
+  QPM_CUDA(cudaGetLastError());
   return QPM_OK;
 }
 

@@ -60,6 +60,34 @@ def test_relaxed_fwd_bwd_against_oracle(q, orc, N):
         assert grad_err(g[r], ref_g) < TOL_G
 
 
+@pytest.mark.parametrize("ld_extra,ldg_extra", [(0, 0), (1, 3), (4, 1)])
+def test_relaxed_ragged_batch_and_strided_rows(q, orc, ld_extra, ldg_extra):
+    """B = 130 rows: a warp takes 64 rows, two per lane, so the last warp holds rows
+    128-129 in its first half and none in its second; N = 1000 domains in rows of
+    N + ld_extra floats (16-byte aligned rows take the asynchronous-copy path, the
+    others register loads) and gradients written into rows of N + ldg_extra floats."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    B, N = 130, 1000
+    theta = W.relaxed_theta(B, N, seed=7)
+    big = torch.zeros((B, N + ld_extra), dtype=torch.float32, device="cuda")
+    big[:, :N] = torch.from_numpy(theta).cuda()
+    th = big[:, :N]
+    D = torch.empty((B, 2), device="cuda")
+    f = torch.empty(B, device="cuda")
+    A = q.relaxed_saved(B, N)
+    q.qpm_deff_relaxed_fwd(N, K1, K2, th, D, f, A)
+    gbig = torch.full((B, N + ldg_extra), 7.0, dtype=torch.float32, device="cuda")
+    q.qpm_deff_relaxed_bwd(N, K1, K2, th, D, A, None, gbig[:, :N])
+    torch.cuda.synchronize()
+    D, gb = D.cpu().numpy(), gbig.cpu().numpy()
+    assert np.all(gb[:, N:] == 7.0)  # nothing written past the rows
+    for r in (0, 31, 32, 63, 64, 127, 128, 129):
+        ref_g, ref_D = orc.grad_relaxed(theta[r].astype(np.float64), K1, K2)
+        assert deff_err(D[r:r + 1], np.array([ref_D]), N).max() < TOL_D, r
+        assert grad_err(gb[r, :N], ref_g) < TOL_G, r
+
+
 def test_tanh_and_derivative_accuracy(q):
     """The kernels form d = tanh(theta) and 1 - d^2 from one hardware exponential
     and reciprocal.  A one-domain row exposes both: its sum of a (the first
@@ -150,6 +178,11 @@ def test_polish_leaders(q, orc, N, NP):
         assert fit_err(f1[lead], ref, N).max() < 2 * TOL_D
         a = acc.cpu().numpy()
         assert set(np.unique(a)) <= {0, 1}
+        # polish does something: at least one leader is replaced by genes whose FP64
+        # fitness is strictly higher than that of the genes they replace
+        old64 = np.abs(orc.deff_genes(X0[lead], K1, K2)) ** 2
+        assert a.sum() >= 1
+        assert np.any((a == 1) & (ref > old64 * (1 + 1e-6)))
         for k in range(3):
             if not a[k]:  # rejected: the leader is untouched
                 assert np.array_equal(X0[lead[k]], X1[lead[k]]) and f1[lead[k]] == f0[lead[k]]

@@ -131,3 +131,36 @@ def test_batched_full_size_sampled(q, orc):
         sel = mask.astype(bool)
         assert fit_err(lt[sel], t64[sel], N).max() < 2 * TOL_D
     st.close()
+
+
+def test_batched_adaptive_F_lockstep(q, orc):
+    """Instances with the adaptive F (f_schedule 2) next to constant-F instances in one
+    batched launch on 2-CTA clusters: each adaptive instance's F history and population
+    equal the oracle's lockstep replay."""
+    import torch
+    G = 10
+    probs = [(N, k1, k2) for N, k1, k2, NP, comp, comb in INSTANCES]
+    prms = [q.Params(NP, G, 0.5, 0.9, 3, comb, comp, 0, 2 if k % 2 == 0 else 0)
+            for k, (N, k1, k2, NP, comp, comb) in enumerate(INSTANCES)]
+    st = q.State(probs, prms)
+    traces = []
+    for k, (N, k1, k2, NP, comp, comb) in enumerate(INSTANCES):
+        tr = torch.full((NP * (1 + 2 * G),), float("nan"), dtype=torch.float32, device="cuda")
+        q.qpm_set_trace(st.h, k, tr)
+        traces.append(tr)
+    st.set_batch_cluster(2)
+    st.init()
+    st.run(G, q.RUN_BATCHED)
+    for k, (N, k1, k2, NP, comp, comb) in enumerate(INSTANCES):
+        X, f, D = st.population(k)
+        Fg = q.qpm_get_F(st.h, k).cpu().numpy()
+        torch.cuda.synchronize()
+        cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 3, k, comb, 2 if k % 2 == 0 else 0)
+        Xo, fo, tro, Fo = orc.hwsda_run(cfg, k1, k2, lockstep=traces[k].cpu().numpy(),
+                                        want_trace=True, want_F=True)
+        assert np.array_equal(X.cpu().numpy(), Xo), k
+        if k % 2 == 0:
+            assert np.array_equal(Fg, Fo), k
+        else:
+            assert np.all(Fg == np.float32(0.5))
+    st.close()

@@ -361,3 +361,29 @@ def test_checkpoint_resume_is_bit_exact(q, mode):
     Xb, fb, Db = snapshot(st2)
     st2.close()
     assert np.array_equal(Xa, Xb) and np.array_equal(fa, fb)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_adaptive_F_lockstep(q, orc, mode):
+    """The adaptive F of Sec. 3.1.1 (f_schedule 2): the GPU decides the F of every
+    generation from its DE survivors' FP32 fitness and improvement flags; the oracle,
+    replaying in lockstep, decides from the same values by the same exact integer
+    statistics.  Population bit for bit, and the whole F history."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    for N, NP, G, k1, k2 in ((16, 32, 60, W.SMALL["kappa1"], W.SMALL["kappa2"]),
+                             (1000, 256, 12, 2 * math.pi / 6.9, 2 * math.pi / 1.55)):
+        st, tr = make(q, N, k1, k2, NP, G, seed=4, comp=1, f_schedule=2)
+        st.init()
+        st.run(G // 2, mode)
+        st.run(G - G // 2, mode)
+        X, f, D = snapshot(st)
+        Fg = q.qpm_get_F(st.h, 0).cpu().numpy()
+        trace = tr.cpu().numpy()
+        st.close()
+        cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 4, f_schedule=2)
+        Xo, fo, tro, Fo = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True, want_F=True)
+        assert np.array_equal(Fg, Fo), (N, np.nonzero(Fg != Fo))
+        assert np.array_equal(X, Xo)
+        assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
+        assert Fg[0] == np.float32(0.1) and np.all((Fg >= 0.01) & (Fg <= 0.1))

@@ -19,6 +19,7 @@ and relaxed gradient -- CPU only.
 import ctypes
 import ctypes.util
 import json
+import math
 import os
 
 import numpy as np
@@ -319,3 +320,97 @@ def test_philox_known_answers_of_the_random123_distribution(orc):
         v = [int(x, 16) for x in r]
         ctr, key, want = v[0:4], v[4:6], v[6:10]
         assert list(orc.philox(ctr, key)) == want, r
+
+
+# ------------------------------------------------------------ adaptive F (Sec. 3.1.1)
+def _acfg(orc, NP=64, G=100):
+    return orc.make_cfg(NP, 16, G, 0.5, 0.9, 1, f_schedule=2)
+
+
+def test_adaptive_F_spread_is_exact_and_matches_the_textbook_variance(orc):
+    """The spread statistic is computed from fitness values quantised against the
+    population maximum with integer operations only.  f = (1, 2, 3, 4) quantises to
+    2^17 (1, 2, 3, 4) exactly, so cv^2 = (4 * 30 - 100) / 100 = 0.2 exactly; on random
+    populations of every scale it agrees with numpy's variance / mean^2 to the
+    quantisation's 2^-20 of the maximum."""
+    import numpy as np
+    cfg = orc.make_cfg(4, 16, 10, 0.5, 0.9, 1, f_schedule=2)
+    _, _, st = orc.adaptive_F(cfg, 0, np.array([1, 2, 3, 4], np.float32), np.ones(4), 0.05)
+    assert st[0] == 0.2 and st[1] == 1.0 and st[2] == 3.0
+    rng = np.random.default_rng(3)
+    for scale in (1e-30, 1e-3, 1.0, 7e5, 3e11, 1e30):
+        for NP in (5, 64, 1000):
+            f = (rng.random(NP) ** 3 * scale).astype(np.float32)
+            cfg = orc.make_cfg(NP, 16, 10, 0.5, 0.9, 1, f_schedule=2)
+            _, _, st = orc.adaptive_F(cfg, 3, f, np.ones(NP), 0.05)
+            f64 = f.astype(np.float64)
+            ref = f64.var() / f64.mean() ** 2
+            assert abs(st[0] - ref) <= 1e-5 * max(ref, 1.0), (scale, NP)
+
+
+def test_adaptive_F_takes_every_branch(orc):
+    """Sec. 3.1.1: low diversity (cv < 0.05, or under 10 % of the trials improved)
+    raises F by 1.25 up to 0.1; high diversity (cv > 0.5) or a fitness range under
+    10^3 lowers it by 0.8 down to 0.01; otherwise F follows the schedule
+    0.1 (cos(pi g / 2G) + 1) / 2 (1 - 0.2 (g / G)^2) of the next generation."""
+    import numpy as np
+    rng = np.random.default_rng(11)
+    NP, G = 64, 100
+    cfg = _acfg(orc, NP, G)
+    imp = np.zeros(NP, np.uint8)
+    imp[:10] = 1  # 10 of 64 improved: a convergence rate above 0.1
+    moderate = (1e6 * (1.0 + rng.random(NP))).astype(np.float32)  # cv ~ 0.19, range ~ 1e6
+    narrow = (1e6 * (1.0 + 0.01 * rng.random(NP))).astype(np.float32)  # cv ~ 0.002
+    wide = (1e6 * rng.random(NP) ** 6).astype(np.float32)  # cv > 1
+    flat = (1000.0 + 400.0 * rng.random(NP)).astype(np.float32)  # cv ~ 0.1, range < 1e3
+    g, Fg = 40, np.float32(0.05)
+    br, Fn, st = orc.adaptive_F(cfg, g, moderate, imp, Fg)
+    assert br == 0 and 0.0025 < st[0] < 0.25 and Fn == orc.F_of(cfg, g + 1)
+    x = (g + 1) / G
+    sched = 0.1 * (math.cos(math.pi * (g + 1) / (2 * G)) + 1) / 2 * (1 - 0.2 * x * x)
+    assert Fn == np.float32(sched)
+    br, Fn, _ = orc.adaptive_F(cfg, g, narrow, imp, Fg)
+    assert br == 1 and Fn == np.float32(Fg * np.float32(1.25))
+    br, Fn, _ = orc.adaptive_F(cfg, g, moderate, np.zeros(NP, np.uint8), Fg)  # stagnating
+    assert br == 1 and Fn == np.float32(Fg * np.float32(1.25))
+    br, Fn, st = orc.adaptive_F(cfg, g, wide, imp, Fg)
+    assert br == 2 and st[0] > 0.25 and Fn == np.float32(Fg * np.float32(0.8))
+    br, Fn, st = orc.adaptive_F(cfg, g, flat, imp, Fg)
+    assert br == 2 and st[2] < 1000.0 and st[0] > 0.0025 and Fn == np.float32(Fg * np.float32(0.8))
+    # the bounds of [0.01, 0.1]
+    assert orc.adaptive_F(cfg, g, narrow, imp, np.float32(0.09))[1] == np.float32(0.1)
+    assert orc.adaptive_F(cfg, g, wide, imp, np.float32(0.011))[1] == np.float32(0.01)
+    # a population of zero fitness has no spread: low
+    assert orc.adaptive_F(cfg, g, np.zeros(NP, np.float32), imp, Fg)[0] == 1
+
+
+def test_adaptive_F_schedule_end_points(orc):
+    cfg = _acfg(orc, 8, 200)
+    assert orc.F_of(cfg, 0) == np.float32(0.1)
+    assert abs(orc.F_of(cfg, 200) - 0.1 * 0.5 * 0.8) < 1e-8
+
+
+def test_adaptive_F_run_equals_its_generations(orc):
+    """hwsda_run with the adaptive F equals the same loop taken generation by
+    generation (population bit for bit, and the F history); every F stays in
+    [0.01, 0.1] and the first is the schedule's 0.1."""
+    import numpy as np
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.SMALL
+    G = 25
+    cfg = orc.make_cfg(c["NP"], c["N"], G, c["F"], c["CR"], c["seed"], f_schedule=2)
+    X, f, Fh = orc.hwsda_run(cfg, c["kappa1"], c["kappa2"], want_F=True)
+    assert Fh[0] == np.float32(0.1) and np.all((Fh >= 0.01) & (Fh <= 0.1))
+    Xg = orc.init_population(cfg)
+    f64 = np.abs(orc.deff_genes(Xg, c["kappa1"], c["kappa2"])) ** 2
+    fdec = f64.astype(np.float32)
+    F = np.float32(orc.F_of(cfg, 0))
+    branches = set()
+    for g in range(G):
+        assert F == Fh[g]
+        Xg, fdec, f64, _, _, _, F, br = orc.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g, Xg,
+                                                             fdec, f64, F=F)
+        branches.add(br)
+    assert F == Fh[G]
+    assert np.array_equal(X, Xg)
+    assert 1 in branches  # the rule does fire on this problem
