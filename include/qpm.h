@@ -89,6 +89,31 @@ typedef struct {
                           holds (qpm_get_F) */
 } qpm_params;
 
+/* The fitness an optimiser state works on (qpm_set_objective; no call: QPM_OBJ_THG).
+ *   QPM_OBJ_THG        |d_eff|^2 of the cascaded integral of Sec. 2.1 at the problem's
+ *                      (kappa1, kappa2), maximised
+ *   QPM_OBJ_SHG        |E|^2 of the SHG field integral of Sec. 2.1's first step,
+ *                      E = int_0^L d(z) e^{-i dk z} dz with dk w = the problem's kappa1,
+ *                      maximised
+ *   QPM_OBJ_MULTI_THG  the multi-wavelength objective of Sec. 5,
+ *                      f = sum_k |G0 - G_k| + beta (G_max - G_min), G_k = |d_eff| of the
+ *                      cascaded integral at (kappa1[k], kappa2[k]), k < K <= 4, minimised
+ *   QPM_OBJ_MULTI_SHG  the same with G_k = |E| of the SHG integral at kappa1[k],
+ *                      k < K <= 8, minimised
+ * The optimiser's d_eff outputs (qpm_get_population, qpm_get_best) hold the field of the
+ * objective (for the multi-wavelength kinds: of the first problem), its fitness
+ * outputs the objective.  The multi-wavelength kinds run in the launches and graph
+ * forms of qpm_run, with plain FP32 scans; their states take (kappa1[0], kappa2[0]) as
+ * the instance's problem. */
+enum { QPM_OBJ_THG = 0, QPM_OBJ_SHG = 1, QPM_OBJ_MULTI_THG = 2, QPM_OBJ_MULTI_SHG = 3 };
+typedef struct {
+  int32_t kind;       /* QPM_OBJ_* */
+  int32_t K;          /* multi-wavelength kinds: the number of problems */
+  double kappa1[8];   /* multi-wavelength kinds: dk1 w (THG) or dk w (SHG) of problem k */
+  double kappa2[8];   /* QPM_OBJ_MULTI_THG: dk2 w of problem k */
+  float G0, beta;     /* multi-wavelength kinds: the reference value and the spread weight */
+} qpm_objective;
+
 /* Execution modes of qpm_run. */
 enum {
   QPM_RUN_LAUNCHES = 0,   /* two kernels per generation, launched one by one */
@@ -322,6 +347,15 @@ qpm_status qpm_get_best(qpm_state *st, int32_t inst, float *genes_out, double *d
  * lr < 0 or tau <= 0 -> QPM_ERR_ARG. */
 qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t steps, float lr, float tau,
                               int32_t *accepted_out, qpm_stream_t stream);
+
+/* The objective of instance `inst` (Sec. 2.1, Sec. 5; see qpm_objective): host call,
+ * before qpm_init; allocates the other problems' phasor tables of a multi-wavelength
+ * kind (state-owned).  Errors: an unknown kind, K outside its range, non-finite
+ * kappa or G0, beta < 0 -> QPM_ERR_ARG; after qpm_init or on another device ->
+ * QPM_ERR_STATE.  qpm_run then returns QPM_ERR_UNSUPPORTED for the multi-wavelength
+ * kinds in the persistent and batched forms, and qpm_polish_leaders for every kind
+ * but QPM_OBJ_THG. */
+qpm_status qpm_set_objective(qpm_state *st, int32_t inst, const qpm_objective *obj);
 
 /* Threads per individual the state uses for instance `inst` (host int32 out). */
 qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out);

@@ -25,7 +25,10 @@ class OrcCfg(ctypes.Structure):
     _fields_ = [("NP", ctypes.c_int32), ("N", ctypes.c_int32), ("ld", ctypes.c_int64),
                 ("G", ctypes.c_int32), ("F", ctypes.c_float), ("CR", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("inst", ctypes.c_uint32),
-                ("combine", ctypes.c_int32), ("f_schedule", ctypes.c_int32)]
+                ("combine", ctypes.c_int32), ("f_schedule", ctypes.c_int32),
+                ("obj", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("kap1", ctypes.c_double * 8), ("kap2", ctypes.c_double * 8),
+                ("G0", ctypes.c_float), ("beta", ctypes.c_float)]
 
 
 def lib():
@@ -65,6 +68,7 @@ def lib():
                                            P, P]
         L.orc_hwsda_generation.restype = ctypes.c_int
         L.orc_adaptive_F.argtypes = [P, i32, P, P, ctypes.c_float, P, P]
+        L.orc_objective_rows.argtypes = [P, dbl, dbl, ctypes.c_int, P, P]
         L.orc_adaptive_F.restype = ctypes.c_int
         L.orc_hwsda_run.argtypes = [P, dbl, dbl, ctypes.c_int, P, P, P, P, P]
         L.orc_hwsda_run.restype = ctypes.c_int
@@ -204,8 +208,23 @@ def a_of(g, G):
     return lib().orc_a_of(g, G)
 
 
-def make_cfg(NP, N, G, F, CR, seed, inst=0, combine=0, f_schedule=0):
-    return OrcCfg(NP, N, N, G, F, CR, seed, inst, combine, f_schedule)
+def make_cfg(NP, N, G, F, CR, seed, inst=0, combine=0, f_schedule=0, obj=0, kappas=(),
+             G0=0.0, beta=0.0):
+    """Loop configuration.  obj: 0 cascaded |d_eff|^2 (maximised), 1 SHG |E|^2 of
+    kappa1 (maximised), 2 / 3 the multi-wavelength objective over the (kappa1, kappa2)
+    pairs in `kappas` with the cascaded / SHG field (minimised)."""
+    k1 = (ctypes.c_double * 8)(*[k[0] for k in kappas])
+    k2 = (ctypes.c_double * 8)(*[k[1] for k in kappas])
+    return OrcCfg(NP, N, N, G, F, CR, seed, inst, combine, f_schedule, obj, len(kappas), k1, k2,
+                  G0, beta)
+
+
+def objective_rows(cfg, X, kappa1=0.0, kappa2=0.0, Q=Q_DEFAULT):
+    """The loop's objective (cfg.obj) of each gene row of X, in FP64."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    out = np.zeros(X.shape[0])
+    lib().orc_objective_rows(ctypes.byref(cfg), kappa1, kappa2, Q, _p(X), _p(out))
+    return out
 
 
 def F_of(cfg, g):

@@ -25,7 +25,11 @@
  *     SC'11), written here from that published definition.
  *
  * Readings of the paper taken here (garbled or silent passages):
- *   - objective: maximise |d_eff|^2 (Sec. 2.1 asks for the largest d_eff);
+ *   - objective: maximise |d_eff|^2 (Sec. 2.1 asks for the largest d_eff); the loop can
+ *     also maximise the SHG field |E|^2 or minimise the multi-wavelength objective of
+ *     Sec. 5, sum_k |G0 - G_k| + beta (G_max - G_min), with G_k the cascaded or SHG
+ *     field magnitude of each (kappa1, kappa2) pair (orc_cfg.obj); selection keeps the
+ *     trial when it is at least as good in the objective's direction;
  *   - greedy selection keeps the trial when f(trial) >= f(target) (Sec. 2.2.1
  *     step 4 is printed garbled and for minimisation; mirrored for maximisation);
  *   - binomial crossover takes the mutant gene when U <= CR or j == jrand;
@@ -567,7 +571,26 @@ typedef struct {
   int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension */
   int32_t f_schedule; /* 0 = constant F; 1 = decaying F of Sec. 3.1.1;
                          2 = the adaptive F of Sec. 3.1.1 (orc_adaptive_F) */
+  /* the fitness the loop optimises (Sec. 2.1 and Sec. 5):
+   *   0: |d_eff(kappa1, kappa2)|^2 of the cascaded integral, maximised (Sec. 2.1);
+   *   1: |E_SHG(kappa1)|^2 of the single SHG integral, maximised;
+   *   2: the multi-wavelength objective sum_k |G0 - G_k| + beta (G_max - G_min) with
+   *      G_k = |d_eff(kap1[k], kap2[k])|, minimised (Sec. 5, cascaded THG designs);
+   *   3: the same with G_k = |E_SHG(kap1[k])|, minimised (Sec. 5, SHG designs) */
+  int32_t obj, K;
+  double kap1[8], kap2[8];
+  float G0, beta;
 } orc_cfg;
+
+/* the objective direction: the multi-wavelength objectives are minimised */
+static inline int minimising(const orc_cfg *c) { return c->obj >= 2; }
+/* a at least as good as b / strictly better, in the objective's direction */
+static inline int better_eq(const orc_cfg *c, double a, double b) {
+  return minimising(c) ? (a <= b) : (a >= b);
+}
+static inline int better(const orc_cfg *c, double a, double b) {
+  return minimising(c) ? (a < b) : (a > b);
+}
 
 /* F of generation g.  Sec. 3.1.1 lets F follow (cos(pi g / 2G) + 1) / 2 times a
  * quadratic factor that falls from 1.0 to 0.8 over the run; the reading taken
@@ -777,6 +800,27 @@ ORC_API void orc_gwo_candidates(const orc_cfg *c, uint32_t g, const float *X,
   }
 }
 
+/* the objective of one +-1 row d (cfg->obj), by the quadratures of Sec. 2.1 */
+static double row_objective(const orc_cfg *c, double kappa1, double kappa2, int Q,
+                            const double *d) {
+  double re, im;
+  if (c->obj == 0 || c->obj == 1) {
+    if (c->obj == 0) deff_quad_one(c->N, kappa1, kappa2, d, Q, &re, &im);
+    else shg_quad_one(c->N, kappa1, d, Q, &re, &im);
+    return re * re + im * im;
+  }
+  double f = 0.0, gmax = -1.0, gmin = 1e300;
+  for (int k = 0; k < c->K; ++k) {
+    if (c->obj == 2) deff_quad_one(c->N, c->kap1[k], c->kap2[k], d, Q, &re, &im);
+    else shg_quad_one(c->N, c->kap1[k], d, Q, &re, &im);
+    const double G = sqrt(re * re + im * im);
+    f += fabs((double)c->G0 - G);
+    if (G > gmax) gmax = G;
+    if (G < gmin) gmin = G;
+  }
+  return f + (double)c->beta * (gmax - gmin);
+}
+
 static void eval_rows(const orc_cfg *c, double kappa1, double kappa2, int Q, const float *X,
                       const uint8_t *mask, double *f64) {
 #pragma omp parallel
@@ -786,12 +830,29 @@ static void eval_rows(const orc_cfg *c, double kappa1, double kappa2, int Q, con
     for (int32_t i = 0; i < c->NP; ++i) {
       if (mask && !mask[i]) { f64[i] = NAN; continue; }
       for (int32_t j = 0; j < c->N; ++j) d[j] = (X[(int64_t)i * c->ld + j] < 0.0f) ? -1.0 : 1.0;
-      double re, im;
-      deff_quad_one(c->N, kappa1, kappa2, d, Q, &re, &im);
-      f64[i] = re * re + im * im;
+      f64[i] = row_objective(c, kappa1, kappa2, Q, d);
     }
     free(d);
   }
+}
+
+/* the objective of every row of X (the loop's fitness, in FP64) */
+ORC_API void orc_objective_rows(const orc_cfg *c, double kappa1, double kappa2, int Q,
+                                const float *X, double *f64) {
+  ensure_rule(Q);
+  eval_rows(c, kappa1, kappa2, Q, X, NULL, f64);
+}
+
+/* the three best of f in the objective's direction, ties to the lower index */
+static void top3_dir(const orc_cfg *c, const float *f, int32_t lead[3]) {
+  for (int k = 0; k < 3; ++k) lead[k] = -1;
+  for (int32_t i = 0; i < c->NP; ++i)
+    for (int k = 0; k < 3; ++k)
+      if (lead[k] < 0 || better(c, f[i], f[lead[k]])) {
+        for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+        lead[k] = i;
+        break;
+      }
 }
 
 /* One generation of the HWSDA loop (Sec. 3.2 Steps 2-6) from population X.
@@ -831,8 +892,8 @@ ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2,
   if (tr_trial) memcpy(tr_trial, ft, sizeof(double) * NP);
   for (int32_t i = 0; i < NP; ++i) {
     /* strict improvement of the trial over its target, in the decision precision */
-    mask[i] = lock ? (lock_trial[i] > fdec[i]) : ((float)ft[i] > fdec[i]);
-    int accept = lock ? (lock_trial[i] >= fdec[i]) : (ft[i] >= f64[i]);
+    mask[i] = lock ? better(c, lock_trial[i], fdec[i]) : better(c, (float)ft[i], fdec[i]);
+    int accept = lock ? better_eq(c, lock_trial[i], fdec[i]) : better_eq(c, ft[i], f64[i]);
     if (accept) {
       memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
       f64[i] = ft[i];
@@ -849,12 +910,12 @@ ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2,
   /* Step 3: the three leaders */
   int32_t lead[3];
   if (lock) {
-    orc_top3(NP, fdec, lead);
+    top3_dir(c, fdec, lead);
   } else {
     for (int k = 0; k < 3; ++k) lead[k] = -1;
     for (int32_t i = 0; i < NP; ++i)
       for (int k = 0; k < 3; ++k)
-        if (lead[k] < 0 || f64[i] > f64[lead[k]]) {
+        if (lead[k] < 0 || better(c, f64[i], f64[lead[k]])) {
           for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
           lead[k] = i;
           break;
@@ -869,7 +930,7 @@ ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2,
   if (tr_cand) memcpy(tr_cand, ft, sizeof(double) * NP);
   for (int32_t i = 0; i < NP; ++i) {
     if (i == lead[0] || i == lead[1] || i == lead[2]) continue;
-    int accept = lock ? (lock_cand[i] >= fdec[i]) : (ft[i] >= f64[i]);
+    int accept = lock ? better_eq(c, lock_cand[i], fdec[i]) : better_eq(c, ft[i], f64[i]);
     if (accept) {
       memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);
       f64[i] = ft[i];

@@ -22,9 +22,11 @@ __all__ = [
     "qpm_set_batch_cluster",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
+    "Objective", "qpm_set_objective", "OBJ_THG", "OBJ_SHG", "OBJ_MULTI_THG", "OBJ_MULTI_SHG",
 ]
 
 RUN_LAUNCHES, RUN_GRAPH, RUN_PERSISTENT, RUN_BATCHED = 0, 1, 2, 3
+OBJ_THG, OBJ_SHG, OBJ_MULTI_THG, OBJ_MULTI_SHG = 0, 1, 2, 3
 STATUS = {0: "QPM_OK", 1: "QPM_ERR_ARG", 2: "QPM_ERR_CUDA", 3: "QPM_ERR_TIMEOUT",
           4: "QPM_ERR_UNSUPPORTED", 5: "QPM_ERR_STATE"}
 
@@ -44,6 +46,12 @@ class Params(ctypes.Structure):
                 ("CR", ctypes.c_float), ("seed", ctypes.c_uint64),
                 ("gwo_combine", ctypes.c_int32), ("compensated", ctypes.c_int32),
                 ("team", ctypes.c_int32), ("f_schedule", ctypes.c_int32)]
+
+
+class Objective(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("kappa1", ctypes.c_double * 8), ("kappa2", ctypes.c_double * 8),
+                ("G0", ctypes.c_float), ("beta", ctypes.c_float)]
 
 
 _lib = None
@@ -86,6 +94,7 @@ def lib(build=True):
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
             "qpm_instance_shape": ([_P, i32, _P, _P, _P], ctypes.c_int),
             "qpm_get_F": ([_P, i32, _P, _P], ctypes.c_int),
+            "qpm_set_objective": ([_P, i32, _P], ctypes.c_int),
             "qpm_set_batch_cluster": ([_P, i32], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
             "qpm_set_population": ([_P, i32, _P, i64, i32, _P], ctypes.c_int),
@@ -411,6 +420,16 @@ def qpm_instance_shape(st, inst=0):
     return n.value, p.value, g.value
 
 
+def qpm_set_objective(st, inst, kind, kappas=(), G0=0.0, beta=0.0):
+    """The fitness instance `inst` optimises (before qpm_init): OBJ_THG, OBJ_SHG, or a
+    multi-wavelength kind over the (kappa1, kappa2) pairs in `kappas` (Sec. 5)."""
+    if len(kappas) > 8:
+        raise ValueError("kappas: at most 8 pairs")
+    o = Objective(int(kind), len(kappas), (ctypes.c_double * 8)(*[float(k[0]) for k in kappas]),
+                  (ctypes.c_double * 8)(*[float(k[1]) for k in kappas]), float(G0), float(beta))
+    _check(lib().qpm_set_objective(st, int(inst), ctypes.byref(o)))
+
+
 def qpm_get_F(st, inst=0, F_out=None, stream=None):
     """F of every generation of instance `inst` (float32 CUDA [G + 1]; allocated when
     F_out is None)."""
@@ -523,6 +542,12 @@ class State:
 
     def set_batch_cluster(self, ctas):
         qpm_set_batch_cluster(self.h, ctas)
+
+    def set_objective(self, kind, kappas=(), G0=0.0, beta=0.0, inst=0):
+        qpm_set_objective(self.h, inst, kind, kappas, G0, beta)
+        if kind >= OBJ_MULTI_THG:  # the first pair becomes the instance's problem
+            N = self.problems[inst][0]
+            self.problems[inst] = (N, float(kappas[0][0]), float(kappas[0][1]))
 
     @property
     def generation(self):

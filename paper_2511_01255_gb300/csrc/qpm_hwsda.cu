@@ -52,7 +52,7 @@ struct InstDev {
   float4 *table;         // [Npad], permuted
   double2 *tpart;        // table reduction scratch
   float2 *konst;         // phi1 phi2, cdiag
-  double2 *konst64;      // phi1 phi2, cdiag, psi (FP64)
+  double2 *konst64;      // phi1 phi2, cdiag, psi, phi1 (FP64)
   int32_t *lead;         // [3]
   unsigned long long *topk;  // [2][NP * 3] partial leader keys (by generation parity)
   unsigned *ctr;         // [4] CTA-completion counters
@@ -63,6 +63,13 @@ struct InstDev {
                          // adaptive F (f_schedule 2) writes entry g + 1 during generation g
   const float *Fbase;    // [G + 1] adaptive F only: the schedule of its intermediate state
   int32_t adaptive;      // f_schedule == 2
+  // the objective (qpm_objective): kind, problems of the multi-wavelength kinds (the
+  // first one's table and constants are table / konst), G0, beta; minimised for the
+  // multi-wavelength kinds
+  int32_t obj, K, minimize;
+  float G0, beta;
+  const float4 *mtab[8];   // [Npad] permuted phasor tables of the K problems
+  const float2 *mkonst[8];  // their FP32 constants
   unsigned long long *dekey;  // [NP] persistent form: DE survivor keys (lead_key) for Step 3
 };
 
@@ -108,6 +115,94 @@ struct Acc {
 
 __device__ __forceinline__ float sgn(float x) { return x < 0.f ? -1.f : 1.f; }
 
+// ----------------------------------------------------------------- objectives
+// The fitness the optimiser works on (qpm_objective.kind): the cascaded d_eff of Sec. 2.1
+// (|d_eff|^2, maximised; the default), the SHG field of Sec. 2.1's first step (|E|^2,
+// maximised), or the multi-wavelength objective of Sec. 5, sum_k |G0 - G_k| + beta
+// (G_max - G_min) over K problems, G_k the cascaded or the SHG field magnitude
+// (minimised).  The two single kinds share the one scan (the SHG field is
+// phi(kappa1) sum_j d_j e^{-i kappa1 j}, the scan's B); the multi-wavelength kinds run K
+// scans of the same vector in their own kernel variants (MK).
+constexpr int OBJ_THG = 0, OBJ_SHG = 1, OBJ_MULTI_THG = 2, OBJ_MULTI_SHG = 3;
+
+// the field of a single kind from its reduced scan
+__device__ __forceinline__ float2 field_of(const InstDev &I, const Mono &m) {
+  if (I.obj == OBJ_SHG) {
+    const float2 ph = I.konst[3];  // phi(kappa1)
+    return make_float2(ph.x * m.B.x - ph.y * m.B.y, ph.x * m.B.y + ph.y * m.B.x);
+  }
+  return deff_from(m, I.konst[0], I.konst[1]);
+}
+
+// selection key of fitness f of individual i: a larger key is a better individual,
+// ties to the lower index (an objective to minimise is >= 0, so ~bits orders it)
+__device__ __forceinline__ unsigned long long sel_key(bool minimize, float f, int i) {
+  const uint32_t b = __float_as_uint(f);
+  return ((unsigned long long)(minimize ? ~b : b) << 32) | (0xFFFFFFFFu - (uint32_t)i);
+}
+
+// MK != 0: the K scans of a multi-wavelength kind, plain FP32 sums, phasors from the
+// problems' tables in global memory (cached by L2)
+template <int MK>
+struct MultiAcc {
+  static constexpr int KMAX = MK == OBJ_MULTI_THG ? 4 : (MK == OBJ_MULTI_SHG ? 8 : 1);
+  Mono m[KMAX];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) m[k] = mono_zero();
+  }
+  // group k4 of this thread's chunk (4 domains of signs u)
+  __device__ __forceinline__ void push4(const InstDev &I, int k4, int t, float4 u) {
+    const float d[4] = {sgn(u.x), sgn(u.y), sgn(u.z), sgn(u.w)};
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < I.K) {
+        const float4 *tb = I.mtab[k] + (size_t)k4 * 4 * I.T + t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 p = __ldg(tb + (size_t)q * I.T);
+          if (MK == OBJ_MULTI_THG) {
+            mono_push(m[k], d[q], p);
+          } else {  // the SHG field needs the running sum of d p1 only
+            m[k].B.x = fmaf(d[q], p.x, m[k].B.x);
+            m[k].B.y = fmaf(d[q], p.y, m[k].B.y);
+          }
+        }
+      }
+    }
+  }
+};
+
+// reduce the K scans (WT: a warp team) and form the objective: f and the first
+// problem's field D0 are valid in the team's first thread; every thread returns
+template <int MK, bool WT>
+__device__ void multi_finish(const InstDev &I, MultiAcc<MK> &acc, Mono *sh, float &f, float2 &D0) {
+  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  float obj = 0.f, gmax = -1.f, gmin = 3.0e38f;
+#pragma unroll
+  for (int k = 0; k < MultiAcc<MK>::KMAX; ++k) {
+    if (k < I.K) {
+      if (!WT && k > 0) __syncthreads();  // the reduction scratch is reused
+      const Mono mk = WT ? warp_reduce(acc.m[k]) : block_reduce(acc.m[k], sh);
+      if (t == 0) {
+        float2 Dk;
+        if (MK == OBJ_MULTI_THG) {
+          Dk = deff_from(mk, I.mkonst[k][0], I.mkonst[k][1]);
+        } else {
+          const float2 ph = I.mkonst[k][3];
+          Dk = make_float2(ph.x * mk.B.x - ph.y * mk.B.y, ph.x * mk.B.y + ph.y * mk.B.x);
+        }
+        const float G = sqrtf(fit_of(Dk));
+        obj += fabsf(I.G0 - G);
+        gmax = fmaxf(gmax, G);
+        gmin = fminf(gmin, G);
+        if (k == 0) D0 = Dk;
+      }
+    }
+  }
+  f = obj + I.beta * (gmax - gmin);
+}
+
 // push the 4 domains of group k4 of this thread's chunk
 template <bool COMP, bool TS>
 __device__ __forceinline__ void push4(Acc<COMP> &acc, const float4 *tbl, int T, int k4, int t,
@@ -136,13 +231,15 @@ __device__ __forceinline__ float4 ld_cur(const InstDev &I, int i, int slot, size
 }
 
 // ---------------------------------------------------- Step 1: initialisation
-template <bool COMP>
+template <bool COMP, int MK = 0>
 __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
   const int t = threadIdx.x;
   const PhiloxKey K = philox_schedule(I.key);
   float *row = row_ptr(I, i, 0);
   Acc<COMP> acc;
   acc.zero();
+  MultiAcc<MK> macc;
+  if (MK) macc.zero();
   for (int k4 = 0; k4 < I.c / 4; ++k4) {
     const int j0 = t * I.c + 4 * k4;
     const uint4 w = rng4(K, I.inst, TAG_INIT, GEN_INIT, (uint32_t)i, (uint32_t)(j0 >> 2));
@@ -152,13 +249,25 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
     x.z = __fsub_rn(__fmul_rn(2.0f, u24(w.z)), 1.0f);
     x.w = __fsub_rn(__fmul_rn(2.0f, u24(w.w)), 1.0f);
     *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
-    push4<COMP, false>(acc, I.table, I.T, k4, t, x);
-    if (k4 & 1) acc.fold();
+    if (MK) {
+      macc.push4(I, k4, t, x);
+    } else {
+      push4<COMP, false>(acc, I.table, I.T, k4, t, x);
+      if (k4 & 1) acc.fold();
+    }
   }
-  const Mono m = block_reduce(acc.get(), sh);
+  float2 D = make_float2(0.f, 0.f);
+  float f = 0.f;
+  if constexpr (MK != 0) {
+    multi_finish<MK, false>(I, macc, sh, f, D);
+  } else {
+    const Mono m = block_reduce(acc.get(), sh);
+    if (t == 0) {
+      D = field_of(I, m);
+      f = fit_of(D);
+    }
+  }
   if (t == 0) {
-    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
-    const float f = fit_of(D);
     I.fit[i] = f;
     I.dval[i] = D;
     I.sel0[i] = 0;
@@ -167,12 +276,12 @@ __device__ void init_individual(const InstDev &I, int i, Mono *sh) {
   }
 }
 
-template <bool COMP>
+template <bool COMP, int MK = 0>
 static __global__ void k_init(InstDev I) {
   extern __shared__ Mono sh[];
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
-    init_individual<COMP>(I, i, sh);
+    init_individual<COMP, MK>(I, i, sh);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *I.gen = 0;
@@ -258,7 +367,7 @@ __device__ __forceinline__ void push4_staged(Acc<COMP> &acc, const float4 *tbl, 
 // STG: rows staged through stg (known slots only, so not with DUAL)
 // has_wcr: wcr is the crossover word of the thread's first group of 4 domains, drawn
 // earlier (while waiting at the grid barrier)
-template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool STG = false>
+template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool STG = false, int MK = 0>
 __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K,
                                             const float4 *tbl, int g, int i, const int4 r,
                                             const int32_t *sel_in, int32_t *sel_out, Mono *sh,
@@ -281,6 +390,8 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
   if (STG) stage_prologue<TS>(stg, n4, I.T, t, ra, rb, rp, rq, tbl);
   Acc<COMP> acc;
   acc.zero();
+  MultiAcc<MK> macc;
+  if (MK) macc.zero();
   for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
     float4 a, b, p, q;
@@ -316,29 +427,42 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
     QPM_DE1(w, w, j0 + 3)
 #undef QPM_DE1
     *(float4 *)(out + off) = u;
-    if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, u);
-    else push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
-    if (k4 & 1) acc.fold();
+    if (MK) {
+      macc.push4(I, k4, t, u);
+    } else {
+      if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, u);
+      else push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
+      if (k4 & 1) acc.fold();
+    }
   }
-  // a single group of 4 domains per thread needs no compensation (its plain sums are
-  // what the fold would return, up to the sign of a zero), and skipping the fold
-  // takes a dependent chain off the phase's critical path
-  const Mono mine = (COMP && !WT && n4 == 1) ? acc.m : acc.get();
-  const Mono m = WT ? warp_reduce(mine) : block_reduce(mine, sh);
+  float2 D = make_float2(0.f, 0.f);
+  float f = 0.f;
+  if constexpr (MK != 0) {
+    multi_finish<MK, WT>(I, macc, sh, f, D);
+  } else {
+    // a single group of 4 domains per thread needs no compensation (its plain sums are
+    // what the fold would return, up to the sign of a zero), and skipping the fold
+    // takes a dependent chain off the phase's critical path
+    const Mono mine = (COMP && !WT && n4 == 1) ? acc.m : acc.get();
+    const Mono m = WT ? warp_reduce(mine) : block_reduce(mine, sh);
+    if (t == 0) {
+      D = field_of(I, m);
+      f = fit_of(D);
+    }
+  }
   unsigned long long key = 0ull;
   if (t == 0) {
-    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
-    const float f = fit_of(D);
-    const bool accept = f >= fx;  // greedy one-to-one selection, maximising
+    // greedy one-to-one selection: maximising, or minimising the multi-wavelength kinds
+    const bool accept = MK ? (f <= fx) : (f >= fx);
     sel_out[i] = accept ? (si ^ 1) : si;
     if (accept) {
       I.fit[i] = f;
       I.dval[i] = D;
     }
     if (I.trace) I.trace[(size_t)I.NP * (1 + 2 * (size_t)g) + i] = f;
-    key = lead_key(accept ? f : fx, i);
+    key = sel_key(MK != 0, accept ? f : fx, i);
     if (slot_out) *slot_out = accept ? (si ^ 1) : si;  // the survivor's slot
-    if (impr_out) *impr_out = f > fx;                   // a strict improvement (adaptive F)
+    if (impr_out) *impr_out = MK ? (f < fx) : (f > fx);  // a strict improvement (adaptive F)
   }
   return key;
 }
@@ -348,7 +472,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 // drawn earlier (while waiting at the grid barrier) and are passed in wpre.
 // One word per leader and gene gives that leader's (r1, r2) as its 16-bit halves.
 template <bool COMP, bool NC, bool TS, bool DUAL, bool WT = false, bool PRE = false,
-          bool STG = false>
+          bool STG = false, int MK = 0>
 __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float4 *tbl, int g,
                                int i, int32_t *sel, int la, int lb, int ld, Mono *sh,
                                const uint4 *wpre = nullptr,
@@ -373,6 +497,8 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   if (STG) stage_prologue<TS>(stg, n4, I.T, t, rx, r0, r1, r2, tbl);
   Acc<COMP> acc;
   acc.zero();
+  MultiAcc<MK> macc;
+  if (MK) macc.zero();
   for (int k4 = 0; k4 < n4; ++k4) {
     const size_t off = ((size_t)k4 * I.T + t) * 4;
     float4 x, L0, L1, L2;
@@ -435,19 +561,31 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
 #undef QPM_GWO1
 #undef QPM_PULL
     *(float4 *)(out + off) = y;
-    if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, y);
-    else push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
-    if (k4 & 1) acc.fold();
+    if (MK) {
+      macc.push4(I, k4, t, y);
+    } else {
+      if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, y);
+      else push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
+      if (k4 & 1) acc.fold();
+    }
   }
-  // a single group of 4 domains per thread needs no compensation (its plain sums are
-  // what the fold would return, up to the sign of a zero), and skipping the fold
-  // takes a dependent chain off the phase's critical path
-  const Mono mine = (COMP && !WT && n4 == 1) ? acc.m : acc.get();
-  const Mono m = WT ? warp_reduce(mine) : block_reduce(mine, sh);
+  float2 D = make_float2(0.f, 0.f);
+  float f = 0.f;
+  if constexpr (MK != 0) {
+    multi_finish<MK, WT>(I, macc, sh, f, D);
+  } else {
+    // a single group of 4 domains per thread needs no compensation (its plain sums are
+    // what the fold would return, up to the sign of a zero), and skipping the fold
+    // takes a dependent chain off the phase's critical path
+    const Mono mine = (COMP && !WT && n4 == 1) ? acc.m : acc.get();
+    const Mono m = WT ? warp_reduce(mine) : block_reduce(mine, sh);
+    if (t == 0) {
+      D = field_of(I, m);
+      f = fit_of(D);
+    }
+  }
   if (t == 0) {
-    const float2 D = deff_from(m, I.konst[0], I.konst[1]);
-    const float f = fit_of(D);
-    const bool accept = f >= fx;
+    const bool accept = MK ? (f <= fx) : (f >= fx);
     if (accept) {
       sel[i] = si ^ 1;
       I.fit[i] = f;
@@ -509,7 +647,7 @@ __device__ void adaptive_F_block(const InstDev &I, const unsigned long long *key
   uint32_t mx = 0u, mn = 0xFFFFFFFFu, cnt = 0u;
   for (int i = threadIdx.x; i < I.NP; i += blockDim.x) {
     const unsigned long long k = keys[i];
-    const uint32_t fb = (uint32_t)(k >> 32);
+    const uint32_t fb = I.minimize ? ~(uint32_t)(k >> 32) : (uint32_t)(k >> 32);  // f's bits
     mx = max(mx, fb);
     mn = min(mn, fb);
     cnt += ((uint32_t)k >> 1) & 1u;
@@ -535,7 +673,8 @@ __device__ void adaptive_F_block(const InstDev &I, const unsigned long long *key
   if (emax == 0) emax = 1;
   unsigned long long s1 = 0ull, s2 = 0ull;
   for (int i = threadIdx.x; i < I.NP; i += blockDim.x) {
-    const uint32_t n = af_quantise((uint32_t)(keys[i] >> 32), emax);
+    const uint32_t hi = (uint32_t)(keys[i] >> 32);
+    const uint32_t n = af_quantise(I.minimize ? ~hi : hi, emax);
     s1 += n;
     s2 += (unsigned long long)n * n;
   }
@@ -637,7 +776,7 @@ __device__ bool last_cta(unsigned *ctr) {
 }
 
 // dynamic shared memory of k_de and k_gwo: [row + table staging (long rows)][reduction]
-template <bool COMP, bool DUAL>
+template <bool COMP, bool DUAL, int MK = 0>
 static __global__ void k_de(InstDev I) {
   constexpr bool STG = !DUAL;
   extern __shared__ float4 dyn[];
@@ -652,7 +791,7 @@ static __global__ void k_de(InstDev I) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
     int slot = 0, impr = 0;
     const unsigned long long key =
-        de_individual<COMP, true, false, DUAL, false, STG>(
+        de_individual<COMP, true, false, DUAL, false, STG, MK>(
             I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh,
             &slot, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr);
     if (threadIdx.x == 0) {
@@ -672,7 +811,7 @@ static __global__ void k_de(InstDev I) {
   }
 }
 
-template <bool COMP, bool DUAL>
+template <bool COMP, bool DUAL, int MK = 0>
 static __global__ void k_gwo(InstDev I) {
   constexpr bool STG = !DUAL;
   extern __shared__ float4 dyn[];
@@ -685,7 +824,7 @@ static __global__ void k_gwo(InstDev I) {
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
     __syncthreads();  // the reduction scratch is reused
-    gwo_individual<COMP, true, false, DUAL, false, false, STG>(
+    gwo_individual<COMP, true, false, DUAL, false, false, STG, MK>(
         I, K, I.table, g, i, sel, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
         make_float4(0.f, 0.f, 0.f, 0.f), nullptr, stg);
   }
@@ -1040,7 +1179,8 @@ static __global__ void __launch_bounds__(BATCH_WARPS * 32, 1)
 static __global__ void k_best(InstDev I, int32_t *index_out) {
   __shared__ unsigned long long shk[3 * 32];
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
-  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) top3_insert(k0, k1, k2, lead_key(I.fit[i], i));
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x)
+    top3_insert(k0, k1, k2, sel_key(I.minimize != 0, I.fit[i], i));
   block_top3(k0, k1, k2, shk);
   if (threadIdx.x == 0) {
     *I.best = key_index(k0);
@@ -1109,9 +1249,16 @@ static __global__ void k_recheck64(InstDev I, double *d64_out, float *fit_out) {
   if (t == 0) {
     Mono64 acc = sh[0];
     for (int k = 1; k < nt; ++k) acc = m64_combine(acc, sh[k]);
-    const double2 p12 = I.konst64[0], cd = I.konst64[1];
-    const double re = p12.x * acc.C.x - p12.y * acc.C.y + cd.x;
-    const double im = p12.x * acc.C.y + p12.y * acc.C.x + cd.y;
+    double re, im;
+    if (I.obj == OBJ_SHG || I.obj == OBJ_MULTI_SHG) {  // SHG field: phi(kappa1) sum d p1
+      const double2 ph = I.konst64[3];
+      re = ph.x * acc.B.x - ph.y * acc.B.y;
+      im = ph.x * acc.B.y + ph.y * acc.B.x;
+    } else {  // cascaded d_eff
+      const double2 p12 = I.konst64[0], cd = I.konst64[1];
+      re = p12.x * acc.C.x - p12.y * acc.C.y + cd.x;
+      im = p12.x * acc.C.y + p12.y * acc.C.x + cd.y;
+    }
     if (d64_out) {
       d64_out[0] = re;
       d64_out[1] = im;
@@ -1129,7 +1276,8 @@ static __global__ void k_recheck64(InstDev I, double *d64_out, float *fit_out) {
 static __global__ void k_polish_pick(InstDev I, int32_t *lead_out) {
   __shared__ unsigned long long shk[3 * 32];
   unsigned long long k0 = 0, k1 = 0, k2 = 0;
-  for (int i = threadIdx.x; i < I.NP; i += blockDim.x) top3_insert(k0, k1, k2, lead_key(I.fit[i], i));
+  for (int i = threadIdx.x; i < I.NP; i += blockDim.x)
+    top3_insert(k0, k1, k2, sel_key(I.minimize != 0, I.fit[i], i));
   block_top3(k0, k1, k2, shk);
   if (threadIdx.x == 0) {
     lead_out[0] = key_index(k0);
@@ -1213,7 +1361,7 @@ static __global__ void k_polish_accept(InstDev I, const int32_t *lead, float tau
 // Natural-order genes [NP][ld] -> slot 0 of every row (permuted), both selectors
 // 0, fitness recomputed with the same scan as every other evaluation (so it is
 // bit-identical to the value the run had), generation counter set.
-template <bool COMP>
+template <bool COMP, int MK = 0>
 static __global__ void k_load_population(InstDev I, const float *__restrict__ genes, int64_t ld,
                                          int generation) {
   extern __shared__ Mono sh[];
@@ -1224,6 +1372,8 @@ static __global__ void k_load_population(InstDev I, const float *__restrict__ ge
     const float *src = genes + (int64_t)i * ld;
     Acc<COMP> acc;
     acc.zero();
+    MultiAcc<MK> macc;
+    if (MK) macc.zero();
     for (int k4 = 0; k4 < I.c / 4; ++k4) {
       const int j0 = t * I.c + 4 * k4;
       float4 x;
@@ -1232,13 +1382,26 @@ static __global__ void k_load_population(InstDev I, const float *__restrict__ ge
       x.z = j0 + 2 < I.N ? src[j0 + 2] : 0.f;
       x.w = j0 + 3 < I.N ? src[j0 + 3] : 0.f;
       *(float4 *)(row + ((size_t)k4 * I.T + t) * 4) = x;
-      push4<COMP, false>(acc, I.table, I.T, k4, t, x);
-      if (k4 & 1) acc.fold();
+      if (MK) {
+        macc.push4(I, k4, t, x);
+      } else {
+        push4<COMP, false>(acc, I.table, I.T, k4, t, x);
+        if (k4 & 1) acc.fold();
+      }
     }
-    const Mono m = block_reduce(acc.get(), sh);
+    float2 D = make_float2(0.f, 0.f);
+    float f = 0.f;
+    if constexpr (MK != 0) {
+      multi_finish<MK, false>(I, macc, sh, f, D);
+    } else {
+      const Mono m = block_reduce(acc.get(), sh);
+      if (t == 0) {
+        D = field_of(I, m);
+        f = fit_of(D);
+      }
+    }
     if (t == 0) {
-      const float2 D = deff_from(m, I.konst[0], I.konst[1]);
-      I.fit[i] = fit_of(D);
+      I.fit[i] = f;
       I.dval[i] = D;
       I.sel0[i] = 0;
       I.sel1[i] = 0;
@@ -1281,6 +1444,8 @@ struct qpm_state {
   int graph_b_n = -1;
   void *polish = nullptr;  // leader-polish scratch (allocated on first use)
   size_t polish_bytes = 0;
+  std::vector<qpm_objective> objs;  // per instance (kind 0 unless qpm_set_objective)
+  std::vector<void *> objmem;       // tables of a multi-wavelength kind's problems 2 .. K
 };
 
 namespace qpm {
@@ -1329,7 +1494,21 @@ static Variant variant2(const InstDev &I) {
   return v;
 }
 
+// the multi-wavelength kinds: launches form only, both slots read (no staging)
+template <int MK>
+static Variant variant_multi(const InstDev &I) {
+  Variant v;
+  v.de = (const void *)k_de<false, true, MK>;
+  v.gwo = (const void *)k_gwo<false, true, MK>;
+  v.smem = smem_bytes(I.T);
+  v.persist = nullptr;
+  v.persist_smem = 0;
+  return v;
+}
+
 static Variant variant_of(const InstDev &I) {
+  if (I.obj == OBJ_MULTI_THG) return variant_multi<OBJ_MULTI_THG>(I);
+  if (I.obj == OBJ_MULTI_SHG) return variant_multi<OBJ_MULTI_SHG>(I);
   const bool dual = I.c <= 8;
   if (I.compensated) return dual ? variant2<true, true>(I) : variant2<true, false>(I);
   return dual ? variant2<false, true>(I) : variant2<false, false>(I);
@@ -1451,6 +1630,8 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
   st->h.resize(n_inst);
   st->grid_plain.resize(n_inst);
   st->grid_persist.resize(n_inst);
+  st->objs.assign(n_inst, qpm_objective{});
+  st->objmem.assign(n_inst, nullptr);
   st->G_min = params[0].G;
   const int nsm = sm_count();
   size_t total = 0;
@@ -1538,7 +1719,10 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.table = (float4 *)take(Np * sizeof(float4));
     I.tpart = (double2 *)take((size_t)table_part_count(I.Npad) * sizeof(double2));
     I.konst = (float2 *)take(4 * sizeof(float2));
-    I.konst64 = (double2 *)take(3 * sizeof(double2));
+    I.K = 1;  // the cascaded d_eff of the problem until qpm_set_objective
+    I.mtab[0] = I.table;
+    I.mkonst[0] = I.konst;
+    I.konst64 = (double2 *)take(4 * sizeof(double2));
     I.lead = (int32_t *)take(3 * sizeof(int32_t));
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
     I.dekey = (unsigned long long *)take(NP * sizeof(unsigned long long));
@@ -1623,8 +1807,17 @@ extern "C" qpm_status qpm_init(qpm_state *st, qpm_stream_t stream) {
     TableSpec ts{I.N, I.Npad, I.T, I.c, I.kappa1, I.kappa2};
     qpm_status r = launch_table(ts, I.table, I.tpart, I.konst, I.konst64, s);
     if (r != QPM_OK) return r;
+    // the other problems of a multi-wavelength kind (one after the other: they share
+    // the reduction scratch on this stream)
+    for (int q = 1; q < (I.obj >= OBJ_MULTI_THG ? I.K : 1); ++q) {
+      TableSpec tq{I.N, I.Npad, I.T, I.c, st->objs[k].kappa1[q], st->objs[k].kappa2[q]};
+      r = launch_table(tq, (float4 *)I.mtab[q], I.tpart, (float2 *)I.mkonst[q], nullptr, s);
+      if (r != QPM_OK) return r;
+    }
     const size_t sm = smem_bytes(I.T);
-    if (I.compensated) k_init<true><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    if (I.obj == OBJ_MULTI_THG) k_init<false, OBJ_MULTI_THG><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    else if (I.obj == OBJ_MULTI_SHG) k_init<false, OBJ_MULTI_SHG><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    else if (I.compensated) k_init<true><<<st->grid_plain[k], I.T, sm, s>>>(I);
     else k_init<false><<<st->grid_plain[k], I.T, sm, s>>>(I);
     QPM_CUDA(cudaGetLastError());
   }
@@ -1677,6 +1870,10 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     }
     QPM_CUDA(cudaGraphLaunch(st->gexec, s));
   } else if (mode == QPM_RUN_PERSISTENT) {
+    for (int k = 0; k < st->n; ++k)
+      if (st->h[k].obj >= OBJ_MULTI_THG)
+        return fail(QPM_ERR_UNSUPPORTED,
+                    "the multi-wavelength objectives run in the launches and graph forms");
     QPM_CUDA(cudaMemsetAsync(st->bar, 0, 3 * sizeof(unsigned), s));
     for (int k = 0; k < st->n; ++k) {
       InstDev I = st->h[k];
@@ -1697,6 +1894,10 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
       return fail(QPM_ERR_TIMEOUT, "persistent kernel: a bounded grid-barrier wait gave up");
     }
   } else if (mode == QPM_RUN_BATCHED) {
+    for (int k = 0; k < st->n; ++k)
+      if (st->h[k].obj >= OBJ_MULTI_THG)
+        return fail(QPM_ERR_UNSUPPORTED,
+                    "the multi-wavelength objectives run in the launches and graph forms");
     for (int k = 0; k < st->n; ++k)
       if (st->h[k].T != 32)
         return fail(QPM_ERR_UNSUPPORTED, "batched form needs 32 threads per individual (team 32)");
@@ -1770,6 +1971,82 @@ extern "C" qpm_status qpm_set_batch_cluster(qpm_state *st, int32_t ctas) {
   return QPM_OK;
 }
 
+extern "C" qpm_status qpm_set_objective(qpm_state *st, int32_t inst, const qpm_objective *o) {
+  if (!st || inst < 0 || inst >= st->n || !o) return fail(QPM_ERR_ARG, "qpm_set_objective: bad arguments");
+  if (st->inited) return fail(QPM_ERR_STATE, "qpm_set_objective: call it before qpm_init");
+  if (o->kind < OBJ_THG || o->kind > OBJ_MULTI_SHG)
+    return fail(QPM_ERR_ARG, "qpm_set_objective: kind must be one of QPM_OBJ_*");
+  const bool multi = o->kind >= OBJ_MULTI_THG;
+  const int kmax = o->kind == OBJ_MULTI_THG ? 4 : 8;
+  if (multi && (o->K < 1 || o->K > kmax))
+    return fail(QPM_ERR_ARG, "qpm_set_objective: need 1 <= K <= 4 (THG) or 8 (SHG)");
+  for (int k = 0; multi && k < o->K; ++k)
+    if (!std::isfinite(o->kappa1[k]) || !std::isfinite(o->kappa2[k]))
+      return fail(QPM_ERR_ARG, "qpm_set_objective: kappa must be finite");
+  if (multi && (!std::isfinite(o->G0) || !(o->beta >= 0.f) || !std::isfinite(o->beta)))
+    return fail(QPM_ERR_ARG, "qpm_set_objective: need finite G0 and beta >= 0");
+  int dev = -1;
+  QPM_CUDA(cudaGetDevice(&dev));
+  if (dev != st->dev) return fail(QPM_ERR_STATE, "state belongs to another device");
+  InstDev &I = st->h[inst];
+  if (st->objmem[inst]) {
+    QPM_CUDA(cudaFree(st->objmem[inst]));
+    st->objmem[inst] = nullptr;
+  }
+  I.obj = o->kind;
+  I.minimize = multi ? 1 : 0;
+  I.K = multi ? o->K : 1;
+  I.G0 = multi ? o->G0 : 0.f;
+  I.beta = multi ? o->beta : 0.f;
+  for (int k = 0; k < 8; ++k) {
+    I.mtab[k] = nullptr;
+    I.mkonst[k] = nullptr;
+  }
+  I.mtab[0] = I.table;
+  I.mkonst[0] = I.konst;
+  if (multi) {
+    // the first problem is the instance's own: its table, constants and FP64 re-check
+    I.kappa1 = o->kappa1[0];
+    I.kappa2 = o->kappa2[0];
+    st->probs[inst].kappa1 = o->kappa1[0];
+    st->probs[inst].kappa2 = o->kappa2[0];
+    if (o->K > 1) {
+      const size_t tb = align_up(sizeof(float4) * (size_t)I.Npad, 256);
+      void *mem = nullptr;
+      QPM_CUDA(cudaMalloc(&mem, (size_t)(o->K - 1) * (tb + 256)));
+      st->objmem[inst] = mem;
+      for (int k = 1; k < o->K; ++k) {
+        char *p = (char *)mem + (size_t)(k - 1) * (tb + 256);
+        I.mtab[k] = (const float4 *)p;
+        I.mkonst[k] = (const float2 *)(p + tb);
+      }
+    }
+  }
+  st->objs[inst] = *o;
+  // the kernel variants of the kind and their occupancy
+  int occ_plain = 1, occ_persist = 1;
+  if (multi) {
+    const Variant v = variant_of(I);
+    int a = 0, b = 0;
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, I.T, v.smem));
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.gwo, I.T, v.smem));
+    occ_plain = std::max(1, std::min(a, b));
+    st->grid_plain[inst] = std::min(I.NP, occ_plain * sm_count());
+  } else {
+    qpm_status r = occupancy(I, &occ_plain, &occ_persist);
+    if (r != QPM_OK) return r;
+    st->grid_plain[inst] = std::min(I.NP, occ_plain * sm_count());
+    st->grid_persist[inst] = std::min(I.NP, occ_persist * sm_count());
+  }
+  if (st->gexec) {
+    cudaGraphExecDestroy(st->gexec);
+    st->gexec = nullptr;
+    st->graph_n = -1;
+  }
+  QPM_CUDA(cudaMemcpy(st->d_insts + inst, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
+  return QPM_OK;
+}
+
 extern "C" qpm_status qpm_team_of(const qpm_state *st, int32_t inst, int32_t *team_out) {
   if (!st || !team_out || inst < 0 || inst >= st->n) return fail(QPM_ERR_ARG, "bad arguments");
   *team_out = st->h[inst].T;
@@ -1817,7 +2094,11 @@ extern "C" qpm_status qpm_set_population(qpm_state *st, int32_t inst, const floa
       return fail(QPM_ERR_UNSUPPORTED, "all instances of a state share one generation count");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t sm = smem_bytes(I.T);
-  if (I.compensated)
+  if (I.obj == OBJ_MULTI_THG)
+    k_load_population<false, OBJ_MULTI_THG><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+  else if (I.obj == OBJ_MULTI_SHG)
+    k_load_population<false, OBJ_MULTI_SHG><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+  else if (I.compensated)
     k_load_population<true><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
   else
     k_load_population<false><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
@@ -1860,6 +2141,8 @@ extern "C" qpm_status qpm_destroy(qpm_state *st) {
   if (st->gexec) cudaGraphExecDestroy(st->gexec);
   if (st->gexec_b) cudaGraphExecDestroy(st->gexec_b);
   if (st->polish) cudaFree(st->polish);
+  for (void *p : st->objmem)
+    if (p) cudaFree(p);
   if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
   cudaFree(st->arena);
   delete st;
@@ -1879,6 +2162,8 @@ extern "C" qpm_status qpm_polish_leaders(qpm_state *st, int32_t inst, int32_t st
   if (steps < 0 || !(lr >= 0.f) || !(tau > 0.f))
     return fail(QPM_ERR_ARG, "qpm_polish_leaders: need steps >= 0, lr >= 0, tau > 0");
   const InstDev &I = st->h[inst];
+  if (I.obj != OBJ_THG)
+    return fail(QPM_ERR_UNSUPPORTED, "qpm_polish_leaders: the cascaded |d_eff|^2 objective only");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t Np = (size_t)I.Npad;
   const size_t saved_bytes = align_up(3 * (size_t)qpm_relaxed_saved_floats(I.N) * sizeof(float), 256);

@@ -27,7 +27,7 @@ struct TableSpec {
   double kappa1, kappa2;
 };
 
-// float2 konst[4] = {phi1*phi2, cdiag, psi, phi1}; double2 konst64[3] = {phi1*phi2, cdiag, psi}
+// float2 konst[4] = {phi1*phi2, cdiag, psi, phi1}; double2 konst64[4] = {phi1*phi2, cdiag, psi, phi1}
 // part: scratch of table_part_count(Npad) double2; table may be NULL (constants only)
 int table_part_count(int32_t Npad);
 qpm_status launch_table(const TableSpec &s, float4 *table, double2 *part, float2 *konst,

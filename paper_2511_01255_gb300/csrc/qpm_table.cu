@@ -102,6 +102,7 @@ static __global__ void k_table_finalize(int nparts, const double2 *__restrict__ 
     konst64[0] = phi12;
     konst64[1] = cdiag;
     konst64[2] = ps;
+    konst64[3] = p1;
   }
 }
 

@@ -76,3 +76,15 @@ def two_tone_signs(N, kappa1, kappa2):
     j = np.arange(N, dtype=np.float64)
     s = np.cos(kappa1 * j) + np.cos(kappa2 * j)
     return np.where(s < 0.0, -1.0, 1.0).astype(np.float32)
+
+
+# The multi-wavelength designs of Sec. 5: a 9 mm crystal of 3 um domains (N = 3000),
+# NP = 5000 and 1000 iterations (the paper's experimental protocol); synthetic
+# mismatches stand in for the PPLN dispersion the paper does not give.
+DESIGN_THG3 = dict(name="multi_thg_k3_n3000_np5000_g1000", N=3000, NP=5000, G=1000, F=0.5, CR=0.9,
+                   seed=1, kind=2, G0=2.0e6, beta=0.5,
+                   kappas=[(TWO_PI / 6.5, TWO_PI / 1.4), (TWO_PI / 6.9, TWO_PI / 1.55),
+                           (TWO_PI / 7.4, TWO_PI / 1.7)])
+DESIGN_SHG5 = dict(name="multi_shg_k5_n3000_np5000_g1000", N=3000, NP=5000, G=1000, F=0.5, CR=0.9,
+                   seed=1, kind=3, G0=2.0e3, beta=0.5,
+                   kappas=[(TWO_PI / x, 0.0) for x in (2.1, 2.6, 3.2, 3.7, 4.4)])

@@ -387,3 +387,81 @@ def test_adaptive_F_lockstep(q, orc, mode):
         assert np.array_equal(X, Xo)
         assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
         assert Fg[0] == np.float32(0.1) and np.all((Fg >= 0.01) & (Fg <= 0.1))
+
+
+KAP3 = [(2 * math.pi / 6.5, 2 * math.pi / 1.4), (2 * math.pi / 6.9, 2 * math.pi / 1.55),
+        (2 * math.pi / 7.4, 2 * math.pi / 1.7)]
+KAP5 = [(2 * math.pi / x, 0.0) for x in (2.1, 2.6, 3.2, 3.7, 4.4)]
+
+
+@pytest.mark.parametrize("kind,N,NP,G,kap,G0,beta,modes", [
+    (1, 333, 24, 12, [(2 * math.pi / 6.9, 0.0)], 0.0, 0.0, (0, 1, 2, 3)),
+    (2, 3000, 32, 6, KAP3, 2.0e5, 0.5, (0, 1)),
+    (3, 3000, 32, 6, KAP5, 1.5e3, 0.5, (0, 1)),
+])
+def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes):
+    """The optimiser on the other objectives of the paper's designs: the SHG field
+    (maximised), the multi-wavelength THG objective of Sec. 5 over three (kappa1,
+    kappa2) pairs at N = 3000 and the multi-wavelength SHG objective over five (the
+    paper's 9 mm / 3 um SHG designs have N = 3000 and five wavelengths), minimised.
+    Populations bit for bit against the oracle's lockstep replay; every FP32 objective
+    within tolerance of the oracle's FP64 one; the best individual's FP64 field
+    re-check against the quadrature."""
+    import torch
+    k1, k2 = kap[0]
+    for mode in modes:
+        team = 32 if mode == 3 else 0
+        prm = q.Params(NP, G, 0.5, 0.9, 6, 0, 0, team)
+        st = q.State([(N, k1, k2)], [prm])
+        st.set_objective(kind, kap if kind >= 2 else (), G0, beta)
+        tr = torch.full((NP * (1 + 2 * G),), float("nan"), dtype=torch.float32, device="cuda")
+        q.qpm_set_trace(st.h, 0, tr)
+        st.init()
+        st.run(G, mode)
+        X, f, D = snapshot(st)
+        x, d64, fb, idx = st.best()
+        torch.cuda.synchronize()
+        trace = tr.cpu().numpy()
+        st.close()
+        cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 6, obj=kind, kappas=kap if kind >= 2 else (),
+                           G0=G0, beta=beta)
+        Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+        assert np.array_equal(X, Xo), mode
+        ok = ~np.isnan(trace)
+        if kind == 1:  # |E|^2: relative, floor at 1e-3 of the all-up |E|^2 = N^2
+            err = np.abs(trace[ok] - tro[ok]) / np.maximum(tro[ok], 1e-6 * N * N)
+            assert err.max() < 2 * TOL_D
+        else:  # each |G0 - G_k| carries G_k's error: scale K G0
+            assert np.max(np.abs(trace[ok] - tro[ok])) <= TOL_D * len(kap) * G0
+        i = int(idx.cpu().item())
+        assert i == (int(np.argmin(f)) if kind >= 2 else int(np.argmax(f)))
+        xi = X[i][None]
+        ref = orc.shg_genes(xi, k1)[0] if kind in (1, 3) else orc.deff_genes(xi, k1, k2)[0]
+        z = complex(*d64.cpu().numpy())
+        assert abs(z - ref) <= 1e-9 * abs(ref)
+
+
+def test_objective_errors(q):
+    import torch
+    st = q.State([(100, 1.0, 2.0)], [q.Params(8, 4, 0.5, 0.9, 1, 0, 0)])
+    with pytest.raises(q.QpmError) as e:
+        st.set_objective(2, [(1.0, 2.0)] * 5, 10.0, 0.5)
+    assert e.value.status == 1
+    with pytest.raises(q.QpmError) as e:
+        st.set_objective(3, [(1.0, 0.0)], 10.0, -1.0)
+    assert e.value.status == 1
+    st.set_objective(2, [(1.0, 2.0), (1.5, 2.5)], 10.0, 0.5)
+    st.init()
+    with pytest.raises(q.QpmError) as e:
+        st.set_objective(0)
+    assert e.value.status == 5
+    for mode in (2, 3):
+        with pytest.raises(q.QpmError) as e:
+            st.run(1, mode)
+        assert e.value.status == 4
+    with pytest.raises(q.QpmError) as e:
+        q.qpm_polish_leaders(st.h, 0)
+    assert e.value.status == 4
+    st.run(2, q.RUN_GRAPH)
+    torch.cuda.synchronize()
+    st.close()

@@ -414,3 +414,86 @@ def test_adaptive_F_run_equals_its_generations(orc):
     assert F == Fh[G]
     assert np.array_equal(X, Xg)
     assert 1 in branches  # the rule does fire on this problem
+
+
+# ------------------------------------------------- the loop's objectives (Sec. 2.1, Sec. 5)
+KAPPAS3 = [(2 * math.pi / 6.5, 2 * math.pi / 1.4), (2 * math.pi / 6.9, 2 * math.pi / 1.55),
+           (2 * math.pi / 7.4, 2 * math.pi / 1.7)]
+
+
+def test_objective_rows_equal_the_field_integrals(orc):
+    """Every objective the loop can optimise, row by row, from the separately pinned
+    field integrals: |d_eff|^2 (cascaded), |E|^2 (SHG), and sum_k |G0 - G_k| +
+    beta (G_max - G_min) with G_k the cascaded or SHG field magnitude (Sec. 5)."""
+    import numpy as np
+    from paper_2511_01255_gb300 import workloads as W
+    N, NP = 300, 7
+    X = W.random_genes(NP, N, seed=9)
+    k1, k2 = KAPPAS3[1]
+    G0, beta = 3.0e4, 0.6
+    cfg0 = orc.make_cfg(NP, N, 5, 0.5, 0.9, 1)
+    assert np.allclose(orc.objective_rows(cfg0, X, k1, k2), np.abs(orc.deff_genes(X, k1, k2)) ** 2,
+                       rtol=1e-13, atol=0)
+    cfg1 = orc.make_cfg(NP, N, 5, 0.5, 0.9, 1, obj=1)
+    assert np.allclose(orc.objective_rows(cfg1, X, k1, k2), np.abs(orc.shg_genes(X, k1)) ** 2,
+                       rtol=1e-13, atol=0)
+    for obj in (2, 3):
+        cfg = orc.make_cfg(NP, N, 5, 0.5, 0.9, 1, obj=obj, kappas=KAPPAS3, G0=G0, beta=beta)
+        if obj == 2:
+            G = np.abs(np.stack([orc.deff_genes(X, a, b) for a, b in KAPPAS3], axis=1))
+        else:
+            G = np.abs(np.stack([orc.shg_genes(X, a) for a, _ in KAPPAS3], axis=1))
+        want = np.abs(np.float32(G0) - G).sum(axis=1) + np.float32(beta) * (G.max(axis=1) - G.min(axis=1))
+        assert np.allclose(orc.objective_rows(cfg, X), want, rtol=1e-12, atol=0), obj
+    # the cascaded multi objective equals the multi_objective oracle used by qpm_eval_multi
+    cfg = orc.make_cfg(NP, N, 5, 0.5, 0.9, 1, obj=2, kappas=KAPPAS3, G0=G0, beta=beta)
+    _, ref = orc.multi_objective(X, KAPPAS3, np.float32(G0), np.float32(beta))
+    assert np.allclose(orc.objective_rows(cfg, X), ref, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("obj", [1, 2, 3])
+def test_objective_loops_keep_their_best_and_lead_with_it(orc, obj):
+    """The loop maximises |E|^2 (obj 1) and minimises the multi-wavelength objectives
+    (obj 2, 3): generation by generation the best value never gets worse, and the
+    three leaders are the three best survivors in the objective's direction (ties to
+    the lower index)."""
+    import numpy as np
+    N, NP, G = 40, 12, 15
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 2, obj=obj, kappas=KAPPAS3[:2], G0=200.0, beta=0.5)
+    k1, k2 = KAPPAS3[0]
+    X = orc.init_population(cfg)
+    f64 = orc.objective_rows(cfg, X, k1, k2)
+    fdec = f64.astype(np.float32)
+    best = f64.min() if obj >= 2 else f64.max()
+    for g in range(G):
+        Xn, fdec_n, f64_n, _, _, lead = orc.hwsda_generation(cfg, k1, k2, g, X, fdec, f64)
+        # leaders: from the DE survivors, i.e. recompute by replaying DE alone
+        U = orc.de_trials(cfg, g, X)
+        fu = orc.objective_rows(cfg, U, k1, k2)
+        surv = np.where(fu <= f64, fu, f64) if obj >= 2 else np.where(fu >= f64, fu, f64)
+        key = surv if obj >= 2 else -surv
+        order = np.lexsort((np.arange(NP), key))
+        assert list(lead) == list(order[:3])
+        X, fdec, f64 = Xn, fdec_n, f64_n
+        nb = f64.min() if obj >= 2 else f64.max()
+        assert (nb <= best) if obj >= 2 else (nb >= best)
+        best = nb
+    assert np.allclose(f64, orc.objective_rows(cfg, X, k1, k2), rtol=0, atol=0)
+
+
+def test_shg_multi_objective_against_exhaustive_search(orc):
+    """A 10-domain, 3-wavelength SHG design: the loop's best objective after 60
+    generations is no better than the exhaustive minimum over all 1024 patterns and
+    no worse than the best of its initial population."""
+    import itertools
+    import numpy as np
+    N, NP, G = 10, 16, 60
+    kap = [(2 * math.pi / 2.3, 0.0), (2 * math.pi / 3.1, 0.0), (2 * math.pi / 4.2, 0.0)]
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 5, obj=3, kappas=kap, G0=8.0, beta=0.5)
+    allX = np.array(list(itertools.product([-1.0, 1.0], repeat=N)), dtype=np.float32)
+    cfg_all = orc.make_cfg(allX.shape[0], N, G, 0.5, 0.9, 5, obj=3, kappas=kap, G0=8.0, beta=0.5)
+    fmin = orc.objective_rows(cfg_all, allX).min()
+    X0 = orc.init_population(cfg)
+    f0 = orc.objective_rows(cfg, X0).min()
+    X, f = orc.hwsda_run(cfg, 0.0, 0.0)
+    assert fmin - 1e-9 <= f.min() <= f0
