@@ -65,7 +65,14 @@ typedef struct {
   float F;             /* DE scale factor, [0, 2] */
   float CR;            /* crossover rate, [0, 1] */
   uint64_t seed;       /* Philox4x32-10 key */
-  int32_t gwo_combine; /* 0: (X1+X2+X3)/3; 1: |X_k|-weighted, per dimension */
+  int32_t gwo_combine; /* the GWO update of the omega wolves: 0: (X1+X2+X3)/3; 1: |X_k|-
+                          weighted, per dimension; 2: the four-leader discrete GWO of
+                          Sec. 3.1.2 (launches and graph forms, single objectives): with
+                          tau = g / G and n of the four leaders' genes at +1, take a random
+                          leader's state with probability 0.3 (1 - tau), else +1 with
+                          probability (1 - delta) q_n + delta / 2, delta = 0.5 (1 - tau),
+                          q_n = (1 - tau) n / 4 + tau [majority of the four, 1/2 on a tie];
+                          then flip with probability 0.1 (1 - tau) + 0.01 tau; genes +-1 */
   int32_t compensated; /* 0: plain FP32 scan; 1: Kahan-compensated FP32 scan */
   int32_t team;        /* threads per individual: 0 = automatic (the smallest power of two in
                           [32, 256] with at most 4 domains per thread; 512 for a single

@@ -69,6 +69,7 @@ def lib():
         L.orc_hwsda_generation.restype = ctypes.c_int
         L.orc_adaptive_F.argtypes = [P, i32, P, P, ctypes.c_float, P, P]
         L.orc_objective_rows.argtypes = [P, dbl, dbl, ctypes.c_int, P, P]
+        L.orc_discrete_thresholds.argtypes = [i32, i32, P]
         L.orc_adaptive_F.restype = ctypes.c_int
         L.orc_hwsda_run.argtypes = [P, dbl, dbl, ctypes.c_int, P, P, P, P, P]
         L.orc_hwsda_run.restype = ctypes.c_int
@@ -251,7 +252,16 @@ def top3(f):
     return o
 
 
+def discrete_thresholds(g, G):
+    """(social, flip, plus[0..4]) 16-bit thresholds of the discrete GWO at generation g."""
+    o = np.zeros(7, dtype=np.uint32)
+    lib().orc_discrete_thresholds(g, G, _p(o))
+    return int(o[0]), int(o[1]), [int(x) for x in o[2:]]
+
+
 def gwo_candidates(cfg, g, X, lead):
+    """Candidates of the omega wolves (leader rows copied unchanged); lead: three
+    leaders, or four for the discrete GWO (cfg.combine == 2)."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     lead = np.ascontiguousarray(lead, dtype=np.int32)
     Y = X.copy()
@@ -287,7 +297,7 @@ def hwsda_generation(cfg, kappa1, kappa2, g, X, fdec, f64=None, lock_trial=None,
     em = None if eval_mask is None else np.ascontiguousarray(eval_mask, dtype=np.uint8)
     tt = np.zeros(cfg.NP)
     tc = np.zeros(cfg.NP)
-    lead = np.zeros(3, dtype=np.int32)
+    lead = np.zeros(4 if cfg.combine == 2 else 3, dtype=np.int32)
     Fio = None if F is None else ctypes.c_float(F)
     br = ctypes.c_int32(-1)
     rc = lib().orc_hwsda_generation(ctypes.byref(cfg), kappa1, kappa2, Q, g, _p(X), _p(fdec),

@@ -568,7 +568,8 @@ typedef struct {
   float F, CR;
   uint64_t seed;
   uint32_t inst;
-  int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension */
+  int32_t combine; /* 0 = mean of X1..X3, 1 = |X_k|-weighted per dimension,
+                      2 = the four-leader discrete GWO of Sec. 3.1.2 */
   int32_t f_schedule; /* 0 = constant F; 1 = decaying F of Sec. 3.1.1;
                          2 = the adaptive F of Sec. 3.1.1 (orc_adaptive_F) */
   /* the fitness the loop optimises (Sec. 2.1 and Sec. 5):
@@ -790,13 +791,83 @@ static void gwo_cand_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X
   }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Improved discrete GWO with four leaders (Sec. 3.1.2), combine = 2.  The paper */
+/* describes it only qualitatively: continuous positions map to +-1 states; the  */
+/* state of a wolf follows transition probabilities taken from the four leaders' */
+/* state distribution, with random disturbance whose strength a dispersion      */
+/* parameter sets; early iterations explore with much disturbance, late ones     */
+/* follow the dominant state with only a small flip probability; a social-      */
+/* learning rate that falls with the iterations lets a wolf copy a random       */
+/* leader's state.  Reading taken (tau = g / G), per omega wolf and gene j, with */
+/* n = the number of the four leaders whose gene j is +1:                        */
+/*   dispersion delta = 0.5 (1 - tau), social rate sigma = 0.3 (1 - tau),        */
+/*   disturbance mu = 0.1 (1 - tau) + 0.01 tau;                                  */
+/*   q_n = (1 - tau) n / 4 + tau m_n, m_n the majority vote (1 for n > 2, 0 for   */
+/*   n < 2, 1/2 for n = 2); P_n = (1 - delta) q_n + delta / 2 (the chance of +1); */
+/*   with probability sigma the wolf takes the state of leader kl (uniform among  */
+/*   the four), else +1 with probability P_n; then the state flips with          */
+/*   probability mu.  Every probability p becomes the 16-bit threshold           */
+/*   floor(65536 p) (FP64, once per generation), tested as u < threshold on      */
+/*   16-bit uniforms from two words per gene: tag 3 gives the social (high) and  */
+/*   transition (low) halves, tag 4 the flip half (high) and kl (low two bits).   */
+/* The new genes are +-1.0.                                                      */
+/* ------------------------------------------------------------------------- */
+typedef struct { uint32_t social, flip, plus[5]; } disc_thr;
+
+ORC_API void orc_discrete_thresholds(int32_t g, int32_t G, uint32_t out[7]) {
+  const double tau = (double)g / (double)G;
+  const double delta = 0.5 * (1.0 - tau), sigma = 0.3 * (1.0 - tau);
+  const double mu = 0.1 * (1.0 - tau) + 0.01 * tau;
+  out[0] = (uint32_t)floor(65536.0 * sigma);
+  out[1] = (uint32_t)floor(65536.0 * mu);
+  for (int n = 0; n <= 4; ++n) {
+    const double m = n > 2 ? 1.0 : (n < 2 ? 0.0 : 0.5);
+    const double qn = (1.0 - tau) * ((double)n / 4.0) + tau * m;
+    const double P = (1.0 - delta) * qn + 0.5 * delta;
+    out[2 + n] = (uint32_t)floor(65536.0 * P);
+  }
+}
+
+static void gwo_discrete_one(const orc_cfg *c, uint32_t g, int32_t i, const float *X,
+                             const int32_t lead[4], float *y) {
+  uint32_t th[7];
+  orc_discrete_thresholds((int32_t)g, c->G, th);
+  for (int32_t j = 0; j < c->N; ++j) {
+    float s[4];
+    int n = 0;
+    for (int k = 0; k < 4; ++k) {
+      s[k] = (X[(int64_t)lead[k] * c->ld + j] < 0.0f) ? -1.0f : 1.0f;
+      n += s[k] > 0.0f;
+    }
+    const uint32_t w1 = rng_word(c->seed, c->inst, TAG_GWO, g, (uint32_t)i, (uint32_t)j);
+    const uint32_t w2 = rng_word(c->seed, c->inst, TAG_GWO + 1, g, (uint32_t)i, (uint32_t)j);
+    float v;
+    if ((w1 >> 16) < th[0]) v = s[w2 & 3u];           /* social learning */
+    else v = ((w1 & 0xFFFFu) < th[2 + n]) ? 1.0f : -1.0f; /* transition */
+    if ((w2 >> 16) < th[1]) v = -v;                   /* disturbance */
+    y[j] = v;
+  }
+}
+
 /* candidate positions for every omega wolf (rows of leaders are left untouched in Y) */
+/* number of leaders: four for the discrete GWO, three otherwise */
+static inline int n_leaders(const orc_cfg *c) { return c->combine == 2 ? 4 : 3; }
+static inline int is_leader(const int32_t *lead, int nl, int32_t i) {
+  for (int k = 0; k < nl; ++k)
+    if (lead[k] == i) return 1;
+  return 0;
+}
+
+/* lead: three leaders (four for the discrete GWO, combine = 2) */
 ORC_API void orc_gwo_candidates(const orc_cfg *c, uint32_t g, const float *X,
-                                const int32_t lead[3], float *Y) {
+                                const int32_t *lead, float *Y) {
+  const int nl = n_leaders(c);
 #pragma omp parallel for schedule(static)
   for (int32_t i = 0; i < c->NP; ++i) {
-    if (i == lead[0] || i == lead[1] || i == lead[2]) continue;
-    gwo_cand_one(c, g, i, X, lead, Y + (int64_t)i * c->ld);
+    if (is_leader(lead, nl, i)) continue;
+    if (c->combine == 2) gwo_discrete_one(c, g, i, X, lead, Y + (int64_t)i * c->ld);
+    else gwo_cand_one(c, g, i, X, lead, Y + (int64_t)i * c->ld);
   }
 }
 
@@ -843,13 +914,13 @@ ORC_API void orc_objective_rows(const orc_cfg *c, double kappa1, double kappa2, 
   eval_rows(c, kappa1, kappa2, Q, X, NULL, f64);
 }
 
-/* the three best of f in the objective's direction, ties to the lower index */
-static void top3_dir(const orc_cfg *c, const float *f, int32_t lead[3]) {
-  for (int k = 0; k < 3; ++k) lead[k] = -1;
+/* the nl best of f in the objective's direction, ties to the lower index */
+static void topn_dir(const orc_cfg *c, int nl, const float *f, int32_t *lead) {
+  for (int k = 0; k < nl; ++k) lead[k] = -1;
   for (int32_t i = 0; i < c->NP; ++i)
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < nl; ++k)
       if (lead[k] < 0 || better(c, f[i], f[lead[k]])) {
-        for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+        for (int m = nl - 1; m > k; --m) lead[m] = lead[m - 1];
         lead[k] = i;
         break;
       }
@@ -867,7 +938,8 @@ static void top3_dir(const orc_cfg *c, const float *f, int32_t lead[3]) {
  *                 fitness computed (lockstep only; decisions do not need them)
  *   tr_trial, tr_cand: if non-NULL, receive the FP64 fitness of trials and
  *                 candidates (NaN where not evaluated)
- *   lead_out[3]:  if non-NULL, receives the leaders of this generation
+ *   lead_out:     if non-NULL, receives the leaders of this generation (three, or
+ *                 four for the discrete GWO)
  *   F_io:         adaptive F (f_schedule = 2) only: in, the F of generation g; out,
  *                 the F of generation g + 1 (orc_adaptive_F on the DE survivors);
  *                 NULL otherwise (F then follows orc_F_of)
@@ -907,29 +979,30 @@ ORC_API int orc_hwsda_generation(const orc_cfg *c, double kappa1, double kappa2,
     *F_io = Fn;
     if (branch_out) *branch_out = br;
   }
-  /* Step 3: the three leaders */
-  int32_t lead[3];
+  /* Step 3: the three leaders (four for the discrete GWO) */
+  const int nl = n_leaders(c);
+  int32_t lead[4] = {-1, -1, -1, -1};
   if (lock) {
-    top3_dir(c, fdec, lead);
+    topn_dir(c, nl, fdec, lead);
   } else {
-    for (int k = 0; k < 3; ++k) lead[k] = -1;
     for (int32_t i = 0; i < NP; ++i)
-      for (int k = 0; k < 3; ++k)
+      for (int k = 0; k < nl; ++k)
         if (lead[k] < 0 || better(c, f64[i], f64[lead[k]])) {
-          for (int m = 2; m > k; --m) lead[m] = lead[m - 1];
+          for (int m = nl - 1; m > k; --m) lead[m] = lead[m - 1];
           lead[k] = i;
           break;
         }
   }
-  if (lead_out) { lead_out[0] = lead[0]; lead_out[1] = lead[1]; lead_out[2] = lead[2]; }
+  if (lead_out)
+    for (int k = 0; k < nl; ++k) lead_out[k] = lead[k];
   /* Step 4: move the omega wolves; Step 5: greedy selection again */
   orc_gwo_candidates(c, (uint32_t)g, X, lead, U);
   for (int32_t i = 0; i < NP; ++i)
-    mask[i] = !(i == lead[0] || i == lead[1] || i == lead[2]) && (!eval_mask || eval_mask[i]);
+    mask[i] = !is_leader(lead, nl, i) && (!eval_mask || eval_mask[i]);
   eval_rows(c, kappa1, kappa2, Q, U, mask, ft);
   if (tr_cand) memcpy(tr_cand, ft, sizeof(double) * NP);
   for (int32_t i = 0; i < NP; ++i) {
-    if (i == lead[0] || i == lead[1] || i == lead[2]) continue;
+    if (is_leader(lead, nl, i)) continue;
     int accept = lock ? better_eq(c, lock_cand[i], fdec[i]) : better_eq(c, ft[i], f64[i]);
     if (accept) {
       memcpy(X + (int64_t)i * c->ld, U + (int64_t)i * c->ld, sizeof(float) * c->N);

@@ -53,7 +53,7 @@ struct InstDev {
   double2 *tpart;        // table reduction scratch
   float2 *konst;         // phi1 phi2, cdiag
   double2 *konst64;      // phi1 phi2, cdiag, psi, phi1 (FP64)
-  int32_t *lead;         // [3]
+  int32_t *lead;         // [3] (four for the discrete GWO)
   unsigned long long *topk;  // [2][NP * 3] partial leader keys (by generation parity)
   unsigned *ctr;         // [4] CTA-completion counters
   int32_t *gen;          // [1] completed generations
@@ -67,6 +67,7 @@ struct InstDev {
   // first one's table and constants are table / konst), G0, beta; minimised for the
   // multi-wavelength kinds
   int32_t obj, K, minimize;
+  const uint32_t *dthr;  // [G][7] discrete GWO (combine 2): social, flip, plus[0..4] thresholds
   float G0, beta;
   const float4 *mtab[8];   // [Npad] permuted phasor tables of the K problems
   const float2 *mkonst[8];  // their FP32 constants
@@ -708,6 +709,94 @@ __device__ void adaptive_F_block(const InstDev &I, const unsigned long long *key
   __syncthreads();
 }
 
+// ------------------------------------------- four-leader discrete GWO (Sec. 3.1.2)
+// The paper describes it only qualitatively (continuous positions mapped to +-1; state
+// transitions from the four leaders' state distribution with a dispersion parameter;
+// much disturbance early, the dominant state and rare flips late; a falling social-
+// learning rate that copies a random leader).  Reading, per omega wolf and gene, with
+// n the number of the four leaders whose gene is +1 and tau = g / G: with probability
+// sigma = 0.3 (1 - tau) take leader kl's state (kl uniform in 0..3), else +1 with
+// probability P_n = (1 - delta) q_n + delta / 2, delta = 0.5 (1 - tau),
+// q_n = (1 - tau) n / 4 + tau [n > 2, or 1/2 for n = 2]; then flip with probability
+// mu = 0.1 (1 - tau) + 0.01 tau.  The probabilities are 16-bit thresholds per
+// generation (computed on the host in FP64, I.dthr), tested against the 16-bit halves
+// of two words per gene (tag GWO: social high, transition low; tag GWO + 1: flip high,
+// kl the low two bits).  The new genes are +-1.
+__device__ __forceinline__ void top4_insert(unsigned long long &k0, unsigned long long &k1,
+                                            unsigned long long &k2, unsigned long long &k3,
+                                            unsigned long long x) {
+  if (x > k0) { k3 = k2; k2 = k1; k1 = k0; k0 = x; }
+  else if (x > k1) { k3 = k2; k2 = k1; k1 = x; }
+  else if (x > k2) { k3 = k2; k2 = x; }
+  else if (x > k3) { k3 = x; }
+}
+
+// the generation's thresholds: social, flip, and P(+1) for 0 .. 4 leaders at +1
+struct DiscThr {
+  uint32_t soc, flip, p0, p1, p2, p3, p4;
+};
+
+// the new state of one gene from the four leaders' genes and the two random words
+__device__ __forceinline__ float disc_gene(float a, float b, float c, float d, uint32_t w1,
+                                           uint32_t w2, const DiscThr &th) {
+  const float s0 = sgn(a), s1 = sgn(b), s2 = sgn(c), s3 = sgn(d);
+  const int n = (s0 > 0.f) + (s1 > 0.f) + (s2 > 0.f) + (s3 > 0.f);
+  const uint32_t kl = w2 & 3u;
+  float v;
+  if ((w1 >> 16) < th.soc) {  // social learning: a random leader's state
+    v = kl == 0u ? s0 : (kl == 1u ? s1 : (kl == 2u ? s2 : s3));
+  } else {  // transition from the leaders' state distribution
+    const uint32_t tp = n == 0 ? th.p0 : (n == 1 ? th.p1 : (n == 2 ? th.p2 : (n == 3 ? th.p3 : th.p4)));
+    v = (w1 & 0xFFFFu) < tp ? 1.f : -1.f;
+  }
+  return (w2 >> 16) < th.flip ? -v : v;  // disturbance
+}
+
+// one candidate of the discrete GWO for omega wolf i and its greedy selection, by the
+// CTA (team T); L: the four leaders' current rows
+template <bool COMP>
+__device__ void gwo_discrete_individual(const InstDev &I, const PhiloxKey &K, int g, int i,
+                                        int32_t *sel, const float *L0, const float *L1,
+                                        const float *L2, const float *L3, Mono *sh) {
+  const int t = threadIdx.x;
+  const float fx = (t == 0) ? I.fit[i] : 0.f;
+  const int si = sel[i];
+  float *out = row_ptr(I, i, si ^ 1);
+  const uint32_t *tg = I.dthr + (size_t)7 * g;
+  const DiscThr th{tg[0], tg[1], tg[2], tg[3], tg[4], tg[5], tg[6]};
+  Acc<COMP> acc;
+  acc.zero();
+  const int n4 = I.c / 4;
+  for (int k4 = 0; k4 < n4; ++k4) {
+    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const float4 l0 = __ldg((const float4 *)(L0 + off)), l1 = __ldg((const float4 *)(L1 + off));
+    const float4 l2 = __ldg((const float4 *)(L2 + off)), l3 = __ldg((const float4 *)(L3 + off));
+    const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
+    const uint4 w1 = rng4(K, I.inst, TAG_GWO, (uint32_t)g, (uint32_t)i, jg);
+    const uint4 w2 = rng4(K, I.inst, TAG_GWO + 1, (uint32_t)g, (uint32_t)i, jg);
+    float4 y;
+    y.x = disc_gene(l0.x, l1.x, l2.x, l3.x, w1.x, w2.x, th);
+    y.y = disc_gene(l0.y, l1.y, l2.y, l3.y, w1.y, w2.y, th);
+    y.z = disc_gene(l0.z, l1.z, l2.z, l3.z, w1.z, w2.z, th);
+    y.w = disc_gene(l0.w, l1.w, l2.w, l3.w, w1.w, w2.w, th);
+    *(float4 *)(out + off) = y;
+    push4<COMP, false>(acc, I.table, I.T, k4, t, y);
+    if (k4 & 1) acc.fold();
+  }
+  const Mono m = block_reduce(acc.get(), sh);
+  if (t == 0) {
+    const float2 D = field_of(I, m);
+    const float f = fit_of(D);
+    const bool accept = f >= fx;
+    if (accept) {
+      sel[i] = si ^ 1;
+      I.fit[i] = f;
+      I.dval[i] = D;
+    }
+    if (I.trace) I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + i] = f;
+  }
+}
+
 // top-3 merge over the CTA: every thread passes its sorted triple, thread 0 gets the result
 __device__ void block_top3(unsigned long long &k0, unsigned long long &k1, unsigned long long &k2,
                            unsigned long long *sh) {
@@ -761,6 +850,31 @@ __device__ void merge_leaders(const unsigned long long *topk, int nparts, int32_
   __syncthreads();
 }
 
+// the same for four leaders (the discrete GWO): topk holds 4 keys per part
+__device__ void merge_leaders4(const unsigned long long *topk, int nparts, int32_t *lead) {
+  if (threadIdx.x < 32) {
+    unsigned long long k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+    for (int e = threadIdx.x; e < 4 * nparts; e += 32) top4_insert(k0, k1, k2, k3, topk[e]);
+    for (int s = 16; s > 0; s >>= 1) {
+      const unsigned long long p0 = __shfl_xor_sync(0xffffffffu, k0, s);
+      const unsigned long long p1 = __shfl_xor_sync(0xffffffffu, k1, s);
+      const unsigned long long p2 = __shfl_xor_sync(0xffffffffu, k2, s);
+      const unsigned long long p3 = __shfl_xor_sync(0xffffffffu, k3, s);
+      top4_insert(k0, k1, k2, k3, p0);
+      top4_insert(k0, k1, k2, k3, p1);
+      top4_insert(k0, k1, k2, k3, p2);
+      top4_insert(k0, k1, k2, k3, p3);
+    }
+    if (threadIdx.x == 0) {
+      lead[0] = key_index(k0);
+      lead[1] = key_index(k1);
+      lead[2] = key_index(k2);
+      lead[3] = key_index(k3);
+    }
+  }
+  __syncthreads();
+}
+
 // true in every thread of the last CTA to finish (classic fence + counter pattern)
 __device__ bool last_cta(unsigned *ctr) {
   __shared__ bool is_last;
@@ -786,7 +900,8 @@ static __global__ void k_de(InstDev I) {
   const PhiloxKey K = philox_schedule(I.key);
   const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
   int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
-  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  const bool four = I.combine == 2;  // the discrete GWO's four leaders
+  unsigned long long k0 = 0, k1 = 0, k2 = 0, k3 = 0;
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
     int slot = 0, impr = 0;
@@ -795,17 +910,26 @@ static __global__ void k_de(InstDev I) {
             I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh,
             &slot, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr);
     if (threadIdx.x == 0) {
-      top3_insert(k0, k1, k2, key);
+      if (four) top4_insert(k0, k1, k2, k3, key);
+      else top3_insert(k0, k1, k2, key);
       if (I.adaptive) I.dekey[i] = slot_key(key, i, slot, impr);
     }
   }
   if (threadIdx.x == 0) {
-    I.topk[3 * blockIdx.x] = k0;
-    I.topk[3 * blockIdx.x + 1] = k1;
-    I.topk[3 * blockIdx.x + 2] = k2;
+    if (four) {
+      I.topk[4 * blockIdx.x] = k0;
+      I.topk[4 * blockIdx.x + 1] = k1;
+      I.topk[4 * blockIdx.x + 2] = k2;
+      I.topk[4 * blockIdx.x + 3] = k3;
+    } else {
+      I.topk[3 * blockIdx.x] = k0;
+      I.topk[3 * blockIdx.x + 1] = k1;
+      I.topk[3 * blockIdx.x + 2] = k2;
+    }
   }
   if (last_cta(&I.ctr[0])) {
-    merge_leaders(I.topk, gridDim.x, I.lead, nullptr);  // Step 3
+    if (four) merge_leaders4(I.topk, gridDim.x, I.lead);  // Step 3
+    else merge_leaders(I.topk, gridDim.x, I.lead, nullptr);
     if (I.adaptive) adaptive_F_block(I, I.dekey, g);     // Step 6: the next F
     if (threadIdx.x == 0) I.ctr[0] = 0u;
   }
@@ -835,6 +959,33 @@ static __global__ void k_gwo(InstDev I) {
   if (last_cta(&I.ctr[1])) {
     if (threadIdx.x == 0) {
       *I.gen = g + 1;  // Step 6/7: next generation (a is derived from g)
+      I.ctr[1] = 0u;
+    }
+  }
+}
+
+// Steps 4-5 with the four-leader discrete GWO (launches form)
+template <bool COMP>
+static __global__ void k_gwo_disc(InstDev I) {
+  extern __shared__ float4 dyn[];
+  Mono *sh = (Mono *)dyn;
+  const int g = *I.gen;
+  const PhiloxKey K = philox_schedule(I.key);
+  int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
+  // the leaders do not move in this phase
+  const int la = I.lead[0], lb = I.lead[1], lc = I.lead[2], ld = I.lead[3];
+  const float *L0 = row_ptr(I, la, sel[la]), *L1 = row_ptr(I, lb, sel[lb]);
+  const float *L2 = row_ptr(I, lc, sel[lc]), *L3 = row_ptr(I, ld, sel[ld]);
+  for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
+    if (i == la || i == lb || i == lc || i == ld) continue;
+    __syncthreads();  // the reduction scratch is reused
+    gwo_discrete_individual<COMP>(I, K, g, i, sel, L0, L1, L2, L3, sh);
+  }
+  if (I.trace && blockIdx.x == 0 && threadIdx.x < 4)
+    I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + I.lead[threadIdx.x]] = __int_as_float(0x7fc00000);
+  if (last_cta(&I.ctr[1])) {
+    if (threadIdx.x == 0) {
+      *I.gen = g + 1;
       I.ctr[1] = 0u;
     }
   }
@@ -1510,8 +1661,11 @@ static Variant variant_of(const InstDev &I) {
   if (I.obj == OBJ_MULTI_THG) return variant_multi<OBJ_MULTI_THG>(I);
   if (I.obj == OBJ_MULTI_SHG) return variant_multi<OBJ_MULTI_SHG>(I);
   const bool dual = I.c <= 8;
-  if (I.compensated) return dual ? variant2<true, true>(I) : variant2<true, false>(I);
-  return dual ? variant2<false, true>(I) : variant2<false, false>(I);
+  Variant v = I.compensated ? (dual ? variant2<true, true>(I) : variant2<true, false>(I))
+                            : (dual ? variant2<false, true>(I) : variant2<false, false>(I));
+  if (I.combine == 2)  // the discrete GWO (launches form): its own GWO kernel
+    v.gwo = I.compensated ? (const void *)k_gwo_disc<true> : (const void *)k_gwo_disc<false>;
+  return v;
 }
 
 // the shared-memory attribute of a persistent variant is the same for every
@@ -1609,8 +1763,8 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     if (q.G < 1) return fail(QPM_ERR_ARG, "qpm_create: G < 1");
     if (!(q.F >= 0.f && q.F <= 2.f)) return fail(QPM_ERR_ARG, "qpm_create: F outside [0, 2]");
     if (!(q.CR >= 0.f && q.CR <= 1.f)) return fail(QPM_ERR_ARG, "qpm_create: CR outside [0, 1]");
-    if (q.gwo_combine != 0 && q.gwo_combine != 1)
-      return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0 or 1");
+    if (q.gwo_combine < 0 || q.gwo_combine > 2)
+      return fail(QPM_ERR_ARG, "qpm_create: gwo_combine must be 0, 1 or 2");
     if (q.team != 0 && q.team != 32 && q.team != 64 && q.team != 128 && q.team != 256 &&
         q.team != 512)
       return fail(QPM_ERR_ARG, "qpm_create: team must be 0, 32, 64, 128, 256 or 512");
@@ -1695,6 +1849,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     total += align_up(6 * NP * sizeof(unsigned long long), 256);
     total += align_up(NP * sizeof(unsigned long long), 256);  // DE survivor keys
     total += 2 * align_up((size_t)(q.G + 1) * sizeof(float), 256);  // F history, F base
+    total += align_up((size_t)q.G * 7 * sizeof(uint32_t), 256);     // discrete GWO thresholds
     total += 256 + 256 + 256;  // ctr, gen, best
   }
   const size_t desc_off = total;
@@ -1723,7 +1878,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     I.mtab[0] = I.table;
     I.mkonst[0] = I.konst;
     I.konst64 = (double2 *)take(4 * sizeof(double2));
-    I.lead = (int32_t *)take(3 * sizeof(int32_t));
+    I.lead = (int32_t *)take(4 * sizeof(int32_t));  // four for the discrete GWO
     I.topk = (unsigned long long *)take(6 * NP * sizeof(unsigned long long));
     I.dekey = (unsigned long long *)take(NP * sizeof(unsigned long long));
     {
@@ -1732,6 +1887,10 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
       I.Fsched = st->params[k].f_schedule ? fs : nullptr;
       I.Fbase = st->params[k].f_schedule == 2 ? fb : nullptr;
       I.adaptive = st->params[k].f_schedule == 2 ? 1 : 0;
+    }
+    {
+      uint32_t *th = (uint32_t *)take((size_t)I.G * 7 * sizeof(uint32_t));
+      I.dthr = I.combine == 2 ? th : nullptr;
     }
     I.ctr = (unsigned *)take(4 * sizeof(unsigned));
     I.gen = (int32_t *)take(sizeof(int32_t));
@@ -1751,6 +1910,28 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
     // generations 0 .. G; from F (f_schedule 1), or from the top 0.1 of the adaptive
     // F's interval (f_schedule 2: its intermediate state's values in Fbase, and its
     // first generation's F in the history)
+    // thresholds of the discrete GWO (Sec. 3.1.2): per generation g (tau = g / G) the
+    // social rate, the disturbance and P(+1) for 0 .. 4 leaders at +1, as 16-bit
+    // thresholds floor(65536 p), evaluated in FP64
+    for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
+      if (!st->h[k].dthr) continue;
+      const int G = st->h[k].G;
+      std::vector<uint32_t> th((size_t)G * 7);
+      for (int g = 0; g < G; ++g) {
+        const double tau = (double)g / (double)G;
+        const double delta = 0.5 * (1.0 - tau), sigma = 0.3 * (1.0 - tau);
+        const double mu = 0.1 * (1.0 - tau) + 0.01 * tau;
+        th[7 * (size_t)g] = (uint32_t)std::floor(65536.0 * sigma);
+        th[7 * (size_t)g + 1] = (uint32_t)std::floor(65536.0 * mu);
+        for (int n = 0; n <= 4; ++n) {
+          const double m = n > 2 ? 1.0 : (n < 2 ? 0.0 : 0.5);
+          const double qn = (1.0 - tau) * ((double)n / 4.0) + tau * m;
+          th[7 * (size_t)g + 2 + n] = (uint32_t)std::floor(65536.0 * ((1.0 - delta) * qn + 0.5 * delta));
+        }
+      }
+      e = cudaMemcpy((void *)st->h[k].dthr, th.data(), sizeof(uint32_t) * th.size(),
+                     cudaMemcpyHostToDevice);
+    }
     for (int k = 0; k < n_inst && e == cudaSuccess; ++k) {
       if (!st->h[k].Fsched) continue;
       const int G = st->h[k].G;
@@ -1871,9 +2052,9 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     QPM_CUDA(cudaGraphLaunch(st->gexec, s));
   } else if (mode == QPM_RUN_PERSISTENT) {
     for (int k = 0; k < st->n; ++k)
-      if (st->h[k].obj >= OBJ_MULTI_THG)
-        return fail(QPM_ERR_UNSUPPORTED,
-                    "the multi-wavelength objectives run in the launches and graph forms");
+      if (st->h[k].obj >= OBJ_MULTI_THG || st->h[k].combine == 2)
+        return fail(QPM_ERR_UNSUPPORTED, "the multi-wavelength objectives and the discrete GWO "
+                                         "run in the launches and graph forms");
     QPM_CUDA(cudaMemsetAsync(st->bar, 0, 3 * sizeof(unsigned), s));
     for (int k = 0; k < st->n; ++k) {
       InstDev I = st->h[k];
@@ -1895,9 +2076,9 @@ extern "C" qpm_status qpm_run(qpm_state *st, int32_t generations, int32_t mode,
     }
   } else if (mode == QPM_RUN_BATCHED) {
     for (int k = 0; k < st->n; ++k)
-      if (st->h[k].obj >= OBJ_MULTI_THG)
-        return fail(QPM_ERR_UNSUPPORTED,
-                    "the multi-wavelength objectives run in the launches and graph forms");
+      if (st->h[k].obj >= OBJ_MULTI_THG || st->h[k].combine == 2)
+        return fail(QPM_ERR_UNSUPPORTED, "the multi-wavelength objectives and the discrete GWO "
+                                         "run in the launches and graph forms");
     for (int k = 0; k < st->n; ++k)
       if (st->h[k].T != 32)
         return fail(QPM_ERR_UNSUPPORTED, "batched form needs 32 threads per individual (team 32)");
@@ -1989,6 +2170,8 @@ extern "C" qpm_status qpm_set_objective(qpm_state *st, int32_t inst, const qpm_o
   QPM_CUDA(cudaGetDevice(&dev));
   if (dev != st->dev) return fail(QPM_ERR_STATE, "state belongs to another device");
   InstDev &I = st->h[inst];
+  if (multi && I.combine == 2)
+    return fail(QPM_ERR_UNSUPPORTED, "qpm_set_objective: the discrete GWO optimises the single kinds");
   if (st->objmem[inst]) {
     QPM_CUDA(cudaFree(st->objmem[inst]));
     st->objmem[inst] = nullptr;

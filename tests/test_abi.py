@@ -50,7 +50,8 @@ def test_argument_errors_without_device(qlib):
     p = q.Problem(16, 1.0, 2.0)
     bad = [q.Params(3, 10, 0.5, 0.9, 1, 0, 0), q.Params(8, 0, 0.5, 0.9, 1, 0, 0),
            q.Params(8, 10, 2.5, 0.9, 1, 0, 0), q.Params(8, 10, 0.5, 1.5, 1, 0, 0),
-           q.Params(8, 10, 0.5, 0.9, 1, 2, 0), q.Params(8, 10, 0.5, 0.9, 1, 0, 0, 48)]
+           q.Params(8, 10, 0.5, 0.9, 1, 3, 0), q.Params(8, 10, 0.5, 0.9, 1, 0, 0, 48),
+           q.Params(8, 10, 0.5, 0.9, 1, 0, 0, 0, 3)]
     for prm in bad:
         assert qlib.qpm_create(ctypes.byref(p), ctypes.byref(prm), 1, ctypes.byref(st)) == 1
         assert not st.value

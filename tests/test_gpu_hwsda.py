@@ -465,3 +465,33 @@ def test_objective_errors(q):
     st.run(2, q.RUN_GRAPH)
     torch.cuda.synchronize()
     st.close()
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_discrete_gwo_lockstep(q, orc, comp):
+    """The four-leader discrete GWO of Sec. 3.1.2 (gwo_combine 2) follows the oracle bit
+    for bit in the launches and graph forms (short rows read both slots, long rows
+    stage them); the forms that do not support it say so."""
+    import torch
+    for N, NP, G in ((333, 24, 12), (5000, 20, 4)):
+        k1, k2 = 2 * math.pi / 7.3, 2 * math.pi / 1.4
+        for mode in (0, 1):
+            st, tr = make(q, N, k1, k2, NP, G, seed=12, combine=2, comp=comp)
+            st.init()
+            st.run(G, mode)
+            X, f, D = snapshot(st)
+            trace = tr.cpu().numpy()
+            st.close()
+            cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 12, 0, 2)
+            Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
+            assert np.array_equal(X, Xo), (N, mode)
+            assert lockstep_errors(trace, tro, N).max() < 2 * TOL_D
+            # four leaders per generation: four NaN entries in every candidate trace
+            cand = trace[NP:].reshape(G, 2, NP)[:, 1]
+            assert np.all(np.isnan(cand).sum(axis=1) == 4)
+    st, _ = make(q, 100, 1.0, 2.0, 8, 4, combine=2, trace=False)
+    st.init()
+    with pytest.raises(q.QpmError) as e:
+        st.run(1, q.RUN_PERSISTENT)
+    assert e.value.status == 4
+    st.close()

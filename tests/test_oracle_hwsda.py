@@ -497,3 +497,72 @@ def test_shg_multi_objective_against_exhaustive_search(orc):
     f0 = orc.objective_rows(cfg, X0).min()
     X, f = orc.hwsda_run(cfg, 0.0, 0.0)
     assert fmin - 1e-9 <= f.min() <= f0
+
+
+# ------------------------------------------------ four-leader discrete GWO (Sec. 3.1.2)
+def test_discrete_gwo_thresholds_at_both_ends(orc):
+    """Start of the run (tau = 0): dispersion 0.5, social rate 0.3, disturbance 0.1 and
+    P(+1) = 0.5 n/4 + 0.25; end (tau = 1): no dispersion, no social learning,
+    disturbance 0.01 and the leaders' majority (a tie stays at 1/2)."""
+    social, flip, plus = orc.discrete_thresholds(0, 100)
+    assert social == 19660 and flip == 6553  # floor(65536 * 0.3), floor(65536 * 0.1)
+    assert plus == [16384, 24576, 32768, 40960, 49152]
+    social, flip, plus = orc.discrete_thresholds(100, 100)
+    assert social == 0 and flip == 655 and plus == [0, 0, 32768, 65536, 65536]
+
+
+def test_discrete_gwo_candidate_frequencies(orc):
+    """Each candidate gene is +-1; for every count n of the four leaders at +1, the
+    frequency of +1 over many genes equals what the rule implies:
+      (1 - sigma) [(1 - mu) P_n + mu (1 - P_n)] + sigma [(1 - mu) n/4 + mu (1 - n/4)]
+    (copy a random leader with probability sigma, else +1 with probability P_n, then
+    flip with probability mu), within 5 binomial standard deviations."""
+    import numpy as np
+    NP, N, G, g = 6, 20000, 50, 20
+    cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 3, combine=2)
+    rng = np.random.default_rng(1)
+    X = rng.uniform(-1, 1, (NP, N)).astype(np.float32)
+    lead = np.array([0, 1, 2, 3], dtype=np.int32)
+    Y = orc.gwo_candidates(cfg, g, X, lead)
+    assert np.array_equal(Y[:4], X[:4])
+    cand = Y[4:]
+    assert np.all(np.abs(cand) == 1.0)
+    n = (X[:4] >= 0).sum(axis=0)
+    tau = g / G
+    sigma, mu = 0.3 * (1 - tau), 0.1 * (1 - tau) + 0.01 * tau
+    _, _, plus = orc.discrete_thresholds(g, G)
+    for k in range(5):
+        sel = n == k
+        if sel.sum() < 200:
+            continue
+        Pn = plus[k] / 65536.0
+        want = (1 - sigma) * ((1 - mu) * Pn + mu * (1 - Pn)) + sigma * ((1 - mu) * k / 4 + mu * (1 - k / 4))
+        got = (cand[:, sel] > 0).mean()
+        m = cand[:, sel].size
+        assert abs(got - want) <= 5 * math.sqrt(want * (1 - want) / m), (k, got, want)
+
+
+def test_discrete_gwo_loop(orc):
+    """The hybrid loop with the discrete four-leader GWO: four leaders (a stable sort of
+    the DE survivors), the best never lost, every moved wolf's accepted genes +-1."""
+    import numpy as np
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.SMALL
+    G = 30
+    cfg = orc.make_cfg(c["NP"], c["N"], G, c["F"], c["CR"], c["seed"], combine=2)
+    X = orc.init_population(cfg)
+    f64 = orc.objective_rows(cfg, X, c["kappa1"], c["kappa2"])  # re^2 + im^2, as the loop
+    fdec = f64.astype(np.float32)
+    best = f64.max()
+    for g in range(G):
+        U = orc.de_trials(cfg, g, X)
+        fu = orc.objective_rows(cfg, U, c["kappa1"], c["kappa2"])
+        surv = np.where(fu >= f64, fu, f64)
+        Xn, fdec, f64n, _, _, lead = orc.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g, X, fdec, f64)
+        assert list(lead) == list(np.lexsort((np.arange(c["NP"]), -surv))[:4])
+        moved = [i for i in range(c["NP"]) if i not in lead and f64n[i] != surv[i]]
+        for i in moved:
+            assert np.all(np.abs(Xn[i]) == 1.0)
+        X, f64 = Xn, f64n
+        assert f64.max() >= best
+        best = f64.max()
