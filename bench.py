@@ -113,9 +113,9 @@ class ClockSampler:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:k_persist -c 1 python -m paper_2511_01255_gb300.profile_run \
 #       --workload paper --form persistent --gens 2000 --reps 1
-# on the current kernel: 1334272 read + 348416 written.  The 2 MB population and
+# on the current kernel: 1501696 read + 329984 written.  The 2 MB population and
 # the phasor table stay in L2; DRAM sees little more than the first touch.
-K_PERSIST_DRAM_BYTES = 1334272 + 348416
+K_PERSIST_DRAM_BYTES = 1501696 + 329984
 
 
 PHILOX_CALLS_PER_GENE_GEN = 0.25 + 0.75  # crossover word + three GWO words, 4 genes per call

@@ -4,8 +4,10 @@
 
 workloads: small (N=16, NP=32), paper (N=1000, NP=256, compensated),
 precision (N=1e5, NP=1024, compensated), eval (qpm_eval of 1024 random rows
-of N=1e5).  forms: launches, graph, persistent.  Prints the mean time per
-repetition measured with CUDA events.
+of N=1e5), batch, relaxed, latency (the grid barrier of the persistent form over
+several CTA counts and a dependent L2 load, from qpm_measure_latency).  forms:
+launches, graph, persistent, batched.  Prints the mean time per repetition
+measured with CUDA events.
 """
 import argparse
 import os
@@ -22,7 +24,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="paper",
-                    choices=["small", "paper", "precision", "eval", "batch", "relaxed"])
+                    choices=["small", "paper", "precision", "eval", "batch", "relaxed", "latency"])
     ap.add_argument("--form", default="launches",
                     choices=["launches", "graph", "persistent", "batched"])
     ap.add_argument("--gens", type=int, default=20)
@@ -34,6 +36,14 @@ def main():
     ap.add_argument("--cluster", type=int, default=1, help="batched form: CTAs per cluster")
     a = ap.parse_args()
     q.lib()
+    if a.workload == "latency":
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        for ctas in (32, nsm, 256, 4 * nsm):
+            best = min(q.qpm_measure_latency(0, ctas) for _ in range(max(1, a.reps)))
+            print(f"grid barrier, {ctas} CTAs of 256 threads: {best / 1e3:.3f} us (best of {max(1, a.reps)})")
+        best = min(q.qpm_measure_latency(1) for _ in range(max(1, a.reps)))
+        print(f"dependent L2 load: {best:.1f} ns (best of {max(1, a.reps)})")
+        return
     if a.workload == "relaxed":
         c = W.RELAXED
         th = torch.from_numpy(W.relaxed_theta(c["B"], c["N"], seed=c["seed"])).cuda()
