@@ -540,6 +540,18 @@ def run_gpu(args):
                              "N = 3000 on an RTX 4070 (Sec. 5); a different GPU and unknown NP, "
                              "context only"}
 
+    # ------------- free run of the 16-domain workload: the population after every generation
+    cs = W.SMALL
+    prm_s = q.Params(cs["NP"], cs["G"], cs["F"], cs["CR"], cs["seed"], 0, cs["compensated"])
+    sts = q.State([(cs["N"], cs["kappa1"], cs["kappa2"])], [prm_s])
+    sts.init()
+    pops = [sts.population()[0].cpu().numpy()]
+    for _ in range(cs["G"]):
+        sts.step()
+        pops.append(sts.population()[0].cpu().numpy())
+    sts.close()
+    samples["free_run"] = pops
+
     # ---------------------------------------------- end to end through qpm_solve
     best_host = torch.empty(N, dtype=torch.float32).pin_memory()
     d64_host = torch.empty(2, dtype=torch.float64).pin_memory()
@@ -633,6 +645,7 @@ def run_gpu(args):
         line["adjoint"]["error_vs_oracle"] = errs["adjoint"]
         for name in designs:
             designs[name]["error_vs_oracle"] = errs["designs." + name]
+        line["free_run"] = free_run_divergence(samples["free_run"])
     print(json.dumps(line), flush=True)
 
 
@@ -752,7 +765,7 @@ def oracle_errors(samples):
                               "G_k's error, so the scale is K G0)"}
 
     out = {k: (design_err(v) if k.startswith("designs.") else rows_err(v))
-           for k, v in samples.items() if k != "adjoint"}
+           for k, v in samples.items() if k not in ("adjoint", "free_run")}
     a = samples["adjoint"]
     g_ref, D_ref = oracle.grad_relaxed(a["theta"].astype(np.float64), a["kappa1"], a["kappa2"])
     g_ref = g_ref[a["cols"]]
@@ -763,6 +776,39 @@ def oracle_errors(samples):
                       "definition": "row: a relaxed two-tone design (theta = 3 sign pattern); "
                                     "grad error = max_k |g_gpu - g_oracle| / max_k |g_oracle|"}
     return out
+
+
+def free_run_divergence(pops):
+    """The GPU's free run of the 16-domain workload (its own FP32 decisions) against
+    the oracle's free run (FP64 decisions) from the same initial population: the
+    first generation after which the populations differ (a near-tie decided
+    differently; None if they never do) and the gap between the two final bests'
+    FP64 fitness."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.SMALL
+    cfg = oracle.make_cfg(c["NP"], c["N"], c["G"], c["F"], c["CR"], c["seed"])
+    X = oracle.init_population(cfg)
+    same_init = bool(np.array_equal(X, pops[0]))
+    f64 = oracle.objective_rows(cfg, X, c["kappa1"], c["kappa2"])
+    fdec = f64.astype(np.float32)
+    first = None
+    for g in range(c["G"]):
+        X, fdec, f64, _, _, _ = oracle.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g, X, fdec, f64)
+        if first is None and not np.array_equal(X, pops[g + 1]):
+            first = g
+    f_gpu = oracle.objective_rows(cfg, pops[-1], c["kappa1"], c["kappa2"]).max()
+    f_orc = f64.max()
+    best, _ = oracle.bruteforce(c["N"], c["kappa1"], c["kappa2"])
+    return {"workload": c["name"], "same_initial_population": same_init,
+            "first_divergence_generation": first, "generations": c["G"],
+            "final_best_f64_gpu": float(f_gpu), "final_best_f64_oracle": float(f_orc),
+            "final_best_gap_rel": float(abs(f_gpu - f_orc) / f_orc),
+            "exhaustive_optimum": float(best),
+            "note": "free runs: each side decides selections and leaders in its own precision "
+                    "(GPU FP32, oracle FP64); lockstep parity is tested separately"}
 
 
 def cpu_closed_form(budget_s=2.0):

@@ -93,7 +93,7 @@ typedef struct {
                           population maximum), so the decision is independent of any
                           summation order.  NP <= 2^23.  A run resumed with
                           qpm_set_population continues from the F history the state
-                          holds (qpm_get_F) */
+                          holds (qpm_get_F; another state takes it with qpm_set_F) */
 } qpm_params;
 
 /* The fitness an optimiser state works on (qpm_set_objective; no call: QPM_OBJ_THG).
@@ -316,6 +316,12 @@ qpm_status qpm_instance_shape(const qpm_state *st, int32_t inst, int32_t *N_out,
  * generation g).  Enqueued on `stream`.  Errors: bad state, instance or NULL output ->
  * QPM_ERR_ARG; before qpm_init -> QPM_ERR_STATE. */
 qpm_status qpm_get_F(qpm_state *st, int32_t inst, float *F_out, qpm_stream_t stream);
+
+/* Restore the F history of instance `inst` from F_in (device float [G + 1], e.g. from
+ * qpm_get_F of the run being resumed), so that an adaptive-F run (f_schedule 2) resumed
+ * with qpm_set_population in another state uses the F it would have used.  Enqueued on
+ * `stream`.  Errors: bad state, instance or NULL input, or f_schedule 0 -> QPM_ERR_ARG. */
+qpm_status qpm_set_F(qpm_state *st, int32_t inst, const float *F_in, qpm_stream_t stream);
 
 /* generation counter of the state as seen by the host (host int32 out) */
 qpm_status qpm_generation(const qpm_state *st, int32_t *g_out);

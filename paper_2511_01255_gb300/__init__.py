@@ -18,7 +18,7 @@ __all__ = [
     "qpm_release_caches", "qpm_measure_issue_peak", "qpm_measure_latency", "qpm_selfcheck", "qpm_relaxed_saved_floats", "relaxed_saved", "qpm_deff_relaxed_fwd",
     "qpm_deff_relaxed_bwd", "deff_relaxed",
     "qpm_create", "qpm_init", "qpm_step", "qpm_run", "qpm_destroy", "qpm_generation", "qpm_team_of",
-    "qpm_instance_shape", "qpm_get_F",
+    "qpm_instance_shape", "qpm_get_F", "qpm_set_F",
     "qpm_set_batch_cluster",
     "qpm_get_population", "qpm_set_population", "qpm_get_best", "qpm_polish_leaders", "qpm_set_trace", "qpm_set_wait_timeout_ns",
     "qpm_solve", "State", "RUN_LAUNCHES", "RUN_GRAPH", "RUN_PERSISTENT", "RUN_BATCHED",
@@ -94,6 +94,7 @@ def lib(build=True):
             "qpm_team_of": ([_P, i32, _P], ctypes.c_int),
             "qpm_instance_shape": ([_P, i32, _P, _P, _P], ctypes.c_int),
             "qpm_get_F": ([_P, i32, _P, _P], ctypes.c_int),
+            "qpm_set_F": ([_P, i32, _P, _P], ctypes.c_int),
             "qpm_set_objective": ([_P, i32, _P], ctypes.c_int),
             "qpm_set_batch_cluster": ([_P, i32], ctypes.c_int),
             "qpm_get_population": ([_P, i32, _P, i64, _P, _P, _P], ctypes.c_int),
@@ -440,6 +441,13 @@ def qpm_get_F(st, inst=0, F_out=None, stream=None):
     _out(F_out, "F_out", G + 1, optional=False)
     _check(lib().qpm_get_F(st, int(inst), _ptr(F_out), _stream(stream)))
     return F_out
+
+
+def qpm_set_F(st, inst, F_in, stream=None):
+    """Restore the F history of instance `inst` (float32 CUDA [G + 1], from qpm_get_F)."""
+    _, _, G = qpm_instance_shape(st, inst)
+    _out(F_in, "F_in", G + 1, optional=False)
+    _check(lib().qpm_set_F(st, int(inst), _ptr(F_in), _stream(stream)))
 
 
 def qpm_get_population(st, inst, genes_out=None, fit_out=None, d_eff_out=None, stream=None):

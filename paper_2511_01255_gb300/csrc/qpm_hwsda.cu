@@ -2259,6 +2259,15 @@ extern "C" qpm_status qpm_get_F(qpm_state *st, int32_t inst, float *F_out, qpm_s
   return QPM_OK;
 }
 
+extern "C" qpm_status qpm_set_F(qpm_state *st, int32_t inst, const float *F_in, qpm_stream_t stream) {
+  if (!st || inst < 0 || inst >= st->n || !F_in) return fail(QPM_ERR_ARG, "bad arguments");
+  const InstDev &I = st->h[inst];
+  if (!I.Fsched) return fail(QPM_ERR_ARG, "qpm_set_F: constant F (f_schedule 0) has no history");
+  QPM_CUDA(cudaMemcpyAsync(I.Fsched, F_in, sizeof(float) * (size_t)(I.G + 1),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return QPM_OK;
+}
+
 extern "C" qpm_status qpm_generation(const qpm_state *st, int32_t *g_out) {
   if (!st || !g_out) return fail(QPM_ERR_ARG, "NULL pointer");
   *g_out = st->g;

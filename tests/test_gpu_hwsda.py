@@ -495,3 +495,68 @@ def test_discrete_gwo_lockstep(q, orc, comp):
         st.run(1, q.RUN_PERSISTENT)
     assert e.value.status == 4
     st.close()
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_checkpoint_resume_with_adaptive_F(q, mode):
+    """With the adaptive F the checkpoint also carries the F history (qpm_get_F); a fresh
+    state given the population (qpm_set_population) and the history (qpm_set_F) at
+    generation 15 continues exactly like the uninterrupted 30-generation run."""
+    import torch
+    N, NP, G = 700, 40, 30
+    k1, k2 = 2 * math.pi / 6.9, 2 * math.pi / 1.55
+    st, _ = make(q, N, k1, k2, NP, G, seed=22, comp=1, trace=False, f_schedule=2)
+    st.init()
+    st.run(G, mode)
+    Xa, fa, _ = snapshot(st)
+    Fa = q.qpm_get_F(st.h, 0).cpu().numpy()
+    st.close()
+    st, _ = make(q, N, k1, k2, NP, G, seed=22, comp=1, trace=False, f_schedule=2)
+    st.init()
+    st.run(15, mode)
+    Xc, _, _ = st.population()
+    Fc = q.qpm_get_F(st.h, 0).clone()
+    torch.cuda.synchronize()
+    st.close()
+    st2, _ = make(q, N, k1, k2, NP, G, seed=22, comp=1, trace=False, f_schedule=2)
+    st2.init()
+    q.qpm_set_population(st2.h, 0, Xc, 15)
+    q.qpm_set_F(st2.h, 0, Fc)
+    st2.run(G - 15, mode)
+    Xb, fb, _ = snapshot(st2)
+    Fb = q.qpm_get_F(st2.h, 0).cpu().numpy()
+    st2.close()
+    assert np.array_equal(Xa, Xb) and np.array_equal(fa, fb) and np.array_equal(Fa, Fb)
+
+
+def test_free_run_against_the_oracle(q, orc):
+    """Free runs (no lockstep) of the 16-domain workload: the GPU decides in FP32, the
+    oracle in FP64.  Both start from the same population; the first generation after
+    which they differ is reported (a near-tie decided differently), and until then
+    they agree bit for bit.  Both final bests are valid designs no better than the
+    exhaustive optimum."""
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    c = W.SMALL
+    prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, c["compensated"])
+    cfg = orc.make_cfg(c["NP"], c["N"], c["G"], c["F"], c["CR"], c["seed"])
+    with q.State([(c["N"], c["kappa1"], c["kappa2"])], [prm]) as st:
+        st.init()
+        pops = [st.population()[0].cpu().numpy()]
+        for _ in range(c["G"]):
+            st.step()
+            pops.append(st.population()[0].cpu().numpy())
+    X = orc.init_population(cfg)
+    assert np.array_equal(X, pops[0])
+    f64 = orc.objective_rows(cfg, X, c["kappa1"], c["kappa2"])
+    fdec = f64.astype(np.float32)
+    first = None
+    for g in range(c["G"]):
+        X, fdec, f64, _, _, _ = orc.hwsda_generation(cfg, c["kappa1"], c["kappa2"], g, X, fdec, f64)
+        if first is None and not np.array_equal(X, pops[g + 1]):
+            first = g
+    best, _ = orc.bruteforce(c["N"], c["kappa1"], c["kappa2"])
+    f_gpu = orc.objective_rows(cfg, pops[-1], c["kappa1"], c["kappa2"]).max()
+    print(f"free run: first divergence at generation {first}; final best GPU {f_gpu:.6g}, "
+          f"oracle {f64.max():.6g}, optimum {best:.6g}")
+    assert f_gpu <= best * (1 + 1e-12) and f64.max() <= best * (1 + 1e-12)
