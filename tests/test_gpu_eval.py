@@ -295,3 +295,55 @@ def test_multi_wavelength_with_a_full_table_cache(q):
         a, b = D.cpu().numpy(), Dm.cpu().numpy()[:, k]
         assert deff_err(b, a[:, 0] + 1j * a[:, 1], N).max() < TOL_D
     q.qpm_release_caches()
+
+
+def test_table_cache_under_concurrent_host_threads(q):
+    """Four host threads, each on its own stream, evaluate 40 distinct problems each (160
+    in all, more than the 64 the cache holds, so tables are evicted while other threads
+    are between their lookups and launches).  The cache's lock is held from a call's
+    first lookup to its last launch, so every result equals the single-threaded one,
+    bit for bit."""
+    import threading
+
+    import torch
+    from paper_2511_01255_gb300 import workloads as W
+    N, NP = 777, 48
+    X = torch.from_numpy(W.random_genes(NP, N, seed=99)).cuda()
+    probs = [[(N, 0.3 + 0.013 * (40 * t + k), 2.0 + 0.007 * k) for k in range(40)] for t in range(4)]
+    q.qpm_release_caches()
+    ref = {}
+    for t in range(4):
+        for p in probs[t]:
+            D = torch.empty((NP, 2), device="cuda")
+            q.qpm_eval(p[0], p[1], p[2], X, D)
+            torch.cuda.synchronize()
+            ref[p] = D.cpu().numpy()
+    q.qpm_release_caches()
+    out, errors = {}, []
+
+    def work(t):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                res = []
+                for p in probs[t]:
+                    D = torch.empty((NP, 2), device="cuda")
+                    if t % 2:
+                        q.qpm_eval_shg(p[0], p[1], X, torch.empty((NP, 2), device="cuda"))
+                    q.qpm_eval(p[0], p[1], p[2], X, D)
+                    res.append((p, D))
+                s.synchronize()
+                for p, D in res:
+                    out[p] = D.cpu().numpy()
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=work, args=(t,)) for t in range(4)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert not errors, errors
+    for p, D in ref.items():
+        assert np.array_equal(out[p], D), p
+    q.qpm_release_caches()
