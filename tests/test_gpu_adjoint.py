@@ -60,17 +60,23 @@ def test_relaxed_fwd_bwd_against_oracle(q, orc, N):
         assert grad_err(g[r], ref_g) < TOL_G
 
 
-@pytest.mark.parametrize("ld_extra,ldg_extra", [(0, 0), (1, 3), (4, 1)])
-def test_relaxed_ragged_batch_and_strided_rows(q, orc, ld_extra, ldg_extra):
-    """B = 130 rows: a warp takes 64 rows, two per lane, so the last warp holds rows
-    128-129 in its first half and none in its second; N = 1000 domains in rows of
-    N + ld_extra floats (16-byte aligned rows take the asynchronous-copy path, the
-    others register loads) and gradients written into rows of N + ldg_extra floats."""
+@pytest.mark.parametrize("N,ld_extra,ldg_extra", [(1000, 0, 0), (1000, 1, 3), (1000, 4, 1),
+                                                   (1000, 1, 0), (4097, 3, 3)])
+def test_relaxed_ragged_batch_and_strided_rows(q, orc, N, ld_extra, ldg_extra):
+    """B = 130 rows: a warp takes 32 rows (lane = row), so the last warp holds rows
+    128-129 and 30 rows past the end; N domains in rows of N + ld_extra floats
+    (rows whose pitch is a multiple of 16 bytes arrive as TMA tiles, the others
+    through registers) and gradients written into rows of N + ldg_extra floats (TMA
+    tile stores for a pitch that is a multiple of 16 bytes, plain stores otherwise).
+    N = 4097 in rows of 4100 floats: the last segment (160 domains from 4000) has a
+    step with one domain inside the row and one entirely past it.  The padding holds
+    NaN, which must neither be read into the sums nor be overwritten."""
     import torch
     from paper_2511_01255_gb300 import workloads as W
-    B, N = 130, 1000
+    B = 130
     theta = W.relaxed_theta(B, N, seed=7)
-    big = torch.zeros((B, N + ld_extra), dtype=torch.float32, device="cuda")
+    # NaN in the padding: nothing past a row's N floats may enter the sums
+    big = torch.full((B, N + ld_extra), float("nan"), dtype=torch.float32, device="cuda")
     big[:, :N] = torch.from_numpy(theta).cuda()
     th = big[:, :N]
     D = torch.empty((B, 2), device="cuda")
@@ -82,6 +88,7 @@ def test_relaxed_ragged_batch_and_strided_rows(q, orc, ld_extra, ldg_extra):
     torch.cuda.synchronize()
     D, gb = D.cpu().numpy(), gbig.cpu().numpy()
     assert np.all(gb[:, N:] == 7.0)  # nothing written past the rows
+    assert np.all(np.isfinite(D)) and np.all(np.isfinite(gb[:, :N]))
     for r in (0, 31, 32, 63, 64, 127, 128, 129):
         ref_g, ref_D = orc.grad_relaxed(theta[r].astype(np.float64), K1, K2)
         assert deff_err(D[r:r + 1], np.array([ref_D]), N).max() < TOL_D, r
