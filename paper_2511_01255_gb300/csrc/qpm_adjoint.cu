@@ -66,6 +66,21 @@ static int rx_nseg(int N) { return (N + rx_seg_len(N) - 1) / rx_seg_len(N); }
 // saved block of a row: [A (2 floats), 2 unused, then per segment 8 floats]
 static int64_t rx_saved_floats(int N) { return 4 + 8 * (int64_t)rx_nseg(N); }
 
+// Packed FP32 pairs (sm_100+): one 64-bit register pair holds (re, im) of a complex
+// sum, and add/mul/fma.rn.f32x2 apply the IEEE-rounded single operation to both
+// halves in one instruction.  The forward keeps its a-, b- and d^2 q-sums this way
+// (operands straight from the phasor loads); its a P product stays scalar.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float lo, float hi) {
+  f2x r; asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi)); return r; }
+__device__ __forceinline__ float2 f2_unpack(f2x v) {
+  float2 r; asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v)); return r; }
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x r; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c)); return r; }
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
 // ------------------------------------------------------------- tanh and tiles
 __device__ __forceinline__ float ex2_approx(float y) {
   float r;
@@ -250,6 +265,8 @@ __device__ __forceinline__ void fwd_sweep(const CUtensorMap *tmap, const float *
   const int nsteps = sh.L / RX_STEP;
   bool ok = true;
   int t_fail = -1;  // first step whose tile did not arrive in time
+  f2x A2 = 0ull, B2 = 0ull, E2 = 0ull;
+  float Cx = 0.f, Cy = 0.f;
   for (int t = 0; t < nsteps; ++t) {
     float4 *T = wt + (t % NST) * (RX_TILE / 16);
     if constexpr (TMA) {
@@ -281,12 +298,18 @@ __device__ __forceinline__ void fwd_sweep(const CUtensorMap *tmap, const float *
       for (int j = 0; j < 4; ++j) {
         float rc;
         const float d = tanh_r(th[j], rc);
-        const float4 p = pe[4 * c4 + j].p;
-        const float2 q = pe[4 * c4 + j].q;
-        mono_push(acc, d, p);
-        const float d2 = d * d;
-        E.x = fmaf(d2, q.x, E.x);
-        E.y = fmaf(d2, q.y, E.y);
+        const ulonglong2 pp = *(const ulonglong2 *)&pe[4 * c4 + j].p;
+        const f2x qq = *(const f2x *)&pe[4 * c4 + j].q;
+        const f2x dd = f2_pack(d, d);
+        const f2x a = f2_mul(dd, pp.y);
+        const float2 av = f2_unpack(a), bv = f2_unpack(B2);
+        Cx = fmaf(av.x, bv.x, Cx);
+        Cx = fmaf(-av.y, bv.y, Cx);
+        Cy = fmaf(av.x, bv.y, Cy);
+        Cy = fmaf(av.y, bv.x, Cy);
+        A2 = f2_add(A2, a);
+        B2 = f2_fma(dd, pp.x, B2);
+        E2 = f2_fma(f2_mul(dd, dd), qq, E2);
       }
     }
     __syncwarp();  // every lane has read T before the copy NST - 1 steps on refills it
@@ -294,6 +317,10 @@ __device__ __forceinline__ void fwd_sweep(const CUtensorMap *tmap, const float *
   if constexpr (TMA) {
     if (!ok) drain_loads(bar0, NST, t_fail, nsteps);
   }
+  acc.A = f2_unpack(A2);
+  acc.B = f2_unpack(B2);
+  acc.C = make_float2(Cx, Cy);
+  E = f2_unpack(E2);
 }
 
 // exclusive prefix over lanes of a float2 (lane 0 gets 0); total in `tot`
