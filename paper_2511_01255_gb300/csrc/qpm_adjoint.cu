@@ -574,10 +574,11 @@ static __global__ void __launch_bounds__(RX_WPC * 32, 5)
         const float2 q = pe[4 * c4 + j].q;
         Rs.x = fmaf(-d, p.z, Rs.x);  // R_k: sum of a after this domain
         Rs.y = fmaf(-d, p.w, Rs.y);
-        // w = p2 P + p1 R
-        const float wr = p.z * P.x - p.w * P.y + (p.x * Rs.x - p.y * Rs.y);
-        const float wi = p.z * P.y + p.w * P.x + (p.x * Rs.y + p.y * Rs.x);
-        const float s = (ur * wr - ui * wi) + d * (vr * q.x - vi * q.y);
+        // w = p2 P + p1 R and the bracket, as chains of fused multiply-adds
+        const float wr = fmaf(p.z, P.x, fmaf(-p.w, P.y, fmaf(p.x, Rs.x, -p.y * Rs.y)));
+        const float wi = fmaf(p.z, P.y, fmaf(p.w, P.x, fmaf(p.x, Rs.y, p.y * Rs.x)));
+        const float vq = fmaf(vr, q.x, -vi * q.y);
+        const float s = fmaf(ur, wr, fmaf(-ui, wi, d * vq));
         out[j] = s * fmaf(-rc, rc, rc);
         P.x = fmaf(d, p.x, P.x);
         P.y = fmaf(d, p.y, P.y);
