@@ -269,6 +269,10 @@ qpm_status qpm_selfcheck(int32_t kind, uint64_t *mismatches, uint32_t *first_bad
  *   grad_theta device float [B][ld_grad] out: dL/dtheta = grad_fit * df/dtheta
  * Phasor table as for qpm_eval (cached per problem).  Errors: N < 1, B < 1,
  * ld < N, NULL theta, d_eff, saved or grad_theta, misaligned saved -> QPM_ERR_ARG.
+ * Rows whose pitch is a multiple of 16 bytes are read as TMA tiles, whose device
+ * waits are bounded (2 s): a wait that runs out makes that call's d_eff, fit or
+ * gradient NaN rather than returning an error (the calls are asynchronous).
+ * Nothing past a row's N floats is read into the sums or written.
  * ------------------------------------------------------------------------- */
 int64_t qpm_relaxed_saved_floats(int32_t N);
 qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float *theta, int64_t ld,
