@@ -116,6 +116,10 @@ class ClockSampler:
 # on the current kernel: 1501696 read + 329984 written.  The 2 MB population and
 # the phasor table stay in L2; DRAM sees little more than the first touch.
 K_PERSIST_DRAM_BYTES = 1501696 + 329984
+# DRAM bytes of one relaxed forward (k_relaxed_fwd + k_relaxed_combine) and one backward
+# at 4096 x 4096, read + write, from the ncu capture in profiles/k_relaxed_b4096_n4096.md
+# (cold caches; the backward's last gradient lines are still in L2 when it ends)
+K_RELAXED_DRAM_BYTES = (67191040 + 679424) + (4265984 + 0) + (71792896 + 14891776)
 
 
 PHILOX_CALLS_PER_GENE_GEN = 0.25 + 0.75  # crossover word + three GWO words, 4 genes per call
@@ -468,7 +472,8 @@ def run_gpu(args):
                "roofline": {"bound": "hbm", "achieved": 12 * elems / (t_f + t_b) / 1e9,
                             "peak": peak_hbm, "unit": "GB/s",
                             "frac": 12 * elems / (t_f + t_b) / 1e9 / peak_hbm,
-                            "bytes_per_element": 12}}
+                            "bytes_per_element": 12, "traffic": K_RELAXED_DRAM_BYTES,
+                            "traffic_unit": "DRAM bytes of one fwd + combine + bwd (ncu)"}}
 
     # ------------------------------ qpm_eval: 1024 rows of N = 1e5 (genes, packed)
     Ne, NPe = 100000, 1024
