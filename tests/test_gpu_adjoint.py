@@ -61,7 +61,7 @@ def test_relaxed_fwd_bwd_against_oracle(q, orc, N):
 
 
 @pytest.mark.parametrize("N,ld_extra,ldg_extra", [(1000, 0, 0), (1000, 1, 3), (1000, 4, 1),
-                                                   (1000, 1, 0), (4097, 3, 3)])
+                                                   (1000, 1, 0), (4097, 3, 3), (100003, 1, 1)])
 def test_relaxed_ragged_batch_and_strided_rows(q, orc, N, ld_extra, ldg_extra):
     """B = 130 rows: a warp takes 32 rows (lane = row), so the last warp holds rows
     128-129 and 30 rows past the end; N domains in rows of N + ld_extra floats
@@ -69,8 +69,10 @@ def test_relaxed_ragged_batch_and_strided_rows(q, orc, N, ld_extra, ldg_extra):
     through registers) and gradients written into rows of N + ldg_extra floats (TMA
     tile stores for a pitch that is a multiple of 16 bytes, plain stores otherwise).
     N = 4097 in rows of 4100 floats: the last segment (160 domains from 4000) has a
-    step with one domain inside the row and one entirely past it.  The padding holds
-    NaN, which must neither be read into the sums nor be overwritten."""
+    step with one domain inside the row and one entirely past it.  N = 100003: 391
+    segments of 256 domains, more than one warp's 32 lanes, so the combine walks the
+    segments in chunks.  The padding holds NaN, which must neither be read into the
+    sums nor be overwritten."""
     import torch
     from paper_2511_01255_gb300 import workloads as W
     B = 130
