@@ -680,7 +680,8 @@ static dim3 rx_grid(const RelaxShape &sh) {
   return dim3((groups + RX_WPC - 1) / RX_WPC, sh.S);
 }
 
-// dynamic shared memory above the default 48 KB is opted into once per kernel
+// dynamic shared memory above the default 48 KB: the kernel's opt-in, set before each
+// launch (a host-side attribute write)
 template <class K>
 static qpm_status rx_launch_attr(K kernel, size_t bytes) {
   QPM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
