@@ -41,6 +41,7 @@
 
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
+#include "qpm_tma.cuh"
 
 namespace qpm {
 
@@ -50,7 +51,7 @@ static constexpr int RX_WPC = 4;     // warps (row groups of 32) per CTA
 static constexpr int RX_TILE = RX_STEP * RX_STEP * 4;  // bytes of one 32 x 32 tile
 static constexpr int RX_NST_F = 2;   // tile buffers per warp, forward (one step ahead)
 static constexpr int RX_NST_B = 2;   // backward
-static constexpr unsigned long long RX_WAIT_NS = 2000000000ull;  // 2 s
+
 
 struct RelaxShape {
   int B, N, L, S;  // rows, domains, segment length, segments
@@ -138,66 +139,6 @@ __device__ __forceinline__ void put_step(float4 *T, const float4 R[8]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 8; ++k) T[tix(4 * k + (lane >> 3), lane & 7)] = R[k];
-}
-
-// ------------------------------------------------------ TMA and mbarriers
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  while (!mbar_try(bar, parity))
-    if (globaltimer_ns() - t0 > RX_WAIT_NS) return false;
-  return true;
-}
-// generic-proxy accesses to shared memory before this point are ordered before
-// later async-proxy (TMA) accesses
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// 32 x 32 float tile at (x = domain, y = row) into shared memory, completing on bar
-__device__ __forceinline__ void tma_load_tile(void *dst, const CUtensorMap *map, int x, int y,
-                                              unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-// the tile back to global memory (the part inside the tensor), as one bulk group
-__device__ __forceinline__ void tma_store_tile(const CUtensorMap *map, int x, int y, const void *src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
-               ::"l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(src))
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-// at most N of this thread's bulk store groups still reading shared memory
-template <int N>
-__device__ __forceinline__ void tma_store_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void tma_store_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // after a wait ran out at step t_fail no further copies were issued; the copies of
@@ -624,37 +565,6 @@ static __global__ void __launch_bounds__(RX_WPC * 32, 5)
 }
 
 // ---------------------------------------------------------------- host side
-// cuTensorMapEncodeTiled from the driver, looked up once
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  });
-  return fn;
-}
-
-// rows x cols float matrix with leading dimension ld as 32 x 32 tiles, 128-byte
-// swizzle, zero fill outside; false where a TMA copy cannot take it (address not
-// 16-byte aligned, row pitch not a multiple of 16 bytes) or the driver refused
-static bool make_tile_map(CUtensorMap *map, const float *base, int rows, int cols, int64_t ld) {
-  if (((uintptr_t)base & 15) != 0 || (ld % 4) != 0 || ld >= ((int64_t)1 << 37)) return false;
-  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  const cuuint32_t box[2] = {RX_STEP, RX_STEP};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // the caller's lease stays alive until its launches are enqueued
 static qpm_status relaxed_setup(const qpm_problem *prob, const float *theta, int64_t ld,
                                 int32_t B, const void *saved, cudaStream_t s, TableLease &lease,

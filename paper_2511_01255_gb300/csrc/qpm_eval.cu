@@ -87,11 +87,16 @@ static __global__ void __launch_bounds__(ER_WPC * 32, 5)
 // of shared memory per CTA, 3 CTAs per SM); the accumulation order equals k_eval_rows'.
 // grid (S, ceil(groups / ER_WPC)).
 constexpr int ER_RING_CTAS = 3;  // resident CTAs per SM (shared memory)
-template <bool COMP>
+// TMA: the gene tiles come by TMA copies (er_ring_sweep_tma, `gmap`), else by cp.async.
+template <bool COMP, bool TMA>
 static __global__ void __launch_bounds__(ER_WPC * 32, ER_RING_CTAS)
-    k_eval_rows_ring(const float *__restrict__ src, int64_t ld, EvalShape sh,
-                     const float4 *__restrict__ blk, float2 *__restrict__ part) {
-  extern __shared__ float4 dyn[];
+    k_eval_rows_ring(const __grid_constant__ CUtensorMap gmap, const float *__restrict__ src,
+                     int64_t ld, EvalShape sh, const float4 *__restrict__ blk,
+                     float2 *__restrict__ part) {
+  extern __shared__ float4 dyn_raw[];
+  float4 *dyn = dyn_raw;
+  if constexpr (TMA)  // 1024-byte aligned for the swizzled tiles (the launch adds the slack)
+    dyn = (float4 *)((unsigned char *)dyn_raw + ((1024 - (smem_u32(dyn_raw) & 1023)) & 1023));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
@@ -99,11 +104,12 @@ static __global__ void __launch_bounds__(ER_WPC * 32, ER_RING_CTAS)
   const float4 *const tabs[1] = {blk};
   ErAcc<COMP> acc;
   acc.zero();
-  er_ring_sweep<1>(dyn, src, ld, sh, tabs, m0, m1, r0, live,
-                   [&](uint32_t e, const float2 *E, int b) {
-                     er_push_block(acc.m, e, E + b * BLK_F2);
-                     if ((b & 3) == 3) acc.fold();
-                   });
+  auto push = [&](uint32_t e, const float2 *E, int b) {
+    er_push_block(acc.m, e, E + b * BLK_F2);
+    if ((b & 3) == 3) acc.fold();
+  };
+  if constexpr (TMA) er_ring_sweep_tma<1>(dyn, &gmap, sh, tabs, m0, m1, r0, live, push);
+  else er_ring_sweep<1>(dyn, src, ld, sh, tabs, m0, m1, r0, live, push);
   if (!live) return;
   acc.fold();
   const Mono run = acc.get();
@@ -349,11 +355,16 @@ static qpm_status launch_eval_rows(bool aligned, bool comp, const float *g, int6
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
   const float4 *b4 = (const float4 *)blk;
   if (aligned) {
-    const void *fn = comp ? (const void *)k_eval_rows_ring<true> : (const void *)k_eval_rows_ring<false>;
-    const size_t smem = er_ring_smem(1);
+    CUtensorMap gmap{};
+    const bool tma = make_tile_map(&gmap, g, sh.NP, sh.N, ld);
+    const void *fn = tma ? (comp ? (const void *)k_eval_rows_ring<true, true>
+                                 : (const void *)k_eval_rows_ring<false, true>)
+                         : (comp ? (const void *)k_eval_rows_ring<true, false>
+                                 : (const void *)k_eval_rows_ring<false, false>);
+    const size_t smem = tma ? 1024 + er_ring_smem_tma(1) : er_ring_smem(1);
     QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (comp) k_eval_rows_ring<true><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
-    else k_eval_rows_ring<false><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);
+    void *args[] = {(void *)&gmap, (void *)&g, (void *)&ld, (void *)&sh, (void *)&b4, (void *)&part};
+    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(ER_WPC * 32), args, smem, stream));
   } else {
     const size_t smem = sizeof(float4) * 2 * ER_STEP_F4_P;
     if (comp) k_eval_rows<true><<<grid, ER_WPC * 32, smem, stream>>>(g, ld, sh, b4, part);

@@ -8,6 +8,7 @@
 #pragma once
 #include "qpm_common.cuh"
 #include "qpm_internal.h"
+#include "qpm_tma.cuh"
 
 namespace qpm {
 
@@ -178,6 +179,93 @@ __device__ __forceinline__ void er_ring_sweep(float4 *dyn, const float *__restri
     }
   }
   cp_async_wait<0>();
+}
+
+// The same sweep with each sub-step's 32 x 32 gene tile brought in by one TMA copy
+// (`gmap`: the genes as an NP x N float matrix, 32 x 32 boxes, 128-byte swizzle, zero
+// fill past the row end and the last row) that completes on the slot's mbarrier; the
+// steps' sign-block entries still come by cp.async, one group per step.  `dyn` must be
+// 1024-byte aligned (the tiles follow the NT tables' 12 KB per table and step); the
+// mbarriers follow the rings: er_ring_smem_tma bytes in all.  A wait that runs out
+// (bounded by %globaltimer) fills the tile with NaN, which makes the rows' results NaN.
+__host__ __device__ constexpr size_t er_ring_smem_tma(int NT) {
+  return er_ring_smem(NT) + (size_t)ER_WPC * ER_RING * 8;
+}
+__device__ __forceinline__ void er_nan_tile(float4 *T) {
+  const float n = __int_as_float(0x7fc00000);
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c4 = 0; c4 < 8; ++c4) T[er_tix(lane, c4)] = make_float4(n, n, n, n);
+}
+template <int NT, class Push>
+__device__ __forceinline__ void er_ring_sweep_tma(float4 *dyn, const CUtensorMap *gmap,
+                                                  const EvalShape &sh, const float4 *const *tabs,
+                                                  int m0, int m1, int r0, bool live, Push &&push) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *ring = dyn + 2 * NT * ER_STEP_F4_P + warp * (ER_RING * 256);
+  const unsigned bar0 =
+      smem_u32(dyn + 2 * NT * ER_STEP_F4_P + ER_WPC * ER_RING * 256) + warp * ER_RING * 8;
+  const int nb = (sh.N + 3) >> 2, nsteps = (m1 - m0 + 127) >> 7, nsub = (m1 - m0 + 31) >> 5;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) er_stage_entries(dyn + t * ER_STEP_F4_P, tabs[t], m0, 0, nb);
+  cp_async_commit();
+  if (live && lane == 0) {
+    for (int k = 0; k < ER_RING; ++k) mbar_init(bar0 + 8 * k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    for (int u = 0; u < ER_RING - 1 && u < nsub; ++u) {
+      mbar_expect_tx(bar0 + 8 * u, 4096);
+      tma_load_tile(ring + u * 256, gmap, m0 + 32 * u, r0, bar0 + 8 * u);
+    }
+  }
+  bool ok = true;
+  int u_fail = -1;  // first sub-step whose tile did not arrive in time
+  int slot = 0;     // u % ER_RING
+  for (int k = 0; k < nsteps; ++k) {
+    const float2 *bp = (const float2 *)dyn + (size_t)(k & 1) * NT * 2 * ER_STEP_F4_P;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {  // 4 sub-steps of 32 domains
+      const int u = 4 * k + q;
+      if (u >= nsub) break;
+      if (q == 0) {
+        cp_async_wait<0>();  // this thread's copies of step k's entries
+        __syncthreads();     // everyone's; everyone done with step k - 1
+      } else {
+        __syncwarp();  // the warp's lanes are done with sub-step u - 1's tile
+      }
+      const int ua = u + ER_RING - 1;
+      const int sa = slot == 0 ? ER_RING - 1 : slot - 1;  // the slot swept at u - 1
+      if (live && lane == 0 && ok && ua < nsub) {
+        fence_async_smem();
+        mbar_expect_tx(bar0 + 8 * sa, 4096);
+        tma_load_tile(ring + sa * 256, gmap, m0 + 32 * ua, r0, bar0 + 8 * sa);
+      }
+      if (q == 0 && k + 1 < nsteps) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          er_stage_entries(dyn + (((k + 1) & 1) * NT + t) * ER_STEP_F4_P, tabs[t], m0, k + 1, nb);
+        cp_async_commit();
+      }
+      float4 *T = ring + slot * 256;
+      const unsigned bar = bar0 + 8 * slot;
+      slot = slot + 1 == ER_RING ? 0 : slot + 1;
+      if (!live) continue;
+      const bool arrived = ok && mbar_wait(bar, (u / ER_RING) & 1);
+      if (!__all_sync(0xffffffffu, arrived)) {  // ok is uniform across the warp
+        if (ok) u_fail = u;
+        ok = false;
+        er_nan_tile(T);
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) push(er_pattern(T[er_tix(lane, c4)]), bp, 8 * q + c4);
+    }
+  }
+  cp_async_wait<0>();
+  if (!ok && lane == 0) {  // copies issued after u_fail may still be in flight
+    for (int v = u_fail; v < min(u_fail + ER_RING - 1, nsub); ++v)
+      mbar_wait(bar0 + 8 * (v % ER_RING), (v / ER_RING) & 1);
+  }
 }
 
 // append stored entry idx (0..7, the pattern with d_0 = +1) of a block whose 8
