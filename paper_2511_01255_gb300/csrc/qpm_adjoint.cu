@@ -52,7 +52,6 @@ static constexpr int RX_TILE = RX_STEP * RX_STEP * 4;  // bytes of one 32 x 32 t
 static constexpr int RX_NST_F = 2;   // tile buffers per warp, forward (one step ahead)
 static constexpr int RX_NST_B = 2;   // backward
 
-
 struct RelaxShape {
   int B, N, L, S;  // rows, domains, segment length, segments
   int64_t ld;      // theta leading dimension

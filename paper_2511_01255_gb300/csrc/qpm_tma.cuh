@@ -4,7 +4,10 @@
 // A tile lands with the 128-byte swizzle (16-byte chunk c of row r at chunk c ^ (r & 7)
 // of a 1024-byte aligned tile), which is the row-walk layout the sweeps index.  Loads
 // complete on an mbarrier with an expected transaction count; every wait on one is
-// bounded by %globaltimer.
+// bounded by %globaltimer.  Past the row end and the last row a load reads zeros.
+// Stores leave as bulk groups; a store of a tile that reaches past the row end was
+// measured writing into the row's padding (N = 4097 in rows of 4100 floats), so callers
+// store only tiles that lie wholly inside the matrix.
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
