@@ -102,13 +102,17 @@ struct MultiTables {
 // grid (S, ceil(groups / ER_WPC)).
 
 // 16-byte aligned rows: er_ring_sweep with K tables; K x 12 KB + 48 KB of shared memory
-// per CTA, so 3 CTAs per SM for K <= 2 and 2 for K = 3, 4
+// per CTA (about 1 KB more with TMA tiles), so 3 CTAs per SM for K <= 2 and 2 for K = 3, 4
 __host__ __device__ constexpr int mw_ring_ctas(int K) { return K <= 2 ? 3 : 2; }
-template <int K>
+// TMA: the gene tiles by TMA copies (er_ring_sweep_tma, `gmap`), else by cp.async
+template <int K, bool TMA>
 static __global__ void __launch_bounds__(ER_WPC * 32, mw_ring_ctas(K))
-    k_multi_rows_ring(const float *__restrict__ genes, int64_t ld, EvalShape sh, MultiTables mt,
-                      float2 *__restrict__ part) {
-  extern __shared__ float4 dyn[];
+    k_multi_rows_ring(const __grid_constant__ CUtensorMap gmap, const float *__restrict__ genes,
+                      int64_t ld, EvalShape sh, MultiTables mt, float2 *__restrict__ part) {
+  extern __shared__ float4 dyn_raw[];
+  float4 *dyn = dyn_raw;
+  if constexpr (TMA)  // 1024-byte aligned for the swizzled tiles (the launch adds the slack)
+    dyn = (float4 *)((unsigned char *)dyn_raw + ((1024 - (smem_u32(dyn_raw) & 1023)) & 1023));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int s = blockIdx.x, m0 = s * sh.L, m1 = min(sh.N, m0 + sh.L);
   const int r0 = (blockIdx.y * ER_WPC + warp) * 32;
@@ -116,12 +120,12 @@ static __global__ void __launch_bounds__(ER_WPC * 32, mw_ring_ctas(K))
   Mono acc[K];
 #pragma unroll
   for (int p = 0; p < K; ++p) acc[p] = mono_zero();
-  er_ring_sweep<K>(dyn, genes, ld, sh, mt.t, m0, m1, r0, live,
-                   [&](uint32_t e, const float2 *E, int b) {
+  auto push = [&](uint32_t e, const float2 *E, int b) {
 #pragma unroll
-                     for (int p = 0; p < K; ++p)
-                       er_push_block(acc[p], e, E + (size_t)p * 2 * ER_STEP_F4_P + b * BLK_F2);
-                   });
+    for (int p = 0; p < K; ++p) er_push_block(acc[p], e, E + (size_t)p * 2 * ER_STEP_F4_P + b * BLK_F2);
+  };
+  if constexpr (TMA) er_ring_sweep_tma<K>(dyn, &gmap, sh, mt.t, m0, m1, r0, live, push);
+  else er_ring_sweep<K>(dyn, genes, ld, sh, mt.t, m0, m1, r0, live, push);
   if (!live) return;
   const size_t stride = (size_t)sh.S * sh.NPpad;
 #pragma unroll
@@ -276,15 +280,21 @@ extern "C" qpm_status qpm_eval_multi(const qpm_problem *probs, int32_t K, const 
     return fail(QPM_ERR_ARG, "qpm_eval_multi: scratch smaller than qpm_eval_multi_scratch_bytes()");
   float2 *part = (float2 *)scratch;
   const dim3 grid(sh.S, (sh.groups + ER_WPC - 1) / ER_WPC);
+  CUtensorMap gmap{};
+  const bool tma = vec && make_tile_map(&gmap, genes, NP, N, ld);
 #define QPM_MW(KK)                                                                          \
   {                                                                                         \
-    const void *fn = vec ? (const void *)k_multi_rows_ring<KK> : (const void *)k_multi_rows<KK>; \
-    const size_t smem = vec ? er_ring_smem(KK) : sizeof(float4) * 2 * (size_t)KK * ER_STEP_F4_P; \
+    const void *fn = !vec ? (const void *)k_multi_rows<KK>                                  \
+                     : tma ? (const void *)k_multi_rows_ring<KK, true>                     \
+                           : (const void *)k_multi_rows_ring<KK, false>;                   \
+    const size_t smem = !vec ? sizeof(float4) * 2 * (size_t)KK * ER_STEP_F4_P               \
+                        : tma ? 1024 + er_ring_smem_tma(KK) : er_ring_smem(KK);             \
     QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     EvalShape shv = sh;                                                                     \
     int64_t ldv = ld;                                                                       \
-    void *args[] = {(void *)&genes, &ldv, &shv, &mt, &part};                                \
-    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(ER_WPC * 32), args, smem, s));                 \
+    void *args_ring[] = {(void *)&gmap, (void *)&genes, &ldv, &shv, &mt, &part};           \
+    void *args_rows[] = {(void *)&genes, &ldv, &shv, &mt, &part};                           \
+    QPM_CUDA(cudaLaunchKernel(fn, grid, dim3(ER_WPC * 32), vec ? args_ring : args_rows, smem, s)); \
     k_multi_combine<KK><<<(NP + 7) / 8, 256, 0, s>>>(sh, part, mt, G0, beta,               \
                                                       (float2 *)d_eff, objective);          \
   }
