@@ -151,6 +151,16 @@ def algorithmic_lane_ops_per_gene_gen(compensated):
             + 2 * (14.25 if compensated else 10))
 
 
+def algorithmic_lane_ops_per_gene_gen_multi(kind, K):
+    """The same count for the multi-wavelength objectives of Sec. 5 (plain scans): the
+    updates as above, and per phase one scan of each of the K problems, 10 lane-ops a
+    domain for a cascaded problem, 2 for an SHG problem (the running sum of d p1 as two
+    FFMA)."""
+    per_domain = DIRECT_SCAN_OPS_PER_DOMAIN if kind == 2 else 2
+    return (algorithmic_lane_ops_per_gene_gen(0) - 2 * DIRECT_SCAN_OPS_PER_DOMAIN
+            + 2 * K * per_domain)
+
+
 def mix_ceiling_gene_gens(compensated, issue):
     """Gene-generations/s the work of a gene-generation allows on this GPU when every
     issue slot does useful work: the Philox4x32-10 calls at the measured rate of the
@@ -521,9 +531,13 @@ def run_gpu(args):
 
     # ------------------------------- the multi-wavelength designs of Sec. 5 (N = 3000)
     designs = {}
+    from paper_2511_01255_gb300 import autotune
     for dc in (W.DESIGN_THG3, W.DESIGN_SHG5):
-        prm_d = q.Params(dc["NP"], dc["G"], dc["F"], dc["CR"], dc["seed"] + rank, 0, 0)
         k1d, k2d = dc["kappas"][0]
+        obj_d = (dc["kind"], dc["kappas"], dc["G0"], dc["beta"])
+        team_d = autotune.autotune_team(dc["N"], k1d, k2d, dc["NP"], 0, q.RUN_LAUNCHES, gens=4,
+                                        objective=obj_d)  # measured, cached
+        prm_d = q.Params(dc["NP"], dc["G"], dc["F"], dc["CR"], dc["seed"] + rank, 0, 0, team_d)
         std = q.State([(dc["N"], k1d, k2d)], [prm_d])
         std.set_objective(dc["kind"], dc["kappas"], dc["G0"], dc["beta"])
         std.init()
@@ -536,11 +550,17 @@ def run_gpu(args):
         rows[0]["cfg"] = dc
         samples["designs." + dc["name"]] = rows
         std.close()
+        ops_d = algorithmic_lane_ops_per_gene_gen_multi(dc["kind"], K)
+        gg_d = dc["NP"] * dc["N"] * dc["G"]  # gene-generations of the timed run
         designs[dc["name"]] = {
             "s_per_1000_iterations": t_d * 1000.0 / dc["G"],
             "domain_evals_per_s": ev_d / t_d,
             "domain_evals_note": "one domain of one problem's scan; K scans per evaluation",
-            "best_objective": rows[0]["objective"], "form": "launches",
+            "best_objective": rows[0]["objective"], "form": "launches", "team": team_d,
+            "roofline": {"bound": "alu", "achieved": ops_d * gg_d / t_d / 1e12,
+                         "peak": peak_alu, "unit": "T lane-ops/s",
+                         "frac": ops_d * gg_d / t_d / 1e12 / peak_alu,
+                         "ops_per_gene_gen": ops_d},
             "paper_context": "about 21 s per 1000 iterations for the 5-wavelength SHG design at "
                              "N = 3000 on an RTX 4070 (Sec. 5); a different GPU and unknown NP, "
                              "context only"}

@@ -29,8 +29,11 @@ def n_bucket(N):
     return f"{b}+{q}/4"
 
 
-def _key(device, N, NP, compensated, form):
-    return f"{device}|N{n_bucket(N)}|NP{NP}|c{int(bool(compensated))}|f{form}"
+def _key(device, N, NP, compensated, form, objective=None):
+    k = f"{device}|N{n_bucket(N)}|NP{NP}|c{int(bool(compensated))}|f{form}"
+    if objective is not None:  # (kind, kappas, G0, beta): the kind and problem count
+        k += f"|o{int(objective[0])}k{len(objective[1])}"
+    return k
 
 
 def load_cache(path=CACHE):
@@ -54,8 +57,10 @@ def choose(timings):
     return min(sorted(timings), key=lambda t: timings[t])
 
 
-def measure_team(N, kappa1, kappa2, NP, team, compensated=0, form=None, gens=40, reps=3):
-    """Seconds per generation of one instance with the given team width."""
+def measure_team(N, kappa1, kappa2, NP, team, compensated=0, form=None, gens=40, reps=3,
+                 objective=None):
+    """Seconds per generation of one instance with the given team width; objective:
+    (kind, kappas, G0, beta) of qpm_set_objective, or None for the cascaded |d_eff|^2."""
     import torch
 
     import paper_2511_01255_gb300 as q
@@ -63,6 +68,8 @@ def measure_team(N, kappa1, kappa2, NP, team, compensated=0, form=None, gens=40,
     G = gens * (reps + 1) + 1
     prm = q.Params(NP, G, 0.5, 0.9, 1, 0, int(compensated), int(team))
     with q.State([(N, kappa1, kappa2)], [prm]) as st:
+        if objective is not None:
+            st.set_objective(*objective)
         st.init()
         st.run(gens, form)  # warm-up (graph instantiation, caches)
         torch.cuda.synchronize()
@@ -79,14 +86,16 @@ def measure_team(N, kappa1, kappa2, NP, team, compensated=0, form=None, gens=40,
 
 
 def autotune_team(N, kappa1, kappa2, NP, compensated=0, form=None, gens=40,
-                  candidates=CANDIDATES, use_cache=True, path=CACHE, measure=None):
-    """Return the fastest team width for this workload (cached)."""
+                  candidates=CANDIDATES, use_cache=True, path=CACHE, measure=None,
+                  objective=None):
+    """Return the fastest team width for this workload (cached).  objective: the
+    (kind, kappas, G0, beta) of qpm_set_objective the instance will optimise, or None."""
     import torch
 
     import paper_2511_01255_gb300 as q
     form = q.RUN_PERSISTENT if form is None else form
     device = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    key = _key(device, N, NP, compensated, form)
+    key = _key(device, N, NP, compensated, form, objective)
     cache = load_cache(path) if use_cache else {}
     if key in cache:
         return cache[key]["team"]
@@ -95,7 +104,11 @@ def autotune_team(N, kappa1, kappa2, NP, compensated=0, form=None, gens=40,
     for t in candidates:
         if t > 32 and N <= 4 * (t // 2):
             continue  # more threads than 4 domains each would leave most of them idle
-        timings[t] = measure(N, kappa1, kappa2, NP, t, compensated, form, gens)
+        if objective is None:
+            timings[t] = measure(N, kappa1, kappa2, NP, t, compensated, form, gens)
+        else:
+            timings[t] = measure(N, kappa1, kappa2, NP, t, compensated, form, gens,
+                                 objective=objective)
     best = choose(timings)
     cache[key] = {"team": best, "s_per_generation": {str(k): v for k, v in timings.items()},
                   "when": time.strftime("%Y-%m-%dT%H:%M:%S")}

@@ -142,8 +142,21 @@ __device__ __forceinline__ unsigned long long sel_key(bool minimize, float f, in
   return ((unsigned long long)(minimize ? ~b : b) << 32) | (0xFFFFFFFFu - (uint32_t)i);
 }
 
+// a phasor-table entry of a multi-wavelength kind: read-only path, kept in L1 ahead of
+// other lines (every team on the SM sweeps the same K tables for every individual)
+__device__ __forceinline__ float4 ld_table_keep(const float4 *p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+
 // MK != 0: the K scans of a multi-wavelength kind, plain FP32 sums, phasors from the
-// problems' tables in global memory (cached by L2)
+// problems' tables in global memory (cached in L1 and L2)
+// smt (optional): the K tables copied into shared memory by the CTA, [K][Npad] in the
+// same permuted order, float4 (p1, p2) entries for the cascaded kind and float2 (p1)
+// entries for the SHG kind, which needs p1 only
 template <int MK>
 struct MultiAcc {
   static constexpr int KMAX = MK == OBJ_MULTI_THG ? 4 : (MK == OBJ_MULTI_SHG ? 8 : 1);
@@ -152,40 +165,127 @@ struct MultiAcc {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) m[k] = mono_zero();
   }
-  // group k4 of this thread's chunk (4 domains of signs u)
-  __device__ __forceinline__ void push4(const InstDev &I, int k4, int t, float4 u) {
+  // one domain of problem k with sign d and its phasors p (p.zw unused for SHG)
+  __device__ __forceinline__ void push1(int k, float d, const float4 &p) {
+    if (MK == OBJ_MULTI_THG) {
+      mono_push(m[k], d, p);
+    } else {  // the SHG field needs the running sum of d p1 only
+      m[k].B.x = fmaf(d, p.x, m[k].B.x);
+      m[k].B.y = fmaf(d, p.y, m[k].B.y);
+    }
+  }
+  // group k4 of this thread's chunk (4 domains of signs u); one uniform branch picks
+  // the tables' place for the whole group
+  __device__ __forceinline__ void push4(const InstDev &I, int k4, int t, float4 u,
+                                        const void *smt = nullptr) {
     const float d[4] = {sgn(u.x), sgn(u.y), sgn(u.z), sgn(u.w)};
+    if (smt) {
+      const int e0 = k4 * 4 * I.T + t;
+#pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (k < I.K) {
+          const int ek = k * I.Npad + e0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 p;
+            if (MK == OBJ_MULTI_SHG) {
+              const float2 p1 = ((const float2 *)smt)[ek + q * I.T];
+              p = make_float4(p1.x, p1.y, 0.f, 0.f);
+            } else {
+              p = ((const float4 *)smt)[ek + q * I.T];
+            }
+            push1(k, d[q], p);
+          }
+        }
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       if (k < I.K) {
         const float4 *tb = I.mtab[k] + (size_t)k4 * 4 * I.T + t;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 p = __ldg(tb + (size_t)q * I.T);
-          if (MK == OBJ_MULTI_THG) {
-            mono_push(m[k], d[q], p);
-          } else {  // the SHG field needs the running sum of d p1 only
-            m[k].B.x = fmaf(d[q], p.x, m[k].B.x);
-            m[k].B.y = fmaf(d[q], p.y, m[k].B.y);
-          }
-        }
+        for (int q = 0; q < 4; ++q) push1(k, d[q], ld_table_keep(tb + (size_t)q * I.T));
       }
     }
   }
 };
 
+// ordered warp reduction of the b-sums alone (the SHG field): the same tree and the
+// same additions as warp_reduce's B
+__device__ __forceinline__ float2 warp_reduce_b(float2 b) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const float rx = __shfl_down_sync(0xffffffffu, b.x, s);
+    const float ry = __shfl_down_sync(0xffffffffu, b.y, s);
+    if ((lane & (2 * s - 1)) == 0) b = make_float2(b.x + rx, b.y + ry);
+  }
+  return b;
+}
+
 // reduce the K scans (WT: a warp team) and form the objective: f and the first
-// problem's field D0 are valid in the team's first thread; every thread returns
+// problem's field D0 are valid in the team's first thread; every thread returns.
+// The K warp reductions are independent and run together; a CTA team then passes
+// the warps' partials through shared memory once (sh holds KMAX x warps monoids)
+// and its thread 0 combines them in warp order, as block_reduce does.
+// Several teams per CTA (the multi-wavelength kinds with shared-memory tables): a team
+// is the T consecutive threads [team T, team T + T); team_sync is the team's own
+// named barrier (1 + team), or the CTA barrier when the CTA is one team.
+__device__ __forceinline__ int team_thread(const InstDev &I) { return (int)threadIdx.x & (I.T - 1); }
+__device__ __forceinline__ void team_sync(const InstDev &I) {
+  if ((int)blockDim.x == I.T) {
+    __syncthreads();
+  } else {
+    const int team = (int)threadIdx.x / I.T;
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(I.T) : "memory");
+  }
+}
+
 template <int MK, bool WT>
 __device__ void multi_finish(const InstDev &I, MultiAcc<MK> &acc, Mono *sh, float &f, float2 &D0) {
-  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
-  float obj = 0.f, gmax = -1.f, gmin = 3.0e38f;
+  constexpr int KM = MultiAcc<MK>::KMAX;
+  constexpr bool SHG = MK == OBJ_MULTI_SHG;
+  const int t = WT ? (int)(threadIdx.x & 31) : team_thread(I);
 #pragma unroll
-  for (int k = 0; k < MultiAcc<MK>::KMAX; ++k) {
+  for (int k = 0; k < KM; ++k) {
     if (k < I.K) {
-      if (!WT && k > 0) __syncthreads();  // the reduction scratch is reused
-      const Mono mk = WT ? warp_reduce(acc.m[k]) : block_reduce(acc.m[k], sh);
+      if (SHG) acc.m[k].B = warp_reduce_b(acc.m[k].B);
+      else acc.m[k] = warp_reduce(acc.m[k]);
+    }
+  }
+  if (!WT) {
+    // the team's warps and its share of the scratch
+    const int lane = threadIdx.x & 31, warp = t >> 5, nw = I.T >> 5;
+    sh += (size_t)((int)threadIdx.x / I.T) * KM * nw;
+    if (nw > 1) {
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+          if (k < I.K) {
+            if (SHG) sh[k * nw + warp].B = acc.m[k].B;
+            else sh[k * nw + warp] = acc.m[k];
+          }
+      }
+      team_sync(I);
       if (t == 0) {
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+          if (k < I.K)
+            for (int w = 1; w < nw; ++w) {
+              const Mono &r = sh[k * nw + w];
+              if (SHG) acc.m[k].B = make_float2(acc.m[k].B.x + r.B.x, acc.m[k].B.y + r.B.y);
+              else acc.m[k] = mono_combine(acc.m[k], r);
+            }
+      }
+    }
+  }
+  float obj = 0.f, gmax = -1.f, gmin = 3.0e38f;
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (k < I.K) {
+        const Mono &mk = acc.m[k];
         float2 Dk;
         if (MK == OBJ_MULTI_THG) {
           Dk = deff_from(mk, I.mkonst[k][0], I.mkonst[k][1]);
@@ -375,9 +475,11 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
                                             int *slot_out = nullptr, float4 *stg = nullptr,
                                             bool has_wcr = false,
                                             uint4 wcr = make_uint4(0u, 0u, 0u, 0u),
-                                            int own_slot = -1, int *impr_out = nullptr) {
+                                            int own_slot = -1, int *impr_out = nullptr,
+                                            const void *smt = nullptr) {
   static_assert(!(STG && DUAL), "staged rows need known slots");
-  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  // only the multi-wavelength kinds put several teams in a CTA
+  const int t = WT ? (int)(threadIdx.x & 31) : (MK ? team_thread(I) : (int)threadIdx.x);
   const float fx = (t == 0) ? I.fit[i] : 0.f;  // issued early, used after the scan
   // own_slot >= 0: the individual's current slot, known to the caller
   const int si = own_slot >= 0 ? own_slot : sel_in[i];
@@ -429,7 +531,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
 #undef QPM_DE1
     *(float4 *)(out + off) = u;
     if (MK) {
-      macc.push4(I, k4, t, u);
+      macc.push4(I, k4, t, u, smt);
     } else {
       if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, u);
       else push4<COMP, TS>(acc, tbl, I.T, k4, t, u);
@@ -480,9 +582,11 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
                                float4 own0 = make_float4(0.f, 0.f, 0.f, 0.f),
                                float4 own1 = make_float4(0.f, 0.f, 0.f, 0.f),
                                const int32_t *lslot = nullptr, float4 *stg = nullptr,
-                               int own_slot = -1, int *slot_out = nullptr) {
+                               int own_slot = -1, int *slot_out = nullptr,
+                               const void *smt = nullptr) {
   static_assert(!(STG && (DUAL || PRE)), "staged rows need known slots and no prefetched row");
-  const int t = WT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  // only the multi-wavelength kinds put several teams in a CTA
+  const int t = WT ? (int)(threadIdx.x & 31) : (MK ? team_thread(I) : (int)threadIdx.x);
   const float fx = (t == 0) ? I.fit[i] : 0.f;
   // lslot: the leaders' current slots, when the leader search delivered them;
   // own_slot >= 0: the individual's current slot, known to the caller
@@ -563,7 +667,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
 #undef QPM_PULL
     *(float4 *)(out + off) = y;
     if (MK) {
-      macc.push4(I, k4, t, y);
+      macc.push4(I, k4, t, y, smt);
     } else {
       if (STG) push4_staged<COMP, TS>(acc, tbl, I.T, k4, t, st, y);
       else push4<COMP, TS>(acc, tbl, I.T, k4, t, y);
@@ -890,12 +994,14 @@ __device__ bool last_cta(unsigned *ctr) {
 }
 
 // dynamic shared memory of k_de and k_gwo: [row + table staging (long rows)][reduction]
+// The multi-wavelength kinds (MK) stage the rows only: their K phasor tables are read
+// through L1, which keeps them (the rows bypass it).
 template <bool COMP, bool DUAL, int MK = 0>
 static __global__ void k_de(InstDev I) {
-  constexpr bool STG = !DUAL;
+  constexpr bool STG = !DUAL, TSS = MK != 0;
   extern __shared__ float4 dyn[];
   float4 *stg = dyn;
-  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(false) * blockDim.x : 0));
+  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(TSS) * blockDim.x : 0));
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
@@ -906,7 +1012,7 @@ static __global__ void k_de(InstDev I) {
     if (i != (int)blockIdx.x) __syncthreads();  // the reduction scratch is reused
     int slot = 0, impr = 0;
     const unsigned long long key =
-        de_individual<COMP, true, false, DUAL, false, STG, MK>(
+        de_individual<COMP, true, TSS, DUAL, false, STG, MK>(
             I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out, sh,
             &slot, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr);
     if (threadIdx.x == 0) {
@@ -937,10 +1043,10 @@ static __global__ void k_de(InstDev I) {
 
 template <bool COMP, bool DUAL, int MK = 0>
 static __global__ void k_gwo(InstDev I) {
-  constexpr bool STG = !DUAL;
+  constexpr bool STG = !DUAL, TSS = MK != 0;
   extern __shared__ float4 dyn[];
   float4 *stg = dyn;
-  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(false) * blockDim.x : 0));
+  Mono *sh = (Mono *)(dyn + (STG ? stg_f4_per_thread(TSS) * blockDim.x : 0));
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
@@ -948,7 +1054,7 @@ static __global__ void k_gwo(InstDev I) {
   for (int i = blockIdx.x; i < I.NP; i += gridDim.x) {
     if (i == la || i == lb || i == ld) continue;  // the leaders do not move
     __syncthreads();  // the reduction scratch is reused
-    gwo_individual<COMP, true, false, DUAL, false, false, STG, MK>(
+    gwo_individual<COMP, true, TSS, DUAL, false, false, STG, MK>(
         I, K, I.table, g, i, sel, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
         make_float4(0.f, 0.f, 0.f, 0.f), nullptr, stg);
   }
@@ -960,6 +1066,140 @@ static __global__ void k_gwo(InstDev I) {
     if (threadIdx.x == 0) {
       *I.gen = g + 1;  // Step 6/7: next generation (a is derived from g)
       I.ctr[1] = 0u;
+    }
+  }
+}
+
+// ------------------------------- the multi-wavelength kinds, tables in shared memory
+// When their K tables fit, the multi-wavelength kinds run several teams of T threads
+// per CTA (threads [team T, team T + T) are the team of one individual, with its own
+// named barrier) so that one copy of the K tables in shared memory serves every team
+// on the SM: read through L1, the tables of three N = 3000 problems (147 KB) did not
+// stay there.  The cascaded kind keeps (p1, p2) per domain, the SHG kind p1 only.
+// Dynamic shared memory: [K tables][row staging][reduction scratch of every team].
+// Teams take individuals from a counter (ctr[2] in DE, ctr[3] in GWO, reset by the
+// phase's last CTA), so that every SM ends within about one individual of the others
+// (a fixed deal of 5000 individuals to 152 x 8 teams leaves the fifth round 11 % full).
+// Which team evaluates an individual does not change any result.
+__device__ __forceinline__ int mt_next(const InstDev &I, unsigned *ctr, int &cur) {
+  __shared__ int next_sh[8];
+  const int team = (int)threadIdx.x / I.T;
+  if (team_thread(I) == 0) next_sh[team] = cur;
+  team_sync(I);  // also: the previous individual's reduction scratch is free again
+  const int i = next_sh[team];
+  // the one after, requested while this one is evaluated
+  if (i < I.NP && team_thread(I) == 0) cur = (int)atomicAdd(ctr, 1u);
+  return i;
+}
+
+template <int MK>
+__host__ __device__ constexpr size_t mt_entry_bytes() {
+  return MK == OBJ_MULTI_SHG ? sizeof(float2) : sizeof(float4);
+}
+template <int MK>
+__device__ void mt_load_tables(const InstDev &I, void *smt) {
+#pragma unroll
+  for (int k = 0; k < MultiAcc<MK>::KMAX; ++k) {
+    if (k < I.K) {
+      const float4 *src = I.mtab[k];
+      for (int j = threadIdx.x; j < I.Npad; j += blockDim.x) {
+        const float4 p = __ldg(src + j);
+        const size_t e = (size_t)k * I.Npad + j;
+        if (MK == OBJ_MULTI_SHG) ((float2 *)smt)[e] = make_float2(p.x, p.y);
+        else ((float4 *)smt)[e] = p;
+      }
+    }
+  }
+  __syncthreads();
+}
+template <int MK>
+__device__ __forceinline__ void mt_layout(const InstDev &I, void *&smt, float4 *&stg, Mono *&sh) {
+  extern __shared__ float4 dyn[];
+  smt = dyn;
+  stg = (float4 *)((char *)dyn + (size_t)I.K * I.Npad * mt_entry_bytes<MK>());
+  sh = (Mono *)(stg + stg_f4_per_thread(true) * blockDim.x);
+}
+
+template <int MK>
+static __global__ void k_de_mt(InstDev I) {
+  void *smt;
+  float4 *stg;
+  Mono *sh;
+  mt_layout<MK>(I, smt, stg, sh);
+  mt_load_tables<MK>(I, smt);
+  const int g = *I.gen;
+  const PhiloxKey K = philox_schedule(I.key);
+  const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
+  int32_t *sel_out = (g & 1) ? I.sel0 : I.sel1;
+  const int nteams = (int)blockDim.x / I.T, team = (int)threadIdx.x / I.T, t = team_thread(I);
+  unsigned long long k0 = 0, k1 = 0, k2 = 0;
+  int cur = t == 0 ? (int)atomicAdd(&I.ctr[2], 1u) : 0;
+  for (;;) {
+    const int i = mt_next(I, &I.ctr[2], cur);
+    if (i >= I.NP) break;
+    int slot = 0, impr = 0;
+    const unsigned long long key = de_individual<false, true, true, false, false, true, MK>(
+        I, K, I.table, g, i, de_indices(K, I.inst, (uint32_t)g, i, I.NP, I.N), sel_in, sel_out,
+        sh, &slot, stg, false, make_uint4(0u, 0u, 0u, 0u), -1, &impr, smt);
+    if (t == 0) {
+      top3_insert(k0, k1, k2, key);
+      if (I.adaptive) I.dekey[i] = slot_key(key, i, slot, impr);
+    }
+  }
+  // the teams' top three, merged by thread 0 (team 0's first thread)
+  __shared__ unsigned long long tk[3 * 16];
+  if (t == 0) {
+    tk[3 * team] = k0;
+    tk[3 * team + 1] = k1;
+    tk[3 * team + 2] = k2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int m = 1; m < nteams; ++m)
+      for (int e = 0; e < 3; ++e) top3_insert(k0, k1, k2, tk[3 * m + e]);
+    I.topk[3 * blockIdx.x] = k0;
+    I.topk[3 * blockIdx.x + 1] = k1;
+    I.topk[3 * blockIdx.x + 2] = k2;
+  }
+  if (last_cta(&I.ctr[0])) {
+    merge_leaders(I.topk, gridDim.x, I.lead, nullptr);  // Step 3
+    if (I.adaptive) adaptive_F_block(I, I.dekey, g);     // Step 6: the next F
+    if (threadIdx.x == 0) {
+      I.ctr[0] = 0u;
+      I.ctr[2] = 0u;
+    }
+  }
+}
+
+template <int MK>
+static __global__ void k_gwo_mt(InstDev I) {
+  void *smt;
+  float4 *stg;
+  Mono *sh;
+  mt_layout<MK>(I, smt, stg, sh);
+  mt_load_tables<MK>(I, smt);
+  const int g = *I.gen;
+  const PhiloxKey K = philox_schedule(I.key);
+  int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
+  const int la = I.lead[0], lb = I.lead[1], ld = I.lead[2];
+  int cur = team_thread(I) == 0 ? (int)atomicAdd(&I.ctr[3], 1u) : 0;
+  for (;;) {
+    const int i = mt_next(I, &I.ctr[3], cur);
+    if (i >= I.NP) break;
+    if (i == la || i == lb || i == ld) continue;  // the leaders do not move
+    gwo_individual<false, true, true, false, false, false, true, MK>(
+        I, K, I.table, g, i, sel, la, lb, ld, sh, nullptr, make_float4(0.f, 0.f, 0.f, 0.f),
+        make_float4(0.f, 0.f, 0.f, 0.f), nullptr, stg, -1, nullptr, smt);
+  }
+  if (I.trace && blockIdx.x == 0 && threadIdx.x < 3) {
+    const int l = threadIdx.x == 0 ? la : (threadIdx.x == 1 ? lb : ld);
+    I.trace[(size_t)I.NP * (2 + 2 * (size_t)g) + l] = __int_as_float(0x7fc00000);
+  }
+  if (last_cta(&I.ctr[1])) {
+    if (threadIdx.x == 0) {
+      *I.gen = g + 1;  // Step 6/7: next generation (a is derived from g)
+      I.ctr[1] = 0u;
+      I.ctr[3] = 0u;
     }
   }
 }
@@ -1576,6 +1816,7 @@ struct qpm_state {
   std::vector<qpm_problem> probs;
   std::vector<qpm_params> params;
   std::vector<int> grid_plain, grid_persist;
+  std::vector<int> grid_mt;  // CTAs of the multi-team kernels of the multi-wavelength kinds
   void *arena = nullptr;
   int g = 0;
   int G_min = 0;
@@ -1612,11 +1853,14 @@ static int choose_team(int N) {
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static size_t smem_bytes(int T) { return sizeof(Mono) * (size_t)(T / 32 + 1); }
+// the reduction scratch of the multi-wavelength kinds: one monoid per problem and warp
+static size_t smem_bytes_multi(int T) { return sizeof(Mono) * (size_t)(8 * (T / 32) + 1); }
 
 // kernel variants of one instance
 struct Variant {
   const void *de, *gwo, *persist;
   size_t smem, persist_smem;
+  int block = 0;  // threads per CTA of de / gwo (0: the team width)
 };
 
 static constexpr int TS_MAX_NPAD = 4096;  // phasor table in shared memory up to 64 KB
@@ -1645,13 +1889,45 @@ static Variant variant2(const InstDev &I) {
   return v;
 }
 
-// the multi-wavelength kinds: launches form only, both slots read (no staging)
+// the multi-wavelength kinds: launches form only, rows staged; their K tables in shared
+// memory shared by up to 8 teams per CTA (512 threads) where they fit, else through L1
+static size_t optin_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return (size_t)v;
+}
 template <int MK>
 static Variant variant_multi(const InstDev &I) {
   Variant v;
-  v.de = (const void *)k_de<false, true, MK>;
-  v.gwo = (const void *)k_gwo<false, true, MK>;
-  v.smem = smem_bytes(I.T);
+  const int nteams = std::max(1, std::min(8, 512 / I.T));
+  const int block = nteams * I.T;
+  const size_t mt = (size_t)I.K * I.Npad * mt_entry_bytes<MK>() +
+                    sizeof(float4) * stg_f4_per_thread(true) * (size_t)block +
+                    sizeof(Mono) * (size_t)MultiAcc<MK>::KMAX * (I.T / 32) * nteams;
+  // the opt-in limit less the kernels' own static shared memory
+  static const size_t cap = [] {
+    cudaFuncAttributes a{}, b{};
+    const size_t optin = optin_smem();
+    if (cudaFuncGetAttributes(&a, (const void *)k_de_mt<MK>) != cudaSuccess ||
+        cudaFuncGetAttributes(&b, (const void *)k_gwo_mt<MK>) != cudaSuccess)
+      return (size_t)0;
+    const size_t st = std::max(a.sharedSizeBytes, b.sharedSizeBytes);
+    return optin > st ? optin - st : (size_t)0;
+  }();
+  if (mt <= cap) {
+    v.de = (const void *)k_de_mt<MK>;
+    v.gwo = (const void *)k_gwo_mt<MK>;
+    v.smem = mt;
+    v.block = block;
+    v.persist = nullptr;
+    v.persist_smem = 0;
+    return v;
+  }
+  v.de = (const void *)k_de<false, false, MK>;
+  v.gwo = (const void *)k_gwo<false, false, MK>;
+  v.smem = sizeof(float4) * stg_f4_per_thread(true) * (size_t)I.T + smem_bytes_multi(I.T);
   v.persist = nullptr;
   v.persist_smem = 0;
   return v;
@@ -1725,7 +2001,8 @@ static qpm_status enqueue_step(qpm_state *st, cudaStream_t s) {
     InstDev I = st->h[k];
     const Variant v = variant_of(I);
     void *args[] = {&I};
-    const dim3 grid(st->grid_plain[k]), block(I.T);
+    const bool mt = v.block != 0;  // several teams per CTA
+    const dim3 grid(mt ? st->grid_mt[k] : st->grid_plain[k]), block(mt ? v.block : I.T);
     QPM_CUDA(cudaLaunchKernel(v.de, grid, block, args, v.smem, s));
     QPM_CUDA(cudaLaunchKernel(v.gwo, grid, block, args, v.smem, s));
   }
@@ -1783,6 +2060,7 @@ extern "C" qpm_status qpm_create(const qpm_problem *probs, const qpm_params *par
   st->params.assign(params, params + n_inst);
   st->h.resize(n_inst);
   st->grid_plain.resize(n_inst);
+  st->grid_mt.assign(n_inst, 0);
   st->grid_persist.resize(n_inst);
   st->objs.assign(n_inst, qpm_objective{});
   st->objmem.assign(n_inst, nullptr);
@@ -1995,9 +2273,9 @@ extern "C" qpm_status qpm_init(qpm_state *st, qpm_stream_t stream) {
       r = launch_table(tq, (float4 *)I.mtab[q], I.tpart, (float2 *)I.mkonst[q], nullptr, s);
       if (r != QPM_OK) return r;
     }
-    const size_t sm = smem_bytes(I.T);
-    if (I.obj == OBJ_MULTI_THG) k_init<false, OBJ_MULTI_THG><<<st->grid_plain[k], I.T, sm, s>>>(I);
-    else if (I.obj == OBJ_MULTI_SHG) k_init<false, OBJ_MULTI_SHG><<<st->grid_plain[k], I.T, sm, s>>>(I);
+    const size_t sm = smem_bytes(I.T), smm = smem_bytes_multi(I.T);
+    if (I.obj == OBJ_MULTI_THG) k_init<false, OBJ_MULTI_THG><<<st->grid_plain[k], I.T, smm, s>>>(I);
+    else if (I.obj == OBJ_MULTI_SHG) k_init<false, OBJ_MULTI_SHG><<<st->grid_plain[k], I.T, smm, s>>>(I);
     else if (I.compensated) k_init<true><<<st->grid_plain[k], I.T, sm, s>>>(I);
     else k_init<false><<<st->grid_plain[k], I.T, sm, s>>>(I);
     QPM_CUDA(cudaGetLastError());
@@ -2208,12 +2486,53 @@ extern "C" qpm_status qpm_set_objective(qpm_state *st, int32_t inst, const qpm_o
   st->objs[inst] = *o;
   // the kernel variants of the kind and their occupancy
   int occ_plain = 1, occ_persist = 1;
-  if (multi) {
+  if (multi && variant_of(I).block != 0) {
+    // several teams per CTA sharing the K tables in shared memory
     const Variant v = variant_of(I);
     int a = 0, b = 0;
+    for (const void *fn : {v.de, v.gwo})
+      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, v.block, v.smem));
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.gwo, v.block, v.smem));
+    if (std::min(a, b) < 1) return fail(QPM_ERR_UNSUPPORTED, "qpm_set_objective: kernels do not fit");
+    const int nteams = v.block / I.T;
+    st->grid_mt[inst] = std::min((I.NP + nteams - 1) / nteams, std::min(a, b) * sm_count());
+    // k_init and k_load_population keep one team per CTA
+    int c = 0;
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &c, I.obj == OBJ_MULTI_THG ? (const void *)k_init<false, OBJ_MULTI_THG>
+                                   : (const void *)k_init<false, OBJ_MULTI_SHG>,
+        I.T, smem_bytes_multi(I.T)));
+    st->grid_plain[inst] = std::min(I.NP, std::max(1, c) * sm_count());
+  } else if (multi) {
+    const Variant v = variant_of(I);
+    // the largest dynamic shared memory a team of up to 512 threads needs
+    const int cap = (int)(sizeof(float4) * stg_f4_per_thread(true) * 512 + smem_bytes_multi(512));
+    int a = 0, b = 0;
+    for (const void *fn : {v.de, v.gwo}) {
+      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutDefault));
+    }
     QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, I.T, v.smem));
     QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.gwo, I.T, v.smem));
     occ_plain = std::max(1, std::min(a, b));
+    // ask for no more shared memory than the resident CTAs use, so that the rest of
+    // the SM's L1 holds the K phasor tables; kept only if the occupancy stays
+    int dev = 0, smem_sm = 0;
+    QPM_CUDA(cudaGetDevice(&dev));
+    QPM_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int pct = (int)std::min<size_t>(
+        100, (100 * (size_t)occ_plain * (v.smem + 1024) + (size_t)smem_sm - 1) / (size_t)smem_sm);
+    for (const void *fn : {v.de, v.gwo})
+      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    int a2 = 0, b2 = 0;
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a2, v.de, I.T, v.smem));
+    QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, v.gwo, I.T, v.smem));
+    if (std::min(a2, b2) < occ_plain)
+      for (const void *fn : {v.de, v.gwo})
+        QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutDefault));
     st->grid_plain[inst] = std::min(I.NP, occ_plain * sm_count());
   } else {
     qpm_status r = occupancy(I, &occ_plain, &occ_persist);
@@ -2285,11 +2604,11 @@ extern "C" qpm_status qpm_set_population(qpm_state *st, int32_t inst, const floa
     if (k != inst && generation != st->g)
       return fail(QPM_ERR_UNSUPPORTED, "all instances of a state share one generation count");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t sm = smem_bytes(I.T);
+  const size_t sm = smem_bytes(I.T), smm = smem_bytes_multi(I.T);
   if (I.obj == OBJ_MULTI_THG)
-    k_load_population<false, OBJ_MULTI_THG><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+    k_load_population<false, OBJ_MULTI_THG><<<st->grid_plain[inst], I.T, smm, s>>>(I, genes, ld, generation);
   else if (I.obj == OBJ_MULTI_SHG)
-    k_load_population<false, OBJ_MULTI_SHG><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
+    k_load_population<false, OBJ_MULTI_SHG><<<st->grid_plain[inst], I.T, smm, s>>>(I, genes, ld, generation);
   else if (I.compensated)
     k_load_population<true><<<st->grid_plain[inst], I.T, sm, s>>>(I, genes, ld, generation);
   else

@@ -3,8 +3,9 @@
   python -m paper_2511_01255_gb300.profile_run --workload paper --form launches --gens 40
 
 workloads: small (N=16, NP=32), paper (N=1000, NP=256, compensated),
-precision (N=1e5, NP=1024, compensated), eval (qpm_eval of 1024 random rows
-of N=1e5), batch, relaxed, latency (the grid barrier of the persistent form over
+precision (N=1e5, NP=1024, compensated), design_thg3 / design_shg5 (the
+multi-wavelength designs of Sec. 5: N=3000, NP=5000, K=3 cascaded or K=5 SHG
+problems), eval (qpm_eval of 1024 random rows of N=1e5), batch, relaxed, latency (the grid barrier of the persistent form over
 several CTA counts and a dependent L2 load, from qpm_measure_latency).  forms:
 launches, graph, persistent, batched.  Prints the mean time per repetition
 measured with CUDA events.
@@ -24,7 +25,8 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="paper",
-                    choices=["small", "paper", "precision", "eval", "batch", "relaxed", "latency"])
+                    choices=["small", "paper", "precision", "design_thg3", "design_shg5", "eval",
+                             "batch", "relaxed", "latency"])
     ap.add_argument("--form", default="launches",
                     choices=["launches", "graph", "persistent", "batched"])
     ap.add_argument("--gens", type=int, default=20)
@@ -108,6 +110,13 @@ def main():
                        for c in inst])
         st.set_batch_cluster(a.cluster)
         c = {"name": f"batch{a.instances}_g1000_cluster{a.cluster}"}
+    elif a.workload.startswith("design"):
+        c = W.DESIGN_THG3 if a.workload == "design_thg3" else W.DESIGN_SHG5
+        comp = 0
+        prm = q.Params(c["NP"], c["G"], c["F"], c["CR"], c["seed"], 0, comp, a.team)
+        k1, k2 = c["kappas"][0]
+        st = q.State([(c["N"], k1, k2)], [prm])
+        st.set_objective(c["kind"], c["kappas"], c["G0"], c["beta"])
     else:
         c = {"small": W.SMALL, "paper": W.PAPER_SCALE, "precision": W.PRECISION}[a.workload]
         comp = c["compensated"] if a.comp < 0 else a.comp

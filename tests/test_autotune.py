@@ -28,6 +28,36 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     assert calls == []  # served from the cache
 
 
+def test_objective_has_its_own_cache_entry(tmp_path, monkeypatch):
+    """A multi-wavelength objective is tuned and cached apart from the single problem
+    of the same size (its kernels differ), and per number of problems."""
+    from paper_2511_01255_gb300 import autotune as A
+    seen = []
+
+    def fake(N, k1, k2, NP, team, comp, form, gens, objective=None):
+        seen.append((team, objective is not None))
+        base = {32: 3.0, 64: 1.0, 128: 1.5, 256: 2.0} if objective else {32: 3.0, 64: 2.0, 128: 1.0, 256: 1.2}
+        return base[team]
+
+    import types
+    fake_torch = types.SimpleNamespace(cuda=types.SimpleNamespace(
+        is_available=lambda: False, get_device_name=lambda: "cpu"))
+    monkeypatch.setitem(__import__("sys").modules, "torch", fake_torch)
+    path = str(tmp_path / "cache.json")
+    obj3 = (2, [(1.0, 2.0), (1.1, 2.1), (1.2, 2.2)], 1e5, 0.5)
+    assert A.autotune_team(1000, 1.0, 2.0, 256, form=0, measure=fake, path=path) == 128
+    assert A.autotune_team(1000, 1.0, 2.0, 256, form=0, measure=fake, path=path,
+                           objective=obj3) == 64
+    assert all(o for t, o in seen[4:]) and not any(o for t, o in seen[:4])
+    n = len(seen)
+    assert A.autotune_team(1000, 1.0, 2.0, 256, form=0, measure=fake, path=path,
+                           objective=obj3) == 64
+    assert len(seen) == n  # cached
+    A.autotune_team(1000, 1.0, 2.0, 256, form=0, measure=fake, path=path,
+                    objective=(2, obj3[1][:2], 1e5, 0.5))
+    assert len(seen) == n + 4  # two problems: a new entry
+
+
 @pytest.mark.gpu
 def test_autotune_on_gpu(tmp_path):
     import torch
@@ -37,6 +67,10 @@ def test_autotune_on_gpu(tmp_path):
     from paper_2511_01255_gb300 import autotune as A
     t = A.autotune_team(1000, 0.9, 4.0, 64, compensated=1, form=q.RUN_PERSISTENT, gens=10,
                         path=str(tmp_path / "c.json"))
+    assert t in A.CANDIDATES
+    obj = (3, [(2.1, 0.0), (2.4, 0.0), (2.9, 0.0)], 1.0e3, 0.5)
+    t = A.autotune_team(1000, 2.1, 0.0, 64, form=q.RUN_LAUNCHES, gens=4,
+                        path=str(tmp_path / "c.json"), objective=obj)
     assert t in A.CANDIDATES
 
 

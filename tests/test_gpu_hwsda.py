@@ -394,12 +394,26 @@ KAP3 = [(2 * math.pi / 6.5, 2 * math.pi / 1.4), (2 * math.pi / 6.9, 2 * math.pi 
 KAP5 = [(2 * math.pi / x, 0.0) for x in (2.1, 2.6, 3.2, 3.7, 4.4)]
 
 
-@pytest.mark.parametrize("kind,N,NP,G,kap,G0,beta,modes", [
-    (1, 333, 24, 12, [(2 * math.pi / 6.9, 0.0)], 0.0, 0.0, (0, 1, 2, 3)),
-    (2, 3000, 32, 6, KAP3, 2.0e5, 0.5, (0, 1)),
-    (3, 3000, 32, 6, KAP5, 1.5e3, 0.5, (0, 1)),
+@pytest.mark.parametrize("kind,N,NP,G,kap,G0,beta,modes,team,fs", [
+    (1, 333, 24, 12, [(2 * math.pi / 6.9, 0.0)], 0.0, 0.0, (0, 1, 2, 3), 0, 0),
+    (2, 3000, 32, 6, KAP3, 2.0e5, 0.5, (0, 1), 0, 0),
+    (3, 3000, 32, 6, KAP5, 1.5e3, 0.5, (0, 1), 0, 0),
+    # other team widths: more groups of 4 domains per thread (128), a team wider than
+    # the rows need (512, N = 1001: padding domains), one CTA per individual of 64
+    (2, 2999, 20, 4, KAP3[:2], 2.0e5, 0.5, (0,), 128, 0),
+    (2, 1001, 12, 4, KAP3, 5.0e4, 0.5, (0,), 512, 0),
+    (3, 3001, 20, 4, KAP5[:4], 1.5e3, 0.25, (0,), 64, 0),
+    # four problems of 4096 padded domains: their tables (256 KB) do not fit shared
+    # memory, so the one-team kernels read them through L1
+    (2, 4000, 16, 3, KAP3 + [(2 * math.pi / 7.1, 2 * math.pi / 1.5)], 2.0e5, 0.5, (0, 1), 0, 0),
+    # five SHG problems of 4096 padded domains in 512-thread teams: tables, staging and
+    # scratch need exactly the opt-in limit, so the kernels' own static shared memory
+    # sends them to the one-team kernels
+    (3, 3000, 8, 3, KAP5, 1.5e3, 0.5, (0,), 512, 0),
+    # the adaptive F of Sec. 3.1.1 on a minimised objective (teams share a CTA)
+    (3, 2000, 40, 8, KAP5[:3], 1.0e3, 0.5, (0, 1), 64, 2),
 ])
-def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes):
+def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes, team, fs):
     """The optimiser on the other objectives of the paper's designs: the SHG field
     (maximised), the multi-wavelength THG objective of Sec. 5 over three (kappa1,
     kappa2) pairs at N = 3000 and the multi-wavelength SHG objective over five (the
@@ -410,8 +424,7 @@ def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes):
     import torch
     k1, k2 = kap[0]
     for mode in modes:
-        team = 32 if mode == 3 else 0
-        prm = q.Params(NP, G, 0.5, 0.9, 6, 0, 0, team)
+        prm = q.Params(NP, G, 0.5, 0.9, 6, 0, 0, 32 if mode == 3 else team, fs)
         st = q.State([(N, k1, k2)], [prm])
         st.set_objective(kind, kap if kind >= 2 else (), G0, beta)
         tr = torch.full((NP * (1 + 2 * G),), float("nan"), dtype=torch.float32, device="cuda")
@@ -424,7 +437,7 @@ def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes):
         trace = tr.cpu().numpy()
         st.close()
         cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 6, obj=kind, kappas=kap if kind >= 2 else (),
-                           G0=G0, beta=beta)
+                           G0=G0, beta=beta, f_schedule=fs)
         Xo, fo, tro = orc.hwsda_run(cfg, k1, k2, lockstep=trace, want_trace=True)
         assert np.array_equal(X, Xo), mode
         ok = ~np.isnan(trace)
