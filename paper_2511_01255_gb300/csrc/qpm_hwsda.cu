@@ -231,11 +231,14 @@ __device__ __forceinline__ float2 warp_reduce_b(float2 b) {
 // and its thread 0 combines them in warp order, as block_reduce does.
 // Several teams per CTA (the multi-wavelength kinds with shared-memory tables): a team
 // is the T consecutive threads [team T, team T + T); team_sync is the team's own
-// named barrier (1 + team), or the CTA barrier when the CTA is one team.
+// named barrier (1 + team), a warp barrier for one-warp teams, or the CTA barrier
+// when the CTA is one team.
 __device__ __forceinline__ int team_thread(const InstDev &I) { return (int)threadIdx.x & (I.T - 1); }
 __device__ __forceinline__ void team_sync(const InstDev &I) {
   if ((int)blockDim.x == I.T) {
     __syncthreads();
+  } else if (I.T == 32) {
+    __syncwarp();
   } else {
     const int team = (int)threadIdx.x / I.T;
     asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(I.T) : "memory");
@@ -1073,7 +1076,8 @@ static __global__ void k_gwo(InstDev I) {
 // ------------------------------- the multi-wavelength kinds, tables in shared memory
 // When their K tables fit, the multi-wavelength kinds run several teams of T threads
 // per CTA (threads [team T, team T + T) are the team of one individual, with its own
-// named barrier) so that one copy of the K tables in shared memory serves every team
+// named barrier, or none for one-warp teams) so that one copy of the K tables in
+// shared memory serves every team
 // on the SM: read through L1, the tables of three N = 3000 problems (147 KB) did not
 // stay there.  The cascaded kind keeps (p1, p2) per domain, the SHG kind p1 only.
 // Dynamic shared memory: [K tables][row staging][reduction scratch of every team].
@@ -1082,7 +1086,7 @@ static __global__ void k_gwo(InstDev I) {
 // (a fixed deal of 5000 individuals to 152 x 8 teams leaves the fifth round 11 % full).
 // Which team evaluates an individual does not change any result.
 __device__ __forceinline__ int mt_next(const InstDev &I, unsigned *ctr, int &cur) {
-  __shared__ int next_sh[8];
+  __shared__ int next_sh[16];
   const int team = (int)threadIdx.x / I.T;
   if (team_thread(I) == 0) next_sh[team] = cur;
   team_sync(I);  // also: the previous individual's reduction scratch is free again
@@ -1890,7 +1894,8 @@ static Variant variant2(const InstDev &I) {
 }
 
 // the multi-wavelength kinds: launches form only, rows staged; their K tables in shared
-// memory shared by up to 8 teams per CTA (512 threads) where they fit, else through L1
+// memory shared by the teams of a CTA of up to 512 threads (at most 8 teams with their
+// named barriers, 16 one-warp teams) where they fit, else through L1
 static size_t optin_smem() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1901,7 +1906,8 @@ static size_t optin_smem() {
 template <int MK>
 static Variant variant_multi(const InstDev &I) {
   Variant v;
-  const int nteams = std::max(1, std::min(8, 512 / I.T));
+  // at most 8 named barriers (1 .. 8); one-warp teams need none (16 per CTA)
+  const int nteams = std::max(1, std::min(I.T == 32 ? 16 : 8, 512 / I.T));
   const int block = nteams * I.T;
   const size_t mt = (size_t)I.K * I.Npad * mt_entry_bytes<MK>() +
                     sizeof(float4) * stg_f4_per_thread(true) * (size_t)block +

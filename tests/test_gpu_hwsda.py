@@ -410,6 +410,8 @@ KAP5 = [(2 * math.pi / x, 0.0) for x in (2.1, 2.6, 3.2, 3.7, 4.4)]
     # scratch need exactly the opt-in limit, so the kernels' own static shared memory
     # sends them to the one-team kernels
     (3, 3000, 8, 3, KAP5, 1.5e3, 0.5, (0,), 512, 0),
+    # one-warp teams, 16 to a CTA (no named barrier)
+    (2, 1500, 40, 4, KAP3[:2], 1.0e5, 0.5, (0,), 32, 0),
     # the adaptive F of Sec. 3.1.1 on a minimised objective (teams share a CTA)
     (3, 2000, 40, 8, KAP5[:3], 1.0e3, 0.5, (0, 1), 64, 2),
 ])
