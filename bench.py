@@ -373,6 +373,10 @@ def run_gpu(args):
     # trips (donor rows, survivor keys, leader rows) and the generation's issue time
     bar_ns = q.qpm_measure_latency(0, grid_persist)
     l2_ns = q.qpm_measure_latency(1)
+    # the alternatives to the counter barrier, on the same grid
+    sync_alt_ns = {"relaxed_counter_barrier_ns": q.qpm_measure_latency(2, grid_persist),
+                   "fence_only_ns": q.qpm_measure_latency(3, grid_persist),
+                   "tagged_word_exchange_ns": q.qpm_measure_latency(4, grid_persist)}
     kdur = statistics.median(dur)
     ops_gene_gen = algorithmic_lane_ops_per_gene_gen(c["compensated"])
     achieved = ops_gene_gen * gene_gens / kdur / 1e12
@@ -639,6 +643,10 @@ def run_gpu(args):
                          "us_per_generation": floor_us,
                          "grid_barrier_ns": bar_ns, "l2_load_ns": l2_ns, "issue_us": issue_us,
                          "grid_ctas": grid_persist,
+                         "sync_alternatives": dict(sync_alt_ns, note=(
+                             "per round on the same grid (qpm_measure_latency kinds 2-4): the "
+                             "barrier without release/acquire, a lone gpu-scope fence, and a "
+                             "counter-free exchange of tagged words that every CTA polls")),
                          "model": "2 grid barriers + 3 dependent L2 loads (donor rows, survivor "
                                   "keys, leader rows) + the generation's lane-ops at the issue "
                                   "peak; barrier and load latency measured by "

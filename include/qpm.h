@@ -226,11 +226,17 @@ qpm_status qpm_measure_issue_peak(int32_t kind, double *lane_ops_per_s, qpm_stre
  *           256 threads, averaged over 2000 barriers in one cooperative launch;
  *   kind 1: one dependent load served by L2 (a single thread chasing a scrambled
  *           cyclic permutation of 16 MB that is L2-resident), averaged over 8192 loads;
- *           `ctas` is ignored.
- * Synchronous (a few ms); allocates and frees its device buffers (256 bytes, or
- * 16 MB).  Errors: NULL output, kind outside [0, 1], ctas outside [1, the co-resident
- * CTA count] for kind 0 -> QPM_ERR_ARG; a barrier wait that ran out (1 s) ->
- * QPM_ERR_TIMEOUT. */
+ *           `ctas` is ignored;
+ *   kind 2: the kind 0 barrier with relaxed arrival and polling (no ordering: how
+ *           fast an arrival reaches the pollers at all);
+ *   kind 3: one gpu-scope fence per CTA between two CTA barriers, no cross-CTA wait;
+ *   kind 4: an all-to-all exchange without a counter: every CTA publishes a
+ *           round-tagged 8-byte word and its threads poll every CTA's word;
+ *   kinds 2-4 per round, `ctas` CTAs of 256 threads, 2000 rounds as for kind 0.
+ * Synchronous (a few ms); allocates and frees its device buffers (256 bytes plus 16
+ * per CTA, or 16 MB).  Errors: NULL output, kind outside [0, 4], ctas outside [1, the
+ * co-resident CTA count] for kinds 0 and 2-4 -> QPM_ERR_ARG; a wait that ran out (1 s,
+ * or 2^22 polls for kinds 2 and 4) -> QPM_ERR_TIMEOUT. */
 qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns_out, qpm_stream_t stream);
 
 /* Exhaustive self-check of one of the library's arithmetic shortcuts against

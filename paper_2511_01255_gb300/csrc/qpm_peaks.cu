@@ -264,6 +264,75 @@ static __global__ void __launch_bounds__(LP_THREADS) k_probe_barrier(Barrier b, 
     if (!grid_sync(b, target)) return;
 }
 
+// The ways a grid could synchronise, for comparison with the barrier above (reps
+// rounds each, every wait bounded by an iteration count that records QPM_ERR_TIMEOUT):
+//   2: the same counter barrier with relaxed arrival and polling -- how fast an
+//      arrival reaches the pollers at all, without the ordering the kernel needs;
+//   3: a gpu-scope fence between two CTA barriers, no cross-CTA wait -- the price of
+//      the ordering alone;
+//   4: an all-to-all exchange without a counter: every CTA publishes a round-tagged
+//      8-byte word (single-copy atomic, relaxed) and its threads poll the words of
+//      all CTAs, one thread per word (what a fence-free leader search would need).
+// words: [2][ctas] u64, zero before the launch (rounds alternate between the halves,
+// so a fast CTA never overwrites a word a slow one still waits for).
+static constexpr unsigned LP_SPIN_LIMIT = 1u << 22;
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+static __global__ void __launch_bounds__(LP_THREADS)
+    k_probe_sync(Barrier b, int kind, unsigned long long *words, int reps) {
+  __shared__ int bad;
+  unsigned target = 0;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int r = 0; r < reps; ++r) {
+    if (kind == 2) {
+      __syncthreads();
+      target += gridDim.x;
+      if (threadIdx.x == 0) {
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(b.count) : "memory");
+        unsigned it = 0;
+        while ((int)(ld_relaxed_u32(b.count) - target) < 0)
+          if (++it > LP_SPIN_LIMIT) {
+            atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+            bad = 1;
+            break;
+          }
+      }
+      __syncthreads();
+    } else if (kind == 3) {
+      __syncthreads();
+      if (threadIdx.x == 0) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      __syncthreads();
+    } else {
+      const unsigned tag = (unsigned)r + 1u;
+      unsigned long long *half = words + (size_t)(r & 1) * gridDim.x;
+      if (threadIdx.x == 0) st_relaxed_u64(half + blockIdx.x, ((unsigned long long)tag << 32) | blockIdx.x);
+      for (unsigned c = threadIdx.x; c < gridDim.x; c += blockDim.x) {
+        unsigned it = 0;
+        while ((unsigned)(ld_relaxed_u64(half + c) >> 32) != tag)
+          if (++it > LP_SPIN_LIMIT) {
+            atomicCAS(b.err, 0, (int)QPM_ERR_TIMEOUT);
+            bad = 1;
+            break;
+          }
+      }
+      __syncthreads();
+    }
+    if (bad) return;
+  }
+}
+
 // one thread follows a cyclic permutation with L2-cached loads: every load depends
 // on the one before, so the time per step is the latency of a load served by L2
 static __global__ void k_probe_chase(const uint32_t *__restrict__ next, int steps,
@@ -279,7 +348,7 @@ extern "C" qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns
                                           qpm_stream_t stream) {
   using namespace qpm;
   if (!ns_out) return fail(QPM_ERR_ARG, "qpm_measure_latency: NULL output");
-  if (kind != 0 && kind != 1) return fail(QPM_ERR_ARG, "qpm_measure_latency: kind must be 0 or 1");
+  if (kind < 0 || kind > 4) return fail(QPM_ERR_ARG, "qpm_measure_latency: kind outside [0, 4]");
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   QPM_CUDA(cudaEventCreate(&e0));
@@ -299,15 +368,18 @@ extern "C" qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
     return e == cudaSuccess ? QPM_OK : cuda_fail(e, "latency probe launch");
   };
-  if (kind == 0) {
+  if (kind != 1) {
+    const void *fn = kind == 0 ? (const void *)k_probe_barrier : (const void *)k_probe_sync;
     int occ = 0;
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_probe_barrier, LP_THREADS, 0);
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, LP_THREADS, 0);
     if (ce != cudaSuccess) st = cuda_fail(ce, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     else if (ctas < 1 || ctas > occ * sm_count())
       st = fail(QPM_ERR_ARG, "qpm_measure_latency: ctas outside [1, co-resident CTAs]");
+    // [count, ..., err at word 32, ...] then the exchanged words [2][ctas]
+    const size_t words_off = 256, bytes = words_off + 2 * sizeof(unsigned long long) * (size_t)ctas;
     if (st == QPM_OK) {
-      ce = cudaMalloc(&buf, 256);
-      if (ce == cudaSuccess) ce = cudaMemsetAsync(buf, 0, 256, s);
+      ce = cudaMalloc(&buf, bytes);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(buf, 0, bytes, s);
       if (ce != cudaSuccess) st = cuda_fail(ce, "cudaMalloc(barrier words)");
     }
     float t[2] = {0.f, 0.f};
@@ -315,12 +387,14 @@ extern "C" qpm_status qpm_measure_latency(int32_t kind, int32_t ctas, double *ns
     for (int k = 0; k < 2 && st == QPM_OK; ++k) {
       for (int w = 0; w < 2 && st == QPM_OK; ++w) {  // the second launch is the timed one
         Barrier b{(unsigned *)buf, (int32_t *)buf + 32, 1000000000ull};  // 1 s per wait
-        int r = reps[k];
-        void *args[] = {&b, &r};
+        int r = reps[k], kd = kind;
+        unsigned long long *words = (unsigned long long *)((char *)buf + words_off);
+        void *args0[] = {&b, &r};
+        void *args[] = {&b, &kd, &words, &r};
         st = timed([&] {
-          cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(unsigned), s);
-          return e == cudaSuccess ? cudaLaunchCooperativeKernel((const void *)k_probe_barrier,
-                                                                ctas, LP_THREADS, args, 0, s)
+          cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
+          return e == cudaSuccess ? cudaLaunchCooperativeKernel(fn, ctas, LP_THREADS,
+                                                                kind == 0 ? args0 : args, 0, s)
                                   : e;
         }, &t[k]);
       }

@@ -45,6 +45,13 @@ def main():
             print(f"grid barrier, {ctas} CTAs of 256 threads: {best / 1e3:.3f} us (best of {max(1, a.reps)})")
         best = min(q.qpm_measure_latency(1) for _ in range(max(1, a.reps)))
         print(f"dependent L2 load: {best:.1f} ns (best of {max(1, a.reps)})")
+        names = {2: "counter barrier, relaxed arrival and polling",
+                 3: "gpu-scope fence between two CTA barriers",
+                 4: "tagged all-to-all word exchange"}
+        for kind, name in names.items():
+            for ctas in (32, nsm, 256):
+                best = min(q.qpm_measure_latency(kind, ctas) for _ in range(max(1, a.reps)))
+                print(f"{name}, {ctas} CTAs: {best / 1e3:.3f} us (best of {max(1, a.reps)})")
         return
     if a.workload == "relaxed":
         c = W.RELAXED

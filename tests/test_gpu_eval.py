@@ -247,10 +247,22 @@ def test_latency_microbenchmark(q):
     assert 50.0 < l2 < 5000.0
     assert l2 < bar < 50000.0
     assert q.qpm_measure_latency(0, 1) > 0.0
+    # the other ways to synchronise the grid: a relaxed counter is no slower than the
+    # ordered one would allow by more than the noise, a lone fence is cheaper than a
+    # barrier, and every form finishes (bounded polls) with a positive time
+    relaxed = q.qpm_measure_latency(2, 256)
+    fence = q.qpm_measure_latency(3, 256)
+    tagged = q.qpm_measure_latency(4, 256)
+    assert 0.0 < fence < bar and 0.0 < relaxed < 1.5 * bar and tagged > 0.0
+    assert q.qpm_measure_latency(4, 1) > 0.0
     with pytest.raises(q.QpmError):
-        q.qpm_measure_latency(2)
+        q.qpm_measure_latency(5)
+    with pytest.raises(q.QpmError):
+        q.qpm_measure_latency(-1)
     with pytest.raises(q.QpmError):
         q.qpm_measure_latency(0, 10 ** 6)
+    with pytest.raises(q.QpmError):
+        q.qpm_measure_latency(4, 10 ** 6)
 
 
 @pytest.mark.parametrize("kind", [0, 1, 2])
