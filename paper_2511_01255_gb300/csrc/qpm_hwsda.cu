@@ -1903,16 +1903,11 @@ static size_t optin_smem() {
     return 0;
   return (size_t)v;
 }
+// the dynamic shared memory the multi-team kernels may take: the opt-in limit less their
+// own static shared memory (their attribute is set to it, so states of any size can
+// take turns on the same kernels)
 template <int MK>
-static Variant variant_multi(const InstDev &I) {
-  Variant v;
-  // at most 8 named barriers (1 .. 8); one-warp teams need none (16 per CTA)
-  const int nteams = std::max(1, std::min(I.T == 32 ? 16 : 8, 512 / I.T));
-  const int block = nteams * I.T;
-  const size_t mt = (size_t)I.K * I.Npad * mt_entry_bytes<MK>() +
-                    sizeof(float4) * stg_f4_per_thread(true) * (size_t)block +
-                    sizeof(Mono) * (size_t)MultiAcc<MK>::KMAX * (I.T / 32) * nteams;
-  // the opt-in limit less the kernels' own static shared memory
+static size_t mt_smem_cap() {
   static const size_t cap = [] {
     cudaFuncAttributes a{}, b{};
     const size_t optin = optin_smem();
@@ -1922,7 +1917,18 @@ static Variant variant_multi(const InstDev &I) {
     const size_t st = std::max(a.sharedSizeBytes, b.sharedSizeBytes);
     return optin > st ? optin - st : (size_t)0;
   }();
-  if (mt <= cap) {
+  return cap;
+}
+template <int MK>
+static Variant variant_multi(const InstDev &I) {
+  Variant v;
+  // at most 8 named barriers (1 .. 8); one-warp teams need none (16 per CTA)
+  const int nteams = std::max(1, std::min(I.T == 32 ? 16 : 8, 512 / I.T));
+  const int block = nteams * I.T;
+  const size_t mt = (size_t)I.K * I.Npad * mt_entry_bytes<MK>() +
+                    sizeof(float4) * stg_f4_per_thread(true) * (size_t)block +
+                    sizeof(Mono) * (size_t)MultiAcc<MK>::KMAX * (I.T / 32) * nteams;
+  if (mt <= mt_smem_cap<MK>()) {
     v.de = (const void *)k_de_mt<MK>;
     v.gwo = (const void *)k_gwo_mt<MK>;
     v.smem = mt;
@@ -2496,8 +2502,11 @@ extern "C" qpm_status qpm_set_objective(qpm_state *st, int32_t inst, const qpm_o
     // several teams per CTA sharing the K tables in shared memory
     const Variant v = variant_of(I);
     int a = 0, b = 0;
+    // the largest any state can need: a smaller value would fail another state's launch
+    const int cap = (int)(I.obj == OBJ_MULTI_THG ? mt_smem_cap<OBJ_MULTI_THG>()
+                                                 : mt_smem_cap<OBJ_MULTI_SHG>());
     for (const void *fn : {v.de, v.gwo})
-      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+      QPM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, v.de, v.block, v.smem));
     QPM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v.gwo, v.block, v.smem));
     if (std::min(a, b) < 1) return fail(QPM_ERR_UNSUPPORTED, "qpm_set_objective: kernels do not fit");

@@ -456,6 +456,35 @@ def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes, team, 
         assert abs(z - ref) <= 1e-9 * abs(ref)
 
 
+def test_objective_states_of_different_sizes_take_turns(q):
+    """Two multi-wavelength states whose shared-memory tables differ in size (147 KB and
+    16 KB) set up one after the other and run in turns: the larger one's launches still
+    fit, and each state's populations equal those of a run of that state alone."""
+    import torch
+
+    def make(N, kap):
+        st = q.State([(N, kap[0][0], kap[0][1])], [q.Params(24, 6, 0.5, 0.9, 3, 0, 0, 0)])
+        st.set_objective(2, kap, 1.0e5, 0.5)
+        st.init()
+        return st
+
+    alone = {}
+    for N, kap in ((3000, KAP3), (1000, KAP3[:1])):
+        st = make(N, kap)
+        st.run(6, 0)
+        alone[N] = st.population()[0].cpu().numpy()
+        st.close()
+    big, small = make(3000, KAP3), make(1000, KAP3[:1])
+    for _ in range(3):
+        big.run(2, 0)
+        small.run(2, 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(big.population()[0].cpu().numpy(), alone[3000])
+    assert np.array_equal(small.population()[0].cpu().numpy(), alone[1000])
+    big.close()
+    small.close()
+
+
 def test_objective_errors(q):
     import torch
     st = q.State([(100, 1.0, 2.0)], [q.Params(8, 4, 0.5, 0.9, 1, 0, 0)])
