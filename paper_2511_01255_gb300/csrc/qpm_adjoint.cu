@@ -590,10 +590,12 @@ static dim3 rx_grid(const RelaxShape &sh) {
 }
 
 // dynamic shared memory above the default 48 KB: the kernel's opt-in, set before each
-// launch (a host-side attribute write)
-template <class K>
-static qpm_status rx_launch_attr(K kernel, size_t bytes) {
-  QPM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+// launch (a host-side attribute write) to what the longest segment needs, so that a
+// launch with shorter segments never lowers it under one captured earlier
+template <int NST, class K>
+static qpm_status rx_launch_attr(K kernel) {
+  QPM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)rx_smem_bytes<NST>(RX_LMAX)));
   return QPM_OK;
 }
 
@@ -621,10 +623,10 @@ extern "C" qpm_status qpm_deff_relaxed_fwd(const qpm_problem *prob, const float 
   const bool tma = make_tile_map(&tmap, theta, B, sh.N, ld);
   const size_t smem = rx_smem_bytes<RX_NST_F>(sh.L);
   if (tma) {
-    if ((st = rx_launch_attr(k_relaxed_fwd<true>, smem)) != QPM_OK) return st;
+    if ((st = rx_launch_attr<RX_NST_F>(k_relaxed_fwd<true>)) != QPM_OK) return st;
     k_relaxed_fwd<true><<<grid, RX_WPC * 32, smem, s>>>(tmap, theta, sh, tab, saved);
   } else {
-    if ((st = rx_launch_attr(k_relaxed_fwd<false>, smem)) != QPM_OK) return st;
+    if ((st = rx_launch_attr<RX_NST_F>(k_relaxed_fwd<false>)) != QPM_OK) return st;
     k_relaxed_fwd<false><<<grid, RX_WPC * 32, smem, s>>>(tmap, theta, sh, tab, saved);
   }
   QPM_CUDA(cudaGetLastError());
@@ -646,7 +648,7 @@ static qpm_status launch_bwd(dim3 grid, size_t smem, cudaStream_t s, const CUten
                              const CUtensorMap &gmap, const float *theta, const RelaxShape &sh,
                              const float4 *tab, const float2 *konst, const float2 *D,
                              const float *saved, const float *gf, float *grad, int64_t ldg) {
-  qpm_status st = rx_launch_attr(k_relaxed_bwd<TI, TO, VG>, smem);
+  qpm_status st = rx_launch_attr<RX_NST_B>(k_relaxed_bwd<TI, TO, VG>);
   if (st != QPM_OK) return st;
   k_relaxed_bwd<TI, TO, VG><<<grid, RX_WPC * 32, smem, s>>>(tmap, gmap, theta, sh, tab, konst, D,
                                                             saved, gf, grad, ldg);

@@ -1972,7 +1972,11 @@ static const void *batch_kernel(bool ts, bool cl) {
 // co-resident CTAs of the batched kernel for clusters of `cs` CTAs (a multiple of cs)
 static qpm_status batch_grid(const qpm_state *st, int cs, int *grid) {
   const void *kb = batch_kernel(st->batch_ts, cs > 1);
-  QPM_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->batch_smem));
+  // the largest any state of this kernel variant can need, so that a state with smaller
+  // tables cannot fail the captured launch of another
+  const size_t cap = sizeof(float4) * stg_f4_per_thread(st->batch_ts) * BATCH_WARPS * 32 +
+                     (st->batch_ts ? BATCH_TS_MAX_BYTES : 0);
+  QPM_CUDA(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

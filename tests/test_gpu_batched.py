@@ -89,6 +89,43 @@ def test_batched_equals_launches(q):
             assert np.array_equal(a, b)
 
 
+def test_batched_states_of_different_sizes_take_turns(q):
+    """Two batched states whose phasor tables in shared memory differ (8000 and 500
+    domains: 125 KB and 8 KB) run in turns, each replaying its captured launch after
+    the other was set up: the larger one's launch still fits, and every population
+    equals that of the same state run alone."""
+    import torch
+
+    def make(N):
+        probs = [(N, 2 * math.pi / 6.9, 2 * math.pi / 1.55), (N // 2, 2 * math.pi / 7.3, 2 * math.pi / 1.7)]
+        prms = [q.Params(16, 6, 0.5, 0.9, 5, 0, 0), q.Params(8, 6, 0.5, 0.9, 5, 0, 0)]
+        st = q.State(probs, prms)
+        st.init()
+        return st
+
+    alone = {}
+    for N in (8000, 500):
+        st = make(N)
+        st.run(2, q.RUN_BATCHED)
+        st.run(2, q.RUN_BATCHED)
+        st.run(2, q.RUN_BATCHED)
+        alone[N] = [st.population(k)[0].cpu().numpy() for k in range(2)]
+        st.close()
+    big = make(8000)
+    big.run(2, q.RUN_BATCHED)  # captured with the large tables
+    small = make(500)
+    small.run(2, q.RUN_BATCHED)
+    big.run(2, q.RUN_BATCHED)  # replayed after the small state was set up
+    small.run(2, q.RUN_BATCHED)
+    big.run(2, q.RUN_BATCHED)
+    small.run(2, q.RUN_BATCHED)
+    torch.cuda.synchronize()
+    for st, N in ((big, 8000), (small, 500)):
+        for k in range(2):
+            assert np.array_equal(st.population(k)[0].cpu().numpy(), alone[N][k]), (N, k)
+        st.close()
+
+
 def test_batched_full_size_sampled(q, orc):
     """512 instances (N ~ U[500, 8000], NP in {64..512}): two batched generations, then
     the third replayed by the oracle for three sampled instances."""
