@@ -19,6 +19,15 @@ def test_op_count_per_gene_generation():
     assert bench.algorithmic_lane_ops_per_gene_gen(1) == 162.5
 
 
+def test_op_count_of_the_multi_wavelength_objectives():
+    # the updates of the single count (134) and per phase one scan of each problem:
+    # 10 lane-ops a domain for a cascaded problem, 2 for an SHG problem
+    assert bench.algorithmic_lane_ops_per_gene_gen_multi(2, 1) == 154.0
+    assert bench.algorithmic_lane_ops_per_gene_gen_multi(2, 3) == 194.0
+    assert bench.algorithmic_lane_ops_per_gene_gen_multi(3, 5) == 154.0
+    assert bench.algorithmic_lane_ops_per_gene_gen_multi(3, 1) == 138.0
+
+
 def test_mix_ceiling_adds_generator_and_other_times():
     n_rest = 154.0 - 80.0
     t = 1.0 / ISSUE["philox_calls_per_s"] + n_rest / (ISSUE["ffma"] * 1e12)
