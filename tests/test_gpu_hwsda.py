@@ -456,6 +456,39 @@ def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes, team, 
         assert abs(z - ref) <= 1e-9 * abs(ref)
 
 
+@pytest.mark.parametrize("kind,kap", [(2, KAP3[:2]), (3, KAP5)])
+def test_checkpoint_resume_multi_objective(q, kind, kap):
+    """Checkpoint and resume of a multi-wavelength design (the multi-team kernels with
+    shared-memory tables): the population re-evaluated by qpm_set_population has the
+    same objective bits, and the resumed run ends exactly like the uninterrupted one."""
+    import torch
+    N, NP, G = 3000, 24, 10
+
+    def make():
+        st = q.State([(N, kap[0][0], kap[0][1])], [q.Params(NP, G, 0.5, 0.9, 9, 0, 0, 0)])
+        st.set_objective(kind, kap, 1.0e5 if kind == 2 else 1.0e3, 0.5)
+        st.init()
+        return st
+
+    st = make()
+    st.run(G, 0)
+    Xa, fa, _ = snapshot(st)
+    st.close()
+    st = make()
+    st.run(5, 0)
+    Xc, fc, _ = st.population()
+    torch.cuda.synchronize()
+    st.close()
+    st2 = make()
+    q.qpm_set_population(st2.h, 0, Xc, 5)
+    X2, f2, _ = snapshot(st2)
+    assert np.array_equal(f2, fc.cpu().numpy())
+    st2.run(G - 5, 0)
+    Xb, fb, _ = snapshot(st2)
+    st2.close()
+    assert np.array_equal(Xa, Xb) and np.array_equal(fa, fb)
+
+
 def test_objective_states_of_different_sizes_take_turns(q):
     """Two multi-wavelength states whose shared-memory tables differ in size (147 KB and
     16 KB) set up one after the other and run in turns: the larger one's launches still
