@@ -456,6 +456,37 @@ def test_objective_lockstep(q, orc, kind, N, NP, G, kap, G0, beta, modes, team, 
         assert abs(z - ref) <= 1e-9 * abs(ref)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_objectives_of_several_instances_lockstep(q, orc, mode):
+    """A state of two instances with different multi-wavelength objectives (three
+    cascaded problems, four SHG problems), one-warp teams 16 to a CTA: each instance
+    bit for bit against the oracle's lockstep replay with its own instance index."""
+    import torch
+    inst = [(2000, KAP3, 16, 2, 1.0e5), (1500, KAP5[:4], 12, 3, 1.0e3)]
+    G = 4
+    probs = [(N, kap[0][0], kap[0][1]) for N, kap, NP, kind, G0 in inst]
+    prms = [q.Params(NP, G, 0.5, 0.9, 13, 0, 0) for N, kap, NP, kind, G0 in inst]
+    st = q.State(probs, prms)
+    traces = []
+    for k, (N, kap, NP, kind, G0) in enumerate(inst):
+        st.set_objective(kind, kap, G0, 0.5, inst=k)
+        tr = torch.full((NP * (1 + 2 * G),), float("nan"), dtype=torch.float32, device="cuda")
+        q.qpm_set_trace(st.h, k, tr)
+        traces.append(tr)
+    st.init()
+    st.run(G, mode)
+    torch.cuda.synchronize()
+    for k, (N, kap, NP, kind, G0) in enumerate(inst):
+        X = st.population(k)[0].cpu().numpy()
+        trace = traces[k].cpu().numpy()
+        cfg = orc.make_cfg(NP, N, G, 0.5, 0.9, 13, inst=k, obj=kind, kappas=kap, G0=G0, beta=0.5)
+        Xo, fo, tro = orc.hwsda_run(cfg, kap[0][0], kap[0][1], lockstep=trace, want_trace=True)
+        assert np.array_equal(X, Xo), k
+        ok = ~np.isnan(trace)
+        assert np.max(np.abs(trace[ok] - tro[ok])) <= TOL_D * len(kap) * G0, k
+    st.close()
+
+
 @pytest.mark.parametrize("kind,kap", [(2, KAP3[:2]), (3, KAP5)])
 def test_checkpoint_resume_multi_objective(q, kind, kap):
     """Checkpoint and resume of a multi-wavelength design (the multi-team kernels with
