@@ -203,7 +203,7 @@ struct MultiAcc {
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
       if (k < I.K) {
-        const float4 *tb = I.mtab[k] + (size_t)k4 * 4 * I.T + t;
+        const float4 *tb = I.mtab[k] + ((uint32_t)k4 * 4u * (uint32_t)I.T + (uint32_t)t);
 #pragma unroll
         for (int q = 0; q < 4; ++q) push1(k, d[q], ld_table_keep(tb + (size_t)q * I.T));
       }
@@ -311,7 +311,7 @@ __device__ void multi_finish(const InstDev &I, MultiAcc<MK> &acc, Mono *sh, floa
 template <bool COMP, bool TS>
 __device__ __forceinline__ void push4(Acc<COMP> &acc, const float4 *tbl, int T, int k4, int t,
                                       float4 u) {
-  const float4 *tb = tbl + (size_t)k4 * 4 * T + t;
+  const float4 *tb = tbl + ((uint32_t)k4 * 4u * (uint32_t)T + (uint32_t)t);
   acc.push(sgn(u.x), ldt<TS>(tb));
   acc.push(sgn(u.y), ldt<TS>(tb + T));
   acc.push(sgn(u.z), ldt<TS>(tb + 2 * T));
@@ -325,7 +325,7 @@ __device__ __forceinline__ float *row_ptr(const InstDev &I, int i, int slot) {
 // float4 group `off` of individual i's current row.  DUAL: both slots are read
 // together with the selector, which takes the selector load off the critical path.
 template <bool NC, bool DUAL>
-__device__ __forceinline__ float4 ld_cur(const InstDev &I, int i, int slot, size_t off) {
+__device__ __forceinline__ float4 ld_cur(const InstDev &I, int i, int slot, uint32_t off) {
   if (DUAL) {
     const float *r0 = I.pop + (size_t)2 * i * I.Npad + off;
     const float4 v0 = ld4<NC>(r0), v1 = ld4<NC>(r0 + I.Npad);
@@ -416,14 +416,14 @@ __device__ __forceinline__ void stage_group(float4 *stg, int stage, int k, int T
                                             const float *r3, const float4 *tbl) {
   constexpr int SPS = stg_f4_per_thread(TS) / stg_stages(TS);
   const int nt = blockDim.x;
-  const size_t off = ((size_t)k * T + t) * 4;
-  float4 *s = stg + (size_t)stage * SPS * nt + threadIdx.x;
+  const uint32_t off = ((uint32_t)k * (uint32_t)T + (uint32_t)t) * 4u;
+  float4 *s = stg + ((uint32_t)(stage * SPS * nt) + threadIdx.x);
   cp_async16(s, r0 + off);
   cp_async16(s + nt, r1 + off);
   cp_async16(s + 2 * nt, r2 + off);
   cp_async16(s + 3 * nt, r3 + off);
   if (!TS) {
-    const float4 *tb = tbl + (size_t)k * 4 * T + t;
+    const float4 *tb = tbl + ((uint32_t)k * 4u * (uint32_t)T + (uint32_t)t);
     cp_async16(s + 4 * nt, tb);
     cp_async16(s + 5 * nt, tb + T);
     cp_async16(s + 6 * nt, tb + 2 * T);
@@ -454,7 +454,7 @@ __device__ __forceinline__ const float4 *staged_group(float4 *stg, int k4, int n
   if (kn < n4) stage_group<TS>(stg, kn % NS, kn, T, t, r0, r1, r2, r3, tbl);
   cp_async_commit();  // possibly empty: keeps one group per iteration
   cp_async_wait<NS - 1>();
-  return stg + (size_t)(k4 % NS) * SPS * blockDim.x + threadIdx.x;
+  return stg + ((uint32_t)((k4 % NS) * SPS) * blockDim.x + threadIdx.x);
 }
 // the push of one staged group: table entries from the stage when !TS
 template <bool COMP, bool TS>
@@ -499,7 +499,7 @@ __device__ unsigned long long de_individual(const InstDev &I, const PhiloxKey &K
   MultiAcc<MK> macc;
   if (MK) macc.zero();
   for (int k4 = 0; k4 < n4; ++k4) {
-    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const uint32_t off = ((uint32_t)k4 * (uint32_t)I.T + (uint32_t)t) * 4u;
     float4 a, b, p, q;
     const float4 *st = nullptr;
     if (STG) {
@@ -608,7 +608,7 @@ __device__ void gwo_individual(const InstDev &I, const PhiloxKey &K, const float
   MultiAcc<MK> macc;
   if (MK) macc.zero();
   for (int k4 = 0; k4 < n4; ++k4) {
-    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const uint32_t off = ((uint32_t)k4 * (uint32_t)I.T + (uint32_t)t) * 4u;
     float4 x, L0, L1, L2;
     const float4 *st = nullptr;
     if (STG) {
@@ -875,7 +875,7 @@ __device__ void gwo_discrete_individual(const InstDev &I, const PhiloxKey &K, in
   acc.zero();
   const int n4 = I.c / 4;
   for (int k4 = 0; k4 < n4; ++k4) {
-    const size_t off = ((size_t)k4 * I.T + t) * 4;
+    const uint32_t off = ((uint32_t)k4 * (uint32_t)I.T + (uint32_t)t) * 4u;
     const float4 l0 = __ldg((const float4 *)(L0 + off)), l1 = __ldg((const float4 *)(L1 + off));
     const float4 l2 = __ldg((const float4 *)(L2 + off)), l3 = __ldg((const float4 *)(L3 + off));
     const uint32_t jg = (uint32_t)((t * I.c + 4 * k4) >> 2);
