@@ -1126,11 +1126,16 @@ __device__ __forceinline__ void mt_layout(const InstDev &I, void *&smt, float4 *
 
 template <int MK>
 static __global__ void k_de_mt(InstDev I) {
+  // launched as a programmatic dependent of the phase before: the next phase's CTAs may
+  // start as this grid's retire, and every CTA loads its tables (fixed per problem)
+  // before it waits for the phase before to complete and its writes to be visible
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   void *smt;
   float4 *stg;
   Mono *sh;
   mt_layout<MK>(I, smt, stg, sh);
   mt_load_tables<MK>(I, smt);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   const int32_t *sel_in = (g & 1) ? I.sel1 : I.sel0;
@@ -1177,11 +1182,16 @@ static __global__ void k_de_mt(InstDev I) {
 
 template <int MK>
 static __global__ void k_gwo_mt(InstDev I) {
+  // launched as a programmatic dependent of the phase before: the next phase's CTAs may
+  // start as this grid's retire, and every CTA loads its tables (fixed per problem)
+  // before it waits for the phase before to complete and its writes to be visible
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   void *smt;
   float4 *stg;
   Mono *sh;
   mt_layout<MK>(I, smt, stg, sh);
   mt_load_tables<MK>(I, smt);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int g = *I.gen;
   const PhiloxKey K = philox_schedule(I.key);
   int32_t *sel = (g & 1) ? I.sel0 : I.sel1;
@@ -2019,6 +2029,21 @@ static qpm_status enqueue_step(qpm_state *st, cudaStream_t s) {
     void *args[] = {&I};
     const bool mt = v.block != 0;  // several teams per CTA
     const dim3 grid(mt ? st->grid_mt[k] : st->grid_plain[k]), block(mt ? v.block : I.T);
+    if (mt) {  // each phase a programmatic dependent of the one before
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = grid;
+      cfg.blockDim = block;
+      cfg.dynamicSmemBytes = v.smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      QPM_CUDA(cudaLaunchKernelExC(&cfg, v.de, args));
+      QPM_CUDA(cudaLaunchKernelExC(&cfg, v.gwo, args));
+      continue;
+    }
     QPM_CUDA(cudaLaunchKernel(v.de, grid, block, args, v.smem, s));
     QPM_CUDA(cudaLaunchKernel(v.gwo, grid, block, args, v.smem, s));
   }
